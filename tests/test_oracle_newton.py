@@ -1,0 +1,69 @@
+"""Pins of the oracle's load-stepped Newton solver (Sec. 3.2, Eq. loadStepping)."""
+import numpy as np
+
+from feti_inputs import mesh
+from oracle import fem, feti
+
+
+def _small_tube(pressure=0.13332):   # 1 mmHg, as in Tables 4-7
+    return mesh.cylinder_problem(2, 16, 2, (1, 4, 1), material=mesh.hgo_material(), pressure=pressure)
+
+
+def _monolithic_newton(prob, steps, follower, tol=1e-10):
+    N = prob.n_nodes
+    U = np.zeros(3 * N)
+    free = np.ones(3 * N, bool)
+    free[prob.dir_dof] = False
+    hist = []
+    for s in range(1, steps + 1):
+        tau = s / steps
+        h = []
+        for _ in range(30):
+            Ke, fint = fem.element_matrices(prob, U.reshape(-1, 3))
+            fext = fem.load_vector(prob, U.reshape(-1, 3), follower)
+            R = fem.internal_force_global(prob, fint) - tau * fext
+            h.append(np.linalg.norm(R[free]) / np.linalg.norm(tau * fext[free]))
+            if h[-1] <= tol:
+                break
+            K = fem.assemble_global(prob, Ke)
+            dU = np.zeros(3 * N)
+            idx = np.nonzero(free)[0]
+            import scipy.sparse.linalg as spla
+            dU[idx] = spla.spsolve(K[idx][:, idx].tocsc(), -R[idx])
+            U = U + dU
+        hist.append(h)
+    return U, hist
+
+
+def test_dead_load_newton_converges_quadratically():
+    prob = _small_tube()
+    _, hist = _monolithic_newton(prob, 1, follower=False)
+    for h in hist:
+        assert h[-1] <= 1e-10
+        # quadratic: once below 1e-2, each step squares the residual (up to a constant)
+        tail = [x for x in h if x < 1e-2]
+        for a, b in zip(tail, tail[1:]):
+            assert b <= 50.0 * a * a + 1e-14
+
+
+def test_feti_newton_equals_monolithic_newton():
+    prob = _small_tube()
+    U_ref, _ = _monolithic_newton(prob, 1, follower=True, tol=1e-12)
+    for method in (feti.CLASSICAL,):
+        U, log = feti.newton_solve(prob, method, "dirichlet", n_load_steps=1, newton_tol=1e-9,
+                                   pcg_tol=1e-12)
+        # residual 1e-9 of a problem whose tangent has condition ~1e5: U to ~1e-6
+        assert np.linalg.norm(U - U_ref) <= 1e-6 * np.linalg.norm(U_ref)
+        assert log[0][-1][0] <= 1e-9
+
+
+def test_tube_inflates_under_pressure():
+    prob = _small_tube()
+    U, _ = feti.newton_solve(prob, feti.CLASSICAL, "dirichlet", n_load_steps=1)
+    x = prob.coords
+    u = U.reshape(-1, 3)
+    ur = (u[:, 0] * x[:, 0] + u[:, 1] * x[:, 1]) / np.hypot(x[:, 0], x[:, 1])
+    inner = np.abs(np.hypot(x[:, 0], x[:, 1]) - 1.0) < 1e-12
+    outer = np.abs(np.hypot(x[:, 0], x[:, 1]) - 1.5) < 1e-12
+    # incompressible-like wall: the inner surface moves out more than the outer one
+    assert ur[inner].mean() > ur[outer].mean() > 0.0
