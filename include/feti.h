@@ -1,0 +1,196 @@
+/*
+ * feti.h -- C ABI of the GB300 (sm_103a) classical / all-floating FETI solver.
+ *
+ * The library solves the linear(ized) elasticity systems of Sec. 3.2 of
+ * Augustin, Holzapfel & Steinbach, "Classical and all-floating FETI methods
+ * for the simulation of arterial tissues" by the dual method of Sec. 4:
+ * tearing into subdomains (Sec. 4.1), all-floating treatment of Dirichlet
+ * conditions (Sec. 4.2, Eq. jumpoperatorAF), generalized local inverses and
+ * projected preconditioned CG on the multipliers (Sec. 4.3, Eqs.
+ * classicalFetiF, projection, dualProblem) with the lumped, Dirichlet or
+ * identity preconditioner (Sec. 4.4, Eqs. LumpedVK, DirichletVK).
+ *
+ * Conventions for every call:
+ *  - Host arrays passed to feti_create are read during the call and copied;
+ *    the caller keeps ownership.  The library owns all device memory it
+ *    allocates and frees it in feti_destroy.
+ *  - DOF numbering: dof = 3 * node + component (component 0, 1, 2 = x, y, z).
+ *  - Every call returns a feti_status.  On failure the context keeps a
+ *    message readable with feti_last_error.  No call exits, aborts or traps.
+ *  - Calls on one context are not thread-safe; different contexts are
+ *    independent.  All device work of a context runs on its stream.
+ *  - There is no CPU fallback: without a usable CUDA device feti_create
+ *    returns FETI_ERR_CUDA.
+ */
+#ifndef FETI_H
+#define FETI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FETI_OK = 0,
+  FETI_ERR_INVALID_ARG = 1,      /* null pointer, size out of range, bad option */
+  FETI_ERR_PARTITION = 2,        /* empty subdomain or unsupported kernel dimension */
+  FETI_ERR_ELEMENT_INVERTED = 3, /* a tetrahedron with non-positive volume or det F <= 0 */
+  FETI_ERR_LOCAL_SINGULAR = 4,   /* non-positive pivot in a local Cholesky factorization */
+  FETI_ERR_KERNEL_DETECT = 5,    /* rigid-body kernel detection failed */
+  FETI_ERR_BREAKDOWN = 6,        /* PCG breakdown: (p, F p) <= 0 or not finite */
+  FETI_ERR_NOT_CONVERGED = 7,    /* PCG reached maxit above tolerance */
+  FETI_ERR_NEWTON_DIVERGED = 8,  /* Newton did not reach its tolerance */
+  FETI_ERR_TIMEOUT = 9,          /* a bounded device wait gave up */
+  FETI_ERR_OOM = 10,             /* device allocation failed */
+  FETI_ERR_CUDA = 11,            /* any other CUDA runtime error */
+  FETI_ERR_STATE = 12            /* call made in the wrong order */
+} feti_status;
+
+enum { FETI_LINEAR_ISO = 0, FETI_HGO_TWO_FIBRE = 1 };          /* feti_material.kind */
+enum { FETI_CLASSICAL = 0, FETI_ALL_FLOATING = 1 };             /* feti_options.method */
+enum { FETI_PREC_IDENTITY = 0, FETI_PREC_LUMPED = 1, FETI_PREC_DIRICHLET = 2 };
+enum { FETI_FP64 = 0 };                                         /* feti_options.precision */
+
+/* Mesh T_N of Sec. 3.2 (P1 tetrahedra) and its non-overlapping decomposition
+ * (Sec. 4, Eq. decomposition).  coords: [n_nodes*3] reference coordinates;
+ * tets: [n_tets*4] node ids, positive orientation; part: [n_tets] subdomain
+ * id in [0, n_parts).  Every subdomain must own at least one tetrahedron. */
+typedef struct {
+  int32_t n_nodes;
+  const double* coords;
+  int32_t n_tets;
+  const int32_t* tets;
+  const int32_t* part;
+  int32_t n_parts;
+} feti_mesh;
+
+/* Material of Sec. 3.1.  LINEAR_ISO: Hooke with (E, nu).  HGO_TWO_FIBRE:
+ * Psi = kappa/2 (J-1)^2 + c/2 (I1bar-3) + sum_f k1/(2 k2) (exp(k2 (I4bar_f-1)^2)-1)
+ * (Eqs. isoaniso, iso, aniso_1, aniso_2), a fibre family contributing only
+ * while I4bar_f - 1 > 1e-12; fibres: [n_tets*6] = a1, a2 per element (unit
+ * vectors, reference configuration), required for HGO_TWO_FIBRE. */
+typedef struct {
+  int32_t kind;
+  double E, nu;
+  double c, k1, k2, kappa;
+  const double* fibres;
+} feti_material;
+
+/* Boundary data (Sec. 3, Eqs. Dirichlet and Neumann).
+ * dir_dof: [n_dir] strictly increasing DOFs with prescribed values dir_val.
+ * press_tri: [n_press*3] triangles oriented so that (x1-x0) x (x2-x0) points
+ * into the solid, press_owner: [n_press] the tetrahedron owning each face;
+ * a pressure p pushes along that area vector (P1-consistent: a third of the
+ * force to each vertex).  trac_tri/trac_owner likewise, with the constant
+ * traction vector traction[3] per unit reference area. */
+typedef struct {
+  int32_t n_dir;
+  const int32_t* dir_dof;
+  const double* dir_val;
+  int32_t n_press;
+  const int32_t* press_tri;
+  const int32_t* press_owner;
+  double pressure;
+  int32_t n_trac;
+  const int32_t* trac_tri;
+  const int32_t* trac_owner;
+  double traction[3];
+} feti_bc;
+
+typedef struct {
+  int32_t method;      /* FETI_CLASSICAL or FETI_ALL_FLOATING */
+  int32_t precond;     /* FETI_PREC_* */
+  int32_t precision;   /* FETI_FP64 */
+  double tol;          /* stop when ||P r_k||_2 <= tol ||P r_0||_2 */
+  int32_t maxit;       /* PCG iteration limit */
+  int32_t chunk;       /* PCG iterations per CUDA-graph launch (0: default 16) */
+  int32_t follower;    /* nonzero: pressure follows the deformed surface (Newton) */
+  int32_t n_load_steps;
+  double newton_tol;
+  int32_t newton_maxit;
+} feti_options;
+
+typedef struct {
+  int32_t iterations;      /* PCG iterations (F applications after lambda_0) */
+  int32_t converged;
+  double rel_residual;     /* ||P r_k|| / ||P r_0|| at exit */
+  double cond_est;         /* Lanczos estimate from the CG coefficients */
+  double t_setup_ms;       /* element matrices + local assembly + factorizations */
+  double t_pcg_ms;         /* lambda_0 -> stop, device time */
+  double t_total_ms;
+  int64_t n_lambda;        /* number of multipliers */
+  int64_t coarse_dim;      /* columns of G */
+  int32_t newton_iters;    /* total Newton iterations (feti_newton) */
+  double newton_rel_res;   /* final relative residual (feti_newton) */
+} feti_report;
+
+typedef struct feti_ctx feti_ctx;
+
+/* Builds the decomposition on the host (local numbering, multipliers, kernels,
+ * fixing DOFs) and uploads the problem to the current CUDA device.  stream: a
+ * cudaStream_t to run on, or NULL for a library-owned stream.  No numerical
+ * work on the device yet. */
+feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat,
+                        const feti_bc* bc, const feti_options* opt, void* stream);
+
+/* Linear problem: element matrices, local assembly, local factorizations,
+ * dense local operators, coarse problem, then projected PCG and recovery.
+ * Writes the displacement [n_nodes*3] to u_out (host or device pointer;
+ * u_on_device says which).  report may be NULL. */
+feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report);
+
+/* Nonlinear problem (Sec. 3.2, Eq. loadStepping): tau = s / n_load_steps,
+ * Newton with one FETI solve per step until ||R|| <= newton_tol ||tau f_ext||.
+ * Requires FETI_HGO_TWO_FIBRE.  Writes U [n_nodes*3] like feti_solve. */
+feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report);
+
+/* Sizes of the decomposition: out[0] n_lambda, out[1] coarse_dim, out[2]
+ * sum of local DOFs, out[3] sum of boundary DOFs, out[4] n_parts. */
+feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]);
+
+/* Multiplier rows in canonical order (Sec. 4.1, Fig. 3a, fully redundant):
+ * interface rows by (global node, component, subdomain pair i<j) with +1 on
+ * i and -1 on j, then (all-floating) Dirichlet rows by (node, component,
+ * subdomain) with +1.  Host arrays of n_lambda*2 entries: row_sub (-1 pad),
+ * row_ldof (local DOF = 3 * local node + component, local nodes = the
+ * subdomain's global node ids in increasing order), row_sign; weight and b
+ * have n_lambda entries.  Any pointer may be NULL. */
+feti_status feti_get_index_maps(const feti_ctx* ctx, int32_t* row_sub, int32_t* row_ldof,
+                                int8_t* row_sign, double* weight, double* b);
+
+/* Fixing DOFs of the generalized inverses (Sec. 5.2, regularization by
+ * fixing nodes): fix_ptr [n_parts+1] and fix_ldof [fix_ptr[n_parts]], local
+ * DOFs per subdomain in selection order.  Either pointer may be NULL. */
+feti_status feti_get_fixing(const feti_ctx* ctx, int32_t* fix_ptr, int32_t* fix_ldof);
+
+/* Hot-path benchmark hook: after feti_solve (or feti_prepare), applies the
+ * dual operator and the preconditioner n_apply times back to back to device
+ * vectors: q = F v, then z = M^-1 q (Sec. 4.3, Eq. classicalFetiF, and Sec.
+ * 4.4, Eq. feti_preconditioner), without projection; v, q, z are device
+ * arrays of n_lambda doubles.  The applies run as one CUDA graph (captured on
+ * the first call for a given (v, q, z, n_apply) and replayed afterwards) on
+ * the context's stream; *ms_per_apply (may be NULL) receives the average
+ * device time per apply of this launch.  Returns after the launch completed. */
+feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z,
+                            int32_t n_apply, double* ms_per_apply);
+
+/* Runs the setup part of feti_solve (element matrices through coarse
+ * factorization) without PCG. */
+feti_status feti_prepare(feti_ctx* ctx);
+
+/* Dominant per-iteration kernel (dense local F_i apply with fused gather):
+ * its device time averaged over the launches inside the last feti_dual_apply
+ * (timed by event nodes around each launch in that graph), the algorithmic
+ * bytes one launch must move (each F_i entry once, gathered multipliers,
+ * local outputs) and its floating-point operations (2 per F_i entry). */
+feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv_bytes,
+                              double* gemv_flops);
+
+const char* feti_last_error(const feti_ctx* ctx);
+void feti_destroy(feti_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FETI_H */

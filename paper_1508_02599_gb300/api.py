@@ -1,0 +1,166 @@
+"""Python face of the C ABI: same calls as include/feti.h, numpy/torch marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+class FetiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return L.LIB_PATH
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None and a.size else None
+
+
+_METHODS = {"classical": L.CLASSICAL, "af": L.ALL_FLOATING, "all_floating": L.ALL_FLOATING}
+_PRECONDS = {"identity": L.PREC_IDENTITY, "lumped": L.PREC_LUMPED, "dirichlet": L.PREC_DIRICHLET}
+
+
+class FetiSolver:
+    """One problem on the current CUDA device (feti_create ... feti_destroy).
+
+    prob: any object with the fields of a boundary-value problem: coords
+    [N,3] float64, tets [E,4] int32, part [E] int32, n_parts, dir_dof,
+    dir_val, press_tri, press_owner, pressure, trac_tri, trac_owner,
+    traction, material (dict: kind, E, nu, c, k1, k2, kappa), fibres.
+    """
+
+    def __init__(self, prob, method: str = "af", precond: str = "dirichlet", tol: float = 1e-10,
+                 maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
+                 n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25):
+        self._lib = L.load()
+        self._ctx = C.c_void_p()
+        self._keep = []
+        keep = self._keep.append
+        coords = np.ascontiguousarray(prob.coords, dtype=np.float64); keep(coords)
+        tets = np.ascontiguousarray(prob.tets, dtype=np.int32); keep(tets)
+        part = np.ascontiguousarray(prob.part, dtype=np.int32); keep(part)
+        self.n_nodes = coords.shape[0]
+        mesh = L.FetiMesh(coords.shape[0], _ptr(coords, C.c_double), tets.shape[0], _ptr(tets, C.c_int32),
+                          _ptr(part, C.c_int32), int(prob.n_parts))
+        m = prob.material
+        fib = None
+        if getattr(prob, "fibres", None) is not None:
+            fib = np.ascontiguousarray(prob.fibres, dtype=np.float64); keep(fib)
+        mat = L.FetiMaterial(int(m["kind"]), float(m["E"]), float(m["nu"]), float(m["c"]), float(m["k1"]),
+                             float(m["k2"]), float(m["kappa"]), _ptr(fib, C.c_double))
+        dd = np.ascontiguousarray(prob.dir_dof, dtype=np.int32); keep(dd)
+        dv = np.ascontiguousarray(prob.dir_val, dtype=np.float64); keep(dv)
+        pt = np.ascontiguousarray(prob.press_tri, dtype=np.int32).reshape(-1, 3); keep(pt)
+        po = np.ascontiguousarray(prob.press_owner, dtype=np.int32); keep(po)
+        tt = np.ascontiguousarray(prob.trac_tri, dtype=np.int32).reshape(-1, 3); keep(tt)
+        to = np.ascontiguousarray(prob.trac_owner, dtype=np.int32); keep(to)
+        bc = L.FetiBC(dd.size, _ptr(dd, C.c_int32), _ptr(dv, C.c_double), pt.shape[0], _ptr(pt, C.c_int32),
+                      _ptr(po, C.c_int32), float(prob.pressure), tt.shape[0], _ptr(tt, C.c_int32),
+                      _ptr(to, C.c_int32), (C.c_double * 3)(*[float(v) for v in prob.traction]))
+        opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], L.FP64, float(tol), int(maxit), int(chunk),
+                            int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit))
+        st = None if stream is None else C.c_void_p(int(stream))
+        self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
+                                          C.byref(opt), st))
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, status: int):
+        if status != L.FETI_OK:
+            msg = self._lib.feti_last_error(self._ctx).decode() if self._ctx else ""
+            raise FetiError(status, msg)
+
+    def close(self):
+        if self._ctx:
+            self._lib.feti_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------------
+    def sizes(self) -> dict:
+        out = (C.c_int64 * 5)()
+        self._check(self._lib.feti_get_sizes(self._ctx, out))
+        return dict(zip(["n_lambda", "coarse_dim", "n_local", "n_boundary", "n_parts"], list(out)))
+
+    def index_maps(self) -> dict:
+        n = self.sizes()["n_lambda"]
+        rs = np.empty((n, 2), np.int32)
+        rl = np.empty((n, 2), np.int32)
+        sg = np.empty((n, 2), np.int8)
+        w = np.empty(n, np.float64)
+        b = np.empty(n, np.float64)
+        self._check(self._lib.feti_get_index_maps(self._ctx, rs.ctypes.data, rl.ctypes.data, sg.ctypes.data,
+                                                  w.ctypes.data, b.ctypes.data))
+        return {"row_sub": rs, "row_ldof": rl, "row_sign": sg, "weight": w, "b": b}
+
+    def fixing(self) -> list:
+        P = self.sizes()["n_parts"]
+        ptr = np.empty(P + 1, np.int32)
+        self._check(self._lib.feti_get_fixing(self._ctx, ptr.ctypes.data, None))
+        ld = np.empty(max(int(ptr[-1]), 1), np.int32)
+        self._check(self._lib.feti_get_fixing(self._ctx, None, ld.ctypes.data))
+        return [ld[ptr[s]:ptr[s + 1]].copy() for s in range(P)]
+
+    def prepare(self):
+        self._check(self._lib.feti_prepare(self._ctx))
+
+    def _report(self, rep: L.FetiReport) -> dict:
+        return {k: getattr(rep, k) for k, _ in L.FetiReport._fields_}
+
+    def solve(self, out=None, check: bool = True):
+        """Linear solve.  out: torch CUDA tensor [N*3] float64 (device) or None (returns numpy)."""
+        rep = L.FetiReport()
+        if out is None:
+            u = np.empty(3 * self.n_nodes, np.float64)
+            st = self._lib.feti_solve(self._ctx, u.ctypes.data, 0, C.byref(rep))
+        else:
+            u = out
+            st = self._lib.feti_solve(self._ctx, C.c_void_p(out.data_ptr()), 1, C.byref(rep))
+        if check:
+            self._check(st)
+        return u, self._report(rep)
+
+    def solve_host(self, u_host):
+        """feti_solve into a caller-owned host buffer (e.g. pinned torch tensor)."""
+        rep = L.FetiReport()
+        ptr = u_host.data_ptr() if hasattr(u_host, "data_ptr") else u_host.ctypes.data
+        self._check(self._lib.feti_solve(self._ctx, C.c_void_p(ptr), 0, C.byref(rep)))
+        return self._report(rep)
+
+    def newton(self, out=None):
+        rep = L.FetiReport()
+        if out is None:
+            u = np.empty(3 * self.n_nodes, np.float64)
+            self._check(self._lib.feti_newton(self._ctx, u.ctypes.data, 0, C.byref(rep)))
+        else:
+            u = out
+            self._check(self._lib.feti_newton(self._ctx, C.c_void_p(out.data_ptr()), 1, C.byref(rep)))
+        return u, self._report(rep)
+
+    def dual_apply(self, v, q, z, n_apply: int) -> float:
+        """q = F v, z = M^-1 q, n_apply times on device tensors; returns ms per apply."""
+        ms = C.c_double()
+        self._check(self._lib.feti_dual_apply(self._ctx, C.c_void_p(v.data_ptr()), C.c_void_p(q.data_ptr()),
+                                              C.c_void_p(z.data_ptr()), int(n_apply), C.byref(ms)))
+        return ms.value
+
+    def kernel_stats(self) -> dict:
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.feti_kernel_stats(self._ctx, C.byref(a), C.byref(b), C.byref(c)))
+        return {"gemv_ms": a.value, "gemv_bytes": b.value, "gemv_flops": c.value}

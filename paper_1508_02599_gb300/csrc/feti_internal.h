@@ -1,0 +1,141 @@
+// Internal interface between the host driver (feti_host.cpp) and the CUDA
+// kernels (feti_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace feti {
+
+// Status codes written by kernels into a device word (first error wins).
+enum DevStatus : int {
+  DEV_OK = 0,
+  DEV_LOCAL_SINGULAR = 1,   // non-positive pivot in a local Cholesky factorization
+  DEV_INVERTED = 2,         // element with non-positive volume or det F
+  DEV_BREAKDOWN = 3,        // (p, F p) <= 0 or not finite
+};
+
+// Per-subdomain dense layout.  Dense local order: [interior | boundary minus
+// fixing (nbp) | fixing (k) | augmentation (nbp)].  The augmentation block
+// holds the identity coupling used to obtain F_i = (S_i[b',b'])^-1 by block
+// elimination.  Offsets are in doubles.
+struct SubLayout {
+  int32_t n;      // free local DOFs (interior + boundary)
+  int32_t nI;     // interior DOFs
+  int32_t nbp;    // boundary DOFs that are not fixing DOFs
+  int32_t k;      // kernel dimension = number of fixing DOFs
+  int32_t ld;     // leading dimension of the dense matrix = n + nbp
+  int32_t boff;   // offset of this subdomain's boundary vector (sum of nb)
+  int32_t voff;   // offset of this subdomain's full local vector (sum of n)
+  int32_t coff;   // first coarse column of this subdomain
+  int64_t aoff;   // offset of the dense (ld x ld) matrix
+  int64_t soff;   // offset of the nb x nb preconditioner block
+  int64_t foff;   // offset of the nbp x nbp dense F_i
+  int64_t roff;   // offset of R_i (n x k, row-major) in dense local order
+};
+
+// Element kernels ------------------------------------------------------------
+void launch_elem_linear(int n_tets, const double* coords, const int32_t* tets, double E, double nu,
+                        double* Ke, int* status, cudaStream_t st);
+void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, const double* U,
+                     const double* fibres, double c, double k1, double k2, double kappa,
+                     double* Ke, double* fe, int* status, cudaStream_t st);
+
+// Local assembly: one CTA per subdomain walks its elements in order (no atomics).
+void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                     const int32_t* elem_dense, const double* Ke, double* A, cudaStream_t st);
+// Local load vectors: surface loads (+ -f_int) (- K_iD u_D).
+void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_ptr, const int32_t* face_dense,
+                         const double* face_force, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                         const int32_t* elem_dense, const double* elem_dirval, const double* Ke,
+                         const double* fe, double tau, double* f, cudaStream_t st);
+void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, const double* U,
+                        int kind, double scale, const double* traction, double* out, cudaStream_t st);
+// Writes the identity coupling of the augmentation block and zeros the rest of it.
+void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st);
+// Partial right-looking Cholesky: columns [c0, c1) of every subdomain,
+// trailing update on rows/cols [c1, n_active).  which = 0: interior
+// (c0 = 0, c1 = nI, n_active = n); which = 1: b' (c0 = nI, c1 = nI + nbp,
+// n_active = ld).
+void launch_chol_partial(int P, const SubLayout* lay, int which, double* A, int* status, cudaStream_t st);
+// Copies the trailing boundary block (nb x nb at [nI, nI)) into S (which=0),
+// or minus the augmentation block into F (which=1).
+void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st);
+// x = K_i^+ g per subdomain (fixing-DOF generalized inverse; zero on fixing DOFs).
+void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st);
+
+// Multiplier maps ----------------------------------------------------------
+struct Maps {
+  int n_lambda;
+  int nb_total;
+  const int32_t* row_pos;   // [2*n_lambda] global boundary position or -1
+  const double* row_sgn;    // [2*n_lambda] +-1 (0 for padding)
+  const double* weight;     // [n_lambda]
+  const int32_t* bt_ptr;    // [nb_total+1]
+  const int32_t* bt_row;    // rows of each boundary position
+  const double* bt_sgn;
+  const int32_t* bpos_sub;  // [nb_total] owning subdomain of each boundary position
+};
+
+// Dense local operator apply with fused gather: for every subdomain,
+// y_b = M_i (B_i^T (wv o x))_b, M_i = F_i (which=0, size nbp) or the
+// preconditioner block (which=1, size nb).  wv may be NULL (no weights).
+void launch_gemv(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay,
+                 int which, const double* M, const Maps& mp, const double* x, const double* wv, double* y,
+                 int max_m, const int* done, cudaStream_t st);
+// y_b = (B_i^T (wv o x))_b without a local operator (identity preconditioner).
+void launch_gather(const Maps& mp, const double* x, const double* wv, double* y, const int* done,
+                   cudaStream_t st);
+// q = wv o (B y) row-wise (deterministic), optional partial sums of (a, q).
+void launch_scatter(const Maps& mp, const double* y, const double* wv, double* q, const double* a,
+                    double* partial, const int* done, cudaStream_t st);
+
+// Coarse space ---------------------------------------------------------------
+// g_i = R_b,i^T (B_i^T x)  for every subdomain with k > 0.
+void launch_gtv(int P, const SubLayout* lay, const double* R, const Maps& mp, const double* x, double* g,
+                const int* done, cudaStream_t st);
+// c = Ginv g (dense coarse inverse, row-major cd x cd).
+void launch_coarse_apply(int cd, const double* Ginv, const double* g, double* c, const int* done,
+                         cudaStream_t st);
+// out = v - G c row-wise; optional partial sums of (a, out) (a NULL: (out,out)).
+void launch_expand(const Maps& mp, const SubLayout* lay, const double* R, const double* v, const double* c,
+                   double* out, const double* a, double* partial, int with_dot, const int* done,
+                   cudaStream_t st);
+// G^T G assembled per pair block, deterministic (one CTA per block).
+void launch_gtg(int n_blocks, const int32_t* blk_i, const int32_t* blk_j, const int32_t* blk_ptr,
+                const int32_t* blk_rows, const SubLayout* lay, const double* R, const Maps& mp, int cd,
+                double* GtG, cudaStream_t st);
+
+// PCG control ------------------------------------------------------------------
+// Device scalar block.
+struct PcgScalars {
+  double rho, rho_prev, alpha, beta, pq, wnorm0, wnorm, tol;
+  int it, done, status, maxit;
+};
+int scatter_partials();  // number of partial sums the row kernels produce
+void launch_ctl_rho(PcgScalars* s, const double* partial, double* beta_hist, cudaStream_t st);
+void launch_ctl_alpha(PcgScalars* s, const double* partial, double* alpha_hist, cudaStream_t st);
+void launch_ctl_conv(PcgScalars* s, const double* partial, int first, cudaStream_t st);
+void launch_axpby(int n, double* y, const double* x, const PcgScalars* s, int mode, cudaStream_t st);
+void launch_update_lr(int n, double* lam, double* r, const double* p, const double* q, const PcgScalars* s,
+                      cudaStream_t st);
+void launch_vsub(int n, const double* a, const double* b, double* out, cudaStream_t st);
+
+// Global displacement by the owner rule.
+void launch_owner_scatter(int n_entries, const int32_t* gdof, const int32_t* vpos, const double* x,
+                          double* U, cudaStream_t st);
+// x_local += R_i gamma_i.
+void launch_add_kernel(int P, const SubLayout* lay, const double* R, const double* gamma, double* x,
+                       cudaStream_t st);
+
+}  // namespace feti
+
+namespace feti {
+// e_i = scale * R_i^T x_i on full local vectors (dense local order).
+void launch_rtx(int P, const SubLayout* lay, const double* R, const double* x, double scale, double* e,
+                cudaStream_t st);
+// loc_b = boundary slice of the full local vectors x.
+void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st);
+// rhs_i = f_i - (boundary vector loc placed at the boundary positions).
+void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
+                      cudaStream_t st);
+}  // namespace feti

@@ -1,0 +1,1059 @@
+// CUDA kernels (sm_103a) of the FETI solver: P1 element matrices, local
+// assembly, dense local factorizations and operators, multiplier gathers,
+// coarse projection and projected-CG vector updates.
+//
+// Design for GB300: FP64 arithmetic issues at about two FMAs per clock per SM,
+// so every FP64 kernel here is bounded by the FP64 pipe or by HBM; gathers are
+// row-major and deterministic (no floating-point atomics anywhere); every
+// subdomain of uneven size is one batch element of a single launch.
+#include "feti_internal.h"
+
+#include <cmath>
+
+namespace feti {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPartials = 304;  // 2 x 152 SMs: fixed grid of the row kernels
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order CTA reduction (deterministic for a fixed launch shape).
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// P1 shape-function gradients: g[a][j] = dN_a/dX_j, volume V.
+__device__ __forceinline__ bool p1_gradients(const double x[4][3], double g[4][3], double& V) {
+  double Jm[3][3];  // columns x_k - x_0
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) Jm[i][k] = x[k + 1][i] - x[0][i];
+  const double c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+  const double c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+  const double c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+  const double det = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
+  V = det / 6.0;
+  if (!(det > 0.0)) return false;
+  const double id = 1.0 / det;
+  double Ji[3][3];  // inverse of Jm
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) * id;
+  Ji[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) * id;
+  Ji[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) * id;
+  Ji[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) * id;
+  Ji[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) * id;
+  Ji[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) * id;
+  // N_1..3 = xi_1..3 (rows of Ji), N_0 = 1 - sum
+  for (int j = 0; j < 3; ++j) {
+    g[1][j] = Ji[0][j];
+    g[2][j] = Ji[1][j];
+    g[3][j] = Ji[2][j];
+    g[0][j] = -(Ji[0][j] + Ji[1][j] + Ji[2][j]);
+  }
+  return true;
+}
+
+__global__ void k_elem_linear(int n_tets, const double* __restrict__ coords, const int32_t* __restrict__ tets,
+                              double E, double nu, double* __restrict__ Ke, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_tets) return;
+  double x[4][3], g[4][3], V;
+  for (int a = 0; a < 4; ++a) {
+    const int n = tets[4 * e + a];
+    for (int i = 0; i < 3; ++i) x[a][i] = coords[3 * n + i];
+  }
+  if (!p1_gradients(x, g, V)) {
+    set_status(status, DEV_INVERTED);
+    return;
+  }
+  const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = E / (2.0 * (1.0 + nu));
+  double* K = Ke + (size_t)e * 144;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double v = lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i];
+          if (i == j) v += mu * gab;
+          K[(3 * a + i) * 12 + 3 * b + j] = V * v;
+        }
+    }
+}
+
+// Two-fibre hyperelastic element (Sec. 3.1 energy, Sec. 3.2 tangent).
+// S = kappa (J-1) J C^-1 + c J^-2/3 (I - I1/3 C^-1) + sum_f 2 psi_f' J^-2/3 (a a - I4/3 C^-1)
+// and CC = 2 dS/dC written out term by term (derivation in the comments).
+__global__ void k_elem_hgo(int n_tets, const double* __restrict__ coords, const int32_t* __restrict__ tets,
+                           const double* __restrict__ U, const double* __restrict__ fibres, double cmat,
+                           double k1, double k2, double kappa, double* __restrict__ Ke,
+                           double* __restrict__ fe, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_tets) return;
+  double x[4][3], g[4][3], V, u[4][3];
+  for (int a = 0; a < 4; ++a) {
+    const int n = tets[4 * e + a];
+    for (int i = 0; i < 3; ++i) {
+      x[a][i] = coords[3 * n + i];
+      u[a][i] = U ? U[3 * n + i] : 0.0;
+    }
+  }
+  if (!p1_gradients(x, g, V)) {
+    set_status(status, DEV_INVERTED);
+    return;
+  }
+  double F[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int a = 0; a < 4; ++a) s += u[a][i] * g[a][j];
+      F[i][j] = s;
+    }
+  double C[3][3];
+  for (int I = 0; I < 3; ++I)
+    for (int J = 0; J < 3; ++J) C[I][J] = F[0][I] * F[0][J] + F[1][I] * F[1][J] + F[2][I] * F[2][J];
+  const double detC = C[0][0] * (C[1][1] * C[2][2] - C[1][2] * C[2][1]) -
+                      C[0][1] * (C[1][0] * C[2][2] - C[1][2] * C[2][0]) +
+                      C[0][2] * (C[1][0] * C[2][1] - C[1][1] * C[2][0]);
+  const double detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                      F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                      F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+  if (!(detF > 0.0)) {
+    set_status(status, DEV_INVERTED);
+    return;
+  }
+  const double J = sqrt(detC);
+  double Ci[3][3];
+  {
+    const double id = 1.0 / detC;
+    Ci[0][0] = (C[1][1] * C[2][2] - C[1][2] * C[2][1]) * id;
+    Ci[0][1] = (C[0][2] * C[2][1] - C[0][1] * C[2][2]) * id;
+    Ci[0][2] = (C[0][1] * C[1][2] - C[0][2] * C[1][1]) * id;
+    Ci[1][0] = Ci[0][1];
+    Ci[1][1] = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) * id;
+    Ci[1][2] = (C[0][2] * C[1][0] - C[0][0] * C[1][2]) * id;
+    Ci[2][0] = Ci[0][2];
+    Ci[2][1] = Ci[1][2];
+    Ci[2][2] = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) * id;
+  }
+  const double J23 = pow(detC, -1.0 / 3.0);  // J^(-2/3)
+  const double I1 = C[0][0] + C[1][1] + C[2][2];
+  // Scalar coefficients of S = sum_t s_t T_t (see the stress formula above).
+  // Volumetric: S_v = A_v C^-1 with A_v = kappa (J-1) J; d(A_v)/dC = kappa (2J-1) J/2 C^-1.
+  // Isochoric matrix: S_m = c J23 I - (c J23 I1/3) C^-1.
+  // Fibre f: S_f = 2 psi' J23 a a - (2 psi' J23 I4/3) C^-1.
+  double S[3][3];
+  const double Av = kappa * (J - 1.0) * J;
+  for (int I = 0; I < 3; ++I)
+    for (int Jj = 0; Jj < 3; ++Jj)
+      S[I][Jj] = Av * Ci[I][Jj] + cmat * J23 * ((I == Jj ? 1.0 : 0.0) - I1 / 3.0 * Ci[I][Jj]);
+  double fa[2][3], I4[2], dpsi[2], d2psi[2];
+  bool act[2];
+  for (int f = 0; f < 2; ++f) {
+    for (int i = 0; i < 3; ++i) fa[f][i] = fibres[6 * e + 3 * f + i];
+    double t = 0.0;
+    for (int I = 0; I < 3; ++I)
+      for (int Jj = 0; Jj < 3; ++Jj) t += fa[f][I] * C[I][Jj] * fa[f][Jj];
+    I4[f] = t;
+    const double I4b = J23 * t;
+    const double dlt = I4b - 1.0;
+    act[f] = dlt > 1e-12;
+    if (act[f]) {
+      const double ex = exp(k2 * dlt * dlt);
+      dpsi[f] = k1 * dlt * ex;                          // dPsi/dI4bar
+      d2psi[f] = k1 * ex * (1.0 + 2.0 * k2 * dlt * dlt);  // d2Psi/dI4bar2
+      for (int I = 0; I < 3; ++I)
+        for (int Jj = 0; Jj < 3; ++Jj)
+          S[I][Jj] += 2.0 * dpsi[f] * J23 * (fa[f][I] * fa[f][Jj] - t / 3.0 * Ci[I][Jj]);
+    } else {
+      dpsi[f] = d2psi[f] = 0.0;
+    }
+  }
+  // Elasticity tensor CC_IJKL = 2 dS_IJ/dC_KL, with Q_IJKL = (Ci_IK Ci_JL + Ci_IL Ci_JK)/2,
+  // dCi/dC = -Q, dJ/dC = J/2 Ci, dJ23/dC = -J23/3 Ci, dI1/dC = I, dI4/dC = a a:
+  //   volumetric  kappa (2J-1) J Ci(x)Ci - 2 A_v Q
+  //   matrix      -(2c/3) J23 (I(x)Ci + Ci(x)I) + (2c/9) J23 I1 Ci(x)Ci + (2c/3) J23 I1 Q
+  //   fibre f     4 psi'' J23^2 B(x)B - (4/3) psi' J23 (B(x)Ci + Ci(x)a a) + (4/3) psi' J23 I4 Q,
+  //               B = a a - I4/3 Ci (the two middle products add up to a major-symmetric term).
+  // Element tangent: K[a i, b j] = V (delta_ij g_a.S g_b + X_ai : CC : X_bj) with the
+  // symmetric X_ai,IJ = (F_iI g_aJ + F_iJ g_aI)/2 (CC has minor symmetries).
+  double Kl[12][12];
+  // geometric part
+  double gSg[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double t = 0.0;
+      for (int I = 0; I < 3; ++I)
+        for (int Jj = 0; Jj < 3; ++Jj) t += g[a][I] * S[I][Jj] * g[b][Jj];
+      gSg[a][b] = t;
+    }
+  // material part via contraction with the tensor blocks written out
+  // E_a,i := symmetrised F_iI g_aJ (3x3 in I,J) for each (a, i).
+  double Ea[12][3][3];
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int I = 0; I < 3; ++I)
+        for (int Jj = 0; Jj < 3; ++Jj)
+          Ea[3 * a + i][I][Jj] = 0.5 * (F[i][I] * g[a][Jj] + F[i][Jj] * g[a][I]);
+  // Contractions needed: for symmetric X, Y:
+  //   X:(Ci(x)Ci):Y = (Ci:X)(Ci:Y);  X:Q:Y = tr(Ci X Ci Y);  X:(I(x)Ci):Y = tr(X) (Ci:Y)
+  //   X:(Ci(x)aa):Y = (Ci:X)(a.Y a);  X:(B(x)B):Y = (B:X)(B:Y)
+  double trX[12], CiX[12], aXa[2][12], BX[2][12];
+  double CiXCi[12][3][3];
+  double Bf[2][3][3];
+  for (int f = 0; f < 2; ++f)
+    for (int I = 0; I < 3; ++I)
+      for (int Jj = 0; Jj < 3; ++Jj) Bf[f][I][Jj] = fa[f][I] * fa[f][Jj] - I4[f] / 3.0 * Ci[I][Jj];
+  for (int p = 0; p < 12; ++p) {
+    double tr = 0.0, cx = 0.0;
+    for (int I = 0; I < 3; ++I) {
+      tr += Ea[p][I][I];
+      for (int Jj = 0; Jj < 3; ++Jj) cx += Ci[I][Jj] * Ea[p][I][Jj];
+    }
+    trX[p] = tr;
+    CiX[p] = cx;
+    for (int f = 0; f < 2; ++f) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int I = 0; I < 3; ++I)
+        for (int Jj = 0; Jj < 3; ++Jj) {
+          s1 += fa[f][I] * Ea[p][I][Jj] * fa[f][Jj];
+          s2 += Bf[f][I][Jj] * Ea[p][I][Jj];
+        }
+      aXa[f][p] = s1;
+      BX[f][p] = s2;
+    }
+    double T[3][3];
+    for (int I = 0; I < 3; ++I)
+      for (int L = 0; L < 3; ++L) {
+        double t = 0.0;
+        for (int Jj = 0; Jj < 3; ++Jj) t += Ci[I][Jj] * Ea[p][Jj][L];
+        T[I][L] = t;
+      }
+    for (int I = 0; I < 3; ++I)
+      for (int L = 0; L < 3; ++L) {
+        double t = 0.0;
+        for (int Jj = 0; Jj < 3; ++Jj) t += T[I][Jj] * Ci[Jj][L];
+        CiXCi[p][I][L] = t;
+      }
+  }
+  const double cvv = kappa * (2.0 * J - 1.0) * J;       // Ci(x)Ci
+  const double cQ = -2.0 * Av + 2.0 * cmat * J23 * I1 / 3.0;  // Q
+  const double cIC = -2.0 * cmat * J23 / 3.0;           // I(x)Ci + Ci(x)I
+  double cCC = cvv + 2.0 * cmat * J23 * I1 / 9.0;       // Ci(x)Ci
+  double cQf = 0.0;
+  for (int f = 0; f < 2; ++f)
+    if (act[f]) {
+      const double m = 2.0 * dpsi[f] * J23;
+      // 2 m dB/dC = 2m(-1/3 Ci(x)aa + I4/3 Q) ; symmetrised Ci(x)aa handled with aXa
+      cQf += 2.0 * m * I4[f] / 3.0;
+    }
+  for (int p = 0; p < 12; ++p)
+    for (int q = p; q < 12; ++q) {
+      const double XQY = [&]() {
+        double t = 0.0;
+        for (int I = 0; I < 3; ++I)
+          for (int L = 0; L < 3; ++L) t += CiXCi[p][I][L] * Ea[q][L][I];
+        return t;
+      }();
+      double v = cCC * CiX[p] * CiX[q] + (cQ + cQf) * XQY + cIC * (trX[p] * CiX[q] + CiX[p] * trX[q]);
+      for (int f = 0; f < 2; ++f)
+        if (act[f]) {
+          const double m = 2.0 * dpsi[f] * J23;
+          v += 4.0 * d2psi[f] * J23 * J23 * BX[f][p] * BX[f][q];
+          // -(4/3) psi' J23 sym(Ci(x)B) and -(2m/3) sym(Ci(x)aa): the derivative of S_f
+          // w.r.t. C through J23 and through Ci; symmetrised over (p, q)
+          v += -(2.0 / 3.0) * dpsi[f] * J23 * 2.0 * 0.5 * (CiX[p] * BX[f][q] + BX[f][p] * CiX[q]);
+          v += -(2.0 * m / 3.0) * 0.5 * (CiX[p] * aXa[f][q] + aXa[f][p] * CiX[q]);
+        }
+      Kl[p][q] = v;
+    }
+  double* Kout = Ke + (size_t)e * 144;
+  for (int p = 0; p < 12; ++p)
+    for (int q = 0; q < 12; ++q) {
+      const int pp = p < q ? p : q, qq = p < q ? q : p;
+      double v = Kl[pp][qq];
+      if (p % 3 == q % 3) v += gSg[p / 3][q / 3];
+      Kout[p * 12 + q] = V * v;
+    }
+  if (fe) {
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) {
+        double t = 0.0;
+        for (int I = 0; I < 3; ++I)
+          for (int Jj = 0; Jj < 3; ++Jj) t += F[i][I] * S[I][Jj] * g[a][Jj];
+        fe[(size_t)e * 12 + 3 * a + i] = V * t;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(const SubLayout* __restrict__ lay, const int32_t* __restrict__ sub_elem_ptr,
+                           const int32_t* __restrict__ sub_elems, const int32_t* __restrict__ elem_dense,
+                           const double* __restrict__ Ke, double* __restrict__ Abase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  double* A = Abase + L.aoff;
+  const int t = threadIdx.x;
+  for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+    const int e = sub_elems[q];
+    if (t < 144) {
+      const int r = elem_dense[12 * e + t / 12], c = elem_dense[12 * e + t % 12];
+      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += Ke[(size_t)e * 144 + t];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_face_forces(int n_faces, const int32_t* __restrict__ tri, const double* __restrict__ coords,
+                              const double* __restrict__ U, int kind, double scale,
+                              const double* __restrict__ traction, double* __restrict__ out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_faces) return;
+  double x[3][3];
+  for (int v = 0; v < 3; ++v) {
+    const int n = tri[3 * f + v];
+    for (int i = 0; i < 3; ++i) x[v][i] = coords[3 * n + i] + (U ? U[3 * n + i] : 0.0);
+  }
+  double e1[3], e2[3], av[3];
+  for (int i = 0; i < 3; ++i) {
+    e1[i] = x[1][i] - x[0][i];
+    e2[i] = x[2][i] - x[0][i];
+  }
+  av[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+  av[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+  av[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+  double force[3];
+  if (kind == 0) {
+    for (int i = 0; i < 3; ++i) force[i] = scale * av[i] / 3.0;
+  } else {
+    const double area = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+    for (int i = 0; i < 3; ++i) force[i] = scale * area * traction[i] / 3.0;
+  }
+  for (int v = 0; v < 3; ++v)
+    for (int i = 0; i < 3; ++i) out[9 * (size_t)f + 3 * v + i] = force[i];
+}
+
+__global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t* __restrict__ sub_face_ptr,
+                               const int32_t* __restrict__ face_dense, const double* __restrict__ face_force,
+                               const int32_t* __restrict__ sub_elem_ptr, const int32_t* __restrict__ sub_elems,
+                               const int32_t* __restrict__ elem_dense, const double* __restrict__ elem_dirval,
+                               const double* __restrict__ Ke, const double* __restrict__ fe, double tau,
+                               double* __restrict__ fbase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  double* f = fbase + L.voff;
+  const int t = threadIdx.x;
+  for (int i = t; i < L.n; i += blockDim.x) f[i] = 0.0;
+  __syncthreads();
+  for (int q = sub_face_ptr[s]; q < sub_face_ptr[s + 1]; ++q) {
+    if (t < 9) {
+      const int r = face_dense[9 * q + t];
+      if (r >= 0) f[r] += tau * face_force[9 * (size_t)q + t];
+    }
+    __syncthreads();
+  }
+  for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+    const int e = sub_elems[q];
+    if (t < 12) {
+      const int r = elem_dense[12 * e + t];
+      if (r >= 0) {
+        double v = fe ? -fe[(size_t)e * 12 + t] : 0.0;
+        if (elem_dirval) {
+          for (int b = 0; b < 12; ++b) {
+            const double ud = elem_dirval[12 * (size_t)e + b];
+            if (ud != 0.0) v -= Ke[(size_t)e * 144 + t * 12 + b] * ud;
+          }
+        }
+        f[r] += v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_augment(const SubLayout* __restrict__ lay, double* __restrict__ Abase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  double* A = Abase + L.aoff;
+  for (int j = threadIdx.x; j < L.nbp; j += blockDim.x) A[(size_t)(L.n + j) * L.ld + L.nI + j] = 1.0;
+}
+
+// Right-looking blocked Cholesky of columns [c0, c1) with trailing update of
+// rows/cols [c1, na); lower triangle, row-major, leading dimension ld.
+constexpr int NB = 32;
+constexpr int TT = 64;
+
+__global__ void __launch_bounds__(kThreads) k_chol_partial(const SubLayout* __restrict__ lay, int which,
+                                                           double* __restrict__ Abase, int* status) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  const int c0 = which ? L.nI : 0;
+  const int c1 = which ? L.nI + L.nbp : L.nI;
+  const int na = which ? L.ld : L.n;
+  __shared__ double D[NB][NB + 1];
+  __shared__ double Pa[TT][NB + 1];
+  __shared__ double Pb[TT][NB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int kb = c0; kb < c1; kb += NB) {
+    const int nk = min(NB, c1 - kb);
+    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+      const int i = idx / NB, j = idx % NB;
+      D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int i = tid;
+      for (int j = 0; j < nk; ++j) {
+        if (i == j) {
+          const double d = D[j][j];
+          if (!(d > 0.0) || !isfinite(d)) bad = 1;
+          D[j][j] = sqrt(d);
+        }
+        __syncwarp();
+        if (bad) break;
+        if (i > j && i < nk) D[i][j] /= D[j][j];
+        __syncwarp();
+        if (i > j && i < nk)
+          for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) set_status(status, DEV_LOCAL_SINGULAR);
+      return;
+    }
+    for (int idx = tid; idx < nk * nk; idx += blockDim.x) {
+      const int i = idx / nk, j = idx % nk;
+      if (j <= i) A[(kb + i) * ld + kb + j] = D[i][j];
+    }
+    // panel solve: rows below the diagonal block, X = A_panel L_D^-T
+    const int r0 = kb + nk;
+    for (int base = r0; base < na; base += TT) {
+      const int nr = min(TT, na - base);
+      for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+        const int r = idx / NB, l = idx % NB;
+        Pa[r][l] = (r < nr && l < nk) ? A[(base + r) * ld + kb + l] : 0.0;
+      }
+      __syncthreads();
+      if (tid < nr) {
+        double xr[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < nk) {
+            double v = xr[j];
+#pragma unroll
+            for (int l = 0; l < NB; ++l)
+              if (l < j) v -= xr[l] * D[j][l];
+            xr[j] = v / D[j][j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) Pa[tid][j] = xr[j];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+        const int r = idx / NB, l = idx % NB;
+        if (r < nr && l < nk) A[(base + r) * ld + kb + l] = Pa[r][l];
+      }
+      __syncthreads();
+    }
+    // trailing update, lower triangle, 64x64 tiles
+    const int ntile = (na - r0 + TT - 1) / TT;
+    for (int ti = 0; ti < ntile; ++ti) {
+      for (int tj = 0; tj <= ti; ++tj) {
+        const int ib = r0 + ti * TT, jb = r0 + tj * TT;
+        for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+          const int r = idx / NB, l = idx % NB;
+          Pa[r][l] = (ib + r < na && l < nk) ? A[(ib + r) * ld + kb + l] : 0.0;
+          Pb[r][l] = (jb + r < na && l < nk) ? A[(jb + r) * ld + kb + l] : 0.0;
+        }
+        __syncthreads();
+        const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int l = 0; l < nk; ++l) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            av[a] = Pa[tr + a][l];
+            bv[a] = Pb[tc + a][l];
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = ib + tr + a, j = jb + tc + b;
+            if (i < na && j < na && j <= i) A[i * ld + j] -= acc[a][b];
+          }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+__global__ void k_extract(const SubLayout* __restrict__ lay, int which, const double* __restrict__ Abase,
+                          double* __restrict__ out) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  const double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  if (which == 0) {
+    const int nb = L.nbp + L.k;
+    double* S = out + L.soff;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int i = idx / nb, j = idx % nb;
+      const int ii = max(i, j), jj = min(i, j);
+      S[idx] = A[(L.nI + ii) * ld + L.nI + jj];
+    }
+  } else {
+    const int m = L.nbp;
+    double* F = out + L.foff;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int i = idx / m, j = idx % m;
+      const int ii = max(i, j), jj = min(i, j);
+      F[idx] = -A[(L.n + ii) * ld + L.n + jj];
+    }
+  }
+}
+
+// x = K^+ g: forward L y = g_r (row dots), backward L^T x = y (row axpys).
+__global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict__ lay,
+                                                    const double* __restrict__ Abase,
+                                                    const double* __restrict__ gbase, double* __restrict__ xbase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  const double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  const double* g = gbase + L.voff;
+  double* x = xbase + L.voff;
+  const int nr = L.nI + L.nbp;
+  __shared__ double red[32];
+  __shared__ double xi;
+  for (int i = 0; i < nr; ++i) {
+    double t = 0.0;
+    for (int j = threadIdx.x; j < i; j += blockDim.x) t += A[i * ld + j] * x[j];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) x[i] = (g[i] - t) / A[i * ld + i];
+    __syncthreads();
+  }
+  for (int i = nr + threadIdx.x; i < L.n; i += blockDim.x) x[i] = 0.0;
+  __syncthreads();
+  for (int i = nr - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      xi = x[i] / A[i * ld + i];
+      x[i] = xi;
+    }
+    __syncthreads();
+    const double v = xi;
+    for (int j = threadIdx.x; j < i; j += blockDim.x) x[j] -= A[i * ld + j] * v;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Hot path: dense local operator apply with fused signed gather.
+constexpr int GEMV_ROWS = 32;
+
+__global__ void __launch_bounds__(kThreads) k_gemv(const int32_t* __restrict__ blk_sub,
+                                                   const int32_t* __restrict__ blk_row0,
+                                                   const SubLayout* __restrict__ lay, int which,
+                                                   const double* __restrict__ M, Maps mp,
+                                                   const double* __restrict__ x, const double* __restrict__ wv,
+                                                   double* __restrict__ y, const int* __restrict__ done) {
+  if (*done) return;
+  extern __shared__ double v[];
+  const int s = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const double* Ms = M + (which == 0 ? L.foff : L.soff);
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    const int gp = L.boff + p;
+    double val = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+      const int row = mp.bt_row[e];
+      val += mp.bt_sgn[e] * x[row] * (wv ? wv[row] : 1.0);
+    }
+    v[p] = val;
+  }
+  if (which == 0 && r0 == 0)
+    for (int p = L.nbp + threadIdx.x; p < L.nbp + L.k; p += blockDim.x) y[L.boff + p] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int RPW = GEMV_ROWS / (kThreads / 32);
+#pragma unroll
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int r = r0 + wid * RPW + rr;
+    if (r < m) {
+      const double* row = Ms + (size_t)r * m;
+      double acc = 0.0;
+      for (int c = lane; c < m; c += 32) acc += row[c] * v[c];
+      acc = warp_sum(acc);
+      if (lane == 0) y[L.boff + r] = acc;
+    }
+  }
+}
+
+__global__ void k_gather(Maps mp, const double* __restrict__ x, const double* __restrict__ wv,
+                         double* __restrict__ y, const int* __restrict__ done) {
+  if (*done) return;
+  for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < mp.nb_total; gp += gridDim.x * blockDim.x) {
+    double val = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+      const int row = mp.bt_row[e];
+      val += mp.bt_sgn[e] * x[row] * (wv ? wv[row] : 1.0);
+    }
+    y[gp] = val;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(Maps mp, const double* __restrict__ y,
+                                                      const double* __restrict__ wv, double* __restrict__ q,
+                                                      const double* __restrict__ a, double* __restrict__ partial,
+                                                      const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[32];
+  double dot = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mp.n_lambda; r += gridDim.x * blockDim.x) {
+    double val = 0.0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int pos = mp.row_pos[2 * r + e];
+      if (pos >= 0) val += mp.row_sgn[2 * r + e] * y[pos];
+    }
+    if (wv) val *= wv[r];
+    q[r] = val;
+    if (partial) dot += (a ? a[r] : val) * val;
+  }
+  if (partial) {
+    dot = block_sum(dot, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = dot;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gtv(const SubLayout* __restrict__ lay, const double* __restrict__ R,
+                                                  Maps mp, const double* __restrict__ x, double* __restrict__ g,
+                                                  const int* __restrict__ done) {
+  if (*done) return;
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  if (L.k == 0) return;
+  __shared__ double red[32];
+  const int nb = L.nbp + L.k;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    const int gp = L.boff + p;
+    double val = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) val += mp.bt_sgn[e] * x[mp.bt_row[e]];
+    const double* Rr = R + L.roff + (size_t)(L.nI + p) * L.k;
+    for (int a = 0; a < L.k; ++a) acc[a] += Rr[a] * val;
+  }
+  for (int a = 0; a < L.k; ++a) {
+    const double t = block_sum(acc[a], red);
+    if (threadIdx.x == 0) g[L.coff + a] = t;
+  }
+}
+
+__global__ void k_coarse_apply(int cd, const double* __restrict__ Ginv, const double* __restrict__ g,
+                               double* __restrict__ c, const int* __restrict__ done) {
+  if (*done) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < cd; r += nwarps) {
+    double acc = 0.0;
+    for (int j = lane; j < cd; j += 32) acc += Ginv[(size_t)r * cd + j] * g[j];
+    acc = warp_sum(acc);
+    if (lane == 0) c[r] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_expand(Maps mp, const SubLayout* __restrict__ lay,
+                                                     const double* __restrict__ R, const double* __restrict__ v,
+                                                     const double* __restrict__ c, double* __restrict__ out,
+                                                     const double* __restrict__ a, double* __restrict__ partial,
+                                                     int with_dot, const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[32];
+  double dot = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mp.n_lambda; r += gridDim.x * blockDim.x) {
+    double val = v[r];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int gp = mp.row_pos[2 * r + e];
+      if (gp >= 0) {
+        const SubLayout L = lay[mp.bpos_sub[gp]];
+        if (L.k) {
+          const double* Rr = R + L.roff + (size_t)(L.nI + gp - L.boff) * L.k;
+          double t = 0.0;
+          for (int k = 0; k < L.k; ++k) t += Rr[k] * c[L.coff + k];
+          val -= mp.row_sgn[2 * r + e] * t;
+        }
+      }
+    }
+    out[r] = val;
+    if (with_dot) dot += (a ? a[r] : val) * val;
+  }
+  if (with_dot) {
+    dot = block_sum(dot, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = dot;
+  }
+}
+
+// G^T G: one CTA per pair block (i, j), thread per entry, rows in fixed order.
+__global__ void k_gtg(const int32_t* __restrict__ blk_i, const int32_t* __restrict__ blk_j,
+                      const int32_t* __restrict__ blk_ptr, const int32_t* __restrict__ blk_rows,
+                      const SubLayout* __restrict__ lay, const double* __restrict__ R, Maps mp, int cd,
+                      double* __restrict__ GtG) {
+  const int b = blockIdx.x;
+  const int si = blk_i[b], sj = blk_j[b];
+  const SubLayout Li = lay[si], Lj = lay[sj];
+  const int t = threadIdx.x;
+  if (t >= Li.k * Lj.k) return;
+  const int a = t / Lj.k, c = t % Lj.k;
+  double acc = 0.0;
+  for (int q = blk_ptr[b]; q < blk_ptr[b + 1]; ++q) {
+    const int r = blk_rows[q];
+    double gi = 0.0, gj = 0.0;
+    for (int e = 0; e < 2; ++e) {
+      const int gp = mp.row_pos[2 * r + e];
+      if (gp < 0) continue;
+      const int s = mp.bpos_sub[gp];
+      if (s == si) gi += mp.row_sgn[2 * r + e] * R[Li.roff + (size_t)(Li.nI + gp - Li.boff) * Li.k + a];
+      if (s == sj) gj += mp.row_sgn[2 * r + e] * R[Lj.roff + (size_t)(Lj.nI + gp - Lj.boff) * Lj.k + c];
+    }
+    acc += gi * gj;
+  }
+  GtG[(size_t)(Li.coff + a) * cd + Lj.coff + c] = acc;
+  GtG[(size_t)(Lj.coff + c) * cd + Li.coff + a] = acc;
+}
+
+// ---------------------------------------------------------------------------
+__device__ double reduce_partials(const double* partial, double* red) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < kPartials; i += blockDim.x) t += partial[i];
+  return block_sum(t, red);
+}
+
+__global__ void k_ctl_rho(PcgScalars* s, const double* __restrict__ partial, double* beta_hist) {
+  if (s->done) return;
+  __shared__ double red[32];
+  const double rho = reduce_partials(partial, red);
+  if (threadIdx.x == 0) {
+    if (!(rho > 0.0) || !isfinite(rho)) {
+      s->status = DEV_BREAKDOWN;
+      s->done = 1;
+      return;
+    }
+    const double beta = s->it > 0 ? rho / s->rho_prev : 0.0;
+    s->beta = beta;
+    s->rho = rho;
+    s->rho_prev = rho;
+    beta_hist[s->it] = beta;
+  }
+}
+
+__global__ void k_ctl_alpha(PcgScalars* s, const double* __restrict__ partial, double* alpha_hist) {
+  if (s->done) return;
+  __shared__ double red[32];
+  const double pq = reduce_partials(partial, red);
+  if (threadIdx.x == 0) {
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      s->status = DEV_BREAKDOWN;
+      s->done = 1;
+      return;
+    }
+    s->pq = pq;
+    s->alpha = s->rho / pq;
+    alpha_hist[s->it] = s->alpha;
+  }
+}
+
+__global__ void k_ctl_conv(PcgScalars* s, const double* __restrict__ partial, int first) {
+  if (s->done) return;
+  __shared__ double red[32];
+  const double wn = sqrt(reduce_partials(partial, red));
+  if (threadIdx.x == 0) {
+    if (first) {
+      s->wnorm0 = wn;
+      s->wnorm = wn;
+      if (!(wn > 0.0)) s->done = 1;
+      if (!isfinite(wn)) {
+        s->status = DEV_BREAKDOWN;
+        s->done = 1;
+      }
+      return;
+    }
+    s->it += 1;
+    s->wnorm = wn;
+    if (!isfinite(wn)) {
+      s->status = DEV_BREAKDOWN;
+      s->done = 1;
+    } else if (wn <= s->tol * s->wnorm0 || s->it >= s->maxit) {
+      s->done = 1;
+    }
+  }
+}
+
+__global__ void k_axpby(int n, double* __restrict__ p, const double* __restrict__ y, const PcgScalars* s, int mode) {
+  if (s->done) return;
+  const double beta = s->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = (mode == 0 && s->it > 0) ? y[i] + beta * p[i] : y[i];
+}
+
+__global__ void k_update_lr(int n, double* __restrict__ lam, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ q, const PcgScalars* s) {
+  if (s->done) return;
+  const double alpha = s->alpha;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    lam[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+__global__ void k_vsub(int n, const double* a, const double* b, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] - b[i];
+}
+
+__global__ void k_owner_scatter(int n, const int32_t* __restrict__ gdof, const int32_t* __restrict__ vpos,
+                                const double* __restrict__ x, double* __restrict__ U) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) U[gdof[i]] = x[vpos[i]];
+}
+
+__global__ void k_add_kernel(const SubLayout* __restrict__ lay, const double* __restrict__ R,
+                             const double* __restrict__ gamma, double* __restrict__ xbase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  if (L.k == 0) return;
+  double* x = xbase + L.voff;
+  for (int d = threadIdx.x; d < L.n; d += blockDim.x) {
+    double t = 0.0;
+    for (int a = 0; a < L.k; ++a) t += R[L.roff + (size_t)d * L.k + a] * gamma[L.coff + a];
+    x[d] += t;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rtx(const SubLayout* __restrict__ lay, const double* __restrict__ R,
+                                                  const double* __restrict__ xbase, double scale,
+                                                  double* __restrict__ e) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  if (L.k == 0) return;
+  __shared__ double red[32];
+  const double* x = xbase + L.voff;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int d = threadIdx.x; d < L.n; d += blockDim.x) {
+    const double* Rr = R + L.roff + (size_t)d * L.k;
+    for (int a = 0; a < L.k; ++a) acc[a] += Rr[a] * x[d];
+  }
+  for (int a = 0; a < L.k; ++a) {
+    const double t = block_sum(acc[a], red);
+    if (threadIdx.x == 0) e[L.coff + a] = scale * t;
+  }
+}
+
+__global__ void k_take_boundary(const SubLayout* __restrict__ lay, const double* __restrict__ xbase,
+                                double* __restrict__ loc) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  for (int p = threadIdx.x; p < L.nbp + L.k; p += blockDim.x) loc[L.boff + p] = xbase[L.voff + L.nI + p];
+}
+
+__global__ void k_local_sub(const SubLayout* __restrict__ lay, const double* __restrict__ fbase,
+                            const double* __restrict__ loc, double* __restrict__ obase) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  const double* f = fbase + L.voff;
+  double* o = obase + L.voff;
+  for (int d = threadIdx.x; d < L.n; d += blockDim.x)
+    o[d] = d < L.nI ? f[d] : f[d] - loc[L.boff + d - L.nI];
+}
+
+inline int grid_for(long n, int threads = kThreads) {
+  long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 65535) b = 65535;
+  return (int)b;
+}
+
+}  // namespace
+
+int scatter_partials() { return kPartials; }
+
+void launch_elem_linear(int n_tets, const double* coords, const int32_t* tets, double E, double nu, double* Ke,
+                        int* status, cudaStream_t st) {
+  if (n_tets <= 0) return;
+  k_elem_linear<<<(n_tets + 127) / 128, 128, 0, st>>>(n_tets, coords, tets, E, nu, Ke, status);
+}
+
+void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, const double* U,
+                     const double* fibres, double c, double k1, double k2, double kappa, double* Ke, double* fe,
+                     int* status, cudaStream_t st) {
+  if (n_tets <= 0) return;
+  k_elem_hgo<<<(n_tets + 63) / 64, 64, 0, st>>>(n_tets, coords, tets, U, fibres, c, k1, k2, kappa, Ke, fe,
+                                                status);
+}
+
+void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                     const int32_t* elem_dense, const double* Ke, double* A, cudaStream_t st) {
+  k_assemble<<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
+}
+
+void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_ptr, const int32_t* face_dense,
+                         const double* face_force, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                         const int32_t* elem_dense, const double* elem_dirval, const double* Ke, const double* fe,
+                         double tau, double* f, cudaStream_t st) {
+  k_assemble_rhs<<<P, 128, 0, st>>>(lay, sub_face_ptr, face_dense, face_force, sub_elem_ptr, sub_elems,
+                                     elem_dense, elem_dirval, Ke, fe, tau, f);
+}
+
+void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, const double* U, int kind,
+                        double scale, const double* traction, double* out, cudaStream_t st) {
+  if (n_faces <= 0) return;
+  k_face_forces<<<(n_faces + 127) / 128, 128, 0, st>>>(n_faces, tri, coords, U, kind, scale, traction, out);
+}
+
+void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st) {
+  k_augment<<<P, kThreads, 0, st>>>(lay, A);
+}
+
+void launch_chol_partial(int P, const SubLayout* lay, int which, double* A, int* status, cudaStream_t st) {
+  k_chol_partial<<<P, kThreads, 0, st>>>(lay, which, A, status);
+}
+
+void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st) {
+  k_extract<<<P, kThreads, 0, st>>>(lay, which, A, out);
+}
+
+void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st) {
+  k_kplus<<<P, kThreads, 0, st>>>(lay, A, g, x);
+}
+
+void launch_gemv(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
+                 const double* M, const Maps& mp, const double* x, const double* wv, double* y, int max_m,
+                 const int* done, cudaStream_t st) {
+  const size_t smem = (size_t)max_m * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemv<<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which, M, mp, x, wv, y, done);
+}
+
+void launch_gather(const Maps& mp, const double* x, const double* wv, double* y, const int* done,
+                   cudaStream_t st) {
+  k_gather<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, x, wv, y, done);
+}
+
+void launch_scatter(const Maps& mp, const double* y, const double* wv, double* q, const double* a,
+                    double* partial, const int* done, cudaStream_t st) {
+  k_scatter<<<kPartials, kThreads, 0, st>>>(mp, y, wv, q, a, partial, done);
+}
+
+void launch_gtv(int P, const SubLayout* lay, const double* R, const Maps& mp, const double* x, double* g,
+                const int* done, cudaStream_t st) {
+  k_gtv<<<P, kThreads, 0, st>>>(lay, R, mp, x, g, done);
+}
+
+void launch_coarse_apply(int cd, const double* Ginv, const double* g, double* c, const int* done,
+                         cudaStream_t st) {
+  if (cd <= 0) return;
+  const int warps = cd < 2432 ? cd : 2432;
+  k_coarse_apply<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(cd, Ginv, g, c, done);
+}
+
+void launch_expand(const Maps& mp, const SubLayout* lay, const double* R, const double* v, const double* c,
+                   double* out, const double* a, double* partial, int with_dot, const int* done,
+                   cudaStream_t st) {
+  k_expand<<<kPartials, kThreads, 0, st>>>(mp, lay, R, v, c, out, a, partial, with_dot, done);
+}
+
+void launch_gtg(int n_blocks, const int32_t* blk_i, const int32_t* blk_j, const int32_t* blk_ptr,
+                const int32_t* blk_rows, const SubLayout* lay, const double* R, const Maps& mp, int cd,
+                double* GtG, cudaStream_t st) {
+  if (n_blocks <= 0) return;
+  k_gtg<<<n_blocks, 64, 0, st>>>(blk_i, blk_j, blk_ptr, blk_rows, lay, R, mp, cd, GtG);
+}
+
+void launch_ctl_rho(PcgScalars* s, const double* partial, double* beta_hist, cudaStream_t st) {
+  k_ctl_rho<<<1, kThreads, 0, st>>>(s, partial, beta_hist);
+}
+void launch_ctl_alpha(PcgScalars* s, const double* partial, double* alpha_hist, cudaStream_t st) {
+  k_ctl_alpha<<<1, kThreads, 0, st>>>(s, partial, alpha_hist);
+}
+void launch_ctl_conv(PcgScalars* s, const double* partial, int first, cudaStream_t st) {
+  k_ctl_conv<<<1, kThreads, 0, st>>>(s, partial, first);
+}
+void launch_axpby(int n, double* y, const double* x, const PcgScalars* s, int mode, cudaStream_t st) {
+  k_axpby<<<grid_for(n), kThreads, 0, st>>>(n, y, x, s, mode);
+}
+void launch_update_lr(int n, double* lam, double* r, const double* p, const double* q, const PcgScalars* s,
+                      cudaStream_t st) {
+  k_update_lr<<<grid_for(n), kThreads, 0, st>>>(n, lam, r, p, q, s);
+}
+void launch_vsub(int n, const double* a, const double* b, double* out, cudaStream_t st) {
+  k_vsub<<<grid_for(n), kThreads, 0, st>>>(n, a, b, out);
+}
+void launch_owner_scatter(int n_entries, const int32_t* gdof, const int32_t* vpos, const double* x, double* U,
+                          cudaStream_t st) {
+  if (n_entries <= 0) return;
+  k_owner_scatter<<<grid_for(n_entries), kThreads, 0, st>>>(n_entries, gdof, vpos, x, U);
+}
+void launch_add_kernel(int P, const SubLayout* lay, const double* R, const double* gamma, double* x,
+                       cudaStream_t st) {
+  k_add_kernel<<<P, kThreads, 0, st>>>(lay, R, gamma, x);
+}
+
+void launch_rtx(int P, const SubLayout* lay, const double* R, const double* x, double scale, double* e,
+                cudaStream_t st) {
+  k_rtx<<<P, kThreads, 0, st>>>(lay, R, x, scale, e);
+}
+void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st) {
+  k_take_boundary<<<P, kThreads, 0, st>>>(lay, x, loc);
+}
+void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
+                      cudaStream_t st) {
+  k_local_sub<<<P, kThreads, 0, st>>>(lay, f, loc, out);
+}
+
+}  // namespace feti
