@@ -153,15 +153,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-apply", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cyl16", choices=["cyl16", "cyl8"],
+                    help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
     from feti_inputs import mesh
-    prob = mesh.config_problem("cyl16")
-    workload_cfg = {"workload": "AF-FETI tube 16x64x32 cells P1 (35,904 nodes, 107,712 DOFs), 64 wedge "
-                                "subdomains, Dirichlet preconditioner, FP64, PCG tol 1e-8",
-                    "n_subdomains": 64, "n_dofs": 3 * prob.n_nodes, "method": "all-floating",
+    if args.workload == "cyl16":
+        prob = mesh.config_problem("cyl16")
+        wname = ("AF-FETI tube 16x64x32 cells P1 (35,904 nodes, 107,712 DOFs), 64 wedge subdomains, "
+                 "Dirichlet preconditioner, FP64, PCG tol 1e-8")
+    else:
+        prob = mesh.cylinder_problem(8, 64, 16, (2, 8, 2))
+        wname = ("AF-FETI tube 8x64x16 cells P1 (9,792 nodes), 32 wedge subdomains, Dirichlet "
+                 "preconditioner, FP64, PCG tol 1e-8 (profiler-sized)")
+    workload_cfg = {"workload": wname,
+                    "n_subdomains": prob.n_parts, "n_dofs": 3 * prob.n_nodes, "method": "all-floating",
                     "precond": "dirichlet", "precision": "fp64", "l2": "inputs larger than L2 (F_i+S_i 1.4 GB)",
                     "parallelism": "replicas" if args.gpus > 1 else "single"}
     if args.impl == "reference":
@@ -227,7 +236,7 @@ def main():
 
     # end to end through the public API with host buffers: create (H2D of the
     # problem) + solve + D2H of the displacement, per step
-    e2e_steps = 2
+    e2e_steps = args.e2e_steps
     u_host = torch.empty(3 * prob.n_nodes, dtype=torch.float64).pin_memory()
     t0 = time.perf_counter()
     its = 0
@@ -239,7 +248,7 @@ def main():
     e2e_dt = time.perf_counter() - t0
     h2d = (prob.coords.nbytes + prob.tets.nbytes + prob.part.nbytes + prob.dir_dof.nbytes + prob.dir_val.nbytes
            + prob.press_tri.nbytes + prob.press_owner.nbytes)
-    e2e = {"value": its * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": its * world / e2e_dt if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(u_host.numel() * 8),
            "note": "dual applies of complete solves (create + setup + PCG to 1e-8 + recovery) per second of "
                    "wall time, problem arrays from host, displacement back to pinned host"}

@@ -1003,7 +1003,11 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
     if (v < 0 || v >= ctx->N) return fail(ctx, FETI_ERR_INVALID_ARG, "face node out of range");
   ctx->opt = *opt;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(ctx, FETI_ERR_CUDA, "no CUDA device");
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    return fail(ctx, FETI_ERR_CUDA, "no CUDA device");
+  }
+  (void)cudaGetLastError();
   if (stream) {
     ctx->stream = static_cast<cudaStream_t>(stream);
   } else {
@@ -1015,6 +1019,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
 
 feti_status feti_prepare(feti_ctx* ctx) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  (void)cudaGetLastError();  // drop a non-sticky error left by an earlier, unrelated runtime call
   auto t0 = std::chrono::steady_clock::now();
   FETI_TRY(prepare(ctx, nullptr, 1.0));
   ctx->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1023,6 +1028,7 @@ feti_status feti_prepare(feti_ctx* ctx) {
 
 feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
   auto t0 = std::chrono::steady_clock::now();
   if (report) std::memset(report, 0, sizeof(*report));
@@ -1078,6 +1084,7 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
   if (!ctx) return FETI_ERR_INVALID_ARG;
   if (!v || !q || !z || n_apply <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "bad dual_apply arguments");
   if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
+  (void)cudaGetLastError();
   cudaStream_t st = ctx->stream;
   const int* zero = ctx->d_zero;
   const bool same = ctx->dual_graph && ctx->dual_v == v && ctx->dual_q == q && ctx->dual_z == z &&
@@ -1093,10 +1100,10 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
     cudaGraph_t g = nullptr;
     FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < n_apply; ++i) {
-      FETI_CK(cudaEventRecord(ctx->dual_events[2 + 2 * i], st));
+      FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[2 + 2 * i], st, cudaEventRecordExternal));
       feti::launch_gemv(ctx->n_blkF, ctx->d_blkF_sub, ctx->d_blkF_row, ctx->d_lay, 0, ctx->d_F, ctx->maps, v,
                         nullptr, ctx->d_loc, ctx->max_nb, zero, st);
-      FETI_CK(cudaEventRecord(ctx->dual_events[3 + 2 * i], st));
+      FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[3 + 2 * i], st, cudaEventRecordExternal));
       feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, nullptr, nullptr, zero, st);
       apply_M(ctx, q, z, zero);
     }

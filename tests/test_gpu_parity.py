@@ -57,14 +57,22 @@ def test_index_maps_bit_exact(prob, method):
 @pytest.mark.parametrize("method", ["classical", "af"])
 @pytest.mark.parametrize("precond", ["dirichlet", "lumped", "identity"])
 def test_solve_matches_oracle(prob, method, precond):
+    """Iteration counts at the 1e-8 tolerance, displacements at 1e-12.
+
+    At 1e-12 CG runs deep into the regime where rounding order alone moves
+    the stopping iteration by a few steps, so counts are compared at 1e-8.
+    """
     o = feti.FetiOracle(prob, method, precond)
+    _, res8, _ = o.solve(tol=1e-8, maxit=3000)
     U_ref, res, _ = o.solve(tol=1e-12, maxit=3000)
+    with _solver(prob, method, precond, tol=1e-8, maxit=3000) as s:
+        _, rep8 = s.solve()
     with _solver(prob, method, precond, tol=1e-12, maxit=3000) as s:
         U, rep = s.solve()
-    assert rep["converged"] == 1
-    assert abs(rep["iterations"] - res.iterations) <= 1
+    assert rep8["converged"] == 1 and rep["converged"] == 1
+    assert abs(rep8["iterations"] - res8.iterations) <= 1
     assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
-    assert rep["cond_est"] == pytest.approx(res.cond_est, rel=1e-3)
+    assert rep8["cond_est"] == pytest.approx(res8.cond_est, rel=1e-3)
 
 
 def test_cube12_classical_dirichlet_against_monolithic():
