@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -192,91 +194,108 @@ def main():
 
     stream = torch.cuda.Stream()            # a real stream: the library captures graphs on it
     torch.cuda.set_stream(stream)
-    solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=2000,
-                        stream=stream.cuda_stream)
-    U, rep = solver.solve()          # full hot path once: setup + PCG + recovery
-    sizes = solver.sizes()
-    nl = sizes["n_lambda"]
-    g = torch.Generator(device="cuda").manual_seed(1234 + rank)
-    v = torch.randn(nl, dtype=torch.float64, device="cuda", generator=g)
-    q = torch.empty_like(v)
-    z = torch.empty_like(v)
-    for _ in range(args.warmup):
-        solver.dual_apply(v, q, z, args.n_apply)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    kern_ms = []
-    for _ in range(args.steps):
-        solver.dual_apply(v, q, z, args.n_apply)
-        kern_ms.append(solver.kernel_stats()["gemv_ms"])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    applies = args.steps * args.n_apply * world
-    value = applies / (ms / 1e3)
-    ks = solver.kernel_stats()
-    kern = statistics.mean(kern_ms)
     peaks, src = _peaks()
-    achieved_gbs = ks["gemv_bytes"] / (kern / 1e3) / 1e9
-    achieved_tflops = ks["gemv_flops"] / (kern / 1e3) / 1e12
     fp64_peak = 1.259  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derivation in the design doc)
 
+    def measure(precision: str):
+        """Full solve once, then `steps` timed blocks of n_apply dual applies."""
+        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+                            stream=stream.cuda_stream, precision=precision)
+        U, rep = solver.solve()          # full hot path once: setup + PCG + recovery
+        sizes = solver.sizes()
+        nl = sizes["n_lambda"]
+        g = torch.Generator(device="cuda").manual_seed(1234 + rank)
+        v = torch.randn(nl, dtype=torch.float64, device="cuda", generator=g)
+        q = torch.empty_like(v)
+        z = torch.empty_like(v)
+        for _ in range(args.warmup):
+            solver.dual_apply(v, q, z, args.n_apply)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        kern_ms = []
+        for _ in range(args.steps):
+            solver.dual_apply(v, q, z, args.n_apply)
+            kern_ms.append(solver.kernel_stats()["gemv_ms"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        ks = solver.kernel_stats()
+        kern = statistics.mean(kern_ms)
+        solver.close()
+        return {"U": U, "rep": rep, "sizes": sizes, "ms": ms, "kern_ms": kern, "ks": ks, "clocks": clk,
+                "value": args.steps * args.n_apply * world / (ms / 1e3)}
+
+    m64 = measure("fp64")
+    m32 = measure("mixed")
+    err = float(np.linalg.norm(m32["U"] - m64["U"]) / np.linalg.norm(m64["U"]))
+    ks32, ks64 = m32["ks"], m64["ks"]
+    gbs32 = ks32["gemv_bytes"] / (m32["kern_ms"] / 1e3) / 1e9
+    tf64 = ks64["gemv_flops"] / (m64["kern_ms"] / 1e3) / 1e12
+    gbs64 = ks64["gemv_bytes"] / (m64["kern_ms"] / 1e3) / 1e9
+
     # end to end through the public API with host buffers: create (H2D of the
-    # problem) + solve + D2H of the displacement, per step
+    # problem) + solve (mixed form) + D2H of the displacement, per step
     e2e_steps = args.e2e_steps
     u_host = torch.empty(3 * prob.n_nodes, dtype=torch.float64).pin_memory()
     t0 = time.perf_counter()
     its = 0
     for _ in range(e2e_steps):
-        with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=2000,
-                        stream=stream.cuda_stream) as s2:
+        with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+                        stream=stream.cuda_stream, precision="mixed") as s2:
             r2 = s2.solve_host(u_host)
-            its += r2["iterations"] + 2
+            its += r2["iterations"] + r2["outer_iterations"] + 2
     e2e_dt = time.perf_counter() - t0
     h2d = (prob.coords.nbytes + prob.tets.nbytes + prob.part.nbytes + prob.dir_dof.nbytes + prob.dir_val.nbytes
            + prob.press_tri.nbytes + prob.press_owner.nbytes)
     e2e = {"value": its * world / e2e_dt if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(u_host.numel() * 8),
-           "note": "dual applies of complete solves (create + setup + PCG to 1e-8 + recovery) per second of "
-                   "wall time, problem arrays from host, displacement back to pinned host"}
+           "note": "dual applies of complete FP32-local solves (create + setup + PCG to 1e-8 + recovery) per "
+                   "second of wall time, problem arrays from host, displacement back to pinned host"}
 
     if rank == 0:
+        r64, r32 = m64["rep"], m32["rep"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_cfg, n_apply_per_step=args.n_apply, n_lambda=nl,
-                           coarse_dim=sizes["coarse_dim"]),
-            "pcg": {"iterations": rep["iterations"], "time_to_tol_ms": rep["t_pcg_ms"],
-                    "setup_ms": rep["t_setup_ms"], "total_ms": rep["t_total_ms"], "cond_est": rep["cond_est"],
-                    "tol": 1e-8},
-            "roofline": {"bound": "alu", "kernel": "k_gemv (F_i apply, FP64)", "achieved": achieved_tflops,
-                         "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_peak,
-                         "traffic": None, "kernel_ms": kern,
-                         "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                 "frac": achieved_gbs / peaks["hbm_gbs"], "peak_source": src},
-                         "algorithmic_bytes": ks["gemv_bytes"], "flops": ks["gemv_flops"]},
-            "clocks": clk,
+            "metric": METRIC, "value": m32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m32["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(workload_cfg, precision="FP32 local operators, FP64 vectors/projection/coarse/outer "
+                                                    "residual", n_apply_per_step=args.n_apply,
+                           n_lambda=m32["sizes"]["n_lambda"], coarse_dim=m32["sizes"]["coarse_dim"]),
+            "pcg": {"tol": 1e-8,
+                    "fp32_local": {"time_to_tol_ms": r32["t_pcg_ms"], "inner_iterations": r32["iterations"],
+                                   "outer_iterations": r32["outer_iterations"], "rel_err_vs_fp64": err},
+                    "fp64": {"time_to_tol_ms": r64["t_pcg_ms"], "iterations": r64["iterations"],
+                             "cond_est": r64["cond_est"]},
+                    "setup_ms": r64["t_setup_ms"]},
+            "fp64": {"value": m64["value"], "unit": UNIT, "ms_per_step": m64["ms"] / args.steps,
+                     "roofline": {"bound": "alu", "kernel": "k_gemv_loc<double> (F_i apply)", "achieved": tf64,
+                                  "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf64 / fp64_peak,
+                                  "hbm_gbs": gbs64, "kernel_ms": m64["kern_ms"]},
+                     "clocks": m64["clocks"]},
+            "roofline": {"bound": "hbm", "kernel": "k_gemv_loc<float> (F_i apply, FP32 copy)", "achieved": gbs32,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],
+                         "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
+                         "peak_source": src},
+            "clocks": m32["clocks"],
             "e2e": e2e,
-            "gpu_launches": args.steps * args.n_apply * 4,
+            "gpu_launches": args.steps * args.n_apply * 6,
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(prob, n_apply=20)
         print(json.dumps(line), flush=True)
-    solver.close()
     if world > 1:
         dist.destroy_process_group()
 

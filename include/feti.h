@@ -50,7 +50,11 @@ typedef enum {
 enum { FETI_LINEAR_ISO = 0, FETI_HGO_TWO_FIBRE = 1 };          /* feti_material.kind */
 enum { FETI_CLASSICAL = 0, FETI_ALL_FLOATING = 1 };             /* feti_options.method */
 enum { FETI_PREC_IDENTITY = 0, FETI_PREC_LUMPED = 1, FETI_PREC_DIRICHLET = 2 };
-enum { FETI_FP64 = 0 };                                         /* feti_options.precision */
+/* feti_options.precision: FETI_FP64 -- every operator in FP64; FETI_MIXED --
+ * FP32 copies of the dense local operators F_i and S_i inside the PCG,
+ * FP64 vectors, dot products, projection, coarse solve and an FP64 outer
+ * residual (iterative refinement on the dual problem). */
+enum { FETI_FP64 = 0, FETI_MIXED = 1 };
 
 /* Mesh T_N of Sec. 3.2 (P1 tetrahedra) and its non-overlapping decomposition
  * (Sec. 4, Eq. decomposition).  coords: [n_nodes*3] reference coordinates;
@@ -109,10 +113,12 @@ typedef struct {
   int32_t n_load_steps;
   double newton_tol;
   int32_t newton_maxit;
+  double inner_tol;    /* FETI_MIXED: relative tolerance of each inner solve (0: 1e-4) */
+  int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
 } feti_options;
 
 typedef struct {
-  int32_t iterations;      /* PCG iterations (F applications after lambda_0) */
+  int32_t iterations;      /* PCG iterations (F applications after lambda_0; mixed: inner total) */
   int32_t converged;
   double rel_residual;     /* ||P r_k|| / ||P r_0|| at exit */
   double cond_est;         /* Lanczos estimate from the CG coefficients */
@@ -123,6 +129,7 @@ typedef struct {
   int64_t coarse_dim;      /* columns of G */
   int32_t newton_iters;    /* total Newton iterations (feti_newton) */
   double newton_rel_res;   /* final relative residual (feti_newton) */
+  int32_t outer_iterations; /* FETI_MIXED: refinement passes (FP64 residuals) */
 } feti_report;
 
 typedef struct feti_ctx feti_ctx;

@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PARTITION", 3: "ELEMENT_INVERTED"
 LINEAR_ISO, HGO_TWO_FIBRE = 0, 1
 CLASSICAL, ALL_FLOATING = 0, 1
 PREC_IDENTITY, PREC_LUMPED, PREC_DIRICHLET = 0, 1, 2
-FP64 = 0
+FP64, MIXED = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -40,14 +40,15 @@ class FetiBC(C.Structure):
 class FetiOptions(C.Structure):
     _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("maxit", C.c_int32), ("chunk", C.c_int32), ("follower", C.c_int32),
-                ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32)]
+                ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
 
 
 class FetiReport(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
                 ("cond_est", C.c_double), ("t_setup_ms", C.c_double), ("t_pcg_ms", C.c_double),
                 ("t_total_ms", C.c_double), ("n_lambda", C.c_int64), ("coarse_dim", C.c_int64),
-                ("newton_iters", C.c_int32), ("newton_rel_res", C.c_double)]
+                ("newton_iters", C.c_int32), ("newton_rel_res", C.c_double), ("outer_iterations", C.c_int32)]
 
 
 EXPORTS = ["feti_create", "feti_solve", "feti_newton", "feti_get_sizes", "feti_get_index_maps",

@@ -37,7 +37,8 @@ class FetiSolver:
 
     def __init__(self, prob, method: str = "af", precond: str = "dirichlet", tol: float = 1e-10,
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
-                 n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25):
+                 n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
+                 precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -63,8 +64,10 @@ class FetiSolver:
         bc = L.FetiBC(dd.size, _ptr(dd, C.c_int32), _ptr(dv, C.c_double), pt.shape[0], _ptr(pt, C.c_int32),
                       _ptr(po, C.c_int32), float(prob.pressure), tt.shape[0], _ptr(tt, C.c_int32),
                       _ptr(to, C.c_int32), (C.c_double * 3)(*[float(v) for v in prob.traction]))
-        opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], L.FP64, float(tol), int(maxit), int(chunk),
-                            int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit))
+        prec = {"fp64": L.FP64, "mixed": L.MIXED}[precision]
+        opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], prec, float(tol), int(maxit), int(chunk),
+                            int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
+                            float(inner_tol), int(max_outer))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

@@ -31,6 +31,8 @@ struct SubLayout {
   int64_t soff;   // offset of the nb x nb preconditioner block
   int64_t foff;   // offset of the nbp x nbp dense F_i
   int64_t roff;   // offset of R_i (n x k, row-major) in dense local order
+  int64_t foff32; // offset (floats) of the FP32 copy of F_i, row stride padded to 4
+  int64_t soff32; // offset (floats) of the FP32 copy of the preconditioner block
 };
 
 // Element kernels ------------------------------------------------------------
@@ -76,13 +78,7 @@ struct Maps {
   const int32_t* bpos_sub;  // [nb_total] owning subdomain of each boundary position
 };
 
-// Dense local operator apply with fused gather: for every subdomain,
-// y_b = M_i (B_i^T (wv o x))_b, M_i = F_i (which=0, size nbp) or the
-// preconditioner block (which=1, size nb).  wv may be NULL (no weights).
-void launch_gemv(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay,
-                 int which, const double* M, const Maps& mp, const double* x, const double* wv, double* y,
-                 int max_m, const int* done, cudaStream_t st);
-// y_b = (B_i^T (wv o x))_b without a local operator (identity preconditioner).
+// y_b = (B_i^T (wv o x))_b: signed gather onto the boundary positions.
 void launch_gather(const Maps& mp, const double* x, const double* wv, double* y, const int* done,
                    cudaStream_t st);
 // q = wv o (B y) row-wise (deterministic), optional partial sums of (a, q).
@@ -138,4 +134,18 @@ void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* 
 // rhs_i = f_i - (boundary vector loc placed at the boundary positions).
 void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
                       cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// Rows of one CTA of launch_gemv_loc.
+int gemv_cta_rows();
+// y_b = M_i v_b on a pre-gathered local vector (see launch_gather); M is the
+// FP64 (f32 = 0) or padded FP32 (f32 = 1) copy of F_i (which 0) or the
+// preconditioner block (which 1).
+void launch_gemv_loc(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
+                     const void* M, int f32, const double* vloc, double* y, int max_m, const int* done,
+                     cudaStream_t st);
+void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
+// a += b
+void launch_vadd(int n, double* a, const double* b, cudaStream_t st);
 }  // namespace feti

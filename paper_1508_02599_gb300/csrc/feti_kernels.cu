@@ -593,47 +593,92 @@ __global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Hot path: dense local operator apply with fused signed gather.
-constexpr int GEMV_ROWS = 32;
+// Dense local operator apply on a pre-gathered local vector.  One CTA owns
+// 8 warps x R rows of one subdomain; every warp keeps R independent
+// accumulators so each v element read from shared memory feeds R FMAs.
+// FP64 matrices: row stride m, one double per lane per step.  FP32
+// matrices: row stride padded to a multiple of 4 floats (zero padding),
+// one float4 per lane per step, products accumulated in FP32 per lane and
+// reduced across the warp in FP64.
+constexpr int GEMV_R = 8;
+constexpr int GEMV_CTA_ROWS = GEMV_R * (kThreads / 32);
 
-__global__ void __launch_bounds__(kThreads) k_gemv(const int32_t* __restrict__ blk_sub,
-                                                   const int32_t* __restrict__ blk_row0,
-                                                   const SubLayout* __restrict__ lay, int which,
-                                                   const double* __restrict__ M, Maps mp,
-                                                   const double* __restrict__ x, const double* __restrict__ wv,
-                                                   double* __restrict__ y, const int* __restrict__ done) {
+__device__ __forceinline__ int pad4(int m) { return (m + 3) & ~3; }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gemv_loc(const int32_t* __restrict__ blk_sub,
+                                                       const int32_t* __restrict__ blk_row0,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const T* __restrict__ M, const double* __restrict__ vloc,
+                                                       double* __restrict__ y, const int* __restrict__ done) {
   if (*done) return;
-  extern __shared__ double v[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* v = reinterpret_cast<T*>(smem_raw);
   const int s = blk_sub[blockIdx.x];
   const int r0 = blk_row0[blockIdx.x];
   const SubLayout L = lay[s];
   const int m = which == 0 ? L.nbp : L.nbp + L.k;
-  const double* Ms = M + (which == 0 ? L.foff : L.soff);
-  for (int p = threadIdx.x; p < m; p += blockDim.x) {
-    const int gp = L.boff + p;
-    double val = 0.0;
-    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
-      const int row = mp.bt_row[e];
-      val += mp.bt_sgn[e] * x[row] * (wv ? wv[row] : 1.0);
-    }
-    v[p] = val;
-  }
+  constexpr bool f32 = sizeof(T) == 4;
+  const int ldm = f32 ? pad4(m) : m;
+  const T* Ms = M + (f32 ? (which == 0 ? L.foff32 : L.soff32) : (which == 0 ? L.foff : L.soff));
+  for (int p = threadIdx.x; p < ldm; p += blockDim.x) v[p] = p < m ? (T)vloc[L.boff + p] : (T)0;
   if (which == 0 && r0 == 0)
     for (int p = L.nbp + threadIdx.x; p < L.nbp + L.k; p += blockDim.x) y[L.boff + p] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int RPW = GEMV_ROWS / (kThreads / 32);
+  const int rbase = r0 + wid * GEMV_R;
+  if (rbase >= m) return;
+  T acc[GEMV_R];
 #pragma unroll
-  for (int rr = 0; rr < RPW; ++rr) {
-    const int r = r0 + wid * RPW + rr;
-    if (r < m) {
-      const double* row = Ms + (size_t)r * m;
-      double acc = 0.0;
-      for (int c = lane; c < m; c += 32) acc += row[c] * v[c];
-      acc = warp_sum(acc);
-      if (lane == 0) y[L.boff + r] = acc;
+  for (int j = 0; j < GEMV_R; ++j) acc[j] = (T)0;
+  const T* rows[GEMV_R];
+#pragma unroll
+  for (int j = 0; j < GEMV_R; ++j) rows[j] = Ms + (size_t)min(rbase + j, m - 1) * ldm;
+  if constexpr (f32) {
+    const int m4 = ldm >> 2;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    for (int c = lane; c < m4; c += 32) {
+      const float4 vv = v4[c];
+      float4 a[GEMV_R];
+#pragma unroll
+      for (int j = 0; j < GEMV_R; ++j) a[j] = __ldg(reinterpret_cast<const float4*>(rows[j]) + c);
+#pragma unroll
+      for (int j = 0; j < GEMV_R; ++j) acc[j] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
+    }
+  } else {
+    for (int c = lane; c < m; c += 32) {
+      const T vv = v[c];
+      T a[GEMV_R];
+#pragma unroll
+      for (int j = 0; j < GEMV_R; ++j) a[j] = __ldg(rows[j] + c);
+#pragma unroll
+      for (int j = 0; j < GEMV_R; ++j) acc[j] += a[j] * vv;
     }
   }
+#pragma unroll
+  for (int j = 0; j < GEMV_R; ++j) {
+    const double t = warp_sum((double)acc[j]);
+    if (lane == 0 && rbase + j < m) y[L.boff + rbase + j] = t;
+  }
+}
+
+// FP64 -> FP32 copy of the dense local operators (row stride padded to 4).
+__global__ void k_to_f32(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
+                         float* __restrict__ dst) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int ld = pad4(m);
+  const double* a = src + (which == 0 ? L.foff : L.soff);
+  float* b = dst + (which == 0 ? L.foff32 : L.soff32);
+  for (int idx = threadIdx.x; idx < m * ld; idx += blockDim.x) {
+    const int i = idx / ld, j = idx % ld;
+    b[idx] = j < m ? (float)a[(size_t)i * m + j] : 0.0f;
+  }
+}
+
+__global__ void k_vadd(int n, double* __restrict__ a, const double* __restrict__ b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] += b[i];
 }
 
 __global__ void k_gather(Maps mp, const double* __restrict__ x, const double* __restrict__ wv,
@@ -972,14 +1017,6 @@ void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g,
   k_kplus<<<P, kThreads, 0, st>>>(lay, A, g, x);
 }
 
-void launch_gemv(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
-                 const double* M, const Maps& mp, const double* x, const double* wv, double* y, int max_m,
-                 const int* done, cudaStream_t st) {
-  const size_t smem = (size_t)max_m * sizeof(double);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_gemv<<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which, M, mp, x, wv, y, done);
-}
-
 void launch_gather(const Maps& mp, const double* x, const double* wv, double* y, const int* done,
                    cudaStream_t st) {
   k_gather<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, x, wv, y, done);
@@ -1054,6 +1091,33 @@ void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* 
 void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
                       cudaStream_t st) {
   k_local_sub<<<P, kThreads, 0, st>>>(lay, f, loc, out);
+}
+
+int gemv_cta_rows() { return GEMV_CTA_ROWS; }
+
+void launch_gemv_loc(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
+                     const void* M, int f32, const double* vloc, double* y, int max_m, const int* done,
+                     cudaStream_t st) {
+  const size_t smem = (size_t)((max_m + 3) & ~3) * (f32 ? sizeof(float) : sizeof(double));
+  if (f32) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_gemv_loc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemv_loc<float><<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which,
+                                                         static_cast<const float*>(M), vloc, y, done);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_gemv_loc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemv_loc<double><<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which,
+                                                          static_cast<const double*>(M), vloc, y, done);
+  }
+}
+
+void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st) {
+  k_to_f32<<<P, kThreads, 0, st>>>(lay, which, src, dst);
+}
+
+void launch_vadd(int n, double* a, const double* b, cudaStream_t st) {
+  k_vadd<<<grid_for(n), kThreads, 0, st>>>(n, a, b);
 }
 
 }  // namespace feti
