@@ -152,6 +152,17 @@ feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_r
  * Requires FETI_HGO_TWO_FIBRE.  Writes U [n_nodes*3] like feti_solve. */
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report);
 
+/* Element level of Sec. 3.2 (Eq. Tangent and the residual K(U)): for every
+ * tetrahedron the 12x12 tangent K_e (row-major, local DOF 3 * vertex +
+ * component, vertices in tets order) into Ke_out [n_tets*144], and for the
+ * hyperelastic material the internal force f_e = V (F S grad N_a) into
+ * fe_out [n_tets*12] (may be NULL; unused for LINEAR_ISO), at the
+ * displacement U [n_nodes*3] (NULL = zero).  U and the outputs are host or
+ * device pointers as u_on_device / out_on_device say.  Fails with
+ * FETI_ERR_ELEMENT_INVERTED if det F <= 0 anywhere. */
+feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, double* Ke_out, double* fe_out,
+                          int32_t out_on_device);
+
 /* Sizes of the decomposition: out[0] n_lambda, out[1] coarse_dim, out[2]
  * sum of local DOFs, out[3] sum of boundary DOFs, out[4] n_parts. */
 feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]);

@@ -51,7 +51,7 @@ class FetiReport(C.Structure):
                 ("newton_iters", C.c_int32), ("newton_rel_res", C.c_double), ("outer_iterations", C.c_int32)]
 
 
-EXPORTS = ["feti_create", "feti_solve", "feti_newton", "feti_get_sizes", "feti_get_index_maps",
+EXPORTS = ["feti_create", "feti_solve", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
            "feti_get_fixing", "feti_dual_apply", "feti_prepare", "feti_kernel_stats", "feti_last_error",
            "feti_destroy"]
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.feti_solve.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_newton.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.feti_elements.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32]
     lib.feti_get_index_maps.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.feti_get_fixing.argtypes = [vp, vp, vp]
     lib.feti_dual_apply.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]

@@ -47,6 +47,7 @@ class FetiSolver:
         tets = np.ascontiguousarray(prob.tets, dtype=np.int32); keep(tets)
         part = np.ascontiguousarray(prob.part, dtype=np.int32); keep(part)
         self.n_nodes = coords.shape[0]
+        self._n_tets = tets.shape[0]
         mesh = L.FetiMesh(coords.shape[0], _ptr(coords, C.c_double), tets.shape[0], _ptr(tets, C.c_int32),
                           _ptr(part, C.c_int32), int(prob.n_parts))
         m = prob.material
@@ -119,6 +120,16 @@ class FetiSolver:
         ld = np.empty(max(int(ptr[-1]), 1), np.int32)
         self._check(self._lib.feti_get_fixing(self._ctx, None, ld.ctypes.data))
         return [ld[ptr[s]:ptr[s + 1]].copy() for s in range(P)]
+
+    def elements(self, U=None, n_tets: int | None = None):
+        """Element tangents [E,12,12] and internal forces [E,12] (hyperelastic) at U (host arrays)."""
+        E = n_tets if n_tets is not None else self._n_tets
+        Ke = np.empty((E, 12, 12), np.float64)
+        fe = np.empty((E, 12), np.float64)
+        Uc = None if U is None else np.ascontiguousarray(U, dtype=np.float64).ravel()
+        self._check(self._lib.feti_elements(self._ctx, None if Uc is None else Uc.ctypes.data, 0, Ke.ctypes.data,
+                                            fe.ctypes.data, 0))
+        return Ke, fe
 
     def prepare(self):
         self._check(self._lib.feti_prepare(self._ctx))

@@ -78,6 +78,9 @@ struct feti_ctx {
   double *d_row_sgn = nullptr, *d_weight = nullptr, *d_bt_sgn = nullptr, *d_b = nullptr;
   int32_t *d_blkF_sub = nullptr, *d_blkF_row = nullptr, *d_blkS_sub = nullptr, *d_blkS_row = nullptr;
   int n_blkF = 0, n_blkS = 0;
+  int32_t *d_chunk_sub = nullptr, *d_chunk_p0 = nullptr, *d_sub_chunk_ptr = nullptr, *d_col_sub = nullptr;
+  double* d_gpart = nullptr;
+  int n_chunks = 0;
   int32_t *d_gtg_i = nullptr, *d_gtg_j = nullptr, *d_gtg_ptr = nullptr, *d_gtg_rows = nullptr;
   int n_gtg = 0;
   double *d_GtG = nullptr, *d_Ginv = nullptr, *d_Acoarse = nullptr;
@@ -602,6 +605,16 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   ctx->n_blkF = (int)bFs.size();
   ctx->n_blkS = (int)bSs.size();
+  // chunks of 256 boundary positions for the projection's G^T v
+  std::vector<int32_t> chunk_sub, chunk_p0, sub_chunk_ptr(P + 1, 0), col_sub(std::max<int64_t>(ctx->cd, 1), 0);
+  for (int s = 0; s < P; ++s) {
+    const SubLayout& L = ctx->lay[s];
+    if (L.k > 0)
+      for (int p0 = 0; p0 < L.nbp + L.k; p0 += 256) { chunk_sub.push_back(s); chunk_p0.push_back(p0); }
+    sub_chunk_ptr[s + 1] = (int32_t)chunk_sub.size();
+    for (int a = 0; a < L.k; ++a) col_sub[L.coff + a] = s;
+  }
+  ctx->n_chunks = (int)chunk_sub.size();
   std::vector<double> Rall(roff);
   for (int s = 0; s < P; ++s) std::copy(Rd[s].begin(), Rd[s].end(), Rall.begin() + ctx->lay[s].roff);
 
@@ -633,6 +646,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_blkF_row, bFr));
   FETI_TRY(upload(ctx, &ctx->d_blkS_sub, bSs));
   FETI_TRY(upload(ctx, &ctx->d_blkS_row, bSr));
+  FETI_TRY(upload(ctx, &ctx->d_chunk_sub, chunk_sub));
+  FETI_TRY(upload(ctx, &ctx->d_chunk_p0, chunk_p0));
+  FETI_TRY(upload(ctx, &ctx->d_sub_chunk_ptr, sub_chunk_ptr));
+  FETI_TRY(upload(ctx, &ctx->d_col_sub, col_sub));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_gpart, 6 * (size_t)std::max(ctx->n_chunks, 1)));
   FETI_TRY(upload(ctx, &ctx->d_gtg_i, gi));
   FETI_TRY(upload(ctx, &ctx->d_gtg_j, gj));
   FETI_TRY(upload(ctx, &ctx->d_gtg_ptr, gptr));
@@ -795,8 +813,10 @@ void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool 
     feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, ctx->d_partial, with_dot, done, st);
     return;
   }
-  feti::launch_gtv(ctx->P, ctx->d_lay, ctx->d_R, ctx->maps, v, ctx->d_g, done, st);
-  feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, ctx->d_g, ctx->d_c, done, st);
+  feti::launch_gtv_part(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_lay, ctx->d_R, ctx->maps, v,
+                        ctx->d_gpart, done, st);
+  feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
+                                 ctx->d_lay, ctx->d_c, done, st);
   feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, ctx->d_partial, with_dot, done, st);
 }
 
@@ -1130,6 +1150,35 @@ feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_r
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
   return fail(ctx, FETI_ERR_STATE, "feti_newton is not available in this build");
+}
+
+feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, double* Ke_out, double* fe_out,
+                          int32_t out_on_device) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  if (!Ke_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null Ke_out");
+  (void)cudaGetLastError();
+  cudaStream_t st = ctx->stream;
+  const bool hgo = ctx->mat.kind == FETI_HGO_TWO_FIBRE;
+  const size_t n3 = 3 * (size_t)ctx->N;
+  if (hgo && !ctx->d_U) FETI_TRY(dev_alloc(ctx, &ctx->d_U, n3));
+  const double* dU = nullptr;
+  if (hgo && U) {
+    FETI_CK(cudaMemcpyAsync(ctx->d_U, U, n3 * sizeof(double), u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    dU = ctx->d_U;
+  }
+  FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  if (hgo)
+    feti::launch_elem_hgo(ctx->E, ctx->d_coords, ctx->d_tets, dU, ctx->d_fibres, ctx->mat.c, ctx->mat.k1, ctx->mat.k2,
+                          ctx->mat.kappa, ctx->d_Ke, ctx->d_fe, ctx->d_status, st);
+  else
+    feti::launch_elem_linear(ctx->E, ctx->d_coords, ctx->d_tets, ctx->mat.E, ctx->mat.nu, ctx->d_Ke, ctx->d_status, st);
+  FETI_CK(cudaGetLastError());
+  FETI_TRY(check_status(ctx, "element matrices"));
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  FETI_CK(cudaMemcpyAsync(Ke_out, ctx->d_Ke, 144 * (size_t)ctx->E * sizeof(double), kind, st));
+  if (fe_out && hgo) FETI_CK(cudaMemcpyAsync(fe_out, ctx->d_fe, 12 * (size_t)ctx->E * sizeof(double), kind, st));
+  FETI_CK(cudaStreamSynchronize(st));
+  return FETI_OK;
 }
 
 feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]) {

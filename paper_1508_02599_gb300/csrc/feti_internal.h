@@ -149,3 +149,15 @@ void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, fl
 // a += b
 void launch_vadd(int n, double* a, const double* b, cudaStream_t st);
 }  // namespace feti
+
+namespace feti {
+// G^T x over chunks of 256 boundary positions of the subdomains with k > 0:
+// partial[6 c + a] for chunk c.
+void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const SubLayout* lay,
+                     const double* R, const Maps& mp, const double* x, double* partial, const int* done,
+                     cudaStream_t st);
+// c = Ginv (sum of chunk partials per coarse column).
+void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial, const int32_t* sub_chunk_ptr,
+                              const int32_t* col_sub, const SubLayout* lay, double* c, const int* done,
+                              cudaStream_t st);
+}  // namespace feti

@@ -741,6 +741,61 @@ __global__ void __launch_bounds__(kThreads) k_gtv(const SubLayout* __restrict__ 
   }
 }
 
+// G^T x split over chunks of 256 boundary positions (many CTAs per
+// subdomain): partial[c*6 + a] = sum over the chunk of R_b[p][a] (B^T x)[p].
+__global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict__ chunk_sub,
+                                                       const int32_t* __restrict__ chunk_p0,
+                                                       const SubLayout* __restrict__ lay,
+                                                       const double* __restrict__ R, Maps mp,
+                                                       const double* __restrict__ x, double* __restrict__ partial,
+                                                       const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const SubLayout L = lay[chunk_sub[c]];
+  const int nb = L.nbp + L.k;
+  const int p = chunk_p0[c] + threadIdx.x;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (p < nb) {
+    const int gp = L.boff + p;
+    double val = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) val += mp.bt_sgn[e] * x[mp.bt_row[e]];
+    const double* Rr = R + L.roff + (size_t)(L.nI + p) * L.k;
+    for (int a = 0; a < L.k; ++a) acc[a] = Rr[a] * val;
+  }
+  for (int a = 0; a < L.k; ++a) {
+    const double t = block_sum(acc[a], red);
+    if (threadIdx.x == 0) partial[6 * c + a] = t;
+  }
+}
+
+// c = Ginv g where g is first summed (fixed order) from the chunk partials of
+// k_gtv_part into shared memory by every CTA.
+__global__ void k_coarse_apply_part(int cd, const double* __restrict__ Ginv, const double* __restrict__ partial,
+                                    const int32_t* __restrict__ sub_chunk_ptr, const int32_t* __restrict__ col_sub,
+                                    const SubLayout* __restrict__ lay, double* __restrict__ c,
+                                    const int* __restrict__ done) {
+  if (*done) return;
+  extern __shared__ double gsh[];
+  for (int j = threadIdx.x; j < cd; j += blockDim.x) {
+    const int s = col_sub[j];
+    const int a = j - lay[s].coff;
+    double t = 0.0;
+    for (int q = sub_chunk_ptr[s]; q < sub_chunk_ptr[s + 1]; ++q) t += partial[6 * q + a];
+    gsh[j] = t;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < cd; r += nwarps) {
+    double acc = 0.0;
+    for (int j = lane; j < cd; j += 32) acc += Ginv[(size_t)r * cd + j] * gsh[j];
+    acc = warp_sum(acc);
+    if (lane == 0) c[r] = acc;
+  }
+}
+
 __global__ void k_coarse_apply(int cd, const double* __restrict__ Ginv, const double* __restrict__ g,
                                double* __restrict__ c, const int* __restrict__ done) {
   if (*done) return;
@@ -1118,6 +1173,26 @@ void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, fl
 
 void launch_vadd(int n, double* a, const double* b, cudaStream_t st) {
   k_vadd<<<grid_for(n), kThreads, 0, st>>>(n, a, b);
+}
+
+void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const SubLayout* lay,
+                     const double* R, const Maps& mp, const double* x, double* partial, const int* done,
+                     cudaStream_t st) {
+  if (n_chunks <= 0) return;
+  k_gtv_part<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, x, partial, done);
+}
+
+void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial, const int32_t* sub_chunk_ptr,
+                              const int32_t* col_sub, const SubLayout* lay, double* c, const int* done,
+                              cudaStream_t st) {
+  if (cd <= 0) return;
+  const size_t smem = (size_t)cd * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_coarse_apply_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int warps = cd < 2432 ? cd : 2432;
+  k_coarse_apply_part<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, smem, st>>>(cd, Ginv, partial,
+                                                                                        sub_chunk_ptr, col_sub, lay,
+                                                                                        c, done);
 }
 
 }  // namespace feti

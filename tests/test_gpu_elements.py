@@ -1,0 +1,58 @@
+"""GPU element kernels (linear and two-fibre hyperelastic) against the oracle, element by element.
+
+Tolerance: 1e-10 relative to the element's largest entry.  Both sides are
+FP64; the oracle's elasticity tensor is a complex-step derivative of its
+stress formula, the kernel's is written out analytically, so agreement
+beyond rounding pins the derivation.
+"""
+import numpy as np
+import pytest
+
+from feti_inputs import mesh
+from oracle import fem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _rel(a, b):
+    scale = np.abs(b).reshape(b.shape[0], -1).max(axis=1)
+    return (np.abs(a - b).reshape(a.shape[0], -1).max(axis=1) / scale).max()
+
+
+def test_linear_elements_match():
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = mesh.cylinder_problem(2, 16, 4, (1, 2, 1))
+    Ke_ref, _ = fem.element_matrices(prob)
+    with FetiSolver(prob) as s:
+        Ke, _ = s.elements()
+    assert _rel(Ke, Ke_ref) <= 1e-12
+
+
+@pytest.mark.parametrize("amp", [0.0, 0.02, 0.08])
+def test_hgo_elements_match(amp):
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = mesh.cylinder_problem(2, 16, 4, (1, 2, 1), material=mesh.hgo_material(), pressure=0.1)
+    rng = np.random.default_rng(17)
+    x = prob.coords
+    # smooth inflation plus noise: both fibre families active in most elements,
+    # compressed in some
+    r = np.hypot(x[:, 0], x[:, 1])[:, None]
+    U = amp * (np.concatenate([x[:, :2] / r, np.zeros((x.shape[0], 1))], axis=1) + 0.5 * rng.normal(size=x.shape))
+    Ke_ref, fe_ref = fem.element_matrices(prob, U)
+    with FetiSolver(prob, method="classical") as s:
+        Ke, fe = s.elements(U)
+    assert _rel(Ke, Ke_ref) <= 1e-10
+    assert np.abs(Ke - Ke.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(Ke).max()
+    if amp > 0:
+        assert _rel(fe, fe_ref) <= 1e-10
+    else:
+        assert np.abs(fe).max() <= 1e-12 * np.abs(Ke).max()
