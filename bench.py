@@ -240,9 +240,10 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         ks = solver.kernel_stats()
+        sched = solver.schedule()
         kern = statistics.mean(kern_ms)
         solver.close()
-        return {"U": U, "rep": rep, "sizes": sizes, "ms": ms, "kern_ms": kern, "ks": ks, "clocks": clk,
+        return {"U": U, "rep": rep, "sizes": sizes, "ms": ms, "kern_ms": kern, "ks": ks, "clocks": clk, "sched": sched,
                 "value": args.steps * args.n_apply * world / (ms / 1e3)}
 
     m64 = measure("fp64")
@@ -298,6 +299,9 @@ def main():
                          "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
                          "peak_source": src},
             "clocks": m32["clocks"],
+            "schedule": {"fp32_F": m32["sched"]["fp32_F"], "fp32_M": m32["sched"]["fp32_M"],
+                         "fp64_F": m64["sched"]["fp64_F"], "fp64_M": m64["sched"]["fp64_M"],
+                         "meaning": "[rows per warp step, rows per CTA] picked by the setup-time autotuner"},
             "e2e": e2e,
             "gpu_launches": args.steps * args.n_apply * 6,
         }

@@ -205,6 +205,12 @@ feti_status feti_prepare(feti_ctx* ctx);
 feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv_bytes,
                               double* gemv_flops);
 
+/* Launch schedules of the dense local applies chosen by the setup-time
+ * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
+ * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
+ * preconditioner apply, out[4..7] the same for the FP32 copies. */
+feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[8]);
+
 const char* feti_last_error(const feti_ctx* ctx);
 void feti_destroy(feti_ctx* ctx);
 

@@ -52,7 +52,8 @@ class FetiReport(C.Structure):
 
 
 EXPORTS = ["feti_create", "feti_solve", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
-           "feti_get_fixing", "feti_dual_apply", "feti_prepare", "feti_kernel_stats", "feti_last_error",
+           "feti_get_fixing", "feti_dual_apply", "feti_prepare", "feti_kernel_stats", "feti_get_schedule",
+           "feti_last_error",
            "feti_destroy"]
 
 _lib = None
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
     lib.feti_dual_apply.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
     lib.feti_prepare.argtypes = [vp]
     lib.feti_kernel_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.feti_get_schedule.argtypes = [vp, vp]
     lib.feti_last_error.argtypes = [vp]
     lib.feti_last_error.restype = C.c_char_p
     lib.feti_destroy.argtypes = [vp]

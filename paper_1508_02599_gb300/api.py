@@ -174,6 +174,12 @@ class FetiSolver:
                                               C.c_void_p(z.data_ptr()), int(n_apply), C.byref(ms)))
         return ms.value
 
+    def schedule(self) -> dict:
+        out = np.zeros(8, np.int32)
+        self._check(self._lib.feti_get_schedule(self._ctx, out.ctypes.data))
+        o = [int(x) for x in out]
+        return {"fp64_F": o[0:2], "fp64_M": o[2:4], "fp32_F": o[4:6], "fp32_M": o[6:8]}
+
     def kernel_stats(self) -> dict:
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         self._check(self._lib.feti_kernel_stats(self._ctx, C.byref(a), C.byref(b), C.byref(c)))

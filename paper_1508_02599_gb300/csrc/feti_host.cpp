@@ -76,10 +76,18 @@ struct feti_ctx {
   int32_t *d_sub_face_ptr = nullptr, *d_face_dense = nullptr;
   int32_t *d_row_pos = nullptr, *d_bt_ptr = nullptr, *d_bt_row = nullptr, *d_bpos_sub = nullptr;
   double *d_row_sgn = nullptr, *d_weight = nullptr, *d_bt_sgn = nullptr, *d_b = nullptr;
-  int32_t *d_blkF_sub = nullptr, *d_blkF_row = nullptr, *d_blkS_sub = nullptr, *d_blkS_row = nullptr;
-  int n_blkF = 0, n_blkS = 0;
+  // CTA tables of the dense local applies for rows-per-CTA 32, 64, 128
+  // ([which][k]), and the schedules picked by the autotuner
+  feti::GemvCfg tab[2][3];
+  feti::GemvCfg cfg64[2], cfg32[2];
+  bool tuned = false;
+  float* d_vloc32 = nullptr;
   int32_t *d_chunk_sub = nullptr, *d_chunk_p0 = nullptr, *d_sub_chunk_ptr = nullptr, *d_col_sub = nullptr;
   double* d_gpart = nullptr;
+  int32_t *d_gs_ptr = nullptr, *d_gs_pos = nullptr, *d_dir_dof = nullptr;
+  int n_gs = 0;
+  double *d_dU = nullptr, *d_Utrial = nullptr, *d_fl = nullptr;
+  std::vector<double> h_partial;
   int n_chunks = 0;
   int32_t *d_gtg_i = nullptr, *d_gtg_j = nullptr, *d_gtg_ptr = nullptr, *d_gtg_rows = nullptr;
   int n_gtg = 0;
@@ -566,6 +574,33 @@ feti_status build_decomposition(feti_ctx* ctx) {
     }
   }
   ctx->n_own = (int)own_gdof.size();
+  // global non-Dirichlet DOF -> local copies (for residual norms)
+  std::vector<int32_t> gs_ptr, gs_pos;
+  {
+    std::vector<int32_t> cnt(3 * (size_t)N + 1, 0);
+    for (int s = 0; s < P; ++s)
+      for (int i = 0; i < ctx->lay[s].n; ++i) {
+        const int d = dense_ldof[s][i];
+        const int g = 3 * ctx->nodes[s][d / 3] + d % 3;
+        if (!is_dir[g]) cnt[g + 1]++;
+      }
+    std::vector<int32_t> gid(3 * (size_t)N, -1);
+    gs_ptr.push_back(0);
+    for (size_t g = 0; g < 3 * (size_t)N; ++g)
+      if (cnt[g + 1] > 0) {
+        gid[g] = (int32_t)gs_ptr.size() - 1;
+        gs_ptr.push_back(gs_ptr.back() + cnt[g + 1]);
+      }
+    gs_pos.assign(gs_ptr.back(), 0);
+    std::vector<int32_t> fill2(gs_ptr.begin(), gs_ptr.end() - 1);
+    for (int s = 0; s < P; ++s)
+      for (int i = 0; i < ctx->lay[s].n; ++i) {
+        const int d = dense_ldof[s][i];
+        const int g = 3 * ctx->nodes[s][d / 3] + d % 3;
+        if (!is_dir[g]) gs_pos[fill2[gid[g]]++] = ctx->lay[s].voff + i;
+      }
+  }
+  ctx->n_gs = (int)gs_ptr.size() - 1;
   ctx->U_init.assign(3 * (size_t)N, 0.0);
   if (!af)
     for (size_t i = 0; i < ctx->dir_dof.size(); ++i) ctx->U_init[ctx->dir_dof[i]] = ctx->dir_val[i];
@@ -596,15 +631,15 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   ctx->n_gtg = (int)gi.size();
   // gemv block tables
-  std::vector<int32_t> bFs, bFr, bSs, bSr;
-  const int cta_rows = feti::gemv_cta_rows();
-  for (int s = 0; s < P; ++s) {
-    const SubLayout& L = ctx->lay[s];
-    for (int r0 = 0; r0 < std::max(L.nbp, 1); r0 += cta_rows) { bFs.push_back(s); bFr.push_back(r0); }
-    for (int r0 = 0; r0 < L.nbp + L.k; r0 += cta_rows) { bSs.push_back(s); bSr.push_back(r0); }
-  }
-  ctx->n_blkF = (int)bFs.size();
-  ctx->n_blkS = (int)bSs.size();
+  std::vector<int32_t> tab_sub[2][3], tab_row[2][3];
+  const int rpcs[3] = {32, 64, 128};
+  for (int w = 0; w < 2; ++w)
+    for (int t = 0; t < 3; ++t)
+      for (int s = 0; s < P; ++s) {
+        const SubLayout& L = ctx->lay[s];
+        const int m = w == 0 ? std::max(L.nbp, 1) : L.nbp + L.k;
+        for (int r0 = 0; r0 < m; r0 += rpcs[t]) { tab_sub[w][t].push_back(s); tab_row[w][t].push_back(r0); }
+      }
   // chunks of 256 boundary positions for the projection's G^T v
   std::vector<int32_t> chunk_sub, chunk_p0, sub_chunk_ptr(P + 1, 0), col_sub(std::max<int64_t>(ctx->cd, 1), 0);
   for (int s = 0; s < P; ++s) {
@@ -642,10 +677,23 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_bt_row, bt_row));
   FETI_TRY(upload(ctx, &ctx->d_bt_sgn, bt_sgn));
   FETI_TRY(upload(ctx, &ctx->d_bpos_sub, bpos_sub));
-  FETI_TRY(upload(ctx, &ctx->d_blkF_sub, bFs));
-  FETI_TRY(upload(ctx, &ctx->d_blkF_row, bFr));
-  FETI_TRY(upload(ctx, &ctx->d_blkS_sub, bSs));
-  FETI_TRY(upload(ctx, &ctx->d_blkS_row, bSr));
+  for (int w = 0; w < 2; ++w)
+    for (int t = 0; t < 3; ++t) {
+      int32_t *ds = nullptr, *dr = nullptr;
+      FETI_TRY(upload(ctx, &ds, tab_sub[w][t]));
+      FETI_TRY(upload(ctx, &dr, tab_row[w][t]));
+      feti::GemvCfg& c = ctx->tab[w][t];
+      c.rpc = rpcs[t];
+      c.n_blocks = (int)tab_sub[w][t].size();
+      c.blk_sub = ds;
+      c.blk_row0 = dr;
+    }
+  for (int w = 0; w < 2; ++w) {
+    ctx->cfg64[w] = ctx->tab[w][0];  // R=4, 32 rows per CTA
+    ctx->cfg64[w].R = 4;
+    ctx->cfg32[w] = ctx->tab[w][1];  // R=8, 64 rows per CTA
+    ctx->cfg32[w].R = 8;
+  }
   FETI_TRY(upload(ctx, &ctx->d_chunk_sub, chunk_sub));
   FETI_TRY(upload(ctx, &ctx->d_chunk_p0, chunk_p0));
   FETI_TRY(upload(ctx, &ctx->d_sub_chunk_ptr, sub_chunk_ptr));
@@ -657,6 +705,9 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_gtg_rows, grows));
   FETI_TRY(upload(ctx, &ctx->d_R, Rall));
   FETI_TRY(upload(ctx, &ctx->d_own_gdof, own_gdof));
+  FETI_TRY(upload(ctx, &ctx->d_gs_ptr, gs_ptr));
+  FETI_TRY(upload(ctx, &ctx->d_dir_dof, ctx->dir_dof));
+  FETI_TRY(upload(ctx, &ctx->d_gs_pos, gs_pos));
   FETI_TRY(upload(ctx, &ctx->d_own_vpos, own_vpos));
   FETI_TRY(upload(ctx, &ctx->d_Uinit, ctx->U_init));
   FETI_TRY(dev_alloc(ctx, &ctx->d_Uout, 3 * (size_t)N));
@@ -666,6 +717,9 @@ feti_status build_decomposition(feti_ctx* ctx) {
   if (ctx->mat.kind == FETI_HGO_TWO_FIBRE) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_fe, 12 * (size_t)E));
     FETI_TRY(dev_alloc(ctx, &ctx->d_U, 3 * (size_t)N));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_dU, 3 * (size_t)N));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_Utrial, 3 * (size_t)N));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_fl, ctx->nloc_total));
   }
   FETI_TRY(dev_alloc(ctx, &ctx->d_A, aoff));
   FETI_TRY(dev_alloc(ctx, &ctx->d_S, soff));
@@ -682,6 +736,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     FETI_TRY(dev_alloc(ctx, v, nlam));
   FETI_TRY(dev_alloc(ctx, &ctx->d_loc, ctx->nb_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_vloc, ctx->nb_total));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_vloc32, ctx->nb_total + 4));
   FETI_TRY(dev_alloc(ctx, &ctx->d_dl, ctx->n_lambda));
   FETI_TRY(dev_alloc(ctx, &ctx->d_g, std::max<int64_t>(ctx->cd, 1)));
   FETI_TRY(dev_alloc(ctx, &ctx->d_c, std::max<int64_t>(ctx->cd, 1)));
@@ -722,6 +777,10 @@ feti_status check_status(feti_ctx* ctx, const char* where) {
   FETI_CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FETI_CK(cudaStreamSynchronize(ctx->stream));
   const int s = *ctx->h_status;
+  if (s != 0) {
+    FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    FETI_CK(cudaStreamSynchronize(ctx->stream));
+  }
   if (s == feti::DEV_LOCAL_SINGULAR) return fail(ctx, FETI_ERR_LOCAL_SINGULAR, std::string(where) + ": non-positive pivot");
   if (s == feti::DEV_INVERTED) return fail(ctx, FETI_ERR_ELEMENT_INVERTED, std::string(where) + ": inverted element");
   if (s != 0) return fail(ctx, FETI_ERR_CUDA, std::string(where) + ": device status " + std::to_string(s));
@@ -820,28 +879,79 @@ void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool 
   feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, ctx->d_partial, with_dot, done, st);
 }
 
+// Signed gather of x (weights wv or none) and the dense local apply of F_i
+// (which 0) or the preconditioner block (which 1) into d_loc.
+void local_apply(feti_ctx* ctx, int which, const double* x, const double* wv, const int* done, bool f32) {
+  if (f32) {
+    feti::launch_gather32(ctx->maps, x, wv, ctx->d_vloc32, done, ctx->stream);
+    feti::launch_gemv_loc(ctx->cfg32[which], ctx->d_lay, which, which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32,
+                          1, ctx->d_vloc32, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+  } else {
+    feti::launch_gather(ctx->maps, x, wv, ctx->d_vloc, done, ctx->stream);
+    feti::launch_gemv_loc(ctx->cfg64[which], ctx->d_lay, which, which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S,
+                          0, ctx->d_vloc, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+  }
+}
+
 // q = F x: signed gather B_i^T x, dense F_i apply, row-major gather back;
 // optional partial dot with a.  f32 selects the FP32 copies of F_i.
 void apply_F(feti_ctx* ctx, const double* x, double* q, const double* a, bool with_dot, const int* done,
              bool f32 = false) {
-  feti::launch_gather(ctx->maps, x, nullptr, ctx->d_vloc, done, ctx->stream);
-  feti::launch_gemv_loc(ctx->n_blkF, ctx->d_blkF_sub, ctx->d_blkF_row, ctx->d_lay, 0,
-                        f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0, ctx->d_vloc,
-                        ctx->d_loc, ctx->max_nb, done, ctx->stream);
+  local_apply(ctx, 0, x, nullptr, done, f32);
   feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, a, with_dot ? ctx->d_partial : nullptr, done, ctx->stream);
 }
 
 // z = M^-1 w = W B Y B^T W w.
 void apply_M(feti_ctx* ctx, const double* w, double* z, const int* done, bool f32 = false) {
-  if (ctx->opt.precond == FETI_PREC_IDENTITY) {
+  if (ctx->opt.precond == FETI_PREC_IDENTITY)
     feti::launch_gather(ctx->maps, w, ctx->d_weight, ctx->d_loc, done, ctx->stream);
-  } else {
-    feti::launch_gather(ctx->maps, w, ctx->d_weight, ctx->d_vloc, done, ctx->stream);
-    feti::launch_gemv_loc(ctx->n_blkS, ctx->d_blkS_sub, ctx->d_blkS_row, ctx->d_lay, 1,
-                          f32 ? (const void*)ctx->d_S32 : (const void*)ctx->d_S, f32 ? 1 : 0, ctx->d_vloc,
-                          ctx->d_loc, ctx->max_nb, done, ctx->stream);
-  }
+  else
+    local_apply(ctx, 1, w, ctx->d_weight, done, f32);
   feti::launch_scatter(ctx->maps, ctx->d_loc, ctx->d_weight, z, nullptr, nullptr, done, ctx->stream);
+}
+
+// Autotuner: times every (rows per warp step, rows per CTA) schedule of the
+// dense local applies on the real operators and keeps the fastest.
+feti_status autotune(feti_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0, e1;
+  FETI_CK(cudaEventCreate(&e0));
+  FETI_CK(cudaEventCreate(&e1));
+  const int Rs[3] = {2, 4, 8};
+  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  FETI_CK(cudaMemsetAsync(ctx->d_vloc, 0, ctx->nb_total * sizeof(double), st));
+  FETI_CK(cudaMemsetAsync(ctx->d_vloc32, 0, ctx->nb_total * sizeof(float), st));
+  for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
+    const bool f32 = prec == 1;
+    for (int w = 0; w < 2; ++w) {
+      if (w == 1 && ctx->opt.precond == FETI_PREC_IDENTITY) continue;
+      const void* M = f32 ? (w == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
+                          : (w == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
+      const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+      float best = 1e30f;
+      feti::GemvCfg bestc = f32 ? ctx->cfg32[w] : ctx->cfg64[w];
+      for (int t = 0; t < 3; ++t)
+        for (int ri = 0; ri < 3; ++ri) {
+          feti::GemvCfg c = ctx->tab[w][t];
+          c.R = Rs[ri];
+          feti::launch_gemv_loc(c, ctx->d_lay, w, M, f32, v, ctx->d_loc, ctx->max_nb, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 3; ++rep)
+            feti::launch_gemv_loc(c, ctx->d_lay, w, M, f32, v, ctx->d_loc, ctx->max_nb, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e1, st));
+          FETI_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) { best = ms; bestc = c; }
+        }
+      (f32 ? ctx->cfg32[w] : ctx->cfg64[w]) = bestc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FETI_CK(cudaGetLastError());
+  ctx->tuned = true;
+  return FETI_OK;
 }
 
 void pcg_iteration(feti_ctx* ctx, double* lam, bool f32) {
@@ -883,6 +993,7 @@ feti_status prepare(feti_ctx* ctx, const double* dU, double tau) {
   FETI_TRY(assemble_all(ctx, dU, tau));
   FETI_TRY(factorize_all(ctx));
   if (!ctx->prepared) FETI_TRY(coarse_setup(ctx));
+  if (!ctx->tuned) FETI_TRY(autotune(ctx));
   ctx->prepared = true;
   return FETI_OK;
 }
@@ -1147,9 +1258,102 @@ feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_r
   return s;
 }
 
+// ||sum_i A_i x_i|| over the non-Dirichlet global DOFs (device reduction,
+// fixed-order sum of the per-CTA partials on the host).
+static feti_status global_norm(feti_ctx* ctx, const double* x, double* out) {
+  const int np = feti::scatter_partials();
+  feti::launch_global_sumsq(ctx->n_gs, ctx->d_gs_ptr, ctx->d_gs_pos, x, ctx->d_partial, ctx->stream);
+  FETI_CK(cudaGetLastError());
+  ctx->h_partial.resize(np);
+  FETI_CK(cudaMemcpyAsync(ctx->h_partial.data(), ctx->d_partial, np * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  for (double v : ctx->h_partial) t += v;
+  *out = std::sqrt(t);
+  return FETI_OK;
+}
+
+// Relative residual ||f_int(U) - tau f_ext(U)|| / ||tau f_ext(U)|| from the
+// local vectors of the last assembly (d_f = tau f_ext - f_int per subdomain).
+static feti_status newton_residual(feti_ctx* ctx, const double* dU, double tau, double* rel) {
+  double rn = 0.0, fn = 0.0;
+  FETI_TRY(global_norm(ctx, ctx->d_f, &rn));
+  feti::launch_assemble_rhs(ctx->P, ctx->d_lay, ctx->d_sub_face_ptr, ctx->d_face_dense, ctx->d_face_force,
+                            ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, nullptr, ctx->d_Ke, nullptr,
+                            tau, ctx->d_fl, ctx->stream);
+  FETI_TRY(global_norm(ctx, ctx->d_fl, &fn));
+  (void)dU;
+  *rel = fn > 0.0 ? rn / fn : rn;
+  return FETI_OK;
+}
+
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
-  return fail(ctx, FETI_ERR_STATE, "feti_newton is not available in this build");
+  if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
+  (void)cudaGetLastError();
+  if (ctx->mat.kind != FETI_HGO_TWO_FIBRE) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton needs HGO_TWO_FIBRE");
+  for (double v : ctx->dir_val)
+    if (v != 0.0) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton needs homogeneous Dirichlet data");
+  if (report) std::memset(report, 0, sizeof(*report));
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = ctx->stream;
+  const int n3 = 3 * ctx->N;
+  const int nsteps = ctx->opt.n_load_steps > 0 ? ctx->opt.n_load_steps : 1;
+  const int maxit = ctx->opt.newton_maxit > 0 ? ctx->opt.newton_maxit : 25;
+  const double ntol = ctx->opt.newton_tol > 0 ? ctx->opt.newton_tol : 1e-8;
+  FETI_CK(cudaMemsetAsync(ctx->d_U, 0, n3 * sizeof(double), st));
+  int newton_total = 0, pcg_total = 0;
+  double rel = 0.0;
+  double t_pcg = 0.0;
+  for (int step = 1; step <= nsteps; ++step) {
+    const double tau = (double)step / nsteps;
+    FETI_TRY(prepare(ctx, ctx->d_U, tau));
+    FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
+    for (int k = 0;; ++k) {
+      if (rel <= ntol) break;
+      if (k >= maxit) {
+        if (report) { report->newton_iters = newton_total; report->newton_rel_res = rel; report->iterations = pcg_total; }
+        return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "Newton reached its iteration limit at load step " + std::to_string(step));
+      }
+      feti_report r{};
+      float ms = 0.f;
+      feti_status s = dual_solve(ctx, &r, &ms);
+      if (s != FETI_OK) return s;
+      pcg_total += r.iterations;
+      t_pcg += ms;
+      // increment on the global DOFs (owner rule), zero on Dirichlet DOFs
+      FETI_CK(cudaMemsetAsync(ctx->d_dU, 0, n3 * sizeof(double), st));
+      feti::launch_owner_scatter(ctx->n_own, ctx->d_own_gdof, ctx->d_own_vpos, ctx->d_x, ctx->d_dU, st);
+      // step length: halve until the local tangents at U + a dU factorize
+      double a = 1.0;
+      for (;;) {
+        feti::launch_axpy_to(n3, ctx->d_U, a, ctx->d_dU, ctx->d_Utrial, st);
+        feti::launch_zero_list((int)ctx->dir_dof.size(), ctx->d_dir_dof, ctx->d_Utrial, st);
+        s = prepare(ctx, ctx->d_Utrial, tau);
+        if (s == FETI_OK) break;
+        if (s != FETI_ERR_LOCAL_SINGULAR && s != FETI_ERR_ELEMENT_INVERTED) return s;
+        a *= 0.5;
+        if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "no step keeps the local tangents positive definite");
+      }
+      FETI_CK(cudaMemcpyAsync(ctx->d_U, ctx->d_Utrial, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      ++newton_total;
+      FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
+    }
+  }
+  FETI_CK(cudaMemcpyAsync(u_out, ctx->d_U, n3 * sizeof(double), u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  FETI_CK(cudaStreamSynchronize(st));
+  if (report) {
+    report->newton_iters = newton_total;
+    report->newton_rel_res = rel;
+    report->iterations = pcg_total;
+    report->converged = 1;
+    report->t_pcg_ms = t_pcg;
+    report->n_lambda = ctx->n_lambda;
+    report->coarse_dim = ctx->cd;
+    report->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return FETI_OK;
 }
 
 feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, double* Ke_out, double* fe_out,
@@ -1232,11 +1436,15 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
     FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const bool f32 = ctx->opt.precision == FETI_MIXED;
     for (int i = 0; i < n_apply; ++i) {
-      feti::launch_gather(ctx->maps, v, nullptr, ctx->d_vloc, zero, st);
+      if (f32)
+        feti::launch_gather32(ctx->maps, v, nullptr, ctx->d_vloc32, zero, st);
+      else
+        feti::launch_gather(ctx->maps, v, nullptr, ctx->d_vloc, zero, st);
       FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[2 + 2 * i], st, cudaEventRecordExternal));
-      feti::launch_gemv_loc(ctx->n_blkF, ctx->d_blkF_sub, ctx->d_blkF_row, ctx->d_lay, 0,
-                            f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0, ctx->d_vloc,
-                            ctx->d_loc, ctx->max_nb, zero, st);
+      feti::launch_gemv_loc(f32 ? ctx->cfg32[0] : ctx->cfg64[0], ctx->d_lay, 0,
+                            f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
+                            f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc, ctx->d_loc, ctx->max_nb,
+                            zero, st);
       FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[3 + 2 * i], st, cudaEventRecordExternal));
       feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, nullptr, nullptr, zero, st);
       apply_M(ctx, q, z, zero, f32);
@@ -1275,6 +1483,17 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
   const double esz = ctx->opt.precision == FETI_MIXED ? 4.0 : 8.0;
   ctx->gemv_bytes = entries * esz + vec * 16.0;
   ctx->gemv_flops = 2.0 * entries;
+  return FETI_OK;
+}
+
+feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[8]) {
+  if (!ctx || !out) return FETI_ERR_INVALID_ARG;
+  for (int w = 0; w < 2; ++w) {
+    out[2 * w] = ctx->cfg64[w].R;
+    out[2 * w + 1] = ctx->cfg64[w].rpc;
+    out[4 + 2 * w] = ctx->cfg32[w].R;
+    out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
+  }
   return FETI_OK;
 }
 

@@ -137,14 +137,22 @@ void launch_local_sub(int P, const SubLayout* lay, const double* f, const double
 }  // namespace feti
 
 namespace feti {
-// Rows of one CTA of launch_gemv_loc.
-int gemv_cta_rows();
-// y_b = M_i v_b on a pre-gathered local vector (see launch_gather); M is the
-// FP64 (f32 = 0) or padded FP32 (f32 = 1) copy of F_i (which 0) or the
+// Launch schedule of the dense local apply: R rows per warp step, rpc rows
+// per CTA, and the (subdomain, first row) table of its n_blocks CTAs.
+struct GemvCfg {
+  int R = 4;
+  int rpc = 64;
+  int n_blocks = 0;
+  const int32_t* blk_sub = nullptr;
+  const int32_t* blk_row0 = nullptr;
+};
+// y_b = M_i v_b on a pre-gathered local vector; M is the FP64 (f32 = 0, v
+// double) or padded FP32 (f32 = 1, v float) copy of F_i (which 0) or the
 // preconditioner block (which 1).
-void launch_gemv_loc(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
-                     const void* M, int f32, const double* vloc, double* y, int max_m, const int* done,
-                     cudaStream_t st);
+void launch_gemv_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, const void* vloc,
+                     double* y, int max_m, const int* done, cudaStream_t st);
+// FP32 signed gather (input of the FP32 apply).
+void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);
 void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // a += b
 void launch_vadd(int n, double* a, const double* b, cudaStream_t st);
@@ -160,4 +168,17 @@ void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chun
 void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial, const int32_t* sub_chunk_ptr,
                               const int32_t* col_sub, const SubLayout* lay, double* c, const int* done,
                               cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// partial[b] = partial sums of (sum of local copies)^2 over n global DOFs (kPartials CTAs).
+void launch_global_sumsq(int n, const int32_t* ptr, const int32_t* pos, const double* x, double* partial,
+                         cudaStream_t st);
+// out = u + a du
+void launch_axpy_to(int n, const double* u, double a, const double* du, double* out, cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// x[idx[i]] = 0
+void launch_zero_list(int n, const int32_t* idx, double* x, cudaStream_t st);
 }  // namespace feti

@@ -593,23 +593,27 @@ __global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Dense local operator apply on a pre-gathered local vector.  One CTA owns
-// 8 warps x R rows of one subdomain; every warp keeps R independent
-// accumulators so each v element read from shared memory feeds R FMAs.
-// FP64 matrices: row stride m, one double per lane per step.  FP32
-// matrices: row stride padded to a multiple of 4 floats (zero padding),
-// one float4 per lane per step, products accumulated in FP32 per lane and
-// reduced across the warp in FP64.
-constexpr int GEMV_R = 8;
-constexpr int GEMV_CTA_ROWS = GEMV_R * (kThreads / 32);
-
+// Dense local operator apply on a pre-gathered local vector.  A CTA of 8
+// warps owns `rpc` consecutive rows of one subdomain; each warp walks its
+// rows R at a time, keeping R independent accumulators so each v element read
+// from shared memory feeds R FMAs.  FP64 matrices: row stride m, one double
+// per lane per step.  FP32 matrices: row stride padded to a multiple of 4
+// floats (zero padding), one float4 per lane per step, the input vector
+// already in FP32, sums kept in FP32 per lane and across the warp (the
+// operator itself carries FP32 rounding; an FP64 cross-lane reduction costs
+// about a quarter of the kernel on GB300's FP64 pipe).
 __device__ __forceinline__ int pad4(int m) { return (m + 3) & ~3; }
 
-template <typename T>
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int R>
 __global__ void __launch_bounds__(kThreads) k_gemv_loc(const int32_t* __restrict__ blk_sub,
-                                                       const int32_t* __restrict__ blk_row0,
+                                                       const int32_t* __restrict__ blk_row0, int rpc,
                                                        const SubLayout* __restrict__ lay, int which,
-                                                       const T* __restrict__ M, const double* __restrict__ vloc,
+                                                       const T* __restrict__ M, const T* __restrict__ vloc,
                                                        double* __restrict__ y, const int* __restrict__ done) {
   if (*done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -621,44 +625,64 @@ __global__ void __launch_bounds__(kThreads) k_gemv_loc(const int32_t* __restrict
   constexpr bool f32 = sizeof(T) == 4;
   const int ldm = f32 ? pad4(m) : m;
   const T* Ms = M + (f32 ? (which == 0 ? L.foff32 : L.soff32) : (which == 0 ? L.foff : L.soff));
-  for (int p = threadIdx.x; p < ldm; p += blockDim.x) v[p] = p < m ? (T)vloc[L.boff + p] : (T)0;
+  for (int p = threadIdx.x; p < ldm; p += blockDim.x) v[p] = p < m ? vloc[L.boff + p] : (T)0;
   if (which == 0 && r0 == 0)
     for (int p = L.nbp + threadIdx.x; p < L.nbp + L.k; p += blockDim.x) y[L.boff + p] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int rbase = r0 + wid * GEMV_R;
-  if (rbase >= m) return;
-  T acc[GEMV_R];
+  const int rend = min(r0 + rpc, m);
+  for (int rbase = r0 + wid * R; rbase < rend; rbase += (kThreads / 32) * R) {
+    T acc[R];
 #pragma unroll
-  for (int j = 0; j < GEMV_R; ++j) acc[j] = (T)0;
-  const T* rows[GEMV_R];
+    for (int j = 0; j < R; ++j) acc[j] = (T)0;
+    const T* rows[R];
 #pragma unroll
-  for (int j = 0; j < GEMV_R; ++j) rows[j] = Ms + (size_t)min(rbase + j, m - 1) * ldm;
-  if constexpr (f32) {
-    const int m4 = ldm >> 2;
-    const float4* v4 = reinterpret_cast<const float4*>(v);
-    for (int c = lane; c < m4; c += 32) {
-      const float4 vv = v4[c];
-      float4 a[GEMV_R];
+    for (int j = 0; j < R; ++j) rows[j] = Ms + (size_t)min(rbase + j, m - 1) * ldm;
+    if constexpr (f32) {
+      const int m4 = ldm >> 2;
+      const float4* v4 = reinterpret_cast<const float4*>(v);
+      for (int c = lane; c < m4; c += 32) {
+        const float4 vv = v4[c];
+        float4 a[R];
 #pragma unroll
-      for (int j = 0; j < GEMV_R; ++j) a[j] = __ldg(reinterpret_cast<const float4*>(rows[j]) + c);
+        for (int j = 0; j < R; ++j) a[j] = __ldg(reinterpret_cast<const float4*>(rows[j]) + c);
 #pragma unroll
-      for (int j = 0; j < GEMV_R; ++j) acc[j] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
-    }
-  } else {
-    for (int c = lane; c < m; c += 32) {
-      const T vv = v[c];
-      T a[GEMV_R];
+        for (int j = 0; j < R; ++j) acc[j] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
+      }
 #pragma unroll
-      for (int j = 0; j < GEMV_R; ++j) a[j] = __ldg(rows[j] + c);
+      for (int j = 0; j < R; ++j) {
+        const float t = warp_sumf(acc[j]);
+        if (lane == 0 && rbase + j < rend) y[L.boff + rbase + j] = (double)t;
+      }
+    } else {
+      for (int c = lane; c < m; c += 32) {
+        const T vv = v[c];
+        T a[R];
 #pragma unroll
-      for (int j = 0; j < GEMV_R; ++j) acc[j] += a[j] * vv;
+        for (int j = 0; j < R; ++j) a[j] = __ldg(rows[j] + c);
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[j] += a[j] * vv;
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const double t = warp_sum(acc[j]);
+        if (lane == 0 && rbase + j < rend) y[L.boff + rbase + j] = t;
+      }
     }
   }
-#pragma unroll
-  for (int j = 0; j < GEMV_R; ++j) {
-    const double t = warp_sum((double)acc[j]);
-    if (lane == 0 && rbase + j < m) y[L.boff + rbase + j] = t;
+}
+
+// Signed gather onto the boundary positions in FP32 (input of the FP32 apply).
+__global__ void k_gather32(Maps mp, const double* __restrict__ x, const double* __restrict__ wv,
+                           float* __restrict__ y, const int* __restrict__ done) {
+  if (*done) return;
+  for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < mp.nb_total; gp += gridDim.x * blockDim.x) {
+    double val = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+      const int row = mp.bt_row[e];
+      val += mp.bt_sgn[e] * x[row] * (wv ? wv[row] : 1.0);
+    }
+    y[gp] = (float)val;
   }
 }
 
@@ -1148,23 +1172,38 @@ void launch_local_sub(int P, const SubLayout* lay, const double* f, const double
   k_local_sub<<<P, kThreads, 0, st>>>(lay, f, loc, out);
 }
 
-int gemv_cta_rows() { return GEMV_CTA_ROWS; }
+template <typename T, int R>
+static void launch_gemv_t(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, int rpc, const SubLayout* lay,
+                          int which, const T* M, const T* vloc, double* y, int max_m, const int* done,
+                          cudaStream_t st) {
+  const size_t smem = (size_t)((max_m + 3) & ~3) * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_gemv_loc<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemv_loc<T, R><<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, rpc, lay, which, M, vloc, y, done);
+}
 
-void launch_gemv_loc(int n_blocks, const int32_t* blk_sub, const int32_t* blk_row0, const SubLayout* lay, int which,
-                     const void* M, int f32, const double* vloc, double* y, int max_m, const int* done,
-                     cudaStream_t st) {
-  const size_t smem = (size_t)((max_m + 3) & ~3) * (f32 ? sizeof(float) : sizeof(double));
+void launch_gemv_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, const void* vloc,
+                     double* y, int max_m, const int* done, cudaStream_t st) {
   if (f32) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_loc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemv_loc<float><<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which,
-                                                         static_cast<const float*>(M), vloc, y, done);
+    const float* Mf = static_cast<const float*>(M);
+    const float* vf = static_cast<const float*>(vloc);
+    switch (cfg.R) {
+      case 2: launch_gemv_t<float, 2>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Mf, vf, y, max_m, done, st); break;
+      case 4: launch_gemv_t<float, 4>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Mf, vf, y, max_m, done, st); break;
+      default: launch_gemv_t<float, 8>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Mf, vf, y, max_m, done, st); break;
+    }
   } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_loc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemv_loc<double><<<n_blocks, kThreads, smem, st>>>(blk_sub, blk_row0, lay, which,
-                                                          static_cast<const double*>(M), vloc, y, done);
+    const double* Md = static_cast<const double*>(M);
+    const double* vd = static_cast<const double*>(vloc);
+    switch (cfg.R) {
+      case 2: launch_gemv_t<double, 2>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Md, vd, y, max_m, done, st); break;
+      case 4: launch_gemv_t<double, 4>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Md, vd, y, max_m, done, st); break;
+      default: launch_gemv_t<double, 8>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Md, vd, y, max_m, done, st); break;
+    }
   }
+}
+
+void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st) {
+  k_gather32<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, x, wv, y, done);
 }
 
 void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st) {
@@ -1193,6 +1232,49 @@ void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial,
   k_coarse_apply_part<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, smem, st>>>(cd, Ginv, partial,
                                                                                         sub_chunk_ptr, col_sub, lay,
                                                                                         c, done);
+}
+
+namespace {
+// Sum of squares of the assembled global vector sum_i A_i x_i on the listed
+// global DOFs (copies summed in a fixed order), per-CTA partials.
+__global__ void __launch_bounds__(kThreads) k_global_sumsq(int n, const int32_t* __restrict__ ptr,
+                                                           const int32_t* __restrict__ pos,
+                                                           const double* __restrict__ x, double* __restrict__ partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int q = ptr[g]; q < ptr[g + 1]; ++q) t += x[pos[q]];
+    acc += t * t;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_axpy_to(int n, const double* __restrict__ u, double a, const double* __restrict__ du,
+                          double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = u[i] + a * du[i];
+}
+}  // namespace
+
+void launch_global_sumsq(int n, const int32_t* ptr, const int32_t* pos, const double* x, double* partial,
+                         cudaStream_t st) {
+  k_global_sumsq<<<kPartials, kThreads, 0, st>>>(n, ptr, pos, x, partial);
+}
+
+void launch_axpy_to(int n, const double* u, double a, const double* du, double* out, cudaStream_t st) {
+  k_axpy_to<<<grid_for(n), kThreads, 0, st>>>(n, u, a, du, out);
+}
+
+namespace {
+__global__ void k_zero_list(int n, const int32_t* __restrict__ idx, double* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[idx[i]] = 0.0;
+}
+}  // namespace
+
+void launch_zero_list(int n, const int32_t* idx, double* x, cudaStream_t st) {
+  if (n <= 0) return;
+  k_zero_list<<<grid_for(n), kThreads, 0, st>>>(n, idx, x);
 }
 
 }  // namespace feti

@@ -56,3 +56,23 @@ def test_hgo_elements_match(amp):
         assert _rel(fe, fe_ref) <= 1e-10
     else:
         assert np.abs(fe).max() <= 1e-12 * np.abs(Ke).max()
+
+
+def test_newton_matches_oracle_classical():
+    """Load-stepped Newton (one step, 1 mmHg as in Tables 4-7) on the small tube.
+
+    Classical FETI: every subdomain touches the Dirichlet boundary, so the
+    local tangents are nonsingular and the FETI increment is the exact Newton
+    increment; GPU and oracle both stop at a relative residual of 1e-9.
+    """
+    from oracle import feti
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = mesh.cylinder_problem(2, 16, 2, (1, 4, 1), material=mesh.hgo_material(), pressure=0.13332)
+    U_ref, log = feti.newton_solve(prob, feti.CLASSICAL, "dirichlet", n_load_steps=1, newton_tol=1e-9,
+                                   pcg_tol=1e-12)
+    with FetiSolver(prob, method="classical", precond="dirichlet", tol=1e-12, maxit=3000, n_load_steps=1,
+                    newton_tol=1e-9, newton_maxit=25) as s:
+        U, rep = s.newton()
+    assert rep["newton_rel_res"] <= 1e-9
+    assert abs(rep["newton_iters"] - len(log[0])) <= 1
+    assert np.linalg.norm(U - U_ref) <= 1e-7 * np.linalg.norm(U_ref)

@@ -123,7 +123,7 @@ def test_full_size_tube_properties():
     closed form within discretization error and the jump-free owner copies.
     """
     prob = mesh.config_problem("cyl16")
-    with _solver(prob, "af", "dirichlet", tol=1e-8, maxit=1000) as s:
+    with _solver(prob, "af", "dirichlet", tol=1e-10, maxit=1000) as s:
         U, rep = s.solve()
     assert rep["converged"] == 1
     Ke, _ = fem.element_matrices(prob)
@@ -132,7 +132,9 @@ def test_full_size_tube_properties():
     free = np.ones(K.shape[0], bool)
     free[prob.dir_dof] = False
     res = (K @ U - f)[free]
-    assert np.linalg.norm(res) <= 1e-6 * np.linalg.norm(f[free])
+    # primal equilibrium residual ~ 1e2 x the dual tolerance here (measured
+    # 1.7e-6 at tol 1e-8)
+    assert np.linalg.norm(res) <= 1e-7 * np.linalg.norm(f[free])
     assert np.abs(U[prob.dir_dof]).max() <= 1e-7 * np.abs(U).max()
     x = prob.coords
     u = U.reshape(-1, 3)
