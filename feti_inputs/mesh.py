@@ -220,8 +220,10 @@ def _helical_fibres(coords, tets, alpha_deg):
 def _rcb(cent, n_parts, rng, frac_jitter):
     """Recursive coordinate bisection of cell centroids (any n_parts >= 1).
 
-    Each cut goes across the longest extent; the left share of cells is
-    (n_left/n_parts) * (1 + U(-frac_jitter, frac_jitter)) of the cells.
+    Each cut goes across the longest extent; the left share of cells aims at
+    (n_left/n_parts) * (1 + U(-frac_jitter, frac_jitter)) and is moved to the
+    nearest gap between distinct centroid coordinates, so every part is a box
+    of whole cell layers (face-connected on a structured grid).
     """
     part = np.zeros(cent.shape[0], dtype=np.int64)
 
@@ -235,8 +237,12 @@ def _rcb(cent, n_parts, rng, frac_jitter):
         u = rng.uniform(-frac_jitter, frac_jitter) if frac_jitter > 0 else 0.0
         frac = (nl / count) * (1.0 + u)
         order = idx[np.argsort(cent[idx, ax], kind="stable")]
-        cut = int(round(frac * idx.size))
-        cut = min(max(cut, 1), idx.size - 1)
+        vals = cent[order, ax]
+        gaps = np.nonzero(vals[1:] > vals[:-1])[0] + 1
+        if gaps.size == 0:
+            raise ValueError("cannot bisect a single layer of cells")
+        target = frac * idx.size
+        cut = int(gaps[np.argmin(np.abs(gaps - target))])
         rec(order[:cut], first, nl)
         rec(order[cut:], first + nl, count - nl)
 

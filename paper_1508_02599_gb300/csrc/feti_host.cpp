@@ -857,7 +857,7 @@ feti_status coarse_setup(feti_ctx* ctx) {
   FETI_CK(cudaMemcpy2DAsync(ctx->d_Acoarse, 2 * cd * sizeof(double), ctx->d_GtG, cd * sizeof(double),
                             cd * sizeof(double), cd, cudaMemcpyDeviceToDevice, st));
   feti::launch_augment(1, ctx->d_lay_coarse, ctx->d_Acoarse, st);
-  feti::launch_chol_partial(1, ctx->d_lay_coarse, 1, ctx->d_Acoarse, ctx->d_status, st);
+  feti::launch_dense_chol_big(ctx->d_Acoarse, 2 * (int)cd, 0, (int)cd, 2 * (int)cd, ctx->d_status, st);
   // extract into Ginv: F layout of the coarse "subdomain" has foff = 0
   feti::launch_extract(1, ctx->d_lay_coarse, 1, ctx->d_Acoarse, ctx->d_Ginv, st);
   FETI_CK(cudaGetLastError());

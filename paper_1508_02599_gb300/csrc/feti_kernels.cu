@@ -1277,4 +1277,148 @@ void launch_zero_list(int n, const int32_t* idx, double* x, cudaStream_t st) {
   k_zero_list<<<grid_for(n), kThreads, 0, st>>>(n, idx, x);
 }
 
+namespace {
+// Multi-CTA right-looking Cholesky of one large dense matrix (the coarse
+// G^T G, augmented by its identity coupling), lower triangle, row-major:
+// per block column a diagonal-block kernel, a panel-solve kernel over row
+// chunks and a trailing-update kernel over the lower-triangular 64x64 tiles.
+__global__ void k_big_diag(double* __restrict__ A, size_t ld, int kb, int nk, int* status) {
+  __shared__ double D[NB][NB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int i = tid;
+    for (int j = 0; j < nk; ++j) {
+      if (i == j) {
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        D[j][j] = sqrt(d);
+      }
+      __syncwarp();
+      if (bad) break;
+      if (i > j && i < nk) D[i][j] /= D[j][j];
+      __syncwarp();
+      if (i > j && i < nk)
+        for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) set_status(status, DEV_LOCAL_SINGULAR);
+    return;
+  }
+  for (int idx = tid; idx < nk * nk; idx += blockDim.x) {
+    const int i = idx / nk, j = idx % nk;
+    if (j <= i) A[(kb + i) * ld + kb + j] = D[i][j];
+  }
+}
+
+__global__ void k_big_trsm(double* __restrict__ A, size_t ld, int kb, int nk, int n_act, const int* status) {
+  if (*status) return;
+  __shared__ double D[NB][NB + 1];
+  __shared__ double Pa[TT][NB + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+  }
+  const int base = kb + nk + blockIdx.x * TT;
+  const int nr = min(TT, n_act - base);
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    Pa[r][l] = (r < nr && l < nk) ? A[(base + r) * ld + kb + l] : 0.0;
+  }
+  __syncthreads();
+  if (tid < nr) {
+    double xr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < nk) {
+        double v = xr[j];
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+          if (l < j) v -= xr[l] * D[j][l];
+        xr[j] = v / D[j][j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) Pa[tid][j] = xr[j];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    if (r < nr && l < nk) A[(base + r) * ld + kb + l] = Pa[r][l];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_big_update(double* __restrict__ A, size_t ld, int kb, int nk,
+                                                         int n_act, const int* status) {
+  if (*status) return;
+  __shared__ double Pa[TT][NB + 1];
+  __shared__ double Pb[TT][NB + 1];
+  const long b = blockIdx.x;
+  // lower-triangular tile index b -> (ti, tj), tj <= ti
+  int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while ((long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+  while ((long)ti * (ti + 1) / 2 > b) --ti;
+  const int tj = (int)(b - (long)ti * (ti + 1) / 2);
+  const int r0 = kb + nk;
+  const int ib = r0 + ti * TT, jb = r0 + tj * TT;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    Pa[r][l] = (ib + r < n_act && l < nk) ? A[(ib + r) * ld + kb + l] : 0.0;
+    Pb[r][l] = (jb + r < n_act && l < nk) ? A[(jb + r) * ld + kb + l] : 0.0;
+  }
+  __syncthreads();
+  const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+  for (int l = 0; l < nk; ++l) {
+    double av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      av[a] = Pa[tr + a][l];
+      bv[a] = Pb[tc + a][l];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] += av[a] * bv[c];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = ib + tr + a, j = jb + tc + c;
+      if (i < n_act && j < n_act && j <= i) A[i * ld + j] -= acc[a][c];
+    }
+}
+}  // namespace
+
+void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int* status, cudaStream_t st) {
+  for (int kb = c0; kb < c1; kb += NB) {
+    const int nk = min(NB, c1 - kb);
+    k_big_diag<<<1, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, status);
+    const int rows = n_act - (kb + nk);
+    if (rows <= 0) continue;
+    const int chunks = (rows + TT - 1) / TT;
+    k_big_trsm<<<chunks, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, n_act, status);
+    const long tiles = (long)chunks * (chunks + 1) / 2;
+    k_big_update<<<(unsigned)tiles, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, n_act, status);
+  }
+}
+
 }  // namespace feti

@@ -210,3 +210,20 @@ def test_mixed_dual_apply_close_to_fp64():
     q_ref = o.apply_F(v)
     err = np.abs(q - q_ref).max() / np.abs(q_ref).max()
     assert 1e-12 < err <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_jittered_uneven_partition_matches_oracle(precision):
+    """Jittered tube with a jittered recursive-bisection partition: subdomains of
+    uneven size (about 2x) in one launch per stage, against the oracle."""
+    prob = mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)
+    sizes = np.bincount(prob.part)
+    assert sizes.max() >= 1.5 * sizes.min()
+    o = feti.FetiOracle(prob, "af", "dirichlet")
+    U_ref, res, _ = o.solve(tol=1e-12, maxit=3000)
+    with _solver(prob, "af", "dirichlet", tol=1e-11, maxit=3000, precision=precision) as s:
+        U, rep = s.solve()
+        m = s.index_maps()
+    assert np.array_equal(m["row_sub"], o.maps.row_sub) and np.array_equal(m["row_ldof"], o.maps.row_ldof)
+    assert rep["converged"] == 1
+    assert np.linalg.norm(U - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
