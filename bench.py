@@ -155,8 +155,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-apply", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cyl16", choices=["cyl16", "cyl8"],
-                    help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures")
+    ap.add_argument("--workload", default="cyl16", choices=["cyl16", "cyl8", "jcyl32"],
+                    help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures; "
+                         "jcyl32: jittered tube, 1024 uneven subdomains")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--apply-only", action="store_true",
                     help="setup only (no PCG solve) before the timed applies: for profiler captures")
@@ -169,6 +170,10 @@ def main():
         prob = mesh.config_problem("cyl16")
         wname = ("AF-FETI tube 16x64x32 cells P1 (35,904 nodes, 107,712 DOFs), 64 wedge subdomains, "
                  "Dirichlet preconditioner, FP64, PCG tol 1e-8")
+    elif args.workload == "jcyl32":
+        prob = mesh.config_problem("jcyl32")
+        wname = ("AF-FETI jittered tube 32x128x64 cells P1 (274,560 nodes, 823,680 DOFs), 1024 uneven "
+                 "subdomains (jittered RCB), Dirichlet preconditioner, PCG tol 1e-8")
     else:
         prob = mesh.cylinder_problem(8, 64, 16, (2, 8, 2))
         wname = ("AF-FETI tube 8x64x16 cells P1 (9,792 nodes), 32 wedge subdomains, Dirichlet "

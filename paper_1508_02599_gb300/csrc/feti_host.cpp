@@ -100,6 +100,7 @@ struct feti_ctx {
   // PCG vectors
   double *d_lam = nullptr, *d_r = nullptr, *d_w = nullptr, *d_z = nullptr, *d_y = nullptr, *d_p = nullptr;
   double *d_q = nullptr, *d_d = nullptr, *d_loc = nullptr, *d_g = nullptr, *d_c = nullptr, *d_e = nullptr;
+  double *d_partial_wy = nullptr, *d_partial_pq = nullptr;
   double *d_partial = nullptr, *d_alpha_hist = nullptr, *d_beta_hist = nullptr;
   feti::PcgScalars* d_sc = nullptr;
   feti::PcgScalars* h_sc = nullptr;  // pinned
@@ -742,6 +743,8 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(dev_alloc(ctx, &ctx->d_c, std::max<int64_t>(ctx->cd, 1)));
   FETI_TRY(dev_alloc(ctx, &ctx->d_e, std::max<int64_t>(ctx->cd, 1)));
   FETI_TRY(dev_alloc(ctx, &ctx->d_partial, feti::scatter_partials()));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_partial_wy, feti::scatter_partials()));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_partial_pq, feti::scatter_partials()));
   FETI_TRY(dev_alloc(ctx, &ctx->d_alpha_hist, ctx->opt.maxit + 2));
   FETI_TRY(dev_alloc(ctx, &ctx->d_beta_hist, ctx->opt.maxit + 2));
   FETI_TRY(dev_alloc(ctx, &ctx->d_sc, 1));
@@ -864,19 +867,22 @@ feti_status coarse_setup(feti_ctx* ctx) {
   return check_status(ctx, "coarse factorization");
 }
 
-// P v -> out (with optional partial dot with a, or the squared norm)
-void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool with_dot, const int* done) {
+// P v -> out (with optional partial dot with a, or the squared norm, into
+// partial, by default d_partial)
+void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool with_dot, const int* done,
+             double* partial = nullptr) {
   cudaStream_t st = ctx->stream;
+  if (!partial) partial = ctx->d_partial;
   if (ctx->cd == 0) {
     // no coarse space: out = v (the expand kernel with c unused)
-    feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, ctx->d_partial, with_dot, done, st);
+    feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, partial, with_dot, done, st);
     return;
   }
   feti::launch_gtv_part(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_lay, ctx->d_R, ctx->maps, v,
                         ctx->d_gpart, done, st);
   feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
                                  ctx->d_lay, ctx->d_c, done, st);
-  feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, ctx->d_partial, with_dot, done, st);
+  feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, partial, with_dot, done, st);
 }
 
 // Signed gather of x (weights wv or none) and the dense local apply of F_i
@@ -954,18 +960,31 @@ feti_status autotune(feti_ctx* ctx) {
   return FETI_OK;
 }
 
+// One projected PCG iteration, 14 launches:
+//   z = M^-1 w (gather, local apply, scatter); y = P z with (w, y) partials
+//   (G^T z, coarse apply, expand); rho, beta and p = y + beta p in one kernel;
+//   q = F p with (p, q) partials; alpha, r -= alpha q, lam += alpha p fused
+//   into w = P r (G^T r, coarse apply, expand) with ||w||^2 partials;
+//   stopping test.  Separate partial buffers keep readers and writers of one
+//   launch apart.
 void pcg_iteration(feti_ctx* ctx, double* lam, bool f32) {
   cudaStream_t st = ctx->stream;
   const int* done = &ctx->d_sc->done;
   const int nl = (int)ctx->n_lambda;
-  apply_M(ctx, ctx->d_w, ctx->d_z, done, f32);                  // z = M^-1 w
-  project(ctx, ctx->d_z, ctx->d_y, ctx->d_w, true, done);         // y = P z, (w, y)
-  feti::launch_ctl_rho(ctx->d_sc, ctx->d_partial, ctx->d_beta_hist, st);
-  feti::launch_axpby(nl, ctx->d_p, ctx->d_y, ctx->d_sc, 0, st);   // p = y + beta p
-  apply_F(ctx, ctx->d_p, ctx->d_q, ctx->d_p, true, done, f32);    // q = F p, (p, q)
-  feti::launch_ctl_alpha(ctx->d_sc, ctx->d_partial, ctx->d_alpha_hist, st);
-  feti::launch_update_lr(nl, lam, ctx->d_r, ctx->d_p, ctx->d_q, ctx->d_sc, st);
-  project(ctx, ctx->d_r, ctx->d_w, nullptr, true, done);          // w = P r, ||w||^2
+  apply_M(ctx, ctx->d_w, ctx->d_z, done, f32);                                   // z = M^-1 w
+  project(ctx, ctx->d_z, ctx->d_y, ctx->d_w, true, done, ctx->d_partial_wy);      // y = P z
+  feti::launch_axpby_rho(nl, ctx->d_p, ctx->d_y, ctx->d_sc, ctx->d_partial_wy, ctx->d_beta_hist, st);
+  local_apply(ctx, 0, ctx->d_p, nullptr, done, f32);                              // q = F p, (p, q)
+  feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, ctx->d_q, ctx->d_p, ctx->d_partial_pq, done, st);
+  if (ctx->cd > 0) {
+    feti::launch_gtv_part(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_lay, ctx->d_R, ctx->maps,
+                          ctx->d_r, ctx->d_gpart, done, st, ctx->d_q, ctx->d_partial_pq, ctx->d_sc,
+                          ctx->d_alpha_hist);
+    feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
+                                   ctx->d_lay, ctx->d_c, done, st);
+  }
+  feti::launch_expand_update(ctx->maps, ctx->d_lay, ctx->d_R, ctx->d_r, ctx->d_c, ctx->d_w, ctx->d_partial, lam,
+                             ctx->d_p, ctx->d_q, ctx->d_partial_pq, ctx->d_sc, ctx->d_alpha_hist, st);
   feti::launch_ctl_conv(ctx->d_sc, ctx->d_partial, 0, st);
 }
 

@@ -106,14 +106,10 @@ void launch_gtg(int n_blocks, const int32_t* blk_i, const int32_t* blk_j, const 
 struct PcgScalars {
   double rho, rho_prev, alpha, beta, pq, wnorm0, wnorm, tol;
   int it, done, status, maxit;
+  double rho_slot[2];  // rho of the last two iterations, by parity
 };
 int scatter_partials();  // number of partial sums the row kernels produce
-void launch_ctl_rho(PcgScalars* s, const double* partial, double* beta_hist, cudaStream_t st);
-void launch_ctl_alpha(PcgScalars* s, const double* partial, double* alpha_hist, cudaStream_t st);
 void launch_ctl_conv(PcgScalars* s, const double* partial, int first, cudaStream_t st);
-void launch_axpby(int n, double* y, const double* x, const PcgScalars* s, int mode, cudaStream_t st);
-void launch_update_lr(int n, double* lam, double* r, const double* p, const double* q, const PcgScalars* s,
-                      cudaStream_t st);
 void launch_vsub(int n, const double* a, const double* b, double* out, cudaStream_t st);
 
 // Global displacement by the owner rule.
@@ -161,9 +157,20 @@ void launch_vadd(int n, double* a, const double* b, cudaStream_t st);
 namespace feti {
 // G^T x over chunks of 256 boundary positions of the subdomains with k > 0:
 // partial[6 c + a] for chunk c.
+// With q != NULL the gathered input is x - alpha q (fused CG update, alpha
+// from the (p, q) partial sums; CTA 0 stores alpha in sc and alpha_hist).
 void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const SubLayout* lay,
                      const double* R, const Maps& mp, const double* x, double* partial, const int* done,
-                     cudaStream_t st);
+                     cudaStream_t st, const double* q = nullptr, const double* pq_partial = nullptr,
+                     PcgScalars* sc = nullptr, double* alpha_hist = nullptr);
+// Fused CG update + projection expand: r -= alpha q, lam += alpha p in place,
+// out = r - G c, partial sums of ||out||^2.
+void launch_expand_update(const Maps& mp, const SubLayout* lay, const double* R, double* r, const double* c,
+                          double* out, double* partial, double* lam, const double* p, const double* q,
+                          const double* pq_partial, PcgScalars* sc, double* alpha_hist, cudaStream_t st);
+// Fused CG step: rho from partial sums, beta, p = y + beta p.
+void launch_axpby_rho(int n, double* p, const double* y, PcgScalars* s, const double* partial, double* beta_hist,
+                      cudaStream_t st);
 // c = Ginv (sum of chunk partials per coarse column).
 void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial, const int32_t* sub_chunk_ptr,
                               const int32_t* col_sub, const SubLayout* lay, double* c, const int* done,

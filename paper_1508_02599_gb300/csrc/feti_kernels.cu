@@ -765,16 +765,41 @@ __global__ void __launch_bounds__(kThreads) k_gtv(const SubLayout* __restrict__ 
   }
 }
 
+__device__ double reduce_partials(const double* partial, double* red) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < kPartials; i += blockDim.x) t += partial[i];
+  return block_sum(t, red);
+}
+
 // G^T x split over chunks of 256 boundary positions (many CTAs per
 // subdomain): partial[c*6 + a] = sum over the chunk of R_b[p][a] (B^T x)[p].
+// With q != NULL the input is the updated residual x - alpha q, alpha =
+// rho / (p, q) evaluated by every CTA from the partial sums of (p, q) (the
+// fused CG step); CTA 0 records alpha and flags a breakdown.
 __global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict__ chunk_sub,
                                                        const int32_t* __restrict__ chunk_p0,
                                                        const SubLayout* __restrict__ lay,
                                                        const double* __restrict__ R, Maps mp,
                                                        const double* __restrict__ x, double* __restrict__ partial,
-                                                       const int* __restrict__ done) {
+                                                       const int* __restrict__ done, const double* __restrict__ q,
+                                                       const double* __restrict__ pq_partial, PcgScalars* sc,
+                                                       double* __restrict__ alpha_hist) {
   if (*done) return;
   __shared__ double red[32];
+  double alpha = 0.0;
+  if (q) {
+    const double pq = reduce_partials(pq_partial, red);
+    alpha = sc->rho / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        sc->status = DEV_BREAKDOWN;
+        sc->done = 1;
+      }
+      sc->alpha = alpha;
+      sc->pq = pq;
+      alpha_hist[sc->it] = alpha;
+    }
+  }
   const int c = blockIdx.x;
   const SubLayout L = lay[chunk_sub[c]];
   const int nb = L.nbp + L.k;
@@ -783,7 +808,10 @@ __global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict
   if (p < nb) {
     const int gp = L.boff + p;
     double val = 0.0;
-    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) val += mp.bt_sgn[e] * x[mp.bt_row[e]];
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+      const int row = mp.bt_row[e];
+      val += mp.bt_sgn[e] * (q ? x[row] - alpha * q[row] : x[row]);
+    }
     const double* Rr = R + L.roff + (size_t)(L.nI + p) * L.k;
     for (int a = 0; a < L.k; ++a) acc[a] = Rr[a] * val;
   }
@@ -834,16 +862,49 @@ __global__ void k_coarse_apply(int cd, const double* __restrict__ Ginv, const do
   }
 }
 
+// Fused CG update (upd != NULL): r <- r - alpha q and lam <- lam + alpha p
+// in place (alpha = rho / (p, q) from the partial sums), then out = r - G c.
+struct ExpandUpdate {
+  double* r;
+  double* lam;
+  const double* p;
+  const double* q;
+  const double* pq_partial;
+  PcgScalars* sc;
+  double* alpha_hist;
+};
+
 __global__ void __launch_bounds__(kThreads) k_expand(Maps mp, const SubLayout* __restrict__ lay,
                                                      const double* __restrict__ R, const double* __restrict__ v,
                                                      const double* __restrict__ c, double* __restrict__ out,
                                                      const double* __restrict__ a, double* __restrict__ partial,
-                                                     int with_dot, const int* __restrict__ done) {
+                                                     int with_dot, const int* __restrict__ done, ExpandUpdate upd) {
   if (*done) return;
   __shared__ double red[32];
+  double alpha = 0.0;
+  if (upd.r) {
+    const double pq = reduce_partials(upd.pq_partial, red);
+    alpha = upd.sc->rho / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        upd.sc->status = DEV_BREAKDOWN;
+        upd.sc->done = 1;
+      }
+      upd.sc->alpha = alpha;
+      upd.sc->pq = pq;
+      upd.alpha_hist[upd.sc->it] = alpha;
+    }
+  }
   double dot = 0.0;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mp.n_lambda; r += gridDim.x * blockDim.x) {
-    double val = v[r];
+    double val;
+    if (upd.r) {
+      val = upd.r[r] - alpha * upd.q[r];
+      upd.r[r] = val;
+      upd.lam[r] += alpha * upd.p[r];
+    } else {
+      val = v[r];
+    }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int gp = mp.row_pos[2 * r + e];
@@ -895,45 +956,6 @@ __global__ void k_gtg(const int32_t* __restrict__ blk_i, const int32_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-__device__ double reduce_partials(const double* partial, double* red) {
-  double t = 0.0;
-  for (int i = threadIdx.x; i < kPartials; i += blockDim.x) t += partial[i];
-  return block_sum(t, red);
-}
-
-__global__ void k_ctl_rho(PcgScalars* s, const double* __restrict__ partial, double* beta_hist) {
-  if (s->done) return;
-  __shared__ double red[32];
-  const double rho = reduce_partials(partial, red);
-  if (threadIdx.x == 0) {
-    if (!(rho > 0.0) || !isfinite(rho)) {
-      s->status = DEV_BREAKDOWN;
-      s->done = 1;
-      return;
-    }
-    const double beta = s->it > 0 ? rho / s->rho_prev : 0.0;
-    s->beta = beta;
-    s->rho = rho;
-    s->rho_prev = rho;
-    beta_hist[s->it] = beta;
-  }
-}
-
-__global__ void k_ctl_alpha(PcgScalars* s, const double* __restrict__ partial, double* alpha_hist) {
-  if (s->done) return;
-  __shared__ double red[32];
-  const double pq = reduce_partials(partial, red);
-  if (threadIdx.x == 0) {
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      s->status = DEV_BREAKDOWN;
-      s->done = 1;
-      return;
-    }
-    s->pq = pq;
-    s->alpha = s->rho / pq;
-    alpha_hist[s->it] = s->alpha;
-  }
-}
 
 __global__ void k_ctl_conv(PcgScalars* s, const double* __restrict__ partial, int first) {
   if (s->done) return;
@@ -961,21 +983,29 @@ __global__ void k_ctl_conv(PcgScalars* s, const double* __restrict__ partial, in
   }
 }
 
-__global__ void k_axpby(int n, double* __restrict__ p, const double* __restrict__ y, const PcgScalars* s, int mode) {
+// Fused CG step: rho = (w, y) from the partial sums (every CTA), beta =
+// rho / rho_prev (rho_prev kept in the slot of the previous iteration's
+// parity), p = y + beta p; CTA 0 records rho and beta and flags a breakdown.
+__global__ void __launch_bounds__(kThreads) k_axpby_rho(int n, double* __restrict__ p, const double* __restrict__ y,
+                                                        PcgScalars* s, const double* __restrict__ partial,
+                                                        double* __restrict__ beta_hist) {
   if (s->done) return;
-  const double beta = s->beta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    p[i] = (mode == 0 && s->it > 0) ? y[i] + beta * p[i] : y[i];
-}
-
-__global__ void k_update_lr(int n, double* __restrict__ lam, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, const PcgScalars* s) {
-  if (s->done) return;
-  const double alpha = s->alpha;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    lam[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
+  __shared__ double red[32];
+  const double rho = reduce_partials(partial, red);
+  const int it = s->it;
+  const double beta = it > 0 ? rho / s->rho_slot[(it + 1) & 1] : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!(rho > 0.0) || !isfinite(rho)) {
+      s->status = DEV_BREAKDOWN;
+      s->done = 1;
+    }
+    s->rho_slot[it & 1] = rho;
+    s->rho = rho;
+    s->beta = beta;
+    beta_hist[it] = beta;
   }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = it > 0 ? y[i] + beta * p[i] : y[i];
 }
 
 __global__ void k_vsub(int n, const double* a, const double* b, double* out) {
@@ -1121,7 +1151,7 @@ void launch_coarse_apply(int cd, const double* Ginv, const double* g, double* c,
 void launch_expand(const Maps& mp, const SubLayout* lay, const double* R, const double* v, const double* c,
                    double* out, const double* a, double* partial, int with_dot, const int* done,
                    cudaStream_t st) {
-  k_expand<<<kPartials, kThreads, 0, st>>>(mp, lay, R, v, c, out, a, partial, with_dot, done);
+  k_expand<<<kPartials, kThreads, 0, st>>>(mp, lay, R, v, c, out, a, partial, with_dot, done, ExpandUpdate{});
 }
 
 void launch_gtg(int n_blocks, const int32_t* blk_i, const int32_t* blk_j, const int32_t* blk_ptr,
@@ -1131,21 +1161,8 @@ void launch_gtg(int n_blocks, const int32_t* blk_i, const int32_t* blk_j, const 
   k_gtg<<<n_blocks, 64, 0, st>>>(blk_i, blk_j, blk_ptr, blk_rows, lay, R, mp, cd, GtG);
 }
 
-void launch_ctl_rho(PcgScalars* s, const double* partial, double* beta_hist, cudaStream_t st) {
-  k_ctl_rho<<<1, kThreads, 0, st>>>(s, partial, beta_hist);
-}
-void launch_ctl_alpha(PcgScalars* s, const double* partial, double* alpha_hist, cudaStream_t st) {
-  k_ctl_alpha<<<1, kThreads, 0, st>>>(s, partial, alpha_hist);
-}
 void launch_ctl_conv(PcgScalars* s, const double* partial, int first, cudaStream_t st) {
   k_ctl_conv<<<1, kThreads, 0, st>>>(s, partial, first);
-}
-void launch_axpby(int n, double* y, const double* x, const PcgScalars* s, int mode, cudaStream_t st) {
-  k_axpby<<<grid_for(n), kThreads, 0, st>>>(n, y, x, s, mode);
-}
-void launch_update_lr(int n, double* lam, double* r, const double* p, const double* q, const PcgScalars* s,
-                      cudaStream_t st) {
-  k_update_lr<<<grid_for(n), kThreads, 0, st>>>(n, lam, r, p, q, s);
 }
 void launch_vsub(int n, const double* a, const double* b, double* out, cudaStream_t st) {
   k_vsub<<<grid_for(n), kThreads, 0, st>>>(n, a, b, out);
@@ -1216,9 +1233,23 @@ void launch_vadd(int n, double* a, const double* b, cudaStream_t st) {
 
 void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const SubLayout* lay,
                      const double* R, const Maps& mp, const double* x, double* partial, const int* done,
-                     cudaStream_t st) {
+                     cudaStream_t st, const double* q, const double* pq_partial, PcgScalars* sc,
+                     double* alpha_hist) {
   if (n_chunks <= 0) return;
-  k_gtv_part<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, x, partial, done);
+  k_gtv_part<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, x, partial, done, q, pq_partial, sc,
+                                            alpha_hist);
+}
+
+void launch_expand_update(const Maps& mp, const SubLayout* lay, const double* R, double* r, const double* c,
+                          double* out, double* partial, double* lam, const double* p, const double* q,
+                          const double* pq_partial, PcgScalars* sc, double* alpha_hist, cudaStream_t st) {
+  ExpandUpdate u{r, lam, p, q, pq_partial, sc, alpha_hist};
+  k_expand<<<kPartials, kThreads, 0, st>>>(mp, lay, R, r, c, out, nullptr, partial, 1, &sc->done, u);
+}
+
+void launch_axpby_rho(int n, double* p, const double* y, PcgScalars* s, const double* partial, double* beta_hist,
+                      cudaStream_t st) {
+  k_axpby_rho<<<grid_for(n), kThreads, 0, st>>>(n, p, y, s, partial, beta_hist);
 }
 
 void launch_coarse_apply_part(int cd, const double* Ginv, const double* partial, const int32_t* sub_chunk_ptr,

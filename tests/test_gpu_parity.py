@@ -227,3 +227,24 @@ def test_jittered_uneven_partition_matches_oracle(precision):
     assert np.array_equal(m["row_sub"], o.maps.row_sub) and np.array_equal(m["row_ldof"], o.maps.row_ldof)
     assert rep["converged"] == 1
     assert np.linalg.norm(U - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
+
+
+@pytest.mark.slow
+def test_full_size_jittered_1024_subdomains():
+    """1024 uneven subdomains (jittered tube 32x128x64), both forms: the
+    equilibrium residual of the assembled system (oracle element route) and
+    agreement of the FP32-local form with the FP64 form."""
+    prob = mesh.config_problem("jcyl32")
+    with _solver(prob, "af", "dirichlet", tol=1e-10, maxit=3000) as s:
+        U64, rep64 = s.solve()
+    with _solver(prob, "af", "dirichlet", tol=1e-10, maxit=6000, precision="mixed") as s:
+        U32, rep32 = s.solve()
+    assert rep64["converged"] == 1 and rep32["converged"] == 1
+    assert rep64["coarse_dim"] == 6 * 1024
+    Ke, _ = fem.element_matrices(prob)
+    K = fem.assemble_global(prob, Ke)
+    f = fem.load_vector(prob)
+    free = np.ones(K.shape[0], bool)
+    free[prob.dir_dof] = False
+    assert np.linalg.norm((K @ U64 - f)[free]) <= 1e-7 * np.linalg.norm(f[free])
+    assert np.linalg.norm(U32 - U64) <= 1e-8 * np.linalg.norm(U64)
