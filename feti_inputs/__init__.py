@@ -9,7 +9,7 @@ cube cut into sub-cubes (Sec. 5.1) and a thick-walled tube under internal
 pressure standing in for the artery segments of Sec. 5.2 (Table 1 material).
 """
 from .mesh import (Problem, cube_problem, cylinder_problem, config_problem,
-                   jittered_cylinder_problem)
+                   jittered_cylinder_problem, kelvin_cube_problem, kelvin_displacement)
 
 __all__ = ["Problem", "cube_problem", "cylinder_problem", "config_problem",
-           "jittered_cylinder_problem"]
+           "jittered_cylinder_problem", "kelvin_cube_problem", "kelvin_displacement"]

@@ -173,6 +173,46 @@ def cube_problem(n: int = 12, parts=(2, 2, 2), E: float = 1.0, nu: float = 0.3,
         material=linear_material(E, nu), meta={"cells": (n, n, n), "parts": tuple(parts)})
 
 
+def kelvin_displacement(x: np.ndarray, E: float, nu: float, x_star=(-0.5, -0.5, -0.5)) -> np.ndarray:
+    """Kelvin's fundamental solution for a unit point force along x_1 at x_star.
+
+    U_k = (1+nu)/(8 pi E (1-nu)) * [(3-4nu) delta_1k / rho + (x_1-x_1*)(x_k-x_k*) / rho^3],
+    rho = |x - x_star| (Sec. 5.1, Eq. fundSol, with its index l read as k).
+    Boundary data of the cube study; x_star lies outside the unit cube.
+    """
+    d = x - np.asarray(x_star, dtype=np.float64)[None, :]
+    rho = np.linalg.norm(d, axis=1)
+    c = (1.0 + nu) / (8.0 * math.pi * E * (1.0 - nu))
+    u = c * d[:, 0:1] * d / rho[:, None] ** 3
+    u[:, 0] += c * (3.0 - 4.0 * nu) / rho
+    return u
+
+
+def kelvin_cube_problem(n: int = 16, parts=(8, 8, 8), E: float = 210.0, nu: float = 0.45,
+                        x_star=(-0.5, -0.5, -0.5)) -> Problem:
+    """Unit cube, n^3 cells, Dirichlet data of Kelvin's solution on the whole surface.
+
+    The shape of the linear cube study of Sec. 5.1 (E = 210, nu = 0.45,
+    Gamma_D = boundary, 8 x 8 x 8 = 512 sub-cubes); no loads.
+    """
+    base = cube_problem(n, parts, E=E, nu=nu)
+    m = n + 1
+    idx = np.arange(base.n_nodes)
+    i, j, k = idx % m, (idx // m) % m, idx // (m * m)
+    on_b = (i == 0) | (i == n) | (j == 0) | (j == n) | (k == 0) | (k == n)
+    bn = np.nonzero(on_b)[0]
+    uD = kelvin_displacement(base.coords[bn], E, nu, x_star)
+    dof = (3 * bn[:, None] + np.arange(3)[None, :]).ravel()
+    order = np.argsort(dof)
+    e_tri, e_own = _empty_tri()
+    return Problem(
+        name=f"kelvin{n}_p{parts[0]}x{parts[1]}x{parts[2]}", coords=base.coords, tets=base.tets, part=base.part,
+        n_parts=base.n_parts, dir_dof=dof[order].astype(np.int32), dir_val=uD.ravel()[order],
+        press_tri=e_tri, press_owner=e_own, pressure=0.0, trac_tri=e_tri.copy(), trac_owner=e_own.copy(),
+        traction=np.zeros(3), material=linear_material(E, nu),
+        meta={"cells": (n, n, n), "parts": tuple(parts), "x_star": tuple(x_star)})
+
+
 def _cylinder_nodes(nr, nt, nz, r_in, r_out, length, jitter, rng):
     ii, jj, kk = np.meshgrid(np.arange(nr + 1), np.arange(nt), np.arange(nz + 1), indexing="ij")
     ii = ii.transpose(2, 1, 0).ravel().astype(np.float64)

@@ -85,6 +85,10 @@ struct feti_ctx {
   int32_t *d_chunk_sub = nullptr, *d_chunk_p0 = nullptr, *d_sub_chunk_ptr = nullptr, *d_col_sub = nullptr;
   double* d_gpart = nullptr;
   int32_t *d_gs_ptr = nullptr, *d_gs_pos = nullptr, *d_dir_dof = nullptr;
+  int32_t *d_lump_ptr = nullptr, *d_lump_col = nullptr;
+  int64_t* d_lump_src = nullptr;
+  double* d_lump_val = nullptr;
+  int64_t lump_nnz = 0;
   int n_gs = 0;
   double *d_dU = nullptr, *d_Utrial = nullptr, *d_fl = nullptr;
   std::vector<double> h_partial;
@@ -532,6 +536,40 @@ feti_status build_decomposition(feti_ctx* ctx) {
       }
     }
   }
+  // lumped preconditioner: CSR pattern of K_bb over the global boundary
+  // positions, from the boundary DOF pairs that share an element
+  std::vector<int32_t> lump_ptr, lump_col;
+  std::vector<int64_t> lump_src;
+  if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    std::vector<std::vector<int32_t>> rows(ctx->nb_total);
+    for (int e = 0; e < E; ++e) {
+      const SubLayout& L = ctx->lay[ctx->part[e]];
+      int bp[12], nbq = 0;
+      for (int a = 0; a < 12; ++a) {
+        const int di = elem_dense[12 * (size_t)e + a];
+        if (di >= L.nI) bp[nbq++] = di - L.nI;
+      }
+      for (int x = 0; x < nbq; ++x)
+        for (int y = 0; y < nbq; ++y) rows[L.boff + bp[x]].push_back(L.boff + bp[y]);
+    }
+    lump_ptr.assign(1, 0);
+    for (int s = 0; s < P; ++s) {
+      const SubLayout& L = ctx->lay[s];
+      for (int p = 0; p < L.nbp + L.k; ++p) {
+        auto& r = rows[L.boff + p];
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+        for (int gq : r) {
+          const int q = gq - L.boff;
+          const int i = std::max(p, q), j = std::min(p, q);
+          lump_col.push_back(gq);
+          lump_src.push_back(L.aoff + (int64_t)(L.nI + i) * L.ld + (L.nI + j));
+        }
+        lump_ptr.push_back((int32_t)lump_col.size());
+      }
+    }
+    ctx->lump_nnz = (int64_t)lump_col.size();
+  }
   // faces grouped by owning subdomain
   const int nf = ctx->n_press + ctx->n_trac;
   std::vector<int32_t> sub_face_ptr(P + 1, 0), face_order(nf), face_dense(9 * (size_t)nf, -1);
@@ -707,6 +745,12 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_R, Rall));
   FETI_TRY(upload(ctx, &ctx->d_own_gdof, own_gdof));
   FETI_TRY(upload(ctx, &ctx->d_gs_ptr, gs_ptr));
+  if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    FETI_TRY(upload(ctx, &ctx->d_lump_ptr, lump_ptr));
+    FETI_TRY(upload(ctx, &ctx->d_lump_col, lump_col));
+    FETI_TRY(upload(ctx, &ctx->d_lump_src, lump_src));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_lump_val, ctx->lump_nnz));
+  }
   FETI_TRY(upload(ctx, &ctx->d_dir_dof, ctx->dir_dof));
   FETI_TRY(upload(ctx, &ctx->d_gs_pos, gs_pos));
   FETI_TRY(upload(ctx, &ctx->d_own_vpos, own_vpos));
@@ -723,11 +767,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_fl, ctx->nloc_total));
   }
   FETI_TRY(dev_alloc(ctx, &ctx->d_A, aoff));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_S, soff));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_S, ctx->opt.precond == FETI_PREC_DIRICHLET ? soff : 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_F, foff));
   if (ctx->opt.precision == FETI_MIXED) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_F32, foff32));
-    FETI_TRY(dev_alloc(ctx, &ctx->d_S32, soff32));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_S32, ctx->opt.precond == FETI_PREC_DIRICHLET ? soff32 : 1));
   }
   FETI_TRY(dev_alloc(ctx, &ctx->d_f, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x, ctx->nloc_total));
@@ -834,14 +878,15 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
 // Local factorizations, dense local operators, coarse problem.
 feti_status factorize_all(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
-  if (ctx->opt.precond == FETI_PREC_LUMPED) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
+  if (ctx->opt.precond == FETI_PREC_LUMPED)
+    feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
   feti::launch_chol_partial(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_status, st);
   if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
   feti::launch_chol_partial(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_status, st);
   feti::launch_extract(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_F, st);
   if (ctx->opt.precision == FETI_MIXED) {
     feti::launch_to_f32(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32, st);
-    if (ctx->opt.precond != FETI_PREC_IDENTITY) feti::launch_to_f32(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32, st);
+    if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_to_f32(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32, st);
   }
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_status(ctx, "local factorization"));
@@ -909,10 +954,15 @@ void apply_F(feti_ctx* ctx, const double* x, double* q, const double* a, bool wi
 
 // z = M^-1 w = W B Y B^T W w.
 void apply_M(feti_ctx* ctx, const double* w, double* z, const int* done, bool f32 = false) {
-  if (ctx->opt.precond == FETI_PREC_IDENTITY)
+  if (ctx->opt.precond == FETI_PREC_IDENTITY) {
     feti::launch_gather(ctx->maps, w, ctx->d_weight, ctx->d_loc, done, ctx->stream);
-  else
+  } else if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    feti::launch_gather(ctx->maps, w, ctx->d_weight, ctx->d_vloc, done, ctx->stream);
+    feti::launch_spmv_lump((int)ctx->nb_total, ctx->d_lump_ptr, ctx->d_lump_col, ctx->d_lump_val, ctx->d_vloc,
+                           ctx->d_loc, done, ctx->stream);
+  } else {
     local_apply(ctx, 1, w, ctx->d_weight, done, f32);
+  }
   feti::launch_scatter(ctx->maps, ctx->d_loc, ctx->d_weight, z, nullptr, nullptr, done, ctx->stream);
 }
 
@@ -930,7 +980,7 @@ feti_status autotune(feti_ctx* ctx) {
   for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
     const bool f32 = prec == 1;
     for (int w = 0; w < 2; ++w) {
-      if (w == 1 && ctx->opt.precond == FETI_PREC_IDENTITY) continue;
+      if (w == 1 && ctx->opt.precond != FETI_PREC_DIRICHLET) continue;
       const void* M = f32 ? (w == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
                           : (w == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
       const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;

@@ -195,3 +195,12 @@ namespace feti {
 // (leading dimension ld): columns [c0, c1), trailing update on [c1, n_act).
 void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int* status, cudaStream_t st);
 }  // namespace feti
+
+namespace feti {
+// Lumped preconditioner K_bb (Sec. 4.4, Eq. LumpedVK) in CSR over the
+// boundary positions: values gathered from the assembled local matrices,
+// then y = K_bb v (one warp per row).
+void launch_lump_fill(long nnz, const int64_t* src, const double* A, double* val, cudaStream_t st);
+void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const double* val, const double* v,
+                      double* y, const int* done, cudaStream_t st);
+}  // namespace feti

@@ -1452,4 +1452,43 @@ void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int* st
   }
 }
 
+namespace {
+// Lumped preconditioner block K_bb in CSR over the boundary positions:
+// values gathered from the assembled (unfactorized) local matrices.
+__global__ void k_lump_fill(long nnz, const int64_t* __restrict__ src, const double* __restrict__ A,
+                            double* __restrict__ val) {
+  for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < nnz; j += (long)gridDim.x * blockDim.x)
+    val[j] = A[src[j]];
+}
+
+// y = K_bb v on every subdomain's boundary positions, one warp per row.
+__global__ void __launch_bounds__(kThreads) k_spmv_lump(int n_rows, const int32_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ v, double* __restrict__ y,
+                                                        const int* __restrict__ done) {
+  if (*done) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < n_rows; r += nwarps) {
+    double acc = 0.0;
+    for (int j = ptr[r] + lane; j < ptr[r + 1]; j += 32) acc += val[j] * v[col[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = acc;
+  }
+}
+}  // namespace
+
+void launch_lump_fill(long nnz, const int64_t* src, const double* A, double* val, cudaStream_t st) {
+  if (nnz <= 0) return;
+  k_lump_fill<<<grid_for(nnz), kThreads, 0, st>>>(nnz, src, A, val);
+}
+
+void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const double* val, const double* v,
+                      double* y, const int* done, cudaStream_t st) {
+  const int warps = n_rows < 65536 ? n_rows : 65536;
+  k_spmv_lump<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n_rows, ptr, col, val, v, y, done);
+}
+
 }  // namespace feti
