@@ -880,9 +880,23 @@ feti_status factorize_all(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   if (ctx->opt.precond == FETI_PREC_LUMPED)
     feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
-  feti::launch_chol_partial(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_status, st);
+  // per step, the largest trailing chunk count over the subdomains
+  std::vector<int> chunks[2];
+  for (int phase = 0; phase < 2; ++phase)
+    for (const auto& L : ctx->lay) {
+      const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp, na = phase == 0 ? L.n : L.ld;
+      for (int t = 0, kb = c0; kb < c1; ++t, kb += 32) {
+        const int r0 = kb + std::min(32, c1 - kb);
+        const int ch = (na - r0 + 63) / 64;
+        if ((int)chunks[phase].size() <= t) chunks[phase].push_back(0);
+        chunks[phase][t] = std::max(chunks[phase][t], ch);
+      }
+    }
+  feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_A, ctx->d_status,
+                            st);
   if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
-  feti::launch_chol_partial(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_status, st);
+  feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), ctx->d_A, ctx->d_status,
+                            st);
   feti::launch_extract(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_F, st);
   if (ctx->opt.precision == FETI_MIXED) {
     feti::launch_to_f32(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32, st);

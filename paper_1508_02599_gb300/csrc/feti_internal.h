@@ -204,3 +204,14 @@ void launch_lump_fill(long nnz, const int64_t* src, const double* A, double* val
 void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const double* val, const double* v,
                       double* y, const int* done, cudaStream_t st);
 }  // namespace feti
+
+namespace feti {
+// Batched multi-CTA partial Cholesky of every subdomain's dense matrix, one
+// launch triple (diagonal block, panel solve, tiled trailing update) per
+// 32-column step; phase 0: interior columns, phase 1: boundary minus fixing
+// columns (see launch_chol_partial).  step_chunks[t] (host array, n_steps
+// entries): the largest number of 64-row trailing chunks over the subdomains
+// at step t (idle CTAs exit at once).
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps, double* A,
+                         int* status, cudaStream_t st);
+}  // namespace feti

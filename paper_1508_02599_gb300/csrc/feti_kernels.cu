@@ -1491,4 +1491,180 @@ void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const 
   k_spmv_lump<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n_rows, ptr, col, val, v, y, done);
 }
 
+namespace {
+// Batched multi-CTA partial Cholesky: one launch per block-column step for
+// all subdomains together (blockIdx.y = subdomain).  Phase 0 eliminates the
+// interior columns [0, nI) with trailing rows/cols [.., n); phase 1 the
+// boundary columns [nI, nI + nbp) with trailing rows/cols [.., ld).
+struct PhaseRange {
+  int c0, c1, na;
+};
+__device__ __forceinline__ PhaseRange phase_range(const SubLayout& L, int phase) {
+  return phase == 0 ? PhaseRange{0, L.nI, L.n} : PhaseRange{L.nI, L.nI + L.nbp, L.ld};
+}
+
+__global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
+                           int* status) {
+  const SubLayout L = lay[blockIdx.y];
+  const PhaseRange pr = phase_range(L, phase);
+  const int kb = pr.c0 + step * NB;
+  if (kb >= pr.c1) return;
+  const int nk = min(NB, pr.c1 - kb);
+  double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  __shared__ double D[NB][NB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int i = tid;
+    for (int j = 0; j < nk; ++j) {
+      if (i == j) {
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        D[j][j] = sqrt(d);
+      }
+      __syncwarp();
+      if (bad) break;
+      if (i > j && i < nk) D[i][j] /= D[j][j];
+      __syncwarp();
+      if (i > j && i < nk)
+        for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) set_status(status, DEV_LOCAL_SINGULAR);
+    return;
+  }
+  for (int idx = tid; idx < nk * nk; idx += blockDim.x) {
+    const int i = idx / nk, j = idx % nk;
+    if (j <= i) A[(kb + i) * ld + kb + j] = D[i][j];
+  }
+}
+
+__global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
+                           const int* status) {
+  if (*status) return;
+  const SubLayout L = lay[blockIdx.y];
+  const PhaseRange pr = phase_range(L, phase);
+  const int kb = pr.c0 + step * NB;
+  if (kb >= pr.c1) return;
+  const int nk = min(NB, pr.c1 - kb);
+  const int base = kb + nk + blockIdx.x * TT;
+  if (base >= pr.na) return;
+  const int nr = min(TT, pr.na - base);
+  double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  __shared__ double D[NB][NB + 1];
+  __shared__ double Pa[TT][NB + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+  }
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    Pa[r][l] = (r < nr && l < nk) ? A[(base + r) * ld + kb + l] : 0.0;
+  }
+  __syncthreads();
+  if (tid < nr) {
+    double xr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < nk) {
+        double v = xr[j];
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+          if (l < j) v -= xr[l] * D[j][l];
+        xr[j] = v / D[j][j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) Pa[tid][j] = xr[j];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    if (r < nr && l < nk) A[(base + r) * ld + kb + l] = Pa[r][l];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __restrict__ lay, int phase, int step,
+                                                         double* __restrict__ Abase, const int* status) {
+  if (*status) return;
+  const SubLayout L = lay[blockIdx.y];
+  const PhaseRange pr = phase_range(L, phase);
+  const int kb = pr.c0 + step * NB;
+  if (kb >= pr.c1) return;
+  const int nk = min(NB, pr.c1 - kb);
+  const int r0 = kb + nk;
+  const int chunks = (pr.na - r0 + TT - 1) / TT;
+  const long b = blockIdx.x;
+  if (b >= (long)chunks * (chunks + 1) / 2) return;
+  int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while ((long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+  while ((long)ti * (ti + 1) / 2 > b) --ti;
+  const int tj = (int)(b - (long)ti * (ti + 1) / 2);
+  const int ib = r0 + ti * TT, jb = r0 + tj * TT;
+  double* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  const int na = pr.na;
+  __shared__ double Pa[TT][NB + 1];
+  __shared__ double Pb[TT][NB + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
+    const int r = idx / NB, l = idx % NB;
+    Pa[r][l] = (ib + r < na && l < nk) ? A[(ib + r) * ld + kb + l] : 0.0;
+    Pb[r][l] = (jb + r < na && l < nk) ? A[(jb + r) * ld + kb + l] : 0.0;
+  }
+  __syncthreads();
+  const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+  for (int l = 0; l < nk; ++l) {
+    double av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      av[a] = Pa[tr + a][l];
+      bv[a] = Pb[tc + a][l];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] += av[a] * bv[c];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = ib + tr + a, j = jb + tc + c;
+      if (i < na && j < na && j <= i) A[i * ld + j] -= acc[a][c];
+    }
+}
+}  // namespace
+
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps, double* A,
+                         int* status, cudaStream_t st) {
+  for (int t = 0; t < n_steps; ++t) {
+    const int chunks = step_chunks[t];
+    k_bat_diag<<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    if (chunks <= 0) continue;
+    k_bat_trsm<<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    const long tiles = (long)chunks * (chunks + 1) / 2;
+    k_bat_update<<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+  }
+}
+
 }  // namespace feti
