@@ -147,6 +147,17 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
  * u_on_device says which).  report may be NULL. */
 feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report);
 
+/* Block form: nrhs (1..16) load cases at once, f_k = load_scale[k] * f (the
+ * pressure and traction loads scaled; Dirichlet data must be homogeneous).
+ * The nrhs projected CG recurrences share every operator apply: each dense
+ * local operator entry read from memory feeds nrhs products (a batched GEMM
+ * instead of a matvec).  A converged right-hand side is frozen while the
+ * others continue.  u_out: [nrhs][n_nodes*3], host or device.  report:
+ * iterations = shared iteration count (until the last right-hand side
+ * converged), summed over refinement passes for FETI_MIXED. */
+feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nrhs, double* u_out,
+                             int32_t u_on_device, feti_report* report);
+
 /* Nonlinear problem (Sec. 3.2, Eq. loadStepping): tau = s / n_load_steps,
  * Newton with one FETI solve per step until ||R|| <= newton_tol ||tau f_ext||.
  * Requires FETI_HGO_TWO_FIBRE.  Writes U [n_nodes*3] like feti_solve. */
@@ -192,6 +203,11 @@ feti_status feti_get_fixing(const feti_ctx* ctx, int32_t* fix_ptr, int32_t* fix_
  * device time per apply of this launch.  Returns after the launch completed. */
 feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z,
                             int32_t n_apply, double* ms_per_apply);
+
+/* Block benchmark hook: like feti_dual_apply on blocks v, q, z of
+ * [n_lambda][nrhs] doubles (row-major, nrhs contiguous per multiplier). */
+feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, double* z, int32_t nrhs,
+                                  int32_t n_apply, double* ms_per_apply);
 
 /* Runs the setup part of feti_solve (element matrices through coarse
  * factorization) without PCG. */

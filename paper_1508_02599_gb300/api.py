@@ -150,6 +150,27 @@ class FetiSolver:
             self._check(st)
         return u, self._report(rep)
 
+    def solve_multi(self, scales, out=None):
+        """Block solve of len(scales) load cases f_k = scales[k] * f; returns [nrhs, 3N]."""
+        sc = np.ascontiguousarray(scales, dtype=np.float64)
+        rep = L.FetiReport()
+        if out is None:
+            u = np.empty((sc.size, 3 * self.n_nodes), np.float64)
+            self._check(self._lib.feti_solve_multi(self._ctx, sc.ctypes.data, sc.size, u.ctypes.data, 0,
+                                                   C.byref(rep)))
+        else:
+            u = out
+            self._check(self._lib.feti_solve_multi(self._ctx, sc.ctypes.data, sc.size,
+                                                   C.c_void_p(out.data_ptr()), 1, C.byref(rep)))
+        return u, self._report(rep)
+
+    def dual_apply_multi(self, v, q, z, nrhs: int, n_apply: int) -> float:
+        ms = C.c_double()
+        self._check(self._lib.feti_dual_apply_multi(self._ctx, C.c_void_p(v.data_ptr()), C.c_void_p(q.data_ptr()),
+                                                    C.c_void_p(z.data_ptr()), int(nrhs), int(n_apply),
+                                                    C.byref(ms)))
+        return ms.value
+
     def solve_host(self, u_host):
         """feti_solve into a caller-owned host buffer (e.g. pinned torch tensor)."""
         rep = L.FetiReport()

@@ -117,6 +117,22 @@ struct feti_ctx {
   bool pcg_graph_mixed = false;
   double t_setup_ms = 0.0;
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
+  // block form (several right-hand sides)
+  int m_cap = 0;  // allocated nrhs capacity of the block buffers
+  double *dm_lam = nullptr, *dm_r = nullptr, *dm_w = nullptr, *dm_z = nullptr, *dm_y = nullptr, *dm_p = nullptr;
+  double *dm_q = nullptr, *dm_d = nullptr, *dm_dl = nullptr, *dm_loc = nullptr, *dm_vloc = nullptr;
+  float* dm_vloc32 = nullptr;
+  double *dm_part_wy = nullptr, *dm_part_pq = nullptr, *dm_part_ww = nullptr, *dm_gpart = nullptr;
+  double *dm_g = nullptr, *dm_c = nullptr, *dm_alpha_hist = nullptr;
+  feti::PcgScalarsM* dm_sc = nullptr;
+  feti::PcgScalarsM* hm_sc = nullptr;  // pinned
+  cudaGraphExec_t pcgm_graph = nullptr;
+  int pcgm_chunk = 0, pcgm_nrhs = 0;
+  bool pcgm_mixed = false;
+  cudaGraphExec_t dualm_graph = nullptr;
+  const double* dualm_v = nullptr;
+  int dualm_n = 0, dualm_nrhs = 0;
+  std::vector<cudaEvent_t> dualm_events;
   cudaGraphExec_t dual_graph = nullptr;
   const double* dual_v = nullptr;
   const double* dual_q = nullptr;
@@ -1119,12 +1135,11 @@ feti_status start_pcg(feti_ctx* ctx, double tol, int maxit) {
 // correction P F P delta = r is solved by PCG with the FP32 copies of F_i and
 // S_i (vectors, dots, projection and coarse solve stay FP64) to a relative
 // tolerance inner_tol, and lambda += delta, until ||r|| <= tol ||r_0||.
-feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
+// d~ = sum B K^+ f - b into d_d and lambda_0 = G (G^T G)^-1 e into d_lam.
+feti_status rhs_setup(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const int nl = (int)ctx->n_lambda;
   const int* zero = ctx->d_zero;
-  const bool mixed = ctx->opt.precision == FETI_MIXED;
-  // d~ = sum B K^+ f - b
   feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_f, ctx->d_x, st);
   feti::launch_take_boundary(ctx->P, ctx->d_lay, ctx->d_x, ctx->d_loc, st);
   feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, ctx->d_q, nullptr, nullptr, zero, st);
@@ -1138,6 +1153,15 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
                         zero, st);
   }
   FETI_CK(cudaGetLastError());
+  return FETI_OK;
+}
+
+feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
+  cudaStream_t st = ctx->stream;
+  const int nl = (int)ctx->n_lambda;
+  const int* zero = ctx->d_zero;
+  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  FETI_TRY(rhs_setup(ctx));
   cudaEvent_t e0, e1;
   FETI_CK(cudaEventCreate(&e0));
   FETI_CK(cudaEventCreate(&e1));
@@ -1220,6 +1244,249 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
   FETI_CK(cudaGetLastError());
   if (!conv) return fail(ctx, FETI_ERR_NOT_CONVERGED, "PCG reached maxit");
+  return FETI_OK;
+}
+
+feti_status write_displacement(feti_ctx* ctx, double* u_out, int on_device, double* d_target);
+
+// ---------------------------------------------------------------------------
+// Block form: nrhs right-hand sides share every operator apply.
+feti_status alloc_multi(feti_ctx* ctx, int nrhs) {
+  if (ctx->m_cap >= nrhs) return FETI_OK;
+  if (ctx->m_cap > 0) return fail(ctx, FETI_ERR_STATE, "block buffers were sized for fewer right-hand sides");
+  const size_t nl = (size_t)ctx->n_lambda * nrhs, nb = (size_t)ctx->nb_total * nrhs;
+  for (double** v : {&ctx->dm_lam, &ctx->dm_r, &ctx->dm_w, &ctx->dm_z, &ctx->dm_y, &ctx->dm_p, &ctx->dm_q, &ctx->dm_d,
+                     &ctx->dm_dl})
+    FETI_TRY(dev_alloc(ctx, v, nl));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_loc, nb));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_vloc, nb));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_vloc32, nb + 4));
+  const size_t np = (size_t)feti::scatter_partials() * feti::kMaxRhs;
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_part_wy, np));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_part_pq, np));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_part_ww, np));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_gpart, (size_t)std::max(ctx->n_chunks, 1) * 6 * nrhs));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_g, (size_t)std::max<int64_t>(ctx->cd, 1) * nrhs));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_c, (size_t)std::max<int64_t>(ctx->cd, 1) * nrhs));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_alpha_hist, (size_t)(ctx->opt.maxit + 2) * feti::kMaxRhs));
+  FETI_TRY(dev_alloc(ctx, &ctx->dm_sc, 1));
+  FETI_CK(cudaMallocHost(&ctx->hm_sc, sizeof(feti::PcgScalarsM)));
+  ctx->m_cap = nrhs;
+  return FETI_OK;
+}
+
+// Y = W B M B^T W X on blocks (which 0: F_i, no weights; which 1: preconditioner).
+void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const double* wv, const int* done, bool f32) {
+  cudaStream_t st = ctx->stream;
+  if (which == 1 && ctx->opt.precond == FETI_PREC_IDENTITY) {
+    feti::launch_gather_m(ctx->maps, nrhs, x, wv, ctx->dm_loc, 0, done, st);
+    return;
+  }
+  if (which == 1 && ctx->opt.precond == FETI_PREC_LUMPED) {
+    feti::launch_gather_m(ctx->maps, nrhs, x, wv, ctx->dm_vloc, 0, done, st);
+    feti::launch_spmv_lump_m((int)ctx->nb_total, nrhs, ctx->d_lump_ptr, ctx->d_lump_col, ctx->d_lump_val, ctx->dm_vloc,
+                             ctx->dm_loc, done, st);
+    return;
+  }
+  feti::GemvCfg cfg = ctx->tab[which][0];  // 32 rows per CTA: the block form has nrhs times the work per row
+  cfg.R = 2;
+  const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
+                      : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
+  void* v = f32 ? (void*)ctx->dm_vloc32 : (void*)ctx->dm_vloc;
+  feti::launch_gather_m(ctx->maps, nrhs, x, wv, v, f32 ? 1 : 0, done, st);
+  feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
+}
+
+void apply_F_m(feti_ctx* ctx, int nrhs, const double* x, double* q, const double* a, double* partial, const int* done,
+               bool f32) {
+  local_apply_m(ctx, 0, nrhs, x, nullptr, done, f32);
+  feti::launch_scatter_m(ctx->maps, nrhs, ctx->dm_loc, nullptr, q, a, partial, done, ctx->stream);
+}
+
+void apply_M_m(feti_ctx* ctx, int nrhs, const double* w, double* z, const int* done, bool f32) {
+  local_apply_m(ctx, 1, nrhs, w, ctx->d_weight, done, f32);
+  feti::launch_scatter_m(ctx->maps, nrhs, ctx->dm_loc, ctx->d_weight, z, nullptr, nullptr, done, ctx->stream);
+}
+
+// out = P (v - alpha q)  (q optional: fused CG update of r and lam, see launch_expand_m)
+void project_m(feti_ctx* ctx, int nrhs, const double* v, double* out, const double* a, double* partial,
+               double* r_upd, double* lam, const double* p, const double* q, const int* done) {
+  const bool coarse = ctx->cd > 0;
+  if (coarse)
+    feti::launch_project_m(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
+                           ctx->d_lay, ctx->d_R, ctx->maps, nrhs, (int)ctx->cd, ctx->d_Ginv, r_upd ? r_upd : v,
+                           r_upd ? q : nullptr, ctx->dm_sc, ctx->dm_gpart, ctx->dm_g, ctx->dm_c, done, ctx->stream);
+  feti::launch_expand_m(ctx->maps, ctx->d_lay, ctx->d_R, nrhs, coarse ? 1 : 0, v, ctx->dm_c, out, a, partial, r_upd,
+                        lam, p, q, ctx->dm_sc, done, ctx->stream);
+}
+
+void pcg_iteration_m(feti_ctx* ctx, int nrhs, double* lam, bool f32) {
+  cudaStream_t st = ctx->stream;
+  const int* done = &ctx->dm_sc->done;
+  const int nl = (int)ctx->n_lambda;
+  apply_M_m(ctx, nrhs, ctx->dm_w, ctx->dm_z, done, f32);
+  project_m(ctx, nrhs, ctx->dm_z, ctx->dm_y, ctx->dm_w, ctx->dm_part_wy, nullptr, nullptr, nullptr, nullptr, done);
+  feti::launch_axpby_rho_m(nl, nrhs, ctx->dm_p, ctx->dm_y, ctx->dm_sc, ctx->dm_part_wy, st);
+  apply_F_m(ctx, nrhs, ctx->dm_p, ctx->dm_q, ctx->dm_p, ctx->dm_part_pq, done, f32);
+  feti::launch_alpha_m(nrhs, ctx->dm_sc, ctx->dm_part_pq, ctx->dm_alpha_hist, st);
+  project_m(ctx, nrhs, ctx->dm_r, ctx->dm_w, nullptr, ctx->dm_part_ww, ctx->dm_r, lam, ctx->dm_p, ctx->dm_q, done);
+  feti::launch_conv_m(nrhs, ctx->dm_sc, ctx->dm_part_ww, 0, st);
+}
+
+feti_status run_pcg_chunks_m(feti_ctx* ctx, int nrhs, bool mixed, int maxit) {
+  const int chunk = ctx->opt.chunk > 0 ? ctx->opt.chunk : 16;
+  if (!(ctx->pcgm_graph && ctx->pcgm_chunk == chunk && ctx->pcgm_nrhs == nrhs && ctx->pcgm_mixed == mixed)) {
+    if (ctx->pcgm_graph) cudaGraphExecDestroy(ctx->pcgm_graph);
+    ctx->pcgm_graph = nullptr;
+    cudaGraph_t g = nullptr;
+    FETI_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) pcg_iteration_m(ctx, nrhs, mixed ? ctx->dm_dl : ctx->dm_lam, mixed);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return fail(ctx, FETI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->pcgm_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, FETI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->pcgm_chunk = chunk;
+    ctx->pcgm_nrhs = nrhs;
+    ctx->pcgm_mixed = mixed;
+  }
+  const int max_launch = maxit / chunk + 2;
+  for (int l = 0; l < max_launch; ++l) {
+    FETI_CK(cudaGraphLaunch(ctx->pcgm_graph, ctx->stream));
+    FETI_CK(cudaMemcpyAsync(ctx->hm_sc, ctx->dm_sc, sizeof(feti::PcgScalarsM), cudaMemcpyDeviceToHost, ctx->stream));
+    FETI_CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->hm_sc->done) break;
+  }
+  return FETI_OK;
+}
+
+// Resets the block scalars (active[k] for k < nrhs unless frozen[k]), projects
+// r into w and evaluates the per-RHS norms (wnorm0).
+feti_status start_pcg_m(feti_ctx* ctx, int nrhs, const double* tol, const std::vector<int>& frozen, int maxit) {
+  feti::PcgScalarsM h{};
+  for (int k = 0; k < nrhs; ++k) {
+    h.tol[k] = tol[k];
+    h.active[k] = frozen.empty() || !frozen[k] ? 1 : 0;
+  }
+  h.maxit = maxit;
+  FETI_CK(cudaMemcpyAsync(ctx->dm_sc, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+  FETI_CK(cudaMemsetAsync(ctx->dm_p, 0, (size_t)ctx->n_lambda * nrhs * sizeof(double), ctx->stream));
+  project_m(ctx, nrhs, ctx->dm_r, ctx->dm_w, nullptr, ctx->dm_part_ww, nullptr, nullptr, nullptr, nullptr,
+            &ctx->dm_sc->done);
+  feti::launch_conv_m(nrhs, ctx->dm_sc, ctx->dm_part_ww, 1, ctx->stream);
+  FETI_CK(cudaGetLastError());
+  FETI_CK(cudaMemcpyAsync(ctx->hm_sc, ctx->dm_sc, sizeof(feti::PcgScalarsM), cudaMemcpyDeviceToHost, ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  return FETI_OK;
+}
+
+// Block solve of nrhs load cases f_k = scale_k f (homogeneous Dirichlet data):
+// right-hand sides from the single-RHS setup, scaled; one PCG (or one
+// refinement loop) over the block; recovery per right-hand side.
+feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, double* u_out, int u_on_device,
+                             feti_report* rep) {
+  cudaStream_t st = ctx->stream;
+  const int nl = (int)ctx->n_lambda;
+  const int* zero = ctx->d_zero;
+  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  FETI_TRY(alloc_multi(ctx, nrhs));
+  FETI_TRY(rhs_setup(ctx));
+  for (int k = 0; k < nrhs; ++k) {
+    feti::launch_col_set(nl, nrhs, k, scale[k], ctx->d_lam, ctx->dm_lam, st);
+    feti::launch_col_set(nl, nrhs, k, scale[k], ctx->d_d, ctx->dm_d, st);
+  }
+  FETI_CK(cudaGetLastError());
+  cudaEvent_t e0, e1;
+  FETI_CK(cudaEventCreate(&e0));
+  FETI_CK(cudaEventCreate(&e1));
+  FETI_CK(cudaEventRecord(e0, st));
+  const int nlb = nl * nrhs;
+  int total_it = 0, outer = 0;
+  bool conv = false, breakdown = false;
+  std::vector<double> nrm0(nrhs, -1.0), tolv(nrhs, ctx->opt.tol);
+  std::vector<int> frozen(nrhs, 0);
+  if (!mixed) {
+    apply_F_m(ctx, nrhs, ctx->dm_lam, ctx->dm_q, nullptr, nullptr, zero, false);
+    feti::launch_vsub(nlb, ctx->dm_d, ctx->dm_q, ctx->dm_r, st);
+    FETI_TRY(start_pcg_m(ctx, nrhs, tolv.data(), frozen, ctx->opt.maxit));
+    if (!ctx->hm_sc->done) FETI_TRY(run_pcg_chunks_m(ctx, nrhs, false, ctx->opt.maxit));
+    const feti::PcgScalarsM& sc = *ctx->hm_sc;
+    total_it = sc.it;
+    breakdown = sc.status != 0;
+    conv = !breakdown;
+    for (int k = 0; k < nrhs; ++k)
+      if (!(sc.wnorm[k] <= sc.tol[k] * sc.wnorm0[k] || sc.wnorm0[k] == 0.0)) conv = false;
+  } else {
+    const double inner_tol = ctx->opt.inner_tol > 0.0 ? ctx->opt.inner_tol : 1e-4;
+    const int max_outer = ctx->opt.max_outer > 0 ? ctx->opt.max_outer : 20;
+    for (;;) {
+      apply_F_m(ctx, nrhs, ctx->dm_lam, ctx->dm_q, nullptr, nullptr, zero, false);   // FP64 residuals
+      feti::launch_vsub(nlb, ctx->dm_d, ctx->dm_q, ctx->dm_r, st);
+      std::vector<int> none;
+      FETI_TRY(start_pcg_m(ctx, nrhs, tolv.data(), none, std::max(1, ctx->opt.maxit - total_it)));
+      bool all = true;
+      std::vector<double> tin(nrhs);
+      for (int k = 0; k < nrhs; ++k) {
+        const double nr = ctx->hm_sc->wnorm0[k];
+        if (nrm0[k] < 0.0) nrm0[k] = nr;
+        if (!std::isfinite(nr)) breakdown = true;
+        frozen[k] = (nr <= ctx->opt.tol * nrm0[k] || nr == 0.0) ? 1 : 0;
+        all = all && frozen[k];
+        tin[k] = nr > 0.0 ? std::max(inner_tol, 0.5 * ctx->opt.tol * nrm0[k] / nr) : inner_tol;
+      }
+      if (breakdown) break;
+      if (all) { conv = true; break; }
+      if (outer >= max_outer || total_it >= ctx->opt.maxit) break;
+      // inner solve on the unconverged right-hand sides only
+      feti::PcgScalarsM h = *ctx->hm_sc;
+      for (int k = 0; k < nrhs; ++k) {
+        h.tol[k] = tin[k];
+        h.active[k] = frozen[k] ? 0 : 1;
+      }
+      FETI_CK(cudaMemcpyAsync(ctx->dm_sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+      FETI_CK(cudaMemsetAsync(ctx->dm_dl, 0, (size_t)nlb * sizeof(double), st));
+      FETI_TRY(run_pcg_chunks_m(ctx, nrhs, true, ctx->opt.maxit - total_it));
+      total_it += ctx->hm_sc->it;
+      if (ctx->hm_sc->status) { breakdown = true; break; }
+      feti::launch_vadd(nlb, ctx->dm_lam, ctx->dm_dl, st);
+      ++outer;
+    }
+  }
+  FETI_CK(cudaEventRecord(e1, st));
+  FETI_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rep) {
+    rep->iterations = total_it;
+    rep->outer_iterations = outer;
+    rep->converged = conv ? 1 : 0;
+    rep->t_pcg_ms = ms;
+    rep->n_lambda = ctx->n_lambda;
+    rep->coarse_dim = ctx->cd;
+  }
+  if (breakdown) return fail(ctx, FETI_ERR_BREAKDOWN, "PCG breakdown (block form)");
+  // recovery, one right-hand side at a time (single-RHS kernels on column k)
+  const size_t n3 = 3 * (size_t)ctx->N;
+  for (int k = 0; k < nrhs; ++k) {
+    feti::launch_col_get(nl, nrhs, k, ctx->dm_lam, ctx->d_lam, st);
+    apply_F(ctx, ctx->d_lam, ctx->d_q, nullptr, false, zero);
+    feti::launch_axpy_to(nl, ctx->d_q, -scale[k], ctx->d_d, ctx->d_z, st);       // F lambda_k - d~_k
+    if (ctx->cd > 0) {
+      feti::launch_gtv(ctx->P, ctx->d_lay, ctx->d_R, ctx->maps, ctx->d_z, ctx->d_g, zero, st);
+      feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, ctx->d_g, ctx->d_c, zero, st);
+    }
+    feti::launch_gather(ctx->maps, ctx->d_lam, nullptr, ctx->d_loc, zero, st);
+    feti::launch_axpy_to((int)ctx->nloc_total, ctx->d_f, scale[k] - 1.0, ctx->d_f, ctx->d_x2, st);   // scale_k f
+    feti::launch_local_sub(ctx->P, ctx->d_lay, ctx->d_x2, ctx->d_loc, ctx->d_x2, st);
+    feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_x2, ctx->d_x, st);
+    if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
+    FETI_CK(cudaGetLastError());
+    double* out_k = u_out + k * n3;
+    FETI_TRY(write_displacement(ctx, out_k, u_on_device, u_on_device ? out_k : ctx->d_Uout));
+  }
+  if (!conv) return fail(ctx, FETI_ERR_NOT_CONVERGED, "PCG reached maxit (block form)");
   return FETI_OK;
 }
 
@@ -1468,6 +1735,90 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
   return FETI_OK;
 }
 
+feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nrhs, double* u_out,
+                             int32_t u_on_device, feti_report* report) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  if (!u_out || !load_scale) return fail(ctx, FETI_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > feti::kMaxRhs) return fail(ctx, FETI_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  (void)cudaGetLastError();
+  if (report) std::memset(report, 0, sizeof(*report));
+  if (ctx->mat.kind != FETI_LINEAR_ISO) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve_multi needs a linear material");
+  for (double v : ctx->dir_val)
+    if (v != 0.0) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve_multi needs homogeneous Dirichlet data");
+  auto t0 = std::chrono::steady_clock::now();
+  FETI_TRY(feti_prepare(ctx));
+  feti_status s = dual_solve_multi(ctx, load_scale, nrhs, u_out, u_on_device, report);
+  if (report) {
+    report->t_setup_ms = ctx->t_setup_ms;
+    report->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return s;
+}
+
+feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, double* z, int32_t nrhs,
+                                  int32_t n_apply, double* ms_per_apply) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  if (!v || !q || !z || n_apply <= 0 || nrhs < 1 || nrhs > feti::kMaxRhs)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "bad dual_apply_multi arguments");
+  if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
+  (void)cudaGetLastError();
+  FETI_TRY(alloc_multi(ctx, nrhs));
+  cudaStream_t st = ctx->stream;
+  const int* zero = ctx->d_zero;
+  const bool f32 = ctx->opt.precision == FETI_MIXED;
+  if (!(ctx->dualm_graph && ctx->dualm_v == v && ctx->dualm_n == n_apply && ctx->dualm_nrhs == nrhs)) {
+    if (ctx->dualm_graph) cudaGraphExecDestroy(ctx->dualm_graph);
+    ctx->dualm_graph = nullptr;
+    for (auto ev : ctx->dualm_events) cudaEventDestroy(ev);
+    ctx->dualm_events.assign(2 * (size_t)n_apply + 2, nullptr);
+    for (auto& ev : ctx->dualm_events) FETI_CK(cudaEventCreate(&ev));
+    feti::GemvCfg cfg = ctx->tab[0][0];
+    cfg.R = 2;
+    cudaGraph_t g = nullptr;
+    FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < n_apply; ++i) {
+      void* vl = f32 ? (void*)ctx->dm_vloc32 : (void*)ctx->dm_vloc;
+      feti::launch_gather_m(ctx->maps, nrhs, v, nullptr, vl, f32 ? 1 : 0, zero, st);
+      FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[2 + 2 * i], st, cudaEventRecordExternal));
+      feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
+                            nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
+      FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[3 + 2 * i], st, cudaEventRecordExternal));
+      feti::launch_scatter_m(ctx->maps, nrhs, ctx->dm_loc, nullptr, q, nullptr, nullptr, zero, st);
+      apply_M_m(ctx, nrhs, q, z, zero, f32);
+    }
+    FETI_CK(cudaStreamEndCapture(st, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->dualm_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, FETI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->dualm_v = v;
+    ctx->dualm_n = n_apply;
+    ctx->dualm_nrhs = nrhs;
+  }
+  FETI_CK(cudaEventRecord(ctx->dualm_events[0], st));
+  FETI_CK(cudaGraphLaunch(ctx->dualm_graph, st));
+  FETI_CK(cudaEventRecord(ctx->dualm_events[1], st));
+  FETI_CK(cudaEventSynchronize(ctx->dualm_events[1]));
+  float ms = 0.f;
+  FETI_CK(cudaEventElapsedTime(&ms, ctx->dualm_events[0], ctx->dualm_events[1]));
+  double kern = 0.0;
+  for (int i = 0; i < n_apply; ++i) {
+    float t = 0.f;
+    FETI_CK(cudaEventElapsedTime(&t, ctx->dualm_events[2 + 2 * i], ctx->dualm_events[3 + 2 * i]));
+    kern += t;
+  }
+  if (ms_per_apply) *ms_per_apply = ms / n_apply;
+  double entries = 0.0, vec = 0.0;
+  for (const auto& L : ctx->lay) {
+    entries += (double)L.nbp * L.nbp;
+    vec += (double)L.nbp;
+  }
+  ctx->gemv_ms = kern / n_apply;
+  const double esz = f32 ? 4.0 : 8.0;
+  ctx->gemv_bytes = entries * esz + vec * (esz + 8.0) * nrhs;
+  ctx->gemv_flops = 2.0 * entries * nrhs;
+  return FETI_OK;
+}
+
 feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]) {
   if (!ctx || !out) return FETI_ERR_INVALID_ARG;
   out[0] = ctx->n_lambda;
@@ -1595,6 +1946,10 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->pcg_graph) cudaGraphExecDestroy(ctx->pcg_graph);
   if (ctx->dual_graph) cudaGraphExecDestroy(ctx->dual_graph);
   for (auto ev : ctx->dual_events) cudaEventDestroy(ev);
+  if (ctx->pcgm_graph) cudaGraphExecDestroy(ctx->pcgm_graph);
+  if (ctx->dualm_graph) cudaGraphExecDestroy(ctx->dualm_graph);
+  for (auto ev : ctx->dualm_events) cudaEventDestroy(ev);
+  if (ctx->hm_sc) cudaFreeHost(ctx->hm_sc);
   for (auto& b : ctx->bufs) cudaFree(b.p);
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);

@@ -54,11 +54,6 @@ void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, c
                         int kind, double scale, const double* traction, double* out, cudaStream_t st);
 // Writes the identity coupling of the augmentation block and zeros the rest of it.
 void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st);
-// Partial right-looking Cholesky: columns [c0, c1) of every subdomain,
-// trailing update on rows/cols [c1, n_active).  which = 0: interior
-// (c0 = 0, c1 = nI, n_active = n); which = 1: b' (c0 = nI, c1 = nI + nbp,
-// n_active = ld).
-void launch_chol_partial(int P, const SubLayout* lay, int which, double* A, int* status, cudaStream_t st);
 // Copies the trailing boundary block (nb x nb at [nI, nI)) into S (which=0),
 // or minus the augmentation block into F (which=1).
 void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st);
@@ -209,9 +204,50 @@ namespace feti {
 // Batched multi-CTA partial Cholesky of every subdomain's dense matrix, one
 // launch triple (diagonal block, panel solve, tiled trailing update) per
 // 32-column step; phase 0: interior columns, phase 1: boundary minus fixing
-// columns (see launch_chol_partial).  step_chunks[t] (host array, n_steps
+// columns, trailing rows/cols up to n (phase 0) or ld (phase 1).  step_chunks[t] (host array, n_steps
 // entries): the largest number of 64-row trailing chunks over the subdomains
 // at step t (idle CTAs exit at once).
 void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps, double* A,
                          int* status, cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// ---- block form: up to kMaxRhs right-hand sides, vectors [n][nrhs] ----
+constexpr int kMaxRhs = 16;
+struct PcgScalarsM {
+  double tol[kMaxRhs];
+  double rho[kMaxRhs];
+  double rho_slot[2][kMaxRhs];
+  double alpha[kMaxRhs];
+  double beta[kMaxRhs];
+  double pq[kMaxRhs];
+  double wnorm0[kMaxRhs];
+  double wnorm[kMaxRhs];
+  int active[kMaxRhs];
+  int it, done, status, maxit;
+};
+void launch_gather_m(const Maps& mp, int nrhs, const double* x, const double* wv, void* y, int f32, const int* done,
+                     cudaStream_t st);
+// Y = M_i V per subdomain (batched GEMM, N = nrhs), FP64 or FP32 copies.
+void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, int nrhs,
+                     const void* vloc, double* y, int max_m, const int* done, cudaStream_t st);
+void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
+                      double* partial, const int* done, cudaStream_t st);
+// c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).
+void launch_project_m(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const int32_t* sub_chunk_ptr,
+                      const int32_t* col_sub, const SubLayout* lay, const double* R, const Maps& mp, int nrhs, int cd,
+                      const double* Ginv, const double* x, const double* q, const PcgScalarsM* sc, double* gpart,
+                      double* g, double* c, const int* done, cudaStream_t st);
+void launch_expand_m(const Maps& mp, const SubLayout* lay, const double* R, int nrhs, int has_coarse, const double* v,
+                     const double* c, double* out, const double* a, double* partial, double* r_upd, double* lam,
+                     const double* p, const double* q, const PcgScalarsM* sc, const int* done, cudaStream_t st);
+void launch_axpby_rho_m(int n, int nrhs, double* p, const double* y, PcgScalarsM* s, const double* partial,
+                        cudaStream_t st);
+void launch_alpha_m(int nrhs, PcgScalarsM* s, const double* partial, double* alpha_hist, cudaStream_t st);
+void launch_conv_m(int nrhs, PcgScalarsM* s, const double* partial, int first, cudaStream_t st);
+void launch_spmv_lump_m(int n_rows, int nrhs, const int32_t* ptr, const int32_t* col, const double* val,
+                        const double* v, double* y, const int* done, cudaStream_t st);
+void launch_col_get(int n, int nrhs, int k, const double* blk, double* v, cudaStream_t st);
+// blk[:, k] = scale * v
+void launch_col_set(int n, int nrhs, int k, double scale, const double* v, double* blk, cudaStream_t st);
 }  // namespace feti

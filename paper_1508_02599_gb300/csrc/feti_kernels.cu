@@ -404,134 +404,9 @@ __global__ void k_augment(const SubLayout* __restrict__ lay, double* __restrict_
   for (int j = threadIdx.x; j < L.nbp; j += blockDim.x) A[(size_t)(L.n + j) * L.ld + L.nI + j] = 1.0;
 }
 
-// Right-looking blocked Cholesky of columns [c0, c1) with trailing update of
-// rows/cols [c1, na); lower triangle, row-major, leading dimension ld.
+// Block sizes of the dense Cholesky kernels: 32-column panels, 64x64 update tiles.
 constexpr int NB = 32;
 constexpr int TT = 64;
-
-__global__ void __launch_bounds__(kThreads) k_chol_partial(const SubLayout* __restrict__ lay, int which,
-                                                           double* __restrict__ Abase, int* status) {
-  const int s = blockIdx.x;
-  const SubLayout L = lay[s];
-  double* A = Abase + L.aoff;
-  const size_t ld = L.ld;
-  const int c0 = which ? L.nI : 0;
-  const int c1 = which ? L.nI + L.nbp : L.nI;
-  const int na = which ? L.ld : L.n;
-  __shared__ double D[NB][NB + 1];
-  __shared__ double Pa[TT][NB + 1];
-  __shared__ double Pb[TT][NB + 1];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int kb = c0; kb < c1; kb += NB) {
-    const int nk = min(NB, c1 - kb);
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-      const int i = idx / NB, j = idx % NB;
-      D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      const int i = tid;
-      for (int j = 0; j < nk; ++j) {
-        if (i == j) {
-          const double d = D[j][j];
-          if (!(d > 0.0) || !isfinite(d)) bad = 1;
-          D[j][j] = sqrt(d);
-        }
-        __syncwarp();
-        if (bad) break;
-        if (i > j && i < nk) D[i][j] /= D[j][j];
-        __syncwarp();
-        if (i > j && i < nk)
-          for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (bad) {
-      if (tid == 0) set_status(status, DEV_LOCAL_SINGULAR);
-      return;
-    }
-    for (int idx = tid; idx < nk * nk; idx += blockDim.x) {
-      const int i = idx / nk, j = idx % nk;
-      if (j <= i) A[(kb + i) * ld + kb + j] = D[i][j];
-    }
-    // panel solve: rows below the diagonal block, X = A_panel L_D^-T
-    const int r0 = kb + nk;
-    for (int base = r0; base < na; base += TT) {
-      const int nr = min(TT, na - base);
-      for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-        const int r = idx / NB, l = idx % NB;
-        Pa[r][l] = (r < nr && l < nk) ? A[(base + r) * ld + kb + l] : 0.0;
-      }
-      __syncthreads();
-      if (tid < nr) {
-        double xr[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < nk) {
-            double v = xr[j];
-#pragma unroll
-            for (int l = 0; l < NB; ++l)
-              if (l < j) v -= xr[l] * D[j][l];
-            xr[j] = v / D[j][j];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j) Pa[tid][j] = xr[j];
-      }
-      __syncthreads();
-      for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-        const int r = idx / NB, l = idx % NB;
-        if (r < nr && l < nk) A[(base + r) * ld + kb + l] = Pa[r][l];
-      }
-      __syncthreads();
-    }
-    // trailing update, lower triangle, 64x64 tiles
-    const int ntile = (na - r0 + TT - 1) / TT;
-    for (int ti = 0; ti < ntile; ++ti) {
-      for (int tj = 0; tj <= ti; ++tj) {
-        const int ib = r0 + ti * TT, jb = r0 + tj * TT;
-        for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-          const int r = idx / NB, l = idx % NB;
-          Pa[r][l] = (ib + r < na && l < nk) ? A[(ib + r) * ld + kb + l] : 0.0;
-          Pb[r][l] = (jb + r < na && l < nk) ? A[(jb + r) * ld + kb + l] : 0.0;
-        }
-        __syncthreads();
-        const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
-        double acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-        for (int l = 0; l < nk; ++l) {
-          double av[4], bv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            av[a] = Pa[tr + a][l];
-            bv[a] = Pb[tc + a][l];
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int i = ib + tr + a, j = jb + tc + b;
-            if (i < na && j < na && j <= i) A[i * ld + j] -= acc[a][b];
-          }
-        __syncthreads();
-      }
-    }
-  }
-}
 
 __global__ void k_extract(const SubLayout* __restrict__ lay, int which, const double* __restrict__ Abase,
                           double* __restrict__ out) {
@@ -1112,10 +987,6 @@ void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, c
 
 void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st) {
   k_augment<<<P, kThreads, 0, st>>>(lay, A);
-}
-
-void launch_chol_partial(int P, const SubLayout* lay, int which, double* A, int* status, cudaStream_t st) {
-  k_chol_partial<<<P, kThreads, 0, st>>>(lay, which, A, status);
 }
 
 void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st) {

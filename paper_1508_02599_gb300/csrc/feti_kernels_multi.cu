@@ -1,0 +1,530 @@
+// Block form of the projected PCG: up to kMaxRhs independent CG recurrences
+// sharing every operator apply (the RHS of several load cases, Sec. 3.2 /
+// Sec. 4.3).  Multiplier-space vectors are row-major [n_lambda][nrhs] and
+// local vectors [n_b][nrhs], so each gather, scatter and projection reads a
+// row's nrhs values contiguously, and every dense local operator entry read
+// from HBM feeds nrhs FMAs (a batched GEMM with N = nrhs instead of a GEMV).
+// Scalars (rho, alpha, beta, norms) are per right-hand side; a converged
+// right-hand side is frozen (alpha = beta = 0 for it) while the others run on.
+#include "feti_internal.h"
+
+#include <cmath>
+
+namespace feti {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPartials = 304;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-RHS CTA reduction of acc[k] (k < nrhs): result valid in thread 0's out[k].
+// red: shared [8][kMaxRhs].
+__device__ void block_sum_vec(const double* acc, int nrhs, double (*red)[kMaxRhs], double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < nrhs; ++k) {
+    const double t = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Sum of the kPartials partial sums of right-hand side k (fixed order).
+__device__ double reduce_partials_k(const double* partial, int k, double* red1) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < kPartials; i += blockDim.x) t += partial[k * kPartials + i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  t = warp_sum(t);
+  __syncthreads();
+  if (lane == 0) red1[wid] = t;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red1[w];
+  __syncthreads();
+  return s;
+}
+
+template <typename T>
+__global__ void k_gather_m(Maps mp, int nrhs, const double* __restrict__ x, const double* __restrict__ wv,
+                           T* __restrict__ y, const int* __restrict__ done) {
+  if (*done) return;
+  for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < mp.nb_total; gp += gridDim.x * blockDim.x) {
+    double val[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) val[k] = 0.0;
+    for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+      const int row = mp.bt_row[e];
+      const double sw = mp.bt_sgn[e] * (wv ? wv[row] : 1.0);
+      for (int k = 0; k < nrhs; ++k) val[k] += sw * x[(size_t)row * nrhs + k];
+    }
+    for (int k = 0; k < nrhs; ++k) y[(size_t)gp * nrhs + k] = (T)val[k];
+  }
+}
+
+// Y (m x nrhs) = M_i V (m x nrhs) for every subdomain.  V is staged in shared
+// memory transposed ([k][column], padded to 4), each warp keeps R x nrhs
+// accumulators: every matrix entry loaded from HBM feeds nrhs FMAs.
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads) k_gemm_loc(const int32_t* __restrict__ blk_sub,
+                                                       const int32_t* __restrict__ blk_row0, int rpc,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const T* __restrict__ M, int nrhs,
+                                                       const T* __restrict__ vloc, double* __restrict__ y,
+                                                       const int* __restrict__ done) {
+  if (*done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* v = reinterpret_cast<T*>(smem_raw);
+  const int s = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  constexpr bool f32 = sizeof(T) == 4;
+  const int ldm = f32 ? ((m + 3) & ~3) : m;
+  const T* Ms = M + (f32 ? (which == 0 ? L.foff32 : L.soff32) : (which == 0 ? L.foff : L.soff));
+  for (int idx = threadIdx.x; idx < ldm * nrhs; idx += blockDim.x) {
+    const int c = idx / nrhs, k = idx % nrhs;
+    v[k * ldm + c] = c < m ? vloc[(size_t)(L.boff + c) * nrhs + k] : (T)0;
+  }
+  if (which == 0 && r0 == 0)
+    for (int idx = threadIdx.x; idx < L.k * nrhs; idx += blockDim.x) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rend = min(r0 + rpc, m);
+  for (int rbase = r0 + wid * R; rbase < rend; rbase += (kThreads / 32) * R) {
+    T acc[R][kMaxRhs];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int k = 0; k < kMaxRhs; ++k) acc[j][k] = (T)0;
+    const T* rows[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) rows[j] = Ms + (size_t)min(rbase + j, m - 1) * ldm;
+    if constexpr (f32) {
+      const int m4 = ldm >> 2;
+      for (int c = lane; c < m4; c += 32) {
+        float4 a[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) a[j] = __ldg(reinterpret_cast<const float4*>(rows[j]) + c);
+#pragma unroll
+        for (int k = 0; k < kMaxRhs; ++k) {
+          if (k < nrhs) {
+            const float4 vv = reinterpret_cast<const float4*>(v + k * ldm)[c];
+#pragma unroll
+            for (int j = 0; j < R; ++j) acc[j][k] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
+          }
+        }
+      }
+    } else {
+      for (int c = lane; c < m; c += 32) {
+        T a[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) a[j] = __ldg(rows[j] + c);
+#pragma unroll
+        for (int k = 0; k < kMaxRhs; ++k) {
+          if (k < nrhs) {
+            const T vv = v[k * ldm + c];
+#pragma unroll
+            for (int j = 0; j < R; ++j) acc[j][k] += a[j] * vv;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int k = 0; k < kMaxRhs; ++k) {
+        if (k < nrhs) {
+          double t;
+          if constexpr (f32) t = (double)warp_sumf(acc[j][k]);
+          else t = warp_sum(acc[j][k]);
+          if (lane == 0 && rbase + j < rend) y[(size_t)(L.boff + rbase + j) * nrhs + k] = t;
+        }
+      }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter_m(Maps mp, int nrhs, const double* __restrict__ y,
+                                                        const double* __restrict__ wv, double* __restrict__ q,
+                                                        const double* __restrict__ a, double* __restrict__ partial,
+                                                        const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8][kMaxRhs];
+  __shared__ double out[kMaxRhs];
+  double dot[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) dot[k] = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mp.n_lambda; r += gridDim.x * blockDim.x) {
+    double val[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) val[k] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int pos = mp.row_pos[2 * r + e];
+      if (pos >= 0) {
+        const double sg = mp.row_sgn[2 * r + e];
+        for (int k = 0; k < nrhs; ++k) val[k] += sg * y[(size_t)pos * nrhs + k];
+      }
+    }
+    const double w = wv ? wv[r] : 1.0;
+    for (int k = 0; k < nrhs; ++k) {
+      const double v = w * val[k];
+      q[(size_t)r * nrhs + k] = v;
+      if (partial) dot[k] += (a ? a[(size_t)r * nrhs + k] : v) * v;
+    }
+  }
+  if (partial) {
+    block_sum_vec(dot, nrhs, red, out);
+    if (threadIdx.x < nrhs) partial[threadIdx.x * kPartials + blockIdx.x] = out[threadIdx.x];
+  }
+}
+
+// G^T x per chunk of 256 boundary positions: partial[(c * 6 + a) * nrhs + k].
+// With q != NULL the input is x - alpha_k q (fused CG update).
+__global__ void __launch_bounds__(kThreads) k_gtv_part_m(const int32_t* __restrict__ chunk_sub,
+                                                         const int32_t* __restrict__ chunk_p0,
+                                                         const SubLayout* __restrict__ lay,
+                                                         const double* __restrict__ R, Maps mp, int nrhs,
+                                                         const double* __restrict__ x, double* __restrict__ partial,
+                                                         const double* __restrict__ q, const PcgScalarsM* sc,
+                                                         const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double acc_sh[kThreads][6];
+  const int c = blockIdx.x;
+  const SubLayout L = lay[chunk_sub[c]];
+  const int nb = L.nbp + L.k;
+  const int k = threadIdx.x % nrhs;
+  const int slot = threadIdx.x / nrhs;
+  const int nslots = kThreads / nrhs;
+  const double alpha = q ? sc->alpha[k] : 0.0;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (slot < nslots) {
+    for (int pp = slot; pp < 256; pp += nslots) {
+      const int p = chunk_p0[c] + pp;
+      if (p >= nb) break;
+      const int gp = L.boff + p;
+      double val = 0.0;
+      for (int e = mp.bt_ptr[gp]; e < mp.bt_ptr[gp + 1]; ++e) {
+        const int row = mp.bt_row[e];
+        const double xv = x[(size_t)row * nrhs + k];
+        val += mp.bt_sgn[e] * (q ? xv - alpha * q[(size_t)row * nrhs + k] : xv);
+      }
+      const double* Rr = R + L.roff + (size_t)(L.nI + p) * L.k;
+      for (int a = 0; a < L.k; ++a) acc[a] += Rr[a] * val;
+    }
+  }
+  for (int a = 0; a < 6; ++a) acc_sh[threadIdx.x][a] = (slot < nslots) ? acc[a] : 0.0;
+  __syncthreads();
+  if (threadIdx.x < L.k * nrhs) {
+    const int a = threadIdx.x / nrhs, kk = threadIdx.x % nrhs;
+    double t = 0.0;
+    for (int sl = 0; sl < nslots; ++sl) t += acc_sh[sl * nrhs + kk][a];
+    partial[((size_t)c * 6 + a) * nrhs + kk] = t;
+  }
+}
+
+// g[j][k] = sum over the chunks of column j's subdomain.
+__global__ void k_gsum_m(int cd, int nrhs, const double* __restrict__ partial,
+                         const int32_t* __restrict__ sub_chunk_ptr, const int32_t* __restrict__ col_sub,
+                         const SubLayout* __restrict__ lay, double* __restrict__ g, const int* __restrict__ done) {
+  if (*done) return;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < cd * nrhs; idx += gridDim.x * blockDim.x) {
+    const int j = idx / nrhs, k = idx % nrhs;
+    const int s = col_sub[j];
+    const int a = j - lay[s].coff;
+    double t = 0.0;
+    for (int qc = sub_chunk_ptr[s]; qc < sub_chunk_ptr[s + 1]; ++qc) t += partial[((size_t)qc * 6 + a) * nrhs + k];
+    g[idx] = t;
+  }
+}
+
+// C (cd x nrhs) = Ginv G, warp per row.
+__global__ void k_coarse_gemm_m(int cd, int nrhs, const double* __restrict__ Ginv, const double* __restrict__ g,
+                                double* __restrict__ c, const int* __restrict__ done) {
+  if (*done) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < cd; r += nwarps) {
+    double acc[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
+    for (int j = lane; j < cd; j += 32) {
+      const double gv = Ginv[(size_t)r * cd + j];
+      for (int k = 0; k < nrhs; ++k) acc[k] += gv * g[(size_t)j * nrhs + k];
+    }
+    for (int k = 0; k < nrhs; ++k) {
+      const double t = warp_sum(acc[k]);
+      if (lane == 0) c[(size_t)r * nrhs + k] = t;
+    }
+  }
+}
+
+// out = v - G c row-wise (v = r - alpha q with the fused update, r and lam
+// updated in place), partial sums of (a, out) or (out, out) per RHS.
+__global__ void __launch_bounds__(kThreads) k_expand_m(Maps mp, const SubLayout* __restrict__ lay,
+                                                       const double* __restrict__ R, int nrhs, int has_coarse,
+                                                       const double* __restrict__ v, const double* __restrict__ c,
+                                                       double* __restrict__ out, const double* __restrict__ a,
+                                                       double* __restrict__ partial, double* __restrict__ r_upd,
+                                                       double* __restrict__ lam, const double* __restrict__ p,
+                                                       const double* __restrict__ q, const PcgScalarsM* sc,
+                                                       const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8][kMaxRhs];
+  __shared__ double outs[kMaxRhs];
+  double alpha[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) alpha[k] = r_upd ? sc->alpha[k] : 0.0;
+  double dot[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) dot[k] = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mp.n_lambda; r += gridDim.x * blockDim.x) {
+    double val[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) {
+      const size_t i = (size_t)r * nrhs + k;
+      if (r_upd) {
+        const double rv = r_upd[i] - alpha[k] * q[i];
+        r_upd[i] = rv;
+        lam[i] += alpha[k] * p[i];
+        val[k] = rv;
+      } else {
+        val[k] = v[i];
+      }
+    }
+    if (has_coarse) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int gp = mp.row_pos[2 * r + e];
+        if (gp < 0) continue;
+        const SubLayout L = lay[mp.bpos_sub[gp]];
+        if (!L.k) continue;
+        const double sg = mp.row_sgn[2 * r + e];
+        const double* Rr = R + L.roff + (size_t)(L.nI + gp - L.boff) * L.k;
+        for (int kk = 0; kk < L.k; ++kk) {
+          const double ra = sg * Rr[kk];
+          const double* cr = c + (size_t)(L.coff + kk) * nrhs;
+          for (int k = 0; k < nrhs; ++k) val[k] -= ra * cr[k];
+        }
+      }
+    }
+    for (int k = 0; k < nrhs; ++k) {
+      out[(size_t)r * nrhs + k] = val[k];
+      dot[k] += (a ? a[(size_t)r * nrhs + k] : val[k]) * val[k];
+    }
+  }
+  block_sum_vec(dot, nrhs, red, outs);
+  if (threadIdx.x < nrhs) partial[threadIdx.x * kPartials + blockIdx.x] = outs[threadIdx.x];
+}
+
+// rho_k = (w, y)_k, beta_k, p = y + beta p (frozen right-hand sides keep p).
+__global__ void __launch_bounds__(kThreads) k_axpby_rho_m(int n, int nrhs, double* __restrict__ p,
+                                                          const double* __restrict__ y, PcgScalarsM* s,
+                                                          const double* __restrict__ partial) {
+  if (s->done) return;
+  __shared__ double red1[8];
+  const int it = s->it;
+  double beta[kMaxRhs];
+  int act[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) {
+    const double rho = reduce_partials_k(partial, k, red1);
+    act[k] = s->active[k];
+    beta[k] = (it > 0 && act[k]) ? rho / s->rho_slot[(it + 1) & 1][k] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (act[k] && (!(rho > 0.0) || !isfinite(rho))) {
+        s->status = DEV_BREAKDOWN;
+        s->done = 1;
+      }
+      s->rho_slot[it & 1][k] = rho;
+      s->rho[k] = rho;
+      s->beta[k] = beta[k];
+    }
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int k = 0; k < nrhs; ++k) {
+      if (!act[k]) continue;
+      const size_t j = (size_t)i * nrhs + k;
+      p[j] = it > 0 ? y[j] + beta[k] * p[j] : y[j];
+    }
+}
+
+// alpha_k = rho_k / (p, q)_k for active right-hand sides, 0 for frozen ones.
+__global__ void k_alpha_m(int nrhs, PcgScalarsM* s, const double* __restrict__ partial, double* alpha_hist) {
+  if (s->done) return;
+  __shared__ double red1[8];
+  for (int k = 0; k < nrhs; ++k) {
+    const double pq = reduce_partials_k(partial, k, red1);
+    if (threadIdx.x == 0) {
+      double al = 0.0;
+      if (s->active[k]) {
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          s->status = DEV_BREAKDOWN;
+          s->done = 1;
+        } else {
+          al = s->rho[k] / pq;
+        }
+      }
+      s->alpha[k] = al;
+      s->pq[k] = pq;
+      alpha_hist[(size_t)s->it * kMaxRhs + k] = al;
+    }
+  }
+}
+
+// Stopping test per right-hand side; done when all are frozen or at maxit.
+__global__ void k_conv_m(int nrhs, PcgScalarsM* s, const double* __restrict__ partial, int first) {
+  if (s->done) return;
+  __shared__ double red1[8];
+  double wn[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) wn[k] = sqrt(reduce_partials_k(partial, k, red1));
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  if (first) {
+    for (int k = 0; k < nrhs; ++k) {
+      s->wnorm0[k] = wn[k];
+      s->wnorm[k] = wn[k];
+      if (!isfinite(wn[k])) s->status = DEV_BREAKDOWN;
+      s->active[k] = (s->active[k] && wn[k] > 0.0) ? 1 : 0;
+      any |= s->active[k];
+    }
+    if (!any || s->status) s->done = 1;
+    return;
+  }
+  s->it += 1;
+  for (int k = 0; k < nrhs; ++k) {
+    if (!s->active[k]) continue;
+    s->wnorm[k] = wn[k];
+    if (!isfinite(wn[k])) {
+      s->status = DEV_BREAKDOWN;
+    } else if (wn[k] <= s->tol[k] * s->wnorm0[k]) {
+      s->active[k] = 0;
+    }
+    any |= s->active[k];
+  }
+  if (!any || s->status || s->it >= s->maxit) s->done = 1;
+}
+
+__global__ void k_spmv_lump_m(int n_rows, int nrhs, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const double* __restrict__ v, double* __restrict__ y,
+                              const int* __restrict__ done) {
+  if (*done) return;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_rows * nrhs; idx += gridDim.x * blockDim.x) {
+    const int r = idx / nrhs, k = idx % nrhs;
+    double acc = 0.0;
+    for (int j = ptr[r]; j < ptr[r + 1]; ++j) acc += val[j] * v[(size_t)col[j] * nrhs + k];
+    y[idx] = acc;
+  }
+}
+
+// Strided column copies between [n][nrhs] blocks and contiguous vectors.
+__global__ void k_col_get(int n, int nrhs, int k, const double* __restrict__ blk, double* __restrict__ v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = blk[(size_t)i * nrhs + k];
+}
+__global__ void k_col_set(int n, int nrhs, int k, double scale, const double* __restrict__ v,
+                          double* __restrict__ blk) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    blk[(size_t)i * nrhs + k] = scale * v[i];
+}
+
+inline int grid_for(long n) {
+  long b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 65535) b = 65535;
+  return (int)b;
+}
+
+template <typename T, int R>
+void launch_gemm_t(const GemvCfg& cfg, const SubLayout* lay, int which, const T* M, int nrhs, const T* vloc, double* y,
+                   int max_m, const int* done, cudaStream_t st) {
+  const size_t smem = (size_t)((max_m + 3) & ~3) * nrhs * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_gemm_loc<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemm_loc<T, R><<<cfg.n_blocks, kThreads, smem, st>>>(cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, M, nrhs, vloc,
+                                                        y, done);
+}
+
+}  // namespace
+
+void launch_gather_m(const Maps& mp, int nrhs, const double* x, const double* wv, void* y, int f32, const int* done,
+                     cudaStream_t st) {
+  if (f32)
+    k_gather_m<float><<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, nrhs, x, wv, static_cast<float*>(y), done);
+  else
+    k_gather_m<double><<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, nrhs, x, wv, static_cast<double*>(y), done);
+}
+
+void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, int nrhs,
+                     const void* vloc, double* y, int max_m, const int* done, cudaStream_t st) {
+  if (f32) {
+    if (cfg.R >= 2)
+      launch_gemm_t<float, 2>(cfg, lay, which, static_cast<const float*>(M), nrhs, static_cast<const float*>(vloc), y,
+                              max_m, done, st);
+    else
+      launch_gemm_t<float, 1>(cfg, lay, which, static_cast<const float*>(M), nrhs, static_cast<const float*>(vloc), y,
+                              max_m, done, st);
+  } else {
+    if (cfg.R >= 2)
+      launch_gemm_t<double, 2>(cfg, lay, which, static_cast<const double*>(M), nrhs, static_cast<const double*>(vloc), y,
+                               max_m, done, st);
+    else
+      launch_gemm_t<double, 1>(cfg, lay, which, static_cast<const double*>(M), nrhs, static_cast<const double*>(vloc), y,
+                               max_m, done, st);
+  }
+}
+
+void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
+                      double* partial, const int* done, cudaStream_t st) {
+  k_scatter_m<<<kPartials, kThreads, 0, st>>>(mp, nrhs, y, wv, q, a, partial, done);
+}
+
+void launch_project_m(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const int32_t* sub_chunk_ptr,
+                      const int32_t* col_sub, const SubLayout* lay, const double* R, const Maps& mp, int nrhs, int cd,
+                      const double* Ginv, const double* x, const double* q, const PcgScalarsM* sc, double* gpart,
+                      double* g, double* c, const int* done, cudaStream_t st) {
+  if (cd <= 0 || n_chunks <= 0) return;
+  k_gtv_part_m<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, nrhs, x, gpart, q, sc, done);
+  k_gsum_m<<<grid_for((long)cd * nrhs), kThreads, 0, st>>>(cd, nrhs, gpart, sub_chunk_ptr, col_sub, lay, g, done);
+  const int warps = cd < 2432 ? cd : 2432;
+  k_coarse_gemm_m<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(cd, nrhs, Ginv, g, c, done);
+}
+
+void launch_expand_m(const Maps& mp, const SubLayout* lay, const double* R, int nrhs, int has_coarse, const double* v,
+                     const double* c, double* out, const double* a, double* partial, double* r_upd, double* lam,
+                     const double* p, const double* q, const PcgScalarsM* sc, const int* done, cudaStream_t st) {
+  k_expand_m<<<kPartials, kThreads, 0, st>>>(mp, lay, R, nrhs, has_coarse, v, c, out, a, partial, r_upd, lam, p, q, sc,
+                                             done);
+}
+
+void launch_axpby_rho_m(int n, int nrhs, double* p, const double* y, PcgScalarsM* s, const double* partial,
+                        cudaStream_t st) {
+  k_axpby_rho_m<<<grid_for(n), kThreads, 0, st>>>(n, nrhs, p, y, s, partial);
+}
+
+void launch_alpha_m(int nrhs, PcgScalarsM* s, const double* partial, double* alpha_hist, cudaStream_t st) {
+  k_alpha_m<<<1, kThreads, 0, st>>>(nrhs, s, partial, alpha_hist);
+}
+
+void launch_conv_m(int nrhs, PcgScalarsM* s, const double* partial, int first, cudaStream_t st) {
+  k_conv_m<<<1, kThreads, 0, st>>>(nrhs, s, partial, first);
+}
+
+void launch_spmv_lump_m(int n_rows, int nrhs, const int32_t* ptr, const int32_t* col, const double* val,
+                        const double* v, double* y, const int* done, cudaStream_t st) {
+  k_spmv_lump_m<<<grid_for((long)n_rows * nrhs), kThreads, 0, st>>>(n_rows, nrhs, ptr, col, val, v, y, done);
+}
+
+void launch_col_get(int n, int nrhs, int k, const double* blk, double* v, cudaStream_t st) {
+  k_col_get<<<grid_for(n), kThreads, 0, st>>>(n, nrhs, k, blk, v);
+}
+
+void launch_col_set(int n, int nrhs, int k, double scale, const double* v, double* blk, cudaStream_t st) {
+  k_col_set<<<grid_for(n), kThreads, 0, st>>>(n, nrhs, k, scale, v, blk);
+}
+
+}  // namespace feti
