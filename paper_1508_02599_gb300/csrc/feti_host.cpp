@@ -80,6 +80,8 @@ struct feti_ctx {
   // ([which][k]), and the schedules picked by the autotuner
   feti::GemvCfg tab[2][3];
   feti::GemvCfg cfg64[2], cfg32[2];
+  feti::GemvCfg cfgm64[2], cfgm32[2];  // block form (N = nrhs) schedules
+  int tuned_m = 0;                     // nrhs the block schedules were tuned for
   bool tuned = false;
   float* d_vloc32 = nullptr;
   int32_t *d_chunk_sub = nullptr, *d_chunk_p0 = nullptr, *d_sub_chunk_ptr = nullptr, *d_col_sub = nullptr;
@@ -131,6 +133,8 @@ struct feti_ctx {
   bool pcgm_mixed = false;
   cudaGraphExec_t dualm_graph = nullptr;
   const double* dualm_v = nullptr;
+  const double* dualm_q = nullptr;
+  const double* dualm_z = nullptr;
   int dualm_n = 0, dualm_nrhs = 0;
   std::vector<cudaEvent_t> dualm_events;
   cudaGraphExec_t dual_graph = nullptr;
@@ -1251,8 +1255,56 @@ feti_status write_displacement(feti_ctx* ctx, double* u_out, int on_device, doub
 
 // ---------------------------------------------------------------------------
 // Block form: nrhs right-hand sides share every operator apply.
+// Times the block-form local GEMM schedules (rows per warp step {1, 2, 4},
+// rows per CTA {32, 64}) on the real operators and keeps the fastest.
+feti_status autotune_m(feti_ctx* ctx, int nrhs) {
+  if (ctx->tuned_m == nrhs) return FETI_OK;
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0, e1;
+  FETI_CK(cudaEventCreate(&e0));
+  FETI_CK(cudaEventCreate(&e1));
+  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  FETI_CK(cudaMemsetAsync(ctx->dm_vloc, 0, (size_t)ctx->nb_total * nrhs * sizeof(double), st));
+  FETI_CK(cudaMemsetAsync(ctx->dm_vloc32, 0, (size_t)ctx->nb_total * nrhs * sizeof(float), st));
+  const int Rs[3] = {1, 2, 4};
+  for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
+    const bool f32 = prec == 1;
+    for (int w = 0; w < 2; ++w) {
+      feti::GemvCfg best = ctx->tab[w][0];
+      best.R = 2;
+      if (!(w == 1 && ctx->opt.precond != FETI_PREC_DIRICHLET)) {
+        const void* M = f32 ? (w == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
+                            : (w == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
+        const void* v = f32 ? (const void*)ctx->dm_vloc32 : (const void*)ctx->dm_vloc;
+        float bt = 1e30f;
+        for (int t = 0; t < 2; ++t)
+          for (int ri = 0; ri < 3; ++ri) {
+            if (!f32 && Rs[ri] == 4) continue;
+            feti::GemvCfg c = ctx->tab[w][t];
+            c.R = Rs[ri];
+            feti::launch_gemm_loc(c, ctx->d_lay, w, M, f32, nrhs, v, ctx->dm_loc, ctx->max_nb, ctx->d_zero, st);
+            FETI_CK(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 3; ++rep)
+              feti::launch_gemm_loc(c, ctx->d_lay, w, M, f32, nrhs, v, ctx->dm_loc, ctx->max_nb, ctx->d_zero, st);
+            FETI_CK(cudaEventRecord(e1, st));
+            FETI_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < bt) { bt = ms; best = c; }
+          }
+      }
+      (f32 ? ctx->cfgm32[w] : ctx->cfgm64[w]) = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FETI_CK(cudaGetLastError());
+  ctx->tuned_m = nrhs;
+  return FETI_OK;
+}
+
 feti_status alloc_multi(feti_ctx* ctx, int nrhs) {
-  if (ctx->m_cap >= nrhs) return FETI_OK;
+  if (ctx->m_cap >= nrhs) return autotune_m(ctx, nrhs);
   if (ctx->m_cap > 0) return fail(ctx, FETI_ERR_STATE, "block buffers were sized for fewer right-hand sides");
   const size_t nl = (size_t)ctx->n_lambda * nrhs, nb = (size_t)ctx->nb_total * nrhs;
   for (double** v : {&ctx->dm_lam, &ctx->dm_r, &ctx->dm_w, &ctx->dm_z, &ctx->dm_y, &ctx->dm_p, &ctx->dm_q, &ctx->dm_d,
@@ -1272,7 +1324,7 @@ feti_status alloc_multi(feti_ctx* ctx, int nrhs) {
   FETI_TRY(dev_alloc(ctx, &ctx->dm_sc, 1));
   FETI_CK(cudaMallocHost(&ctx->hm_sc, sizeof(feti::PcgScalarsM)));
   ctx->m_cap = nrhs;
-  return FETI_OK;
+  return autotune_m(ctx, nrhs);
 }
 
 // Y = W B M B^T W X on blocks (which 0: F_i, no weights; which 1: preconditioner).
@@ -1288,8 +1340,7 @@ void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const do
                              ctx->dm_loc, done, st);
     return;
   }
-  feti::GemvCfg cfg = ctx->tab[which][0];  // 32 rows per CTA: the block form has nrhs times the work per row
-  cfg.R = 2;
+  const feti::GemvCfg& cfg = f32 ? ctx->cfgm32[which] : ctx->cfgm64[which];
   const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
                       : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
   void* v = f32 ? (void*)ctx->dm_vloc32 : (void*)ctx->dm_vloc;
@@ -1766,14 +1817,14 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
   cudaStream_t st = ctx->stream;
   const int* zero = ctx->d_zero;
   const bool f32 = ctx->opt.precision == FETI_MIXED;
-  if (!(ctx->dualm_graph && ctx->dualm_v == v && ctx->dualm_n == n_apply && ctx->dualm_nrhs == nrhs)) {
+  if (!(ctx->dualm_graph && ctx->dualm_v == v && ctx->dualm_q == q && ctx->dualm_z == z && ctx->dualm_n == n_apply &&
+        ctx->dualm_nrhs == nrhs)) {
     if (ctx->dualm_graph) cudaGraphExecDestroy(ctx->dualm_graph);
     ctx->dualm_graph = nullptr;
     for (auto ev : ctx->dualm_events) cudaEventDestroy(ev);
     ctx->dualm_events.assign(2 * (size_t)n_apply + 2, nullptr);
     for (auto& ev : ctx->dualm_events) FETI_CK(cudaEventCreate(&ev));
-    feti::GemvCfg cfg = ctx->tab[0][0];
-    cfg.R = 2;
+    const feti::GemvCfg cfg = f32 ? ctx->cfgm32[0] : ctx->cfgm64[0];
     cudaGraph_t g = nullptr;
     FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < n_apply; ++i) {
@@ -1791,6 +1842,8 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(ctx, FETI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     ctx->dualm_v = v;
+    ctx->dualm_q = q;
+    ctx->dualm_z = z;
     ctx->dualm_n = n_apply;
     ctx->dualm_nrhs = nrhs;
   }

@@ -462,7 +462,10 @@ void launch_gather_m(const Maps& mp, int nrhs, const double* x, const double* wv
 void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, int nrhs,
                      const void* vloc, double* y, int max_m, const int* done, cudaStream_t st) {
   if (f32) {
-    if (cfg.R >= 2)
+    if (cfg.R >= 4)
+      launch_gemm_t<float, 4>(cfg, lay, which, static_cast<const float*>(M), nrhs, static_cast<const float*>(vloc), y,
+                              max_m, done, st);
+    else if (cfg.R >= 2)
       launch_gemm_t<float, 2>(cfg, lay, which, static_cast<const float*>(M), nrhs, static_cast<const float*>(vloc), y,
                               max_m, done, st);
     else
