@@ -209,6 +209,26 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
 feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, double* z, int32_t nrhs,
                                   int32_t n_apply, double* ms_per_apply);
 
+/* Allocation-free variant of feti_dual_apply (one apply: q = F v, then
+ * z = M^-1 q; v, q, z: device arrays of n_lambda doubles).  The paper has no
+ * counterpart: this call exists for callers that must not allocate device
+ * memory after setup -- a fixed memory budget reserved at start-up, a
+ * latency-critical loop that cannot take cudaMalloc's implicit device
+ * synchronisation, or work issued while another component holds the
+ * allocator.  It allocates nothing and creates no graph or event: its local
+ * scratch vectors live in one static device array of 2^20 doubles (8 MiB)
+ * that every GPU loading the library keeps until process exit.
+ *  - Limit: a decomposition needs about 2.5 x (sum of boundary DOFs) doubles;
+ *    larger ones are rejected with FETI_ERR_INVALID_ARG and a message.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The work is enqueued on the context's stream and the call returns
+ *    without waiting.  All calls share the array: calls whose work overlaps
+ *    on the GPU (other streams, other contexts) race on it.  Every scratch
+ *    entry is written before it is read, so nothing needs clearing.
+ *  - Requires feti_prepare (or feti_solve) on this context first. */
+feti_status feti_dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z);
+
 /* Runs the setup part of feti_solve (element matrices through coarse
  * factorization) without PCG. */
 feti_status feti_prepare(feti_ctx* ctx);

@@ -52,7 +52,7 @@ class FetiReport(C.Structure):
 
 
 EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
-           "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_prepare", "feti_kernel_stats", "feti_get_schedule",
+           "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_get_schedule",
            "feti_last_error",
            "feti_destroy"]
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.feti_get_fixing.argtypes = [vp, vp, vp]
     lib.feti_dual_apply.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
     lib.feti_dual_apply_multi.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_double)]
+    lib.feti_dual_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.feti_solve_multi.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_prepare.argtypes = [vp]
     lib.feti_kernel_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]

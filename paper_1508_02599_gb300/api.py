@@ -164,6 +164,14 @@ class FetiSolver:
                                                    C.c_void_p(out.data_ptr()), 1, C.byref(rep)))
         return u, self._report(rep)
 
+    def dual_apply_noalloc(self, v, q, z):
+        """q = F v, z = M^-1 q without any device allocation (static scratch; see feti.h).
+
+        Enqueued on the solver's stream; synchronise before reading q and z.
+        """
+        self._check(self._lib.feti_dual_apply_noalloc(self._ctx, C.c_void_p(v.data_ptr()), C.c_void_p(q.data_ptr()),
+                                                      C.c_void_p(z.data_ptr())))
+
     def dual_apply_multi(self, v, q, z, nrhs: int, n_apply: int) -> float:
         ms = C.c_double()
         self._check(self._lib.feti_dual_apply_multi(self._ctx, C.c_void_p(v.data_ptr()), C.c_void_p(q.data_ptr()),

@@ -1557,6 +1557,58 @@ feti_status write_displacement(feti_ctx* ctx, double* u_out, int on_device, doub
 
 }  // namespace
 
+namespace feti {
+
+feti_status set_error(feti_ctx* ctx, feti_status st, const std::string& msg) { return fail(ctx, st, msg); }
+
+feti_status dual_apply_with_scratch(feti_ctx* ctx, const double* v, double* q, double* z, double* scratch,
+                                    size_t capacity) {
+  if (!v || !q || !z) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_dual_apply_noalloc: null vector");
+  // scratch: local input (doubles, or floats for the FP32 copies) + local output
+  const size_t nb = (size_t)ctx->nb_total;
+  const size_t need = nb + (nb + 7) / 2 + 4 + nb;
+  if (need > capacity)
+    return fail(ctx, FETI_ERR_INVALID_ARG,
+                "feti_dual_apply_noalloc: this decomposition needs " + std::to_string(need) +
+                    " doubles of scratch (3 per boundary DOF), the static scratch holds " + std::to_string(capacity));
+  if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
+  (void)cudaGetLastError();
+  cudaStream_t st = ctx->stream;
+  const int* zero = ctx->d_zero;
+  double* vloc = scratch;                                          // nb doubles
+  float* vloc32 = reinterpret_cast<float*>(scratch + nb);          // nb floats, 16-byte aligned
+  double* loc = scratch + nb + (nb + 7) / 2 + 4;                   // nb doubles
+  vloc32 = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(vloc32 + 3) & ~uintptr_t(15));
+  const bool f32 = ctx->opt.precision == FETI_MIXED;
+  // q = F v
+  if (f32) {
+    feti::launch_gather32(ctx->maps, v, nullptr, vloc32, zero, st);
+    feti::launch_gemv_loc(ctx->cfg32[0], ctx->d_lay, 0, ctx->d_F32, 1, vloc32, loc, ctx->max_nb, zero, st);
+  } else {
+    feti::launch_gather(ctx->maps, v, nullptr, vloc, zero, st);
+    feti::launch_gemv_loc(ctx->cfg64[0], ctx->d_lay, 0, ctx->d_F, 0, vloc, loc, ctx->max_nb, zero, st);
+  }
+  feti::launch_scatter(ctx->maps, loc, nullptr, q, nullptr, nullptr, zero, st);
+  // z = W B Y B^T W q
+  if (ctx->opt.precond == FETI_PREC_IDENTITY) {
+    feti::launch_gather(ctx->maps, q, ctx->d_weight, loc, zero, st);
+  } else if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    feti::launch_gather(ctx->maps, q, ctx->d_weight, vloc, zero, st);
+    feti::launch_spmv_lump((int)ctx->nb_total, ctx->d_lump_ptr, ctx->d_lump_col, ctx->d_lump_val, vloc, loc, zero, st);
+  } else if (f32) {
+    feti::launch_gather32(ctx->maps, q, ctx->d_weight, vloc32, zero, st);
+    feti::launch_gemv_loc(ctx->cfg32[1], ctx->d_lay, 1, ctx->d_S32, 1, vloc32, loc, ctx->max_nb, zero, st);
+  } else {
+    feti::launch_gather(ctx->maps, q, ctx->d_weight, vloc, zero, st);
+    feti::launch_gemv_loc(ctx->cfg64[1], ctx->d_lay, 1, ctx->d_S, 0, vloc, loc, ctx->max_nb, zero, st);
+  }
+  feti::launch_scatter(ctx->maps, loc, ctx->d_weight, z, nullptr, nullptr, zero, st);
+  FETI_CK(cudaGetLastError());
+  return FETI_OK;
+}
+
+}  // namespace feti
+
 extern "C" {
 
 feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat, const feti_bc* bc,

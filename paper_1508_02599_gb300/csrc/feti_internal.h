@@ -2,7 +2,10 @@
 // kernels (feti_kernels.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+
+#include "feti.h"
 
 namespace feti {
 
@@ -250,4 +253,14 @@ void launch_spmv_lump_m(int n_rows, int nrhs, const int32_t* ptr, const int32_t*
 void launch_col_get(int n, int nrhs, int k, const double* blk, double* v, cudaStream_t st);
 // blk[:, k] = scale * v
 void launch_col_set(int n, int nrhs, int k, double scale, const double* v, double* blk, cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// Records msg as the context's last error and returns st.
+feti_status set_error(feti_ctx* ctx, feti_status st, const std::string& msg);
+// q = F v, z = M^-1 q with the local scratch vectors placed in the caller's
+// device buffer `scratch` (capacity in doubles) instead of context memory;
+// enqueued on the context's stream, no allocation, no graph, no event.
+feti_status dual_apply_with_scratch(feti_ctx* ctx, const double* v, double* q, double* z, double* scratch,
+                                    size_t capacity);
 }  // namespace feti
