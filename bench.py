@@ -281,8 +281,10 @@ def main():
         ms = ev0.elapsed_time(ev1)
         ks = solver.kernel_stats()
         km = statistics.mean(kern)
+        sched = solver.schedule()
         solver.close()
         return {"rhs_applies_per_s": nrhs * args.steps * n_ap / (ms / 1e3), "nrhs": nrhs,
+                "gemm_schedule": sched["block_fp32_F"] if precision == "mixed" else None,
                 "pcg_time_to_tol_ms": rep["t_pcg_ms"], "iterations": rep["iterations"],
                 "outer_iterations": rep["outer_iterations"], "converged": rep["converged"],
                 "gemm_kernel_ms": km, "gemm_gbs": ks["gemv_bytes"] / (km / 1e3) / 1e9,

@@ -115,6 +115,7 @@ typedef struct {
   int32_t newton_maxit;
   double inner_tol;    /* FETI_MIXED: relative tolerance of each inner solve (0: 1e-4) */
   int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
+  int32_t no_tensor_cores; /* nonzero: keep the FP32 block GEMM on CUDA cores */
 } feti_options;
 
 typedef struct {
@@ -244,8 +245,10 @@ feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv
 /* Launch schedules of the dense local applies chosen by the setup-time
  * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
  * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
- * preconditioner apply, out[4..7] the same for the FP32 copies. */
-feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[8]);
+ * preconditioner apply, out[4..7] the same for the FP32 copies, out[8..11]
+ * the FP32 block-form GEMMs (rows per warp step 0 = tensor-core kernel;
+ * -1 = block form not tuned yet). */
+feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]);
 
 const char* feti_last_error(const feti_ctx* ctx);
 void feti_destroy(feti_ctx* ctx);

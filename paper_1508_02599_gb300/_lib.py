@@ -41,7 +41,7 @@ class FetiOptions(C.Structure):
     _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("maxit", C.c_int32), ("chunk", C.c_int32), ("follower", C.c_int32),
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32)]
 
 
 class FetiReport(C.Structure):

@@ -38,7 +38,8 @@ class FetiSolver:
     def __init__(self, prob, method: str = "af", precond: str = "dirichlet", tol: float = 1e-10,
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
-                 precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0):
+                 precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
+                 tensor_cores: bool = True):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -68,7 +69,7 @@ class FetiSolver:
         prec = {"fp64": L.FP64, "mixed": L.MIXED}[precision]
         opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], prec, float(tol), int(maxit), int(chunk),
                             int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
-                            float(inner_tol), int(max_outer))
+                            float(inner_tol), int(max_outer), int(not tensor_cores))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))
@@ -204,10 +205,11 @@ class FetiSolver:
         return ms.value
 
     def schedule(self) -> dict:
-        out = np.zeros(8, np.int32)
+        out = np.zeros(12, np.int32)
         self._check(self._lib.feti_get_schedule(self._ctx, out.ctypes.data))
         o = [int(x) for x in out]
-        return {"fp64_F": o[0:2], "fp64_M": o[2:4], "fp32_F": o[4:6], "fp32_M": o[6:8]}
+        return {"fp64_F": o[0:2], "fp64_M": o[2:4], "fp32_F": o[4:6], "fp32_M": o[6:8],
+                "block_fp32_F": o[8:10], "block_fp32_M": o[10:12]}
 
     def kernel_stats(self) -> dict:
         a, b, c = C.c_double(), C.c_double(), C.c_double()

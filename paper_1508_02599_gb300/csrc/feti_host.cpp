@@ -81,6 +81,8 @@ struct feti_ctx {
   feti::GemvCfg tab[2][3];
   feti::GemvCfg cfg64[2], cfg32[2];
   feti::GemvCfg cfgm64[2], cfgm32[2];  // block form (N = nrhs) schedules
+  bool tc_m[2] = {false, false};       // FP32 block GEMM on the tensor cores (tcgen05)
+  int* d_tc_err = nullptr;
   int tuned_m = 0;                     // nrhs the block schedules were tuned for
   bool tuned = false;
   float* d_vloc32 = nullptr;
@@ -1292,6 +1294,24 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
             FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < bt) { bt = ms; best = c; }
           }
+        if (f32 && !ctx->opt.no_tensor_cores) {
+          // tensor-core candidate: kept only if faster and no bounded wait timed out
+          if (!ctx->d_tc_err) FETI_TRY(dev_alloc(ctx, &ctx->d_tc_err, 1));
+          FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
+          const float* Mf = static_cast<const float*>(M);
+          const float* vf = static_cast<const float*>(v);
+          feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err, st);
+          FETI_CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 3; ++rep)
+            feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err, st);
+          FETI_CK(cudaEventRecord(e1, st));
+          FETI_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+          int herr = 0;
+          FETI_CK(cudaMemcpy(&herr, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+          ctx->tc_m[w] = herr == 0 && ms < bt;
+        }
       }
       (f32 ? ctx->cfgm32[w] : ctx->cfgm64[w]) = best;
     }
@@ -1345,7 +1365,11 @@ void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const do
                       : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
   void* v = f32 ? (void*)ctx->dm_vloc32 : (void*)ctx->dm_vloc;
   feti::launch_gather_m(ctx->maps, nrhs, x, wv, v, f32 ? 1 : 0, done, st);
-  feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
+  if (f32 && ctx->tc_m[which])
+    feti::launch_gemm_tc(ctx->tab[which][2], ctx->d_lay, which, static_cast<const float*>(M), nrhs,
+                         static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, st);
+  else
+    feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
 }
 
 void apply_F_m(feti_ctx* ctx, int nrhs, const double* x, double* q, const double* a, double* partial, const int* done,
@@ -1883,8 +1907,12 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
       void* vl = f32 ? (void*)ctx->dm_vloc32 : (void*)ctx->dm_vloc;
       feti::launch_gather_m(ctx->maps, nrhs, v, nullptr, vl, f32 ? 1 : 0, zero, st);
       FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[2 + 2 * i], st, cudaEventRecordExternal));
-      feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
-                            nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
+      if (f32 && ctx->tc_m[0])
+        feti::launch_gemm_tc(ctx->tab[0][2], ctx->d_lay, 0, ctx->d_F32, nrhs, static_cast<const float*>(vl), ctx->dm_loc,
+                             zero, ctx->d_tc_err, st);
+      else
+        feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
+                              nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
       FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[3 + 2 * i], st, cudaEventRecordExternal));
       feti::launch_scatter_m(ctx->maps, nrhs, ctx->dm_loc, nullptr, q, nullptr, nullptr, zero, st);
       apply_M_m(ctx, nrhs, q, z, zero, f32);
@@ -2025,13 +2053,18 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
   return FETI_OK;
 }
 
-feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[8]) {
+feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
   if (!ctx || !out) return FETI_ERR_INVALID_ARG;
+  for (int i = 8; i < 12; ++i) out[i] = -1;
   for (int w = 0; w < 2; ++w) {
     out[2 * w] = ctx->cfg64[w].R;
     out[2 * w + 1] = ctx->cfg64[w].rpc;
     out[4 + 2 * w] = ctx->cfg32[w].R;
     out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
+    if (ctx->tuned_m) {
+      out[8 + 2 * w] = ctx->tc_m[w] ? 0 : ctx->cfgm32[w].R;
+      out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;
+    }
   }
   return FETI_OK;
 }

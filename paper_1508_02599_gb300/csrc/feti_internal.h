@@ -234,6 +234,11 @@ void launch_gather_m(const Maps& mp, int nrhs, const double* x, const double* wv
 // Y = M_i V per subdomain (batched GEMM, N = nrhs), FP64 or FP32 copies.
 void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, int nrhs,
                      const void* vloc, double* y, int max_m, const int* done, cudaStream_t st);
+// Tensor-core (tcgen05, 3xTF32) variant of the FP32 block GEMM; cfg must be
+// the 128-rows-per-CTA table; nrhs <= 16; *err is set if a bounded wait
+// timed out.
+void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
+                    double* y, const int* done, int* err, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
 // c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).

@@ -433,6 +433,206 @@ __global__ void k_col_set(int n, int nrhs, int k, double scale, const double* __
     blk[(size_t)i * nrhs + k] = scale * v[i];
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core block GEMM (tcgen05, kind::tf32, 3xTF32): Y (m x nrhs) = M_i V
+// for the FP32 copies.  A CTA owns 128 rows of one subdomain; K runs in
+// chunks of 32 columns through two shared-memory stages.  Each operand tile
+// is split into a TF32 head and a tail (x = hi + lo, lo exact in FP32) while
+// it is staged, and the three products hi*hi + hi*lo + lo*hi accumulate in
+// FP32 in tensor memory (128 lanes x 16 columns), which gives FP32-level
+// accuracy from TF32 tensor-core passes.  Staged tiles use the 128-byte
+// swizzled K-major layout (8 rows x 128 B atoms), so the row-contiguous
+// global loads map onto conflict-free shared-memory stores.  One thread
+// issues the MMAs and commits them to an mbarrier per stage; all waits are
+// bounded (about 0.1 s of clock cycles) and report a timeout in *err.
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t par) {
+  uint32_t ok;
+  asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+               : "=r"(ok)
+               : "r"(su32(b)), "r"(par)
+               : "memory");
+  return ok != 0;
+}
+
+// Shared-memory matrix descriptor: 128-byte swizzle, K-major, 1024 B between
+// 8-row groups.
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  uint64_t d = (su32(p) >> 4) & 0x3FFF;
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ int sw_off(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
+                   tmem),
+               "l"(a), "l"(b), "r"(idesc), "r"(acc)
+               : "memory");
+}
+
+constexpr int TC_A_BYTES = 128 * 128;
+constexpr int TC_B_BYTES = 16 * 128;
+constexpr int TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr int TC_SMEM = 2 * TC_STAGE + 1024;
+
+__global__ void __launch_bounds__(kThreads) k_gemm_tc(const int32_t* __restrict__ blk_sub,
+                                                      const int32_t* __restrict__ blk_row0,
+                                                      const SubLayout* __restrict__ lay, int which,
+                                                      const float* __restrict__ M, int nrhs,
+                                                      const float* __restrict__ vloc, double* __restrict__ y,
+                                                      const int* __restrict__ done, int* __restrict__ err) {
+  if (*done) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+  unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  const int s_id = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s_id];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int ldm = (m + 3) & ~3;
+  const float* Ms = M + (which == 0 ? L.foff32 : L.soff32);
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  if (which == 0 && r0 == 0)
+    for (int idx = tid; idx < L.k * nrhs; idx += blockDim.x) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // instruction descriptor: D FP32, A and B TF32, both K-major, N = 16, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  const int nk = (m + 31) / 32;
+  bool timed_out = false;
+  // register prefetch: each thread holds the 4 A chunks (16 B each) and up to
+  // one B chunk of the next K step while the current step is staged and
+  // multiplied
+  float4 ra[4], rb;
+  auto load_chunk = [&](int kc2) {
+    const int k0 = kc2 * 32;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * kThreads;
+      const int r = idx >> 3, c = idx & 7;
+      const int row = r0 + r, col = k0 + 4 * c;
+      ra[q] = (row < m && col < ldm) ? __ldg(reinterpret_cast<const float4*>(Ms + (size_t)row * ldm + col))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid < 16 * 8) {
+      const int n = tid >> 3, c = tid & 7;
+      float v4[4];
+      for (int e = 0; e < 4; ++e) {
+        const int kk = k0 + 4 * c + e;
+        v4[e] = (kk < m && n < nrhs) ? vloc[(size_t)(L.boff + kk) * nrhs + n] : 0.f;
+      }
+      rb = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+  };
+  if (nk > 0) load_chunk(0);
+  for (int kc = 0; kc < nk; ++kc) {
+    const int st = kc & 1;
+    float4 ca[4], cb = rb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ca[q] = ra[q];
+    if (kc + 1 < nk) load_chunk(kc + 1);
+    if (kc >= 2) {
+      const uint32_t par = ((kc - 2) >> 1) & 1;
+      const long long t0 = clock64();
+      while (!timed_out && !mbar_try(&mbar[st], par))
+        if (clock64() - t0 > 200000000LL) timed_out = true;
+    }
+    unsigned char* sb = smem + st * TC_STAGE;
+    unsigned char* Ahi = sb;
+    unsigned char* Alo = sb + TC_A_BYTES;
+    unsigned char* Bhi = sb + 2 * TC_A_BYTES;
+    unsigned char* Blo = Bhi + TC_B_BYTES;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * kThreads;
+      const int r = idx >> 3, c = idx & 7;
+      float4 h, l;
+      split_tf32(ca[q].x, h.x, l.x);
+      split_tf32(ca[q].y, h.y, l.y);
+      split_tf32(ca[q].z, h.z, l.z);
+      split_tf32(ca[q].w, h.w, l.w);
+      *reinterpret_cast<float4*>(Ahi + sw_off(r, c)) = h;
+      *reinterpret_cast<float4*>(Alo + sw_off(r, c)) = l;
+    }
+    if (tid < 16 * 8) {
+      const int n = tid >> 3, c = tid & 7;
+      float4 h, l;
+      split_tf32(cb.x, h.x, l.x);
+      split_tf32(cb.y, h.y, l.y);
+      split_tf32(cb.z, h.z, l.z);
+      split_tf32(cb.w, h.w, l.w);
+      *reinterpret_cast<float4*>(Bhi + sw_off(n, c)) = h;
+      *reinterpret_cast<float4*>(Blo + sw_off(n, c)) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
+        const uint64_t bh = sw128_desc(Bhi + 32 * j), bl = sw128_desc(Blo + 32 * j);
+        tc_mma(tmem, ah, bh, idesc, (kc > 0 || j > 0) ? 1u : 0u);
+        tc_mma(tmem, ah, bl, idesc, 1u);
+        tc_mma(tmem, al, bh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&mbar[st]))
+                   : "memory");
+    }
+  }
+  if (nk > 0) {
+    const int st = (nk - 1) & 1;
+    const uint32_t par = ((nk - 1) >> 1) & 1;
+    const long long t0 = clock64();
+    while (!timed_out && !mbar_try(&mbar[st], par))
+      if (clock64() - t0 > 200000000LL) timed_out = true;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (timed_out && lane == 0) atomicExch(err, 1);
+  if (wid < 4) {
+    uint32_t r[16];
+    const uint32_t taddr = tmem + ((uint32_t)(wid * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = r0 + wid * 32 + lane;
+    if (row < m && !timed_out)
+      for (int n = 0; n < nrhs; ++n) y[(size_t)(L.boff + row) * nrhs + n] = (double)__uint_as_float(r[n]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
 inline int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -479,6 +679,16 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
       launch_gemm_t<double, 1>(cfg, lay, which, static_cast<const double*>(M), nrhs, static_cast<const double*>(vloc), y,
                                max_m, done, st);
   }
+}
+
+void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
+                    double* y, const int* done, int* err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    attr = true;
+  }
+  k_gemm_tc<<<cfg.n_blocks, kThreads, TC_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, M, nrhs, vloc, y, done, err);
 }
 
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
