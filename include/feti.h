@@ -115,7 +115,8 @@ typedef struct {
   int32_t newton_maxit;
   double inner_tol;    /* FETI_MIXED: relative tolerance of each inner solve (0: 1e-4) */
   int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
-  int32_t no_tensor_cores; /* nonzero: keep the FP32 block GEMM on CUDA cores */
+  int32_t no_tensor_cores; /* FP32 block GEMM: 0 = autotuner picks tensor cores if faster,
+                              1 = CUDA cores only, 2 = tensor cores whenever they run cleanly */
 } feti_options;
 
 typedef struct {

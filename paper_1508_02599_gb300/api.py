@@ -39,7 +39,7 @@ class FetiSolver:
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
-                 tensor_cores: bool = True):
+                 tensor_cores="auto"):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -69,7 +69,8 @@ class FetiSolver:
         prec = {"fp64": L.FP64, "mixed": L.MIXED}[precision]
         opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], prec, float(tol), int(maxit), int(chunk),
                             int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
-                            float(inner_tol), int(max_outer), int(not tensor_cores))
+                            float(inner_tol), int(max_outer),
+                            {"auto": 0, False: 1, "off": 1, True: 2, "force": 2}[tensor_cores])
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

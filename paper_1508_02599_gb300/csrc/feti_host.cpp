@@ -1294,7 +1294,7 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
             FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < bt) { bt = ms; best = c; }
           }
-        if (f32 && !ctx->opt.no_tensor_cores) {
+        if (f32 && ctx->opt.no_tensor_cores != 1) {
           // tensor-core candidate: kept only if faster and no bounded wait timed out
           if (!ctx->d_tc_err) FETI_TRY(dev_alloc(ctx, &ctx->d_tc_err, 1));
           FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
@@ -1310,7 +1310,7 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
           int herr = 0;
           FETI_CK(cudaMemcpy(&herr, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-          ctx->tc_m[w] = herr == 0 && ms < bt;
+          ctx->tc_m[w] = herr == 0 && (ms < bt || ctx->opt.no_tensor_cores == 2);
         }
       }
       (f32 ? ctx->cfgm32[w] : ctx->cfgm64[w]) = best;

@@ -61,3 +61,37 @@ def test_block_apply_equals_single_applies():
             torch.cuda.synchronize()
             assert (Q[:, k] - q).abs().max().item() <= 1e-12 * q.abs().max().item()
             assert (Z[:, k] - z).abs().max().item() <= 1e-12 * z.abs().max().item()
+
+
+def test_tensor_core_block_gemm_matches_cuda_cores():
+    """The tcgen05 3xTF32 block GEMM against the CUDA-core FP32 GEMM (same FP32
+    operator copies): agreement to 1e-5 relative (TF32 head + tail products
+    reproduce FP32 products to about 2^-22 each), then a full block solve on
+    the tensor cores against the oracle."""
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = TUBE_FLOAT
+    rng = np.random.default_rng(8)
+    outs = {}
+    for tc in ("off", "force"):
+        with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", tensor_cores=tc) as s:
+            s.prepare()
+            nl = s.sizes()["n_lambda"]
+            V = torch.tensor(np.random.default_rng(8).normal(size=(nl, 16)), device="cuda", dtype=torch.float64)
+            Q = torch.empty_like(V)
+            Z = torch.empty_like(V)
+            s.dual_apply_multi(V, Q, Z, 16, 1)
+            torch.cuda.synchronize()
+            outs[tc] = (Q.cpu().numpy(), Z.cpu().numpy(), s.schedule())
+    assert outs["force"][2]["block_fp32_F"][0] == 0       # the tensor-core kernel ran
+    assert outs["off"][2]["block_fp32_F"][0] > 0
+    for i in range(2):
+        a, b = outs["force"][i], outs["off"][i]
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+    o = feti.FetiOracle(prob, "af", "dirichlet")
+    U_ref, _, _ = o.solve(tol=1e-12, maxit=3000)
+    with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-11, maxit=5000, precision="mixed",
+                    tensor_cores="force") as s:
+        U, rep = s.solve_multi(SCALES)
+    assert rep["converged"] == 1
+    for k, sc in enumerate(SCALES):
+        assert np.linalg.norm(U[k] - sc * U_ref) <= 1e-8 * np.linalg.norm(sc * U_ref)
