@@ -160,6 +160,10 @@ def main():
                          "jcyl32: jittered tube, 1024 uneven subdomains")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--block", type=int, default=1, help="also measure the 16-RHS block form (0: skip)")
+    ap.add_argument("--elements", type=int, default=1,
+                    help="also time the hyperelastic element kernel on the 256-subdomain tube (0: skip)")
+    ap.add_argument("--elements-only", action="store_true",
+                    help="only the element-kernel leg: for profiler captures")
     ap.add_argument("--apply-only", action="store_true",
                     help="setup only (no PCG solve) before the timed applies: for profiler captures")
     args = ap.parse_args()
@@ -205,10 +209,12 @@ def main():
     peaks, src = _peaks()
     fp64_peak = 1.259  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derivation in the design doc)
 
-    def measure(precision: str):
+    def measure(precision: str, batched: bool = True, n_apply: int = 0, steps: int = 0):
         """Full solve once, then `steps` timed blocks of n_apply dual applies."""
+        n_apply = n_apply or args.n_apply
+        steps = steps or args.steps
         solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
-                            stream=stream.cuda_stream, precision=precision)
+                            stream=stream.cuda_stream, precision=precision, batched=batched)
         if args.apply_only:
             solver.prepare()
             U, rep = np.zeros(3 * prob.n_nodes), {"t_pcg_ms": None, "iterations": 0, "outer_iterations": 0,
@@ -222,7 +228,7 @@ def main():
         q = torch.empty_like(v)
         z = torch.empty_like(v)
         for _ in range(args.warmup):
-            solver.dual_apply(v, q, z, args.n_apply)
+            solver.dual_apply(v, q, z, n_apply)
         clocks = ClockSampler(local)
         clocks.start()
         if world > 1:
@@ -232,8 +238,8 @@ def main():
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         kern_ms = []
-        for _ in range(args.steps):
-            solver.dual_apply(v, q, z, args.n_apply)
+        for _ in range(steps):
+            solver.dual_apply(v, q, z, n_apply)
             kern_ms.append(solver.kernel_stats()["gemv_ms"])
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -250,7 +256,7 @@ def main():
         kern = statistics.mean(kern_ms)
         solver.close()
         return {"U": U, "rep": rep, "sizes": sizes, "ms": ms, "kern_ms": kern, "ks": ks, "clocks": clk, "sched": sched,
-                "value": args.steps * args.n_apply * world / (ms / 1e3)}
+                "value": steps * n_apply * world / (ms / 1e3), "steps": steps}
 
     def measure_block(precision: str, nrhs: int = 16):
         """Block form: nrhs load cases p_k ~ U[8, 16] x the reference pressure (seeded), one block
@@ -290,8 +296,42 @@ def main():
                 "gemm_kernel_ms": km, "gemm_gbs": ks["gemv_bytes"] / (km / 1e3) / 1e9,
                 "gemm_tflops": ks["gemv_flops"] / (km / 1e3) / 1e12, "U": U, "scales": scales}
 
+    def measure_elements():
+        """Element tangents + internal forces of the two-fibre hyperelastic model (Table 1) on the
+        24x96x48-cell tube (663,552 tets), at a 5 % radial expansion (fibres stretched, active)."""
+        ep = mesh.config_problem("cyl24_hgo")
+        U = np.zeros((ep.n_nodes, 3))
+        U[:, :2] = 0.05 * ep.coords[:, :2]
+        solver = FetiSolver(ep, method="af", precond="dirichlet", stream=stream.cuda_stream)
+        dU = torch.tensor(U.ravel(), device="cuda")
+        Ke = torch.empty((ep.tets.shape[0], 12, 12), dtype=torch.float64, device="cuda")
+        fe = torch.empty((ep.tets.shape[0], 12), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            solver.elements(dU, out=(Ke, fe))
+        ms = []
+        for _ in range(max(3, args.steps // 4)):
+            solver.elements(dU, out=(Ke, fe))
+            ms.append(solver.element_stats()["elem_ms"])
+        st_ = solver.element_stats()
+        solver.close()
+        kms = statistics.median(ms)
+        gbs = st_["elem_bytes"] / (kms / 1e3) / 1e9
+        return {"workload": "tube 24x96x48 cells P1, 663,552 tets, two-fibre hyperelastic (Table 1), U = 5 % "
+                            "radial expansion", "kernel": "k_elem_hgo", "kernel_ms": kms,
+                "elements_per_s": st_["n_elements"] / (kms / 1e3), "achieved_gbs": gbs,
+                "hbm_frac": gbs / peaks["hbm_gbs"], "algorithmic_bytes": st_["elem_bytes"],
+                "bound": "alu (FP64); ncu FP64-pipe share in profiles/"}
+
+    if args.elements_only:
+        el = measure_elements()
+        if rank == 0:
+            print(json.dumps({"elements": el}), flush=True)
+        return
     m64 = measure("fp64")
     m32 = measure("mixed")
+    # the plain FP64 form: the same kernels with the local applies launched once
+    # per subdomain (p launches per apply instead of one batched launch)
+    mp = measure("fp64", batched=False, n_apply=max(1, args.n_apply // 4), steps=max(1, args.steps // 4))
     b64 = measure_block("fp64") if args.block else None
     b32 = measure_block("mixed") if args.block else None
     n64 = np.linalg.norm(m64["U"])
@@ -340,6 +380,11 @@ def main():
                                   "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf64 / fp64_peak,
                                   "hbm_gbs": gbs64, "kernel_ms": m64["kern_ms"]},
                      "clocks": m64["clocks"]},
+            "fp64_per_subdomain": {"value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms"] / mp["steps"],
+                                   "time_to_tol_ms": mp["rep"]["t_pcg_ms"], "iterations": mp["rep"]["iterations"],
+                                   "local_apply_kernel_ms": mp["kern_ms"],
+                                   "note": "plain form: FP64, one local-apply launch per subdomain instead of "
+                                           "one batched launch; same kernels, graphs and schedule"},
             "roofline": {"bound": "hbm", "kernel": "k_gemv_loc<float> (F_i apply, FP32 copy)", "achieved": gbs32,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],
                          "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
@@ -363,6 +408,8 @@ def main():
             blk["note"] = ("16 load cases (pressure x U[8,16], seeded) solved as one block: every dense F_i/S_i "
                            "entry read feeds 16 products; rhs_applies_per_s counts right-hand sides")
             line["block16"] = blk
+        if args.elements:
+            line["elements"] = measure_elements()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(prob, n_apply=20)
         print(json.dumps(line), flush=True)

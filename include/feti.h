@@ -116,7 +116,13 @@ typedef struct {
   double inner_tol;    /* FETI_MIXED: relative tolerance of each inner solve (0: 1e-4) */
   int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
   int32_t no_tensor_cores; /* FP32 block GEMM: 0 = autotuner picks tensor cores if faster,
-                              1 = CUDA cores only, 2 = tensor cores whenever they run cleanly */
+                              1 = CUDA cores only, 2 = tensor cores whenever they run cleanly
+                              (faster of the two staging variants), 3 / 4 = only the
+                              register-staged / bulk-copy staged tensor-core kernel */
+  int32_t per_subdomain;   /* nonzero: the dense local applies of F_i and S_i are launched once per
+                              subdomain (p launches per apply, the plain non-batched form) instead
+                              of one batched launch over all subdomains; same results, for
+                              measuring what batching buys */
 } feti_options;
 
 typedef struct {
@@ -243,12 +249,23 @@ feti_status feti_prepare(feti_ctx* ctx);
 feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv_bytes,
                               double* gemv_flops);
 
+/* Element kernel of the last feti_elements call (the P1 tangent and
+ * internal-force kernel of Sec. 3, hyperelastic or linear): its device time
+ * (CUDA events on the context's stream around the one launch), the
+ * algorithmic bytes it must move (connectivity 16 B, fibres 48 B, the
+ * symmetric tangent 78 x 8 B and the force 12 x 8 B per element, coordinates
+ * and displacement 48 B per node, each read once) and the element count.
+ * Zeros before the first feti_elements call. */
+feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* elem_bytes,
+                               double* n_elements);
+
 /* Launch schedules of the dense local applies chosen by the setup-time
  * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
  * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
  * preconditioner apply, out[4..7] the same for the FP32 copies, out[8..11]
- * the FP32 block-form GEMMs (rows per warp step 0 = tensor-core kernel;
- * -1 = block form not tuned yet). */
+ * the FP32 block-form GEMMs (rows per warp step 0 = tensor-core kernel with
+ * register-staged operands, -1 = tensor-core kernel with bulk-copy staged
+ * operands; both -1 = block form not tuned yet). */
 feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]);
 
 const char* feti_last_error(const feti_ctx* ctx);

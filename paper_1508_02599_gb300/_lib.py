@@ -41,7 +41,8 @@ class FetiOptions(C.Structure):
     _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("maxit", C.c_int32), ("chunk", C.c_int32), ("follower", C.c_int32),
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32),
+                ("per_subdomain", C.c_int32)]
 
 
 class FetiReport(C.Structure):
@@ -52,7 +53,7 @@ class FetiReport(C.Structure):
 
 
 EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
-           "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_get_schedule",
+           "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_element_stats", "feti_get_schedule",
            "feti_last_error",
            "feti_destroy"]
 
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.feti_solve_multi.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_prepare.argtypes = [vp]
     lib.feti_kernel_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.feti_element_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.feti_get_schedule.argtypes = [vp, vp]
     lib.feti_last_error.argtypes = [vp]
     lib.feti_last_error.restype = C.c_char_p

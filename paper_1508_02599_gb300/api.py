@@ -39,7 +39,7 @@ class FetiSolver:
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
-                 tensor_cores="auto"):
+                 tensor_cores="auto", batched: bool = True):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -70,7 +70,9 @@ class FetiSolver:
         opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], prec, float(tol), int(maxit), int(chunk),
                             int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
                             float(inner_tol), int(max_outer),
-                            {"auto": 0, False: 1, "off": 1, True: 2, "force": 2}[tensor_cores])
+                            {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
+                             "force_bulk": 4}[tensor_cores],
+                            int(not batched))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))
@@ -123,9 +125,19 @@ class FetiSolver:
         self._check(self._lib.feti_get_fixing(self._ctx, None, ld.ctypes.data))
         return [ld[ptr[s]:ptr[s + 1]].copy() for s in range(P)]
 
-    def elements(self, U=None, n_tets: int | None = None):
-        """Element tangents [E,12,12] and internal forces [E,12] (hyperelastic) at U (host arrays)."""
+    def elements(self, U=None, n_tets: int | None = None, out=None):
+        """Element tangents [E,12,12] and internal forces [E,12] (hyperelastic) at U.
+
+        Host arrays by default; with out = (Ke, fe) torch CUDA float64 tensors
+        of those shapes, U must be a torch CUDA tensor (or None) and the
+        results stay on the device."""
         E = n_tets if n_tets is not None else self._n_tets
+        if out is not None:
+            Ke, fe = out
+            up = None if U is None else C.c_void_p(U.data_ptr())
+            self._check(self._lib.feti_elements(self._ctx, up, 1, C.c_void_p(Ke.data_ptr()),
+                                                C.c_void_p(fe.data_ptr()), 1))
+            return Ke, fe
         Ke = np.empty((E, 12, 12), np.float64)
         fe = np.empty((E, 12), np.float64)
         Uc = None if U is None else np.ascontiguousarray(U, dtype=np.float64).ravel()
@@ -211,6 +223,11 @@ class FetiSolver:
         o = [int(x) for x in out]
         return {"fp64_F": o[0:2], "fp64_M": o[2:4], "fp32_F": o[4:6], "fp32_M": o[6:8],
                 "block_fp32_F": o[8:10], "block_fp32_M": o[10:12]}
+
+    def element_stats(self) -> dict:
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.feti_element_stats(self._ctx, C.byref(a), C.byref(b), C.byref(c)))
+        return {"elem_ms": a.value, "elem_bytes": b.value, "n_elements": int(c.value)}
 
     def kernel_stats(self) -> dict:
         a, b, c = C.c_double(), C.c_double(), C.c_double()

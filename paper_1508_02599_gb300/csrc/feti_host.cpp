@@ -79,9 +79,10 @@ struct feti_ctx {
   // CTA tables of the dense local applies for rows-per-CTA 32, 64, 128
   // ([which][k]), and the schedules picked by the autotuner
   feti::GemvCfg tab[2][3];
+  std::vector<int32_t> tab_ptr[2][3];  // first CTA of each subdomain in tab[which][k] (p + 1 entries)
   feti::GemvCfg cfg64[2], cfg32[2];
   feti::GemvCfg cfgm64[2], cfgm32[2];  // block form (N = nrhs) schedules
-  bool tc_m[2] = {false, false};       // FP32 block GEMM on the tensor cores (tcgen05)
+  int tc_m[2] = {0, 0};  // FP32 block GEMM on the tensor cores: 0 no, 1 register-staged, 2 bulk-copy staged
   int* d_tc_err = nullptr;
   int tuned_m = 0;                     // nrhs the block schedules were tuned for
   bool tuned = false;
@@ -121,6 +122,9 @@ struct feti_ctx {
   bool pcg_graph_mixed = false;
   double t_setup_ms = 0.0;
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
+  double elem_ms = 0.0, elem_bytes = 0.0;
+  int64_t op_elems[5] = {0, 0, 0, 0, 0};  // sizes of d_A, d_S, d_F, d_F32, d_S32 (elements)
+  cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
   int m_cap = 0;  // allocated nrhs capacity of the block buffers
   double *dm_lam = nullptr, *dm_r = nullptr, *dm_w = nullptr, *dm_z = nullptr, *dm_y = nullptr, *dm_p = nullptr;
@@ -699,7 +703,9 @@ feti_status build_decomposition(feti_ctx* ctx) {
       for (int s = 0; s < P; ++s) {
         const SubLayout& L = ctx->lay[s];
         const int m = w == 0 ? std::max(L.nbp, 1) : L.nbp + L.k;
+        ctx->tab_ptr[w][t].push_back((int32_t)tab_sub[w][t].size());
         for (int r0 = 0; r0 < m; r0 += rpcs[t]) { tab_sub[w][t].push_back(s); tab_row[w][t].push_back(r0); }
+        if (s == P - 1) ctx->tab_ptr[w][t].push_back((int32_t)tab_sub[w][t].size());
       }
   // chunks of 256 boundary positions for the projection's G^T v
   std::vector<int32_t> chunk_sub, chunk_p0, sub_chunk_ptr(P + 1, 0), col_sub(std::max<int64_t>(ctx->cd, 1), 0);
@@ -788,13 +794,13 @@ feti_status build_decomposition(feti_ctx* ctx) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_Utrial, 3 * (size_t)N));
     FETI_TRY(dev_alloc(ctx, &ctx->d_fl, ctx->nloc_total));
   }
-  FETI_TRY(dev_alloc(ctx, &ctx->d_A, aoff));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_S, ctx->opt.precond == FETI_PREC_DIRICHLET ? soff : 1));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_F, foff));
-  if (ctx->opt.precision == FETI_MIXED) {
-    FETI_TRY(dev_alloc(ctx, &ctx->d_F32, foff32));
-    FETI_TRY(dev_alloc(ctx, &ctx->d_S32, ctx->opt.precond == FETI_PREC_DIRICHLET ? soff32 : 1));
-  }
+  // the dense local operators (the bulk of the memory) are allocated by the
+  // first setup, so that element-only use of a context does not hold them
+  ctx->op_elems[0] = aoff;
+  ctx->op_elems[1] = ctx->opt.precond == FETI_PREC_DIRICHLET ? soff : 1;
+  ctx->op_elems[2] = foff;
+  ctx->op_elems[3] = foff32;
+  ctx->op_elems[4] = ctx->opt.precond == FETI_PREC_DIRICHLET ? soff32 : 1;
   FETI_TRY(dev_alloc(ctx, &ctx->d_f, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x2, ctx->nloc_total));
@@ -966,18 +972,39 @@ void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool 
   feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, partial, with_dot, done, st);
 }
 
+// Dense local apply of F_i (which 0) or the preconditioner block (which 1)
+// on the gathered local vector (d_vloc / d_vloc32) into d_loc: one batched
+// launch over all subdomains, or, in the plain form, the same kernel and
+// schedule launched once per subdomain.
+void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
+  const feti::GemvCfg& cfg = f32 ? ctx->cfg32[which] : ctx->cfg64[which];
+  const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
+                      : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
+  const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+  if (!ctx->opt.per_subdomain) {
+    feti::launch_gemv_loc(cfg, ctx->d_lay, which, M, f32, v, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+    return;
+  }
+  int t = 0;
+  while (t < 2 && ctx->tab[which][t].rpc != cfg.rpc) ++t;
+  const std::vector<int32_t>& ptr = ctx->tab_ptr[which][t];
+  for (size_t s = 0; s + 1 < ptr.size(); ++s) {
+    feti::GemvCfg c = cfg;
+    c.n_blocks = ptr[s + 1] - ptr[s];
+    c.blk_sub = cfg.blk_sub + ptr[s];
+    c.blk_row0 = cfg.blk_row0 + ptr[s];
+    if (c.n_blocks > 0) feti::launch_gemv_loc(c, ctx->d_lay, which, M, f32, v, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+  }
+}
+
 // Signed gather of x (weights wv or none) and the dense local apply of F_i
 // (which 0) or the preconditioner block (which 1) into d_loc.
 void local_apply(feti_ctx* ctx, int which, const double* x, const double* wv, const int* done, bool f32) {
-  if (f32) {
+  if (f32)
     feti::launch_gather32(ctx->maps, x, wv, ctx->d_vloc32, done, ctx->stream);
-    feti::launch_gemv_loc(ctx->cfg32[which], ctx->d_lay, which, which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32,
-                          1, ctx->d_vloc32, ctx->d_loc, ctx->max_nb, done, ctx->stream);
-  } else {
+  else
     feti::launch_gather(ctx->maps, x, wv, ctx->d_vloc, done, ctx->stream);
-    feti::launch_gemv_loc(ctx->cfg64[which], ctx->d_lay, which, which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S,
-                          0, ctx->d_vloc, ctx->d_loc, ctx->max_nb, done, ctx->stream);
-  }
+  gemv_apply(ctx, which, done, f32);
 }
 
 // q = F x: signed gather B_i^T x, dense F_i apply, row-major gather back;
@@ -1093,8 +1120,22 @@ feti_status build_pcg_graph(feti_ctx* ctx, int chunk, bool mixed) {
   return FETI_OK;
 }
 
+// Dense local matrices (factorized in place), S_i, F_i and their FP32 copies.
+feti_status alloc_operators(feti_ctx* ctx) {
+  if (ctx->d_A) return FETI_OK;
+  FETI_TRY(dev_alloc(ctx, &ctx->d_A, (size_t)ctx->op_elems[0]));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_S, (size_t)ctx->op_elems[1]));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_F, (size_t)ctx->op_elems[2]));
+  if (ctx->opt.precision == FETI_MIXED) {
+    FETI_TRY(dev_alloc(ctx, &ctx->d_F32, (size_t)ctx->op_elems[3]));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_S32, (size_t)ctx->op_elems[4]));
+  }
+  return FETI_OK;
+}
+
 // Setup: element matrices through the coarse inverse.
 feti_status prepare(feti_ctx* ctx, const double* dU, double tau) {
+  FETI_TRY(alloc_operators(ctx));
   FETI_TRY(assemble_all(ctx, dU, tau));
   FETI_TRY(factorize_all(ctx));
   if (!ctx->prepared) FETI_TRY(coarse_setup(ctx));
@@ -1300,17 +1341,30 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
           const float* Mf = static_cast<const float*>(M);
           const float* vf = static_cast<const float*>(v);
-          feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err, st);
-          FETI_CK(cudaEventRecord(e0, st));
-          for (int rep = 0; rep < 3; ++rep)
-            feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err, st);
-          FETI_CK(cudaEventRecord(e1, st));
-          FETI_CK(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
-          int herr = 0;
-          FETI_CK(cudaMemcpy(&herr, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-          ctx->tc_m[w] = herr == 0 && (ms < bt || ctx->opt.no_tensor_cores == 2);
+          float bt_tc = 1e30f;
+          ctx->tc_m[w] = 0;
+          const int ntc = ctx->opt.no_tensor_cores;
+          for (int variant = 1; variant <= 2; ++variant) {
+            if ((ntc == 3 && variant != 1) || (ntc == 4 && variant != 2)) continue;
+            FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
+            feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,
+                                 variant, st);
+            FETI_CK(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 3; ++rep)
+              feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero,
+                                   ctx->d_tc_err, variant, st);
+            FETI_CK(cudaEventRecord(e1, st));
+            FETI_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+            int herr = 0;
+            FETI_CK(cudaMemcpy(&herr, ctx->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (herr == 0 && ms < bt_tc) {
+              bt_tc = ms;
+              if (ms < bt || ntc >= 2) ctx->tc_m[w] = variant;
+            }
+          }
+          FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
         }
       }
       (f32 ? ctx->cfgm32[w] : ctx->cfgm64[w]) = best;
@@ -1367,7 +1421,7 @@ void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const do
   feti::launch_gather_m(ctx->maps, nrhs, x, wv, v, f32 ? 1 : 0, done, st);
   if (f32 && ctx->tc_m[which])
     feti::launch_gemm_tc(ctx->tab[which][2], ctx->d_lay, which, static_cast<const float*>(M), nrhs,
-                         static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, st);
+                         static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, ctx->tc_m[which], st);
   else
     feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
 }
@@ -1848,13 +1902,29 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
     dU = ctx->d_U;
   }
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  if (!ctx->elem_ev[0]) {
+    FETI_CK(cudaEventCreate(&ctx->elem_ev[0]));
+    FETI_CK(cudaEventCreate(&ctx->elem_ev[1]));
+  }
+  FETI_CK(cudaEventRecord(ctx->elem_ev[0], st));
   if (hgo)
     feti::launch_elem_hgo(ctx->E, ctx->d_coords, ctx->d_tets, dU, ctx->d_fibres, ctx->mat.c, ctx->mat.k1, ctx->mat.k2,
                           ctx->mat.kappa, ctx->d_Ke, ctx->d_fe, ctx->d_status, st);
   else
     feti::launch_elem_linear(ctx->E, ctx->d_coords, ctx->d_tets, ctx->mat.E, ctx->mat.nu, ctx->d_Ke, ctx->d_status, st);
   FETI_CK(cudaGetLastError());
+  FETI_CK(cudaEventRecord(ctx->elem_ev[1], st));
   FETI_TRY(check_status(ctx, "element matrices"));
+  {
+    float ms = 0.f;
+    FETI_CK(cudaEventElapsedTime(&ms, ctx->elem_ev[0], ctx->elem_ev[1]));
+    ctx->elem_ms = ms;
+    // connectivity, fibres (hyperelastic), packed symmetric tangent and force
+    // per element; coordinates (+ displacement) per node
+    const double per_elem = 16.0 + 78.0 * 8.0 + (hgo ? 48.0 + 12.0 * 8.0 : 0.0);
+    const double per_node = hgo ? 48.0 : 24.0;
+    ctx->elem_bytes = per_elem * (double)ctx->E + per_node * (double)ctx->N;
+  }
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   FETI_CK(cudaMemcpyAsync(Ke_out, ctx->d_Ke, 144 * (size_t)ctx->E * sizeof(double), kind, st));
   if (fe_out && hgo) FETI_CK(cudaMemcpyAsync(fe_out, ctx->d_fe, 12 * (size_t)ctx->E * sizeof(double), kind, st));
@@ -1909,7 +1979,7 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
       FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[2 + 2 * i], st, cudaEventRecordExternal));
       if (f32 && ctx->tc_m[0])
         feti::launch_gemm_tc(ctx->tab[0][2], ctx->d_lay, 0, ctx->d_F32, nrhs, static_cast<const float*>(vl), ctx->dm_loc,
-                             zero, ctx->d_tc_err, st);
+                             zero, ctx->d_tc_err, ctx->tc_m[0], st);
       else
         feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
                               nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
@@ -2008,10 +2078,7 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
       else
         feti::launch_gather(ctx->maps, v, nullptr, ctx->d_vloc, zero, st);
       FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[2 + 2 * i], st, cudaEventRecordExternal));
-      feti::launch_gemv_loc(f32 ? ctx->cfg32[0] : ctx->cfg64[0], ctx->d_lay, 0,
-                            f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
-                            f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc, ctx->d_loc, ctx->max_nb,
-                            zero, st);
+      gemv_apply(ctx, 0, zero, f32);
       FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[3 + 2 * i], st, cudaEventRecordExternal));
       feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, nullptr, nullptr, zero, st);
       apply_M(ctx, q, z, zero, f32);
@@ -2053,6 +2120,15 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
   return FETI_OK;
 }
 
+feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* elem_bytes, double* n_elements) {
+  if (!ctx || !elem_ms || !elem_bytes || !n_elements) return FETI_ERR_INVALID_ARG;
+  const bool run = ctx->elem_ms > 0.0;
+  *elem_ms = ctx->elem_ms;
+  *elem_bytes = ctx->elem_bytes;
+  *n_elements = run ? (double)ctx->E : 0.0;
+  return FETI_OK;
+}
+
 feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
   if (!ctx || !out) return FETI_ERR_INVALID_ARG;
   for (int i = 8; i < 12; ++i) out[i] = -1;
@@ -2062,7 +2138,7 @@ feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
     out[4 + 2 * w] = ctx->cfg32[w].R;
     out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
     if (ctx->tuned_m) {
-      out[8 + 2 * w] = ctx->tc_m[w] ? 0 : ctx->cfgm32[w].R;
+      out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;
       out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;
     }
   }
@@ -2084,6 +2160,8 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->pcg_graph) cudaGraphExecDestroy(ctx->pcg_graph);
   if (ctx->dual_graph) cudaGraphExecDestroy(ctx->dual_graph);
   for (auto ev : ctx->dual_events) cudaEventDestroy(ev);
+  for (auto ev : ctx->elem_ev)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->pcgm_graph) cudaGraphExecDestroy(ctx->pcgm_graph);
   if (ctx->dualm_graph) cudaGraphExecDestroy(ctx->dualm_graph);
   for (auto ev : ctx->dualm_events) cudaEventDestroy(ev);
