@@ -238,7 +238,7 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // the 128-rows-per-CTA table; nrhs <= 16; *err is set if a bounded wait
 // timed out.
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
-                    double* y, const int* done, int* err, cudaStream_t st);
+                    double* y, const int* done, int* err, int variant, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
 // c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).

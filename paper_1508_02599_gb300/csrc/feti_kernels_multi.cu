@@ -633,6 +633,192 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const int32_t* __restrict_
   if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
+// Bulk-copy staged variant: the FP32 rows of M_i are streamed into NRAW
+// shared-memory stages by cp.async.bulk (one 128-byte row segment per thread,
+// completion counted in bytes on a per-stage mbarrier), so several K chunks
+// are in flight per CTA without holding registers; each chunk is then split
+// into the TF32 head and tail from shared memory into the one swizzled MMA
+// stage.  The timeout flag is made CTA-uniform at every step; after a timeout
+// no further copies are issued, and the copies and MMAs already in flight
+// are drained (with fresh bounded waits) before tensor memory is freed.
+constexpr int TC2_NRAW = 3;
+constexpr int TC2_RAW = 128 * 128;
+constexpr int TC2_SMEM = TC_STAGE + TC2_NRAW * TC2_RAW + 1024;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t par) {
+  const long long t0 = clock64();
+  while (!mbar_try(b, par))
+    if (clock64() - t0 > 200000000LL) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads) k_gemm_tc2(const int32_t* __restrict__ blk_sub,
+                                                       const int32_t* __restrict__ blk_row0,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const float* __restrict__ M, int nrhs,
+                                                       const float* __restrict__ vloc, double* __restrict__ y,
+                                                       const int* __restrict__ done, int* __restrict__ err) {
+  if (*done) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+  unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
+  unsigned char* Ahi = smem;
+  unsigned char* Alo = smem + TC_A_BYTES;
+  unsigned char* Bhi = smem + 2 * TC_A_BYTES;
+  unsigned char* Blo = Bhi + TC_B_BYTES;
+  unsigned char* raw0 = smem + TC_STAGE;
+  __shared__ uint64_t mbar;
+  __shared__ uint64_t rbar[TC2_NRAW];
+  __shared__ uint32_t tmem_base;
+  const int s_id = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s_id];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int ldm = (m + 3) & ~3;
+  const float* Ms = M + (which == 0 ? L.foff32 : L.soff32);
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  if (which == 0 && r0 == 0)
+    for (int idx = tid; idx < L.k * nrhs; idx += blockDim.x) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    for (int i = 0; i < TC2_NRAW; ++i) mbar_init(&rbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  const int nk = (m + 31) / 32;
+  const int nrows = min(128, m - r0);
+  // chunk kc2 of rows r0 .. r0 + nrows - 1 into raw stage kc2 % NRAW; the
+  // row segments start on 16-byte boundaries (row stride and chunk offset are
+  // multiples of 4 floats) and are multiples of 16 bytes long
+  auto issue_raw = [&](int kc2) {
+    const int k0 = kc2 * 32;
+    const uint32_t seg = (uint32_t)min(32, ldm - k0) * 4u;
+    uint64_t* b = &rbar[kc2 % TC2_NRAW];
+    unsigned char* dst = raw0 + (kc2 % TC2_NRAW) * TC2_RAW;
+    if (tid == 0) mbar_expect_tx(b, seg * (uint32_t)nrows);
+    if (tid < nrows) bulk_g2s(dst + tid * 128, Ms + (size_t)(r0 + tid) * ldm + k0, seg, b);
+  };
+  int issued = 0;
+  for (; issued < TC2_NRAW && issued < nk; ++issued) issue_raw(issued);
+  float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto load_b = [&](int kc2) {
+    if (tid < 16 * 8) {
+      const int n = tid >> 3, c = tid & 7, k0 = kc2 * 32;
+      float v4[4];
+      for (int e = 0; e < 4; ++e) {
+        const int kk = k0 + 4 * c + e;
+        v4[e] = (kk < m && n < nrhs) ? vloc[(size_t)(L.boff + kk) * nrhs + n] : 0.f;
+      }
+      rb = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+  };
+  if (nk > 0) load_b(0);
+  bool timed_out = false;
+  int n_mma = 0, kc = 0;
+  for (; kc < nk; ++kc) {
+    const float4 cb = rb;
+    if (kc + 1 < nk) load_b(kc + 1);
+    if (!mbar_wait_bounded(&rbar[kc % TC2_NRAW], (uint32_t)(kc / TC2_NRAW) & 1u)) timed_out = true;
+    const unsigned char* raw = raw0 + (kc % TC2_NRAW) * TC2_RAW;
+    const int k0 = kc * 32;
+    float4 ca[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * kThreads;
+      const int r = idx >> 3, c = idx & 7;
+      ca[q] = (!timed_out && r < nrows && k0 + 4 * c < ldm) ? *reinterpret_cast<const float4*>(raw + r * 128 + c * 16)
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (kc >= 1 && !timed_out && !mbar_wait_bounded(&mbar, (uint32_t)(kc - 1) & 1u)) timed_out = true;
+    if (!timed_out) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = tid + q * kThreads;
+        const int r = idx >> 3, c = idx & 7;
+        float4 h, l;
+        split_tf32(ca[q].x, h.x, l.x);
+        split_tf32(ca[q].y, h.y, l.y);
+        split_tf32(ca[q].z, h.z, l.z);
+        split_tf32(ca[q].w, h.w, l.w);
+        *reinterpret_cast<float4*>(Ahi + sw_off(r, c)) = h;
+        *reinterpret_cast<float4*>(Alo + sw_off(r, c)) = l;
+      }
+      if (tid < 16 * 8) {
+        const int n = tid >> 3, c = tid & 7;
+        float4 h, l;
+        split_tf32(cb.x, h.x, l.x);
+        split_tf32(cb.y, h.y, l.y);
+        split_tf32(cb.z, h.z, l.z);
+        split_tf32(cb.w, h.w, l.w);
+        *reinterpret_cast<float4*>(Bhi + sw_off(n, c)) = h;
+        *reinterpret_cast<float4*>(Blo + sw_off(n, c)) = l;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    timed_out = __syncthreads_or(timed_out ? 1 : 0) != 0;
+    if (timed_out) break;
+    if (kc + TC2_NRAW < nk) {
+      issue_raw(kc + TC2_NRAW);
+      issued = kc + TC2_NRAW + 1;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
+        const uint64_t bh = sw128_desc(Bhi + 32 * j), bl = sw128_desc(Blo + 32 * j);
+        tc_mma(tmem, ah, bh, idesc, (kc > 0 || j > 0) ? 1u : 0u);
+        tc_mma(tmem, ah, bl, idesc, 1u);
+        tc_mma(tmem, al, bh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&mbar))
+                   : "memory");
+    }
+    n_mma = kc + 1;
+  }
+  // drain: copies issued for chunks not consumed (only after a timeout) and
+  // the last MMA group, each with its own bounded wait
+  bool drained = true;
+  for (int j = kc; j < issued; ++j)
+    if (!mbar_wait_bounded(&rbar[j % TC2_NRAW], (uint32_t)(j / TC2_NRAW) & 1u)) drained = false;
+  if (n_mma > 0 && !mbar_wait_bounded(&mbar, (uint32_t)(n_mma - 1) & 1u)) drained = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if ((timed_out || !drained) && lane == 0) atomicExch(err, 1);
+  if (wid < 4) {
+    uint32_t r[16];
+    const uint32_t taddr = tmem + ((uint32_t)(wid * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = r0 + wid * 32 + lane;
+    if (row < m && !timed_out && drained)
+      for (int n = 0; n < nrhs; ++n) y[(size_t)(L.boff + row) * nrhs + n] = (double)__uint_as_float(r[n]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
 inline int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -682,13 +868,19 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 }
 
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
-                    double* y, const int* done, int* err, cudaStream_t st) {
+                    double* y, const int* done, int* err, int variant, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
     attr = true;
   }
-  k_gemm_tc<<<cfg.n_blocks, kThreads, TC_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, M, nrhs, vloc, y, done, err);
+  if (variant == 2)
+    k_gemm_tc2<<<cfg.n_blocks, kThreads, TC2_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, M, nrhs, vloc, y, done,
+                                                         err);
+  else
+    k_gemm_tc<<<cfg.n_blocks, kThreads, TC_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, M, nrhs, vloc, y, done,
+                                                       err);
 }
 
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,

@@ -63,16 +63,21 @@ def test_block_apply_equals_single_applies():
             assert (Z[:, k] - z).abs().max().item() <= 1e-12 * z.abs().max().item()
 
 
-def test_tensor_core_block_gemm_matches_cuda_cores():
-    """The tcgen05 3xTF32 block GEMM against the CUDA-core FP32 GEMM (same FP32
-    operator copies): agreement to 1e-5 relative (TF32 head + tail products
-    reproduce FP32 products to about 2^-22 each), then a full block solve on
-    the tensor cores against the oracle."""
+JITTER = mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)
+
+
+@pytest.mark.parametrize("prob", [TUBE_FLOAT, JITTER], ids=["tube", "jittered"])
+@pytest.mark.parametrize("variant,code", [("force_reg", 0), ("force_bulk", -1)])
+def test_tensor_core_block_gemm_matches_cuda_cores(prob, variant, code):
+    """Each tcgen05 3xTF32 block GEMM (register-staged and bulk-copy staged
+    operands) against the CUDA-core FP32 GEMM on the same FP32 operator
+    copies: agreement to 1e-5 relative (TF32 head + tail products reproduce
+    FP32 products to about 2^-22 each), on subdomains whose boundary sizes are
+    not multiples of the 32-column chunk or the 128-row tile; then a full
+    block solve on the tensor cores against the oracle."""
     from paper_1508_02599_gb300 import FetiSolver
-    prob = TUBE_FLOAT
-    rng = np.random.default_rng(8)
     outs = {}
-    for tc in ("off", "force"):
+    for tc in ("off", variant):
         with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", tensor_cores=tc) as s:
             s.prepare()
             nl = s.sizes()["n_lambda"]
@@ -82,15 +87,16 @@ def test_tensor_core_block_gemm_matches_cuda_cores():
             s.dual_apply_multi(V, Q, Z, 16, 1)
             torch.cuda.synchronize()
             outs[tc] = (Q.cpu().numpy(), Z.cpu().numpy(), s.schedule())
-    assert outs["force"][2]["block_fp32_F"][0] == 0       # the tensor-core kernel ran
+    assert outs[variant][2]["block_fp32_F"][0] == code      # that tensor-core kernel ran
+    assert outs[variant][2]["block_fp32_M"][0] == code
     assert outs["off"][2]["block_fp32_F"][0] > 0
     for i in range(2):
-        a, b = outs["force"][i], outs["off"][i]
+        a, b = outs[variant][i], outs["off"][i]
         assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
     o = feti.FetiOracle(prob, "af", "dirichlet")
     U_ref, _, _ = o.solve(tol=1e-12, maxit=3000)
     with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-11, maxit=5000, precision="mixed",
-                    tensor_cores="force") as s:
+                    tensor_cores=variant) as s:
         U, rep = s.solve_multi(SCALES)
     assert rep["converged"] == 1
     for k, sc in enumerate(SCALES):
