@@ -107,18 +107,45 @@ __global__ void k_elem_linear(int n_tets, const double* __restrict__ coords, con
     }
 }
 
-// Two-fibre hyperelastic element (Sec. 3.1 energy, Sec. 3.2 tangent).
-// S = kappa (J-1) J C^-1 + c J^-2/3 (I - I1/3 C^-1) + sum_f 2 psi_f' J^-2/3 (a a - I4/3 C^-1)
-// and CC = 2 dS/dC written out term by term (derivation in the comments).
-__global__ void k_elem_hgo(int n_tets, const double* __restrict__ coords, const int32_t* __restrict__ tets,
-                           const double* __restrict__ U, const double* __restrict__ fibres, double cmat,
-                           double k1, double k2, double kappa, double* __restrict__ Ke,
-                           double* __restrict__ fe, int* status) {
+// Two-fibre hyperelastic element (Sec. 3.1 energy, Sec. 3.2 tangent), one
+// thread per element, evaluated in the current configuration.
+//
+// Material form.  With J23 = J^(-2/3), A_v = kappa (J-1) J and, per fibre
+// family f, psi'_f, psi''_f the derivatives of its energy in I4bar = J23 I4:
+//   S = A_v C^-1 + c J23 (I - I1/3 C^-1) + sum_f 2 psi'_f J23 (a a - I4/3 C^-1)
+//   CC = 2 dS/dC = c_11 C^-1(x)C^-1 + c_Q Q + c_IC (I(x)C^-1 + C^-1(x)I)
+//        + sum_f [4 psi''_f J23^2 B(x)B - (2/3) psi'_f J23 (C^-1(x)B + B(x)C^-1 + C^-1(x)aa + aa(x)C^-1)]
+//   with Q_IJKL = (Ci_IK Ci_JL + Ci_IL Ci_JK)/2, B = a a - I4/3 C^-1 and
+//   c_11 = kappa (2J-1) J + (2c/9) J23 I1, c_IC = -(2c/3) J23,
+//   c_Q = -2 A_v + (2c/3) J23 I1 + sum_f (4/3) psi'_f J23 I4_f
+//   (dC^-1/dC = -Q, dJ/dC = J/2 C^-1, dJ23/dC = -J23/3 C^-1, dI1/dC = I, dI4/dC = a a).
+//
+// Spatial evaluation.  The tangent block K[(a,i),(b,j)] = V (delta_ij g_a.S g_b
+// + sum F_iI g_aJ CC_IJKL F_jK g_bL) is the same number when every tensor is
+// pushed forward by F: with the current gradients h_a = F^-T g_a, C^-1 -> 1,
+// I -> b = F F^T, a a -> A A (A = F a), Q -> the symmetric identity, S -> the
+// Kirchhoff stress tau = F S F^T, and the tangent becomes
+//   K[(a,i),(b,j)] = V [ c_11 h_ai h_bj + (c_Q/2)(delta_ij h_a.h_b + h_aj h_bi)
+//       + c_IC ((b h_a)_i h_bj + h_ai (b h_b)_j)
+//       + sum_f ( 4 psi''_f J23^2 (beta_f h_a)_i (beta_f h_b)_j
+//                 - (2/3) psi'_f J23 (h_ai w_fbj + w_fai h_bj) )
+//       + delta_ij h_a.tau h_b ],
+//   beta_f = A A - I4/3 1,  w_fa = beta_f h_a + (A.h_a) A,
+// and the internal force f_a = V tau h_a.  Every term is a product of
+// per-node 3-vectors, about a fifth of the FP64 operations of contracting the
+// material tensor entry by entry; all arrays stay in registers.
+__global__ void __launch_bounds__(64) k_elem_hgo(int n_tets, const double* __restrict__ coords,
+                                                 const int32_t* __restrict__ tets, const double* __restrict__ U,
+                                                 const double* __restrict__ fibres, double cmat, double k1,
+                                                 double k2, double kappa, double* __restrict__ Ke,
+                                                 double* __restrict__ fe, int* status) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_tets) return;
   double x[4][3], g[4][3], V, u[4][3];
+#pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int n = tets[4 * e + a];
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       x[a][i] = coords[3 * n + i];
       u[a][i] = U ? U[3 * n + i] : 0.0;
@@ -129,186 +156,139 @@ __global__ void k_elem_hgo(int n_tets, const double* __restrict__ coords, const 
     return;
   }
   double F[3][3];
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
       double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
       for (int a = 0; a < 4; ++a) s += u[a][i] * g[a][j];
       F[i][j] = s;
     }
-  double C[3][3];
-  for (int I = 0; I < 3; ++I)
-    for (int J = 0; J < 3; ++J) C[I][J] = F[0][I] * F[0][J] + F[1][I] * F[1][J] + F[2][I] * F[2][J];
-  const double detC = C[0][0] * (C[1][1] * C[2][2] - C[1][2] * C[2][1]) -
-                      C[0][1] * (C[1][0] * C[2][2] - C[1][2] * C[2][0]) +
-                      C[0][2] * (C[1][0] * C[2][1] - C[1][1] * C[2][0]);
-  const double detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
-                      F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
-                      F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
-  if (!(detF > 0.0)) {
+  // cofactor matrix: cof(F) = J F^-T
+  double cf[3][3];
+  cf[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+  cf[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+  cf[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+  cf[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+  cf[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+  cf[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+  cf[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+  cf[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+  cf[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  const double J = F[0][0] * cf[0][0] + F[0][1] * cf[0][1] + F[0][2] * cf[0][2];
+  if (!(J > 0.0)) {
     set_status(status, DEV_INVERTED);
     return;
   }
-  const double J = sqrt(detC);
-  double Ci[3][3];
-  {
-    const double id = 1.0 / detC;
-    Ci[0][0] = (C[1][1] * C[2][2] - C[1][2] * C[2][1]) * id;
-    Ci[0][1] = (C[0][2] * C[2][1] - C[0][1] * C[2][2]) * id;
-    Ci[0][2] = (C[0][1] * C[1][2] - C[0][2] * C[1][1]) * id;
-    Ci[1][0] = Ci[0][1];
-    Ci[1][1] = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) * id;
-    Ci[1][2] = (C[0][2] * C[1][0] - C[0][0] * C[1][2]) * id;
-    Ci[2][0] = Ci[0][2];
-    Ci[2][1] = Ci[1][2];
-    Ci[2][2] = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) * id;
-  }
-  const double J23 = pow(detC, -1.0 / 3.0);  // J^(-2/3)
-  const double I1 = C[0][0] + C[1][1] + C[2][2];
-  // Scalar coefficients of S = sum_t s_t T_t (see the stress formula above).
-  // Volumetric: S_v = A_v C^-1 with A_v = kappa (J-1) J; d(A_v)/dC = kappa (2J-1) J/2 C^-1.
-  // Isochoric matrix: S_m = c J23 I - (c J23 I1/3) C^-1.
-  // Fibre f: S_f = 2 psi' J23 a a - (2 psi' J23 I4/3) C^-1.
-  double S[3][3];
+  const double iJ = 1.0 / J;
+  double h[4][3];  // h_a = F^-T g_a
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) h[a][m] = (cf[m][0] * g[a][0] + cf[m][1] * g[a][1] + cf[m][2] * g[a][2]) * iJ;
+  double bm[3][3];  // b = F F^T
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      bm[i][j] = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
+      bm[j][i] = bm[i][j];
+    }
+  const double I1 = bm[0][0] + bm[1][1] + bm[2][2];
+  const double J23 = rcbrt(J * J);
   const double Av = kappa * (J - 1.0) * J;
-  for (int I = 0; I < 3; ++I)
-    for (int Jj = 0; Jj < 3; ++Jj)
-      S[I][Jj] = Av * Ci[I][Jj] + cmat * J23 * ((I == Jj ? 1.0 : 0.0) - I1 / 3.0 * Ci[I][Jj]);
-  double fa[2][3], I4[2], dpsi[2], d2psi[2];
-  bool act[2];
+  // Kirchhoff stress: tau = t0 1 + c J23 b + sum_f 2 psi'_f J23 A_f A_f
+  double t0 = Av - cmat * J23 * I1 / 3.0;
+  double tau[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tau[i][j] = cmat * J23 * bm[i][j];
+  double Af[2][3], I4[2], dpsi[2], d2psi[2];
+  double cQ = -2.0 * Av + 2.0 * cmat * J23 * I1 / 3.0;
+#pragma unroll
   for (int f = 0; f < 2; ++f) {
-    for (int i = 0; i < 3; ++i) fa[f][i] = fibres[6 * e + 3 * f + i];
-    double t = 0.0;
-    for (int I = 0; I < 3; ++I)
-      for (int Jj = 0; Jj < 3; ++Jj) t += fa[f][I] * C[I][Jj] * fa[f][Jj];
-    I4[f] = t;
-    const double I4b = J23 * t;
-    const double dlt = I4b - 1.0;
-    act[f] = dlt > 1e-12;
-    if (act[f]) {
+    double a0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a0[i] = fibres[6 * e + 3 * f + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Af[f][i] = F[i][0] * a0[0] + F[i][1] * a0[1] + F[i][2] * a0[2];
+    I4[f] = Af[f][0] * Af[f][0] + Af[f][1] * Af[f][1] + Af[f][2] * Af[f][2];
+    const double dlt = J23 * I4[f] - 1.0;
+    if (dlt > 1e-12) {
       const double ex = exp(k2 * dlt * dlt);
-      dpsi[f] = k1 * dlt * ex;                          // dPsi/dI4bar
+      dpsi[f] = k1 * dlt * ex;                            // dPsi/dI4bar
       d2psi[f] = k1 * ex * (1.0 + 2.0 * k2 * dlt * dlt);  // d2Psi/dI4bar2
-      for (int I = 0; I < 3; ++I)
-        for (int Jj = 0; Jj < 3; ++Jj)
-          S[I][Jj] += 2.0 * dpsi[f] * J23 * (fa[f][I] * fa[f][Jj] - t / 3.0 * Ci[I][Jj]);
     } else {
       dpsi[f] = d2psi[f] = 0.0;
     }
-  }
-  // Elasticity tensor CC_IJKL = 2 dS_IJ/dC_KL, with Q_IJKL = (Ci_IK Ci_JL + Ci_IL Ci_JK)/2,
-  // dCi/dC = -Q, dJ/dC = J/2 Ci, dJ23/dC = -J23/3 Ci, dI1/dC = I, dI4/dC = a a:
-  //   volumetric  kappa (2J-1) J Ci(x)Ci - 2 A_v Q
-  //   matrix      -(2c/3) J23 (I(x)Ci + Ci(x)I) + (2c/9) J23 I1 Ci(x)Ci + (2c/3) J23 I1 Q
-  //   fibre f     4 psi'' J23^2 B(x)B - (4/3) psi' J23 (B(x)Ci + Ci(x)a a) + (4/3) psi' J23 I4 Q,
-  //               B = a a - I4/3 Ci (the two middle products add up to a major-symmetric term).
-  // Element tangent: K[a i, b j] = V (delta_ij g_a.S g_b + X_ai : CC : X_bj) with the
-  // symmetric X_ai,IJ = (F_iI g_aJ + F_iJ g_aI)/2 (CC has minor symmetries).
-  double Kl[12][12];
-  // geometric part
-  double gSg[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) {
-      double t = 0.0;
-      for (int I = 0; I < 3; ++I)
-        for (int Jj = 0; Jj < 3; ++Jj) t += g[a][I] * S[I][Jj] * g[b][Jj];
-      gSg[a][b] = t;
-    }
-  // material part via contraction with the tensor blocks written out
-  // E_a,i := symmetrised F_iI g_aJ (3x3 in I,J) for each (a, i).
-  double Ea[12][3][3];
-  for (int a = 0; a < 4; ++a)
+    const double m2 = 2.0 * dpsi[f] * J23;
+    t0 -= m2 * I4[f] / 3.0;
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-      for (int I = 0; I < 3; ++I)
-        for (int Jj = 0; Jj < 3; ++Jj)
-          Ea[3 * a + i][I][Jj] = 0.5 * (F[i][I] * g[a][Jj] + F[i][Jj] * g[a][I]);
-  // Contractions needed: for symmetric X, Y:
-  //   X:(Ci(x)Ci):Y = (Ci:X)(Ci:Y);  X:Q:Y = tr(Ci X Ci Y);  X:(I(x)Ci):Y = tr(X) (Ci:Y)
-  //   X:(Ci(x)aa):Y = (Ci:X)(a.Y a);  X:(B(x)B):Y = (B:X)(B:Y)
-  double trX[12], CiX[12], aXa[2][12], BX[2][12];
-  double CiXCi[12][3][3];
-  double Bf[2][3][3];
-  for (int f = 0; f < 2; ++f)
-    for (int I = 0; I < 3; ++I)
-      for (int Jj = 0; Jj < 3; ++Jj) Bf[f][I][Jj] = fa[f][I] * fa[f][Jj] - I4[f] / 3.0 * Ci[I][Jj];
-  for (int p = 0; p < 12; ++p) {
-    double tr = 0.0, cx = 0.0;
-    for (int I = 0; I < 3; ++I) {
-      tr += Ea[p][I][I];
-      for (int Jj = 0; Jj < 3; ++Jj) cx += Ci[I][Jj] * Ea[p][I][Jj];
-    }
-    trX[p] = tr;
-    CiX[p] = cx;
-    for (int f = 0; f < 2; ++f) {
-      double s1 = 0.0, s2 = 0.0;
-      for (int I = 0; I < 3; ++I)
-        for (int Jj = 0; Jj < 3; ++Jj) {
-          s1 += fa[f][I] * Ea[p][I][Jj] * fa[f][Jj];
-          s2 += Bf[f][I][Jj] * Ea[p][I][Jj];
-        }
-      aXa[f][p] = s1;
-      BX[f][p] = s2;
-    }
-    double T[3][3];
-    for (int I = 0; I < 3; ++I)
-      for (int L = 0; L < 3; ++L) {
-        double t = 0.0;
-        for (int Jj = 0; Jj < 3; ++Jj) t += Ci[I][Jj] * Ea[p][Jj][L];
-        T[I][L] = t;
-      }
-    for (int I = 0; I < 3; ++I)
-      for (int L = 0; L < 3; ++L) {
-        double t = 0.0;
-        for (int Jj = 0; Jj < 3; ++Jj) t += T[I][Jj] * Ci[Jj][L];
-        CiXCi[p][I][L] = t;
-      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tau[i][j] += m2 * Af[f][i] * Af[f][j];
+    cQ += 2.0 * m2 * I4[f] / 3.0;
   }
-  const double cvv = kappa * (2.0 * J - 1.0) * J;       // Ci(x)Ci
-  const double cQ = -2.0 * Av + 2.0 * cmat * J23 * I1 / 3.0;  // Q
-  const double cIC = -2.0 * cmat * J23 / 3.0;           // I(x)Ci + Ci(x)I
-  double cCC = cvv + 2.0 * cmat * J23 * I1 / 9.0;       // Ci(x)Ci
-  double cQf = 0.0;
-  for (int f = 0; f < 2; ++f)
-    if (act[f]) {
-      const double m = 2.0 * dpsi[f] * J23;
-      // 2 m dB/dC = 2m(-1/3 Ci(x)aa + I4/3 Q) ; symmetrised Ci(x)aa handled with aXa
-      cQf += 2.0 * m * I4[f] / 3.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tau[i][i] += t0;
+  const double c11 = kappa * (2.0 * J - 1.0) * J + 2.0 * cmat * J23 * I1 / 9.0;
+  const double cIC = -2.0 * cmat * J23 / 3.0;
+  // per-node vectors, scaled by V: P_a = V (c_IC b h_a - (2/3) sum_f psi'_f J23 w_fa),
+  // Pv_a = P_a + V c_11 h_a, r_fa = sqrt(4 V psi''_f) J23 beta_f h_a; tau h_a
+  double P[4][3], Pv[4][3], r[2][4][3], th[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      th[a][i] = tau[i][0] * h[a][0] + tau[i][1] * h[a][1] + tau[i][2] * h[a][2];
+      P[a][i] = cIC * (bm[i][0] * h[a][0] + bm[i][1] * h[a][1] + bm[i][2] * h[a][2]);
     }
-  for (int p = 0; p < 12; ++p)
-    for (int q = p; q < 12; ++q) {
-      const double XQY = [&]() {
-        double t = 0.0;
-        for (int I = 0; I < 3; ++I)
-          for (int L = 0; L < 3; ++L) t += CiXCi[p][I][L] * Ea[q][L][I];
-        return t;
-      }();
-      double v = cCC * CiX[p] * CiX[q] + (cQ + cQf) * XQY + cIC * (trX[p] * CiX[q] + CiX[p] * trX[q]);
-      for (int f = 0; f < 2; ++f)
-        if (act[f]) {
-          const double m = 2.0 * dpsi[f] * J23;
-          v += 4.0 * d2psi[f] * J23 * J23 * BX[f][p] * BX[f][q];
-          // -(4/3) psi' J23 sym(Ci(x)B) and -(2m/3) sym(Ci(x)aa): the derivative of S_f
-          // w.r.t. C through J23 and through Ci; symmetrised over (p, q)
-          v += -(2.0 / 3.0) * dpsi[f] * J23 * 2.0 * 0.5 * (CiX[p] * BX[f][q] + BX[f][p] * CiX[q]);
-          v += -(2.0 * m / 3.0) * 0.5 * (CiX[p] * aXa[f][q] + aXa[f][p] * CiX[q]);
-        }
-      Kl[p][q] = v;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const double sa = Af[f][0] * h[a][0] + Af[f][1] * h[a][1] + Af[f][2] * h[a][2];
+      const double cw = -(2.0 / 3.0) * dpsi[f] * J23;
+      const double cr = 2.0 * J23 * sqrt(V * d2psi[f]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double bh = sa * Af[f][i] - I4[f] / 3.0 * h[a][i];  // beta_f h_a
+        P[a][i] += cw * (bh + sa * Af[f][i]);
+        r[f][a][i] = cr * bh;
+      }
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      P[a][i] *= V;
+      Pv[a][i] = P[a][i] + V * c11 * h[a][i];
+    }
+  }
+  // diagonal-in-(i,j) part: D_ab = V ((c_Q/2) h_a.h_b + h_a.tau h_b)
+  const double hq = 0.5 * cQ * V;
   double* Kout = Ke + (size_t)e * 144;
-  for (int p = 0; p < 12; ++p)
-    for (int q = 0; q < 12; ++q) {
-      const int pp = p < q ? p : q, qq = p < q ? q : p;
-      double v = Kl[pp][qq];
-      if (p % 3 == q % 3) v += gSg[p / 3][q / 3];
-      Kout[p * 12 + q] = V * v;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      const double D = hq * (h[a][0] * h[b][0] + h[a][1] * h[b][1] + h[a][2] * h[b][2]) +
+                       V * (h[a][0] * th[b][0] + h[a][1] * th[b][1] + h[a][2] * th[b][2]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (a == b && j < i) continue;
+          double v = Pv[a][i] * h[b][j] + h[a][i] * P[b][j] + hq * h[a][j] * h[b][i] + r[0][a][i] * r[0][b][j] +
+                     r[1][a][i] * r[1][b][j];
+          if (i == j) v += D;
+          Kout[(3 * a + i) * 12 + 3 * b + j] = v;
+          Kout[(3 * b + j) * 12 + 3 * a + i] = v;
+        }
     }
   if (fe) {
+#pragma unroll
     for (int a = 0; a < 4; ++a)
-      for (int i = 0; i < 3; ++i) {
-        double t = 0.0;
-        for (int I = 0; I < 3; ++I)
-          for (int Jj = 0; Jj < 3; ++Jj) t += F[i][I] * S[I][Jj] * g[a][Jj];
-        fe[(size_t)e * 12 + 3 * a + i] = V * t;
-      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) fe[(size_t)e * 12 + 3 * a + i] = V * th[a][i];
   }
 }
 
