@@ -155,11 +155,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-apply", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cyl16", choices=["cyl16", "cyl8", "jcyl32"],
+    ap.add_argument("--workload", default="cyl16", choices=["cyl16", "cyl8", "jcyl32", "jcyl48"],
                     help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures; "
-                         "jcyl32: jittered tube, 1024 uneven subdomains")
+                         "jcyl32: jittered tube, 1024 uneven subdomains; jcyl48: jittered tube, 4096 uneven "
+                         "subdomains (about 180 GB of device memory)")
+    ap.add_argument("--plain", type=int, default=1,
+                    help="also time the plain FP64 form with one local-apply launch per subdomain (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--block", type=int, default=1, help="also measure the 16-RHS block form (0: skip)")
+    ap.add_argument("--block-fp64", type=int, default=1, help="include the FP64 16-RHS block leg (0: skip)")
     ap.add_argument("--elements", type=int, default=1,
                     help="also time the hyperelastic element kernel on the 256-subdomain tube (0: skip)")
     ap.add_argument("--elements-only", action="store_true",
@@ -179,13 +183,17 @@ def main():
         prob = mesh.config_problem("jcyl32")
         wname = ("AF-FETI jittered tube 32x128x64 cells P1 (274,560 nodes, 823,680 DOFs), 1024 uneven "
                  "subdomains (jittered RCB), Dirichlet preconditioner, PCG tol 1e-8")
+    elif args.workload == "jcyl48":
+        prob = mesh.config_problem("jcyl48")
+        wname = ("AF-FETI jittered tube 48x192x96 cells P1 (912,576 nodes, 2,737,728 DOFs), 4096 uneven "
+                 "subdomains (jittered RCB), Dirichlet preconditioner, PCG tol 1e-8")
     else:
         prob = mesh.cylinder_problem(8, 64, 16, (2, 8, 2))
         wname = ("AF-FETI tube 8x64x16 cells P1 (9,792 nodes), 32 wedge subdomains, Dirichlet "
                  "preconditioner, FP64, PCG tol 1e-8 (profiler-sized)")
     workload_cfg = {"workload": wname,
                     "n_subdomains": prob.n_parts, "n_dofs": 3 * prob.n_nodes, "method": "all-floating",
-                    "precond": "dirichlet", "precision": "fp64", "l2": "inputs larger than L2 (F_i+S_i 1.4 GB)",
+                    "precond": "dirichlet", "precision": "fp64", "l2": "inputs larger than L2 (the F_i and S_i read per apply exceed the 129 MB L2)",
                     "parallelism": "replicas" if args.gpus > 1 else "single"}
     if args.impl == "reference":
         run_reference(args, prob, workload_cfg)
@@ -331,8 +339,9 @@ def main():
     m32 = measure("mixed")
     # the plain FP64 form: the same kernels with the local applies launched once
     # per subdomain (p launches per apply instead of one batched launch)
-    mp = measure("fp64", batched=False, n_apply=max(1, args.n_apply // 4), steps=max(1, args.steps // 4))
-    b64 = measure_block("fp64") if args.block else None
+    mp = (measure("fp64", batched=False, n_apply=max(1, args.n_apply // 4), steps=max(1, args.steps // 4))
+          if args.plain else None)
+    b64 = measure_block("fp64") if args.block and args.block_fp64 else None
     b32 = measure_block("mixed") if args.block else None
     n64 = np.linalg.norm(m64["U"])
     err = float(np.linalg.norm(m32["U"] - m64["U"]) / n64) if n64 > 0 else None
@@ -380,11 +389,12 @@ def main():
                                   "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf64 / fp64_peak,
                                   "hbm_gbs": gbs64, "kernel_ms": m64["kern_ms"]},
                      "clocks": m64["clocks"]},
-            "fp64_per_subdomain": {"value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms"] / mp["steps"],
-                                   "time_to_tol_ms": mp["rep"]["t_pcg_ms"], "iterations": mp["rep"]["iterations"],
-                                   "local_apply_kernel_ms": mp["kern_ms"],
-                                   "note": "plain form: FP64, one local-apply launch per subdomain instead of "
-                                           "one batched launch; same kernels, graphs and schedule"},
+            "fp64_per_subdomain": None if mp is None else {
+                "value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms"] / mp["steps"],
+                "time_to_tol_ms": mp["rep"]["t_pcg_ms"], "iterations": mp["rep"]["iterations"],
+                "local_apply_kernel_ms": mp["kern_ms"],
+                "note": "plain form: FP64, one local-apply launch per subdomain instead of one batched launch; "
+                        "same kernels, graphs and schedule"},
             "roofline": {"bound": "hbm", "kernel": "k_gemv_loc<float> (F_i apply, FP32 copy)", "achieved": gbs32,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],
                          "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
@@ -399,6 +409,8 @@ def main():
         if b32 is not None:
             blk = {}
             for name, b in (("fp32_local", b32), ("fp64", b64)):
+                if b is None:
+                    continue
                 # u_k = s_k u for these load cases: check against the single-RHS FP64 solution
                 errs = [float(np.linalg.norm(b["U"][k] - b["scales"][k] * m64["U"]) /
                               np.linalg.norm(b["scales"][k] * m64["U"])) for k in range(b["nrhs"])]

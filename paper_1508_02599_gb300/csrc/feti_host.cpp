@@ -11,10 +11,14 @@
 #include "feti.h"
 #include "feti_internal.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -82,7 +86,8 @@ struct feti_ctx {
   std::vector<int32_t> tab_ptr[2][3];  // first CTA of each subdomain in tab[which][k] (p + 1 entries)
   feti::GemvCfg cfg64[2], cfg32[2];
   feti::GemvCfg cfgm64[2], cfgm32[2];  // block form (N = nrhs) schedules
-  int tc_m[2] = {0, 0};  // FP32 block GEMM on the tensor cores: 0 no, 1 register-staged, 2 bulk-copy staged
+  int tc_m[2] = {0, 0};  // FP32 block GEMM on the tensor cores: 0 no, 1 register-staged, 2 bulk-copy staged, 3 TMA
+  CUtensorMap* d_tmap[2] = {nullptr, nullptr};  // per-subdomain tensor maps of the FP32 F_i and S_i copies
   int* d_tc_err = nullptr;
   int tuned_m = 0;                     // nrhs the block schedules were tuned for
   bool tuned = false;
@@ -825,9 +830,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_CK(cudaMemsetAsync(ctx->d_zero, 0, sizeof(int), ctx->stream));
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   if (ctx->cd > 0) {
-    FETI_TRY(dev_alloc(ctx, &ctx->d_GtG, (size_t)ctx->cd * ctx->cd));
     FETI_TRY(dev_alloc(ctx, &ctx->d_Ginv, (size_t)ctx->cd * ctx->cd));
-    FETI_TRY(dev_alloc(ctx, &ctx->d_Acoarse, (size_t)4 * ctx->cd * ctx->cd));
     SubLayout Lc{};
     Lc.n = (int)ctx->cd; Lc.nI = 0; Lc.nbp = (int)ctx->cd; Lc.k = 0; Lc.ld = 2 * (int)ctx->cd;
     std::vector<SubLayout> lc(1, Lc);
@@ -935,10 +938,30 @@ feti_status factorize_all(feti_ctx* ctx) {
   return FETI_OK;
 }
 
+// G^T G and the elimination workspace (5 cd^2 doubles) exist only during
+// this call; the context keeps (G^T G)^-1.
 feti_status coarse_setup(feti_ctx* ctx) {
   if (ctx->cd == 0) return FETI_OK;
   cudaStream_t st = ctx->stream;
   const size_t cd = ctx->cd;
+  struct Scratch {
+    void* p[2] = {nullptr, nullptr};
+    ~Scratch() {
+      for (void* q : p)
+        if (q) cudaFree(q);
+    }
+  } scratch;
+  {
+    cudaError_t e = cudaMalloc(&scratch.p[0], cd * cd * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&scratch.p[1], 4 * cd * cd * sizeof(double));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(ctx, e == cudaErrorMemoryAllocation ? FETI_ERR_OOM : FETI_ERR_CUDA,
+                  std::string("coarse workspace: ") + cudaGetErrorString(e));
+    }
+  }
+  ctx->d_GtG = static_cast<double*>(scratch.p[0]);
+  ctx->d_Acoarse = static_cast<double*>(scratch.p[1]);
   FETI_CK(cudaMemsetAsync(ctx->d_GtG, 0, cd * cd * sizeof(double), st));
   feti::launch_gtg(ctx->n_gtg, ctx->d_gtg_i, ctx->d_gtg_j, ctx->d_gtg_ptr, ctx->d_gtg_rows, ctx->d_lay, ctx->d_R,
                    ctx->maps, (int)cd, ctx->d_GtG, st);
@@ -951,7 +974,9 @@ feti_status coarse_setup(feti_ctx* ctx) {
   // extract into Ginv: F layout of the coarse "subdomain" has foff = 0
   feti::launch_extract(1, ctx->d_lay_coarse, 1, ctx->d_Acoarse, ctx->d_Ginv, st);
   FETI_CK(cudaGetLastError());
-  return check_status(ctx, "coarse factorization");
+  const feti_status status = check_status(ctx, "coarse factorization");  // synchronises the stream
+  ctx->d_GtG = ctx->d_Acoarse = nullptr;
+  return status;
 }
 
 // P v -> out (with optional partial dot with a, or the squared norm, into
@@ -1300,6 +1325,41 @@ feti_status write_displacement(feti_ctx* ctx, double* u_out, int on_device, doub
 // Block form: nrhs right-hand sides share every operator apply.
 // Times the block-form local GEMM schedules (rows per warp step {1, 2, 4},
 // rows per CTA {32, 64}) on the real operators and keeps the fastest.
+// One 2-D tensor map per subdomain over its FP32 copy of F_i (which 0) or of
+// the preconditioner block (which 1): (columns, rows) = (m, m), row pitch the
+// padded stride, 32 x 128 boxes, 128-byte swizzle, out-of-range elements
+// zero-filled.  Encoded through the runtime's driver entry point.
+feti_status build_tensor_maps(feti_ctx* ctx) {
+  if (ctx->d_tmap[0]) return FETI_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  FETI_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return fail(ctx, FETI_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  for (int w = 0; w < 2; ++w) {
+    if (w == 1 && ctx->opt.precond != FETI_PREC_DIRICHLET) break;  // no dense preconditioner block
+    std::vector<CUtensorMap> maps(ctx->P);
+    const float* base = w == 0 ? ctx->d_F32 : ctx->d_S32;
+    for (int s = 0; s < ctx->P; ++s) {
+      const SubLayout& L = ctx->lay[s];
+      const int m = w == 0 ? std::max(L.nbp, 1) : std::max(L.nbp + L.k, 1);
+      const cuuint64_t ld = (cuuint64_t)((m + 3) & ~3);
+      const cuuint64_t dim[2] = {(cuuint64_t)m, (cuuint64_t)m};
+      const cuuint64_t stride[1] = {ld * sizeof(float)};
+      const cuuint32_t box[2] = {32, 128};
+      const cuuint32_t estr[2] = {1, 1};
+      void* addr = (void*)(base + (w == 0 ? L.foff32 : L.soff32));
+      const CUresult r = encode(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr, dim, stride, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(ctx, FETI_ERR_CUDA, "tensor map of subdomain " + std::to_string(s) + ": error " + std::to_string((int)r));
+    }
+    FETI_TRY(upload(ctx, &ctx->d_tmap[w], maps));
+  }
+  return FETI_OK;
+}
+
 feti_status autotune_m(feti_ctx* ctx, int nrhs) {
   if (ctx->tuned_m == nrhs) return FETI_OK;
   cudaStream_t st = ctx->stream;
@@ -1344,15 +1404,16 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           float bt_tc = 1e30f;
           ctx->tc_m[w] = 0;
           const int ntc = ctx->opt.no_tensor_cores;
-          for (int variant = 1; variant <= 2; ++variant) {
-            if ((ntc == 3 && variant != 1) || (ntc == 4 && variant != 2)) continue;
+          FETI_TRY(build_tensor_maps(ctx));
+          for (int variant = 1; variant <= 3; ++variant) {
+            if (ntc >= 3 && variant != ntc - 2) continue;
             FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
             feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,
-                                 variant, st);
+                                 variant, ctx->d_tmap[w], st);
             FETI_CK(cudaEventRecord(e0, st));
             for (int rep = 0; rep < 3; ++rep)
               feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero,
-                                   ctx->d_tc_err, variant, st);
+                                   ctx->d_tc_err, variant, ctx->d_tmap[w], st);
             FETI_CK(cudaEventRecord(e1, st));
             FETI_CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -1421,7 +1482,8 @@ void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const do
   feti::launch_gather_m(ctx->maps, nrhs, x, wv, v, f32 ? 1 : 0, done, st);
   if (f32 && ctx->tc_m[which])
     feti::launch_gemm_tc(ctx->tab[which][2], ctx->d_lay, which, static_cast<const float*>(M), nrhs,
-                         static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, ctx->tc_m[which], st);
+                         static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, ctx->tc_m[which],
+                         ctx->d_tmap[which], st);
   else
     feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
 }
@@ -1834,6 +1896,9 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
   const int maxit = ctx->opt.newton_maxit > 0 ? ctx->opt.newton_maxit : 25;
   const double ntol = ctx->opt.newton_tol > 0 ? ctx->opt.newton_tol : 1e-8;
   FETI_CK(cudaMemsetAsync(ctx->d_U, 0, n3 * sizeof(double), st));
+  // FETI_LOG=1 in the environment prints one line per Newton iteration to stderr
+  const char* log_env = std::getenv("FETI_LOG");
+  const bool log = log_env && log_env[0] && log_env[0] != '0';
   int newton_total = 0, pcg_total = 0;
   double rel = 0.0;
   double t_pcg = 0.0;
@@ -1841,6 +1906,7 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
     const double tau = (double)step / nsteps;
     FETI_TRY(prepare(ctx, ctx->d_U, tau));
     FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
+    if (log) std::fprintf(stderr, "feti_newton: load step %d tau %.4f start rel %.3e\n", step, tau, rel);
     for (int k = 0;; ++k) {
       if (rel <= ntol) break;
       if (k >= maxit) {
@@ -1863,6 +1929,8 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
         feti::launch_zero_list((int)ctx->dir_dof.size(), ctx->d_dir_dof, ctx->d_Utrial, st);
         s = prepare(ctx, ctx->d_Utrial, tau);
         if (s == FETI_OK) break;
+        if (log) std::fprintf(stderr, "feti_newton: step %d it %d step length %.4f rejected (%s)\n", step, k + 1, a,
+                              ctx->err.c_str());
         if (s != FETI_ERR_LOCAL_SINGULAR && s != FETI_ERR_ELEMENT_INVERTED) return s;
         a *= 0.5;
         if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "no step keeps the local tangents positive definite");
@@ -1870,6 +1938,10 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
       FETI_CK(cudaMemcpyAsync(ctx->d_U, ctx->d_Utrial, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
       ++newton_total;
       FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
+      if (log) {
+        std::fprintf(stderr, "feti_newton: step %d it %d pcg %d (%s, rel %.2e) step length %.4f -> rel %.3e\n", step,
+                     k + 1, r.iterations, r.converged ? "converged" : "not converged", r.rel_residual, a, rel);
+      }
     }
   }
   FETI_CK(cudaMemcpyAsync(u_out, ctx->d_U, n3 * sizeof(double), u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -1979,7 +2051,7 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
       FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[2 + 2 * i], st, cudaEventRecordExternal));
       if (f32 && ctx->tc_m[0])
         feti::launch_gemm_tc(ctx->tab[0][2], ctx->d_lay, 0, ctx->d_F32, nrhs, static_cast<const float*>(vl), ctx->dm_loc,
-                             zero, ctx->d_tc_err, ctx->tc_m[0], st);
+                             zero, ctx->d_tc_err, ctx->tc_m[0], ctx->d_tmap[0], st);
       else
         feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
                               nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
@@ -2138,7 +2210,7 @@ feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
     out[4 + 2 * w] = ctx->cfg32[w].R;
     out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
     if (ctx->tuned_m) {
-      out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;
+      out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;  // 0, -1, -2: tensor-core variants
       out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;
     }
   }

@@ -237,8 +237,11 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // Tensor-core (tcgen05, 3xTF32) variant of the FP32 block GEMM; cfg must be
 // the 128-rows-per-CTA table; nrhs <= 16; *err is set if a bounded wait
 // timed out.
+// Tensor-core block GEMM on the FP32 copies: variant 1 register-staged,
+// 2 bulk-copy staged, 3 tensor-map (TMA) fed; tmaps = one CUtensorMap per
+// subdomain for the matrix `which` (variant 3 only).
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
-                    double* y, const int* done, int* err, int variant, cudaStream_t st);
+                    double* y, const int* done, int* err, int variant, const void* tmaps, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
 // c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).

@@ -8,6 +8,8 @@
 // right-hand side is frozen (alpha = beta = 0 for it) while the others run on.
 #include "feti_internal.h"
 
+#include <cuda.h>
+
 #include <cmath>
 
 namespace feti {
@@ -819,6 +821,185 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc2(const int32_t* __restrict
   if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
+// TMA-fed variant: each K chunk of M_i (128 rows x 32 columns, FP32) is one
+// 2-D tensor-map load (cp.async.bulk.tensor) into a 128B-swizzled stage, rows
+// and columns beyond the block zero-filled by the copy engine.  The tensor
+// core reads an FP32 operand of kind::tf32 through its TF32 part (the low 13
+// mantissa bits are dropped, i.e. truncation toward zero), so the loaded
+// tile is the head operand as it is and threads only write the tail
+// x - trunc(x) beside it at the same swizzled offsets.  TC3_NS stages with a
+// full and an MMA-done mbarrier each: thread 0 refills the stage of chunk
+// kc - 1 as soon as its MMAs complete, while chunk kc's MMAs run.  The
+// three products of a K step accumulate into separate tensor-memory columns
+// (summed in the epilogue), so consecutive MMAs do not wait on one
+// accumulator.  Timeouts are CTA-uniform; copies and MMAs in flight are
+// drained with fresh bounded waits before tensor memory is freed.
+constexpr int TC3_NS = 3;
+constexpr int TC3_NACC = 3;  // hi*hi, hi*lo, lo*hi each in its own accumulator
+constexpr int TC3_TCOLS = TC3_NACC == 1 ? 32 : (TC3_NACC * 16 <= 64 ? 64 : (TC3_NACC * 16 <= 128 ? 128 : 256));
+constexpr int TC3_SMEM = TC3_NS * TC_STAGE + 1024;
+
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__global__ void __launch_bounds__(kThreads) k_gemm_tc3(const int32_t* __restrict__ blk_sub,
+                                                       const int32_t* __restrict__ blk_row0,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const CUtensorMap* __restrict__ maps, int nrhs,
+                                                       const float* __restrict__ vloc, double* __restrict__ y,
+                                                       const int* __restrict__ done, int* __restrict__ err) {
+  if (*done) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+  unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
+  __shared__ uint64_t full[TC3_NS], mdone[TC3_NS];
+  __shared__ uint32_t tmem_base;
+  const int s_id = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s_id];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const CUtensorMap* tm = maps + s_id;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  if (which == 0 && r0 == 0)
+    for (int idx = tid; idx < L.k * nrhs; idx += blockDim.x) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(TC3_TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < TC3_NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&mdone[i], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  const int nk = (m + 31) / 32;
+  // chunk kc2 -> stage kc2 % NS: box (32 columns from kc2 * 32, 128 rows from
+  // r0); the x coordinate is a multiple of 32 floats (128 bytes)
+  auto issue = [&](int kc2) {
+    const int st = kc2 % TC3_NS;
+    mbar_expect_tx(&full[st], (uint32_t)TC_A_BYTES);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(smem + st * TC_STAGE)),
+        "l"(tm), "r"(kc2 * 32), "r"(r0), "r"(su32(&full[st]))
+        : "memory");
+  };
+  if (tid == 0)
+    for (int j = 0; j < TC3_NS && j < nk; ++j) issue(j);
+  int issued = min(TC3_NS, nk);
+  float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto load_b = [&](int kc2) {
+    if (tid < 16 * 8) {
+      const int n = tid >> 3, c = tid & 7, k0 = kc2 * 32;
+      float v4[4];
+      for (int e = 0; e < 4; ++e) {
+        const int kk = k0 + 4 * c + e;
+        v4[e] = (kk < m && n < nrhs) ? vloc[(size_t)(L.boff + kk) * nrhs + n] : 0.f;
+      }
+      rb = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+  };
+  if (nk > 0) load_b(0);
+  bool timed_out = false;
+  int kc = 0, n_mma = 0;
+  for (; kc < nk; ++kc) {
+    const int st = kc % TC3_NS;
+    const float4 cb = rb;
+    if (kc + 1 < nk) load_b(kc + 1);
+    if (!mbar_wait_bounded(&full[st], (uint32_t)(kc / TC3_NS) & 1u)) timed_out = true;
+    unsigned char* Ahi = smem + st * TC_STAGE;
+    unsigned char* Alo = Ahi + TC_A_BYTES;
+    unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+    unsigned char* Blo = Bhi + TC_B_BYTES;
+    if (!timed_out) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int off = (tid + q * kThreads) * 16;
+        const float4 x = *reinterpret_cast<const float4*>(Ahi + off);
+        const float4 l = make_float4(x.x - tf32_trunc(x.x), x.y - tf32_trunc(x.y), x.z - tf32_trunc(x.z),
+                                     x.w - tf32_trunc(x.w));
+        *reinterpret_cast<float4*>(Alo + off) = l;
+      }
+      if (tid < 16 * 8) {
+        const int n = tid >> 3, c = tid & 7;
+        const float4 l = make_float4(cb.x - tf32_trunc(cb.x), cb.y - tf32_trunc(cb.y), cb.z - tf32_trunc(cb.z),
+                                     cb.w - tf32_trunc(cb.w));
+        *reinterpret_cast<float4*>(Bhi + sw_off(n, c)) = cb;
+        *reinterpret_cast<float4*>(Blo + sw_off(n, c)) = l;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    timed_out = __syncthreads_or(timed_out ? 1 : 0) != 0;
+    if (timed_out) break;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
+        const uint64_t bh = sw128_desc(Bhi + 32 * j), bl = sw128_desc(Blo + 32 * j);
+        const int a0 = (3 * j) % TC3_NACC, a1 = (3 * j + 1) % TC3_NACC, a2 = (3 * j + 2) % TC3_NACC;
+        // an accumulator is initialised by its first product of the first chunk
+        const uint32_t f0 = (kc > 0 || 3 * j >= TC3_NACC) ? 1u : 0u;
+        const uint32_t f1 = (kc > 0 || 3 * j + 1 >= TC3_NACC) ? 1u : 0u;
+        const uint32_t f2 = (kc > 0 || 3 * j + 2 >= TC3_NACC) ? 1u : 0u;
+        tc_mma(tmem + 16u * a0, ah, bh, idesc, f0);
+        tc_mma(tmem + 16u * a1, ah, bl, idesc, f1);
+        tc_mma(tmem + 16u * a2, al, bh, idesc, f2);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&mdone[st]))
+                   : "memory");
+      if (kc >= 1 && kc - 1 + TC3_NS < nk) {
+        if (mbar_wait_bounded(&mdone[(kc - 1) % TC3_NS], (uint32_t)((kc - 1) / TC3_NS) & 1u))
+          issue(kc - 1 + TC3_NS);
+        else
+          atomicExch(err, 1);
+      }
+    }
+    if (kc >= 1 && kc - 1 + TC3_NS < nk) issued = kc + TC3_NS;
+    n_mma = kc + 1;
+  }
+  // drain: loads issued but not consumed (only after a timeout), then the
+  // last MMA groups, each with its own bounded wait
+  bool drained = true;
+  if (tid == 0)
+    for (int j = kc; j < issued; ++j)
+      if (!mbar_wait_bounded(&full[j % TC3_NS], (uint32_t)(j / TC3_NS) & 1u)) drained = false;
+  for (int j = max(0, n_mma - TC3_NS); j < n_mma; ++j)
+    if (!mbar_wait_bounded(&mdone[j % TC3_NS], (uint32_t)(j / TC3_NS) & 1u)) drained = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if ((timed_out || !drained) && lane == 0) atomicExch(err, 1);
+  if (wid < 4) {
+    float acc[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) acc[n] = 0.f;
+    for (int a = 0; a < TC3_NACC; ++a) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(wid * 32) << 16) + 16u * (uint32_t)a));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int n = 0; n < 16; ++n) acc[n] += __uint_as_float(r[n]);
+    }
+    const int row = r0 + wid * 32 + lane;
+    if (row < m && !timed_out && drained)
+      for (int n = 0; n < nrhs; ++n) y[(size_t)(L.boff + row) * nrhs + n] = (double)acc[n];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC3_TCOLS) : "memory");
+}
+
 inline int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -868,14 +1049,19 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 }
 
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
-                    double* y, const int* done, int* err, int variant, cudaStream_t st) {
+                    double* y, const int* done, int* err, int variant, const void* tmaps, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_gemm_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
     attr = true;
   }
-  if (variant == 2)
+  if (variant == 3)
+    k_gemm_tc3<<<cfg.n_blocks, kThreads, TC3_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which,
+                                                         static_cast<const CUtensorMap*>(tmaps), nrhs, vloc, y, done,
+                                                         err);
+  else if (variant == 2)
     k_gemm_tc2<<<cfg.n_blocks, kThreads, TC2_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, M, nrhs, vloc, y, done,
                                                          err);
   else

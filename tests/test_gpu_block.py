@@ -67,10 +67,10 @@ JITTER = mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)
 
 
 @pytest.mark.parametrize("prob", [TUBE_FLOAT, JITTER], ids=["tube", "jittered"])
-@pytest.mark.parametrize("variant,code", [("force_reg", 0), ("force_bulk", -1)])
+@pytest.mark.parametrize("variant,code", [("force_reg", 0), ("force_bulk", -1), ("force_tma", -2)])
 def test_tensor_core_block_gemm_matches_cuda_cores(prob, variant, code):
-    """Each tcgen05 3xTF32 block GEMM (register-staged and bulk-copy staged
-    operands) against the CUDA-core FP32 GEMM on the same FP32 operator
+    """Each tcgen05 3xTF32 block GEMM (register-staged, bulk-copy staged and
+    tensor-map fed operands) against the CUDA-core FP32 GEMM on the same FP32 operator
     copies: agreement to 1e-5 relative (TF32 head + tail products reproduce
     FP32 products to about 2^-22 each), on subdomains whose boundary sizes are
     not multiples of the 32-column chunk or the 128-row tile; then a full
@@ -101,3 +101,43 @@ def test_tensor_core_block_gemm_matches_cuda_cores(prob, variant, code):
     assert rep["converged"] == 1
     for k, sc in enumerate(SCALES):
         assert np.linalg.norm(U[k] - sc * U_ref) <= 1e-8 * np.linalg.norm(sc * U_ref)
+
+
+def _linear_residual(prob, U, chunk=262144):
+    """||K u - f|| / ||f|| on the free DOFs, K u formed element by element
+    from the oracle's linear element matrices (chunked: bounded host memory)."""
+    from oracle import fem
+    Ur = U.reshape(-1, 3)
+    out = np.zeros(U.size)
+    E = prob.tets.shape[0]
+    for s0 in range(0, E, chunk):
+        t = prob.tets[s0:s0 + chunk]
+        Ke = fem.linear_element(prob.coords[t], prob.material["E"], prob.material["nu"])
+        fe = np.einsum("eij,ej->ei", Ke, Ur[t].reshape(-1, 12))
+        np.add.at(out, (3 * t[:, :, None] + np.arange(3)[None, None, :]).reshape(-1), fe.ravel())
+    f = fem.load_vector(prob)
+    free = np.ones(U.size, bool)
+    free[prob.dir_dof] = False
+    return np.linalg.norm((out - f)[free]) / np.linalg.norm(f[free])
+
+
+@pytest.mark.slow
+def test_full_size_4096_subdomains_16_rhs():
+    """The 48x192x96-cell jittered tube (2,737,728 DOFs) in 4096 uneven
+    subdomains, 16 load cases p_k ~ U[8, 16] (seeded), FP32-local block PCG
+    (FP64 outer residual) to 1e-10 on one GPU.  The load cases are collinear, so u_k / p_k must agree
+    across k; each u_k is checked for equilibrium by the oracle's element
+    route (K u_k formed element by element on the host)."""
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = mesh.config_problem("jcyl48")
+    scales = np.random.Generator(np.random.PCG64(16)).uniform(8.0, 16.0, size=16)
+    with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-10, maxit=6000, precision="mixed") as s:
+        U, rep = s.solve_multi(scales)
+        sz = s.sizes()
+    assert rep["converged"] == 1
+    assert sz["coarse_dim"] == 6 * 4096
+    base = U[0] / scales[0]
+    for k in range(16):
+        assert np.linalg.norm(U[k] / scales[k] - base) <= 1e-7 * np.linalg.norm(base)
+    for k in (0, 15):
+        assert _linear_residual(prob, U[k] / scales[k]) <= 1e-6
