@@ -117,8 +117,9 @@ typedef struct {
   int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
   int32_t no_tensor_cores; /* FP32 block GEMM: 0 = autotuner picks tensor cores if faster,
                               1 = CUDA cores only, 2 = tensor cores whenever they run cleanly
-                              (fastest staging variant), 3 / 4 / 5 = only the register-staged /
-                              bulk-copy staged / tensor-map (TMA) fed tensor-core kernel */
+                              (fastest staging variant), 3 / 4 / 5 / 6 / 7 = only the
+                              register-staged / bulk-copy staged / tensor-map (TMA) fed /
+                              warp-specialised TMA-fed 3-stage / 2-stage tensor-core kernel */
   int32_t per_subdomain;   /* nonzero: the dense local applies of F_i and S_i are launched once per
                               subdomain (p launches per apply, the plain non-batched form) instead
                               of one batched launch over all subdomains; same results, for
@@ -263,9 +264,10 @@ feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* ele
  * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
  * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
  * preconditioner apply, out[4..7] the same for the FP32 copies, out[8..11]
- * the FP32 block-form GEMMs (rows per warp step 0 / -1 / -2 = tensor-core
- * kernel with register-staged / bulk-copy staged / tensor-map fed operands;
- * both entries -1 = block form not tuned yet). */
+ * the FP32 block-form GEMMs (rows per warp step 0 / -1 / -2 / -3 / -4 =
+ * tensor-core kernel with register-staged / bulk-copy staged / tensor-map fed
+ * operands / warp-specialised 3-stage / 2-stage; both entries -1 = block form
+ * not tuned yet). */
 feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]);
 
 const char* feti_last_error(const feti_ctx* ctx);

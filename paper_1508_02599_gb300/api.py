@@ -71,7 +71,7 @@ class FetiSolver:
                             int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
-                             "force_bulk": 4, "force_tma": 5}[tensor_cores],
+                             "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
                             int(not batched))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),

@@ -86,7 +86,9 @@ struct feti_ctx {
   std::vector<int32_t> tab_ptr[2][3];  // first CTA of each subdomain in tab[which][k] (p + 1 entries)
   feti::GemvCfg cfg64[2], cfg32[2];
   feti::GemvCfg cfgm64[2], cfgm32[2];  // block form (N = nrhs) schedules
-  int tc_m[2] = {0, 0};  // FP32 block GEMM on the tensor cores: 0 no, 1 register-staged, 2 bulk-copy staged, 3 TMA
+  // FP32 block GEMM on the tensor cores: 0 no, 1 register-staged, 2 bulk-copy staged, 3 TMA-fed,
+  // 4 / 5 warp-specialised TMA-fed with 3 / 2 stages
+  int tc_m[2] = {0, 0};
   CUtensorMap* d_tmap[2] = {nullptr, nullptr};  // per-subdomain tensor maps of the FP32 F_i and S_i copies
   int* d_tc_err = nullptr;
   int tuned_m = 0;                     // nrhs the block schedules were tuned for
@@ -95,6 +97,8 @@ struct feti_ctx {
   int32_t *d_chunk_sub = nullptr, *d_chunk_p0 = nullptr, *d_sub_chunk_ptr = nullptr, *d_col_sub = nullptr;
   double* d_gpart = nullptr;
   int32_t *d_gs_ptr = nullptr, *d_gs_pos = nullptr, *d_dir_dof = nullptr;
+  int32_t *d_gs_gdof = nullptr, *d_elem_gs = nullptr, *d_inc_ptr = nullptr, *d_inc = nullptr;
+  double* d_nk = nullptr;  // Newton-Krylov vectors: 5 x n_gs
   int32_t *d_lump_ptr = nullptr, *d_lump_col = nullptr;
   int64_t* d_lump_src = nullptr;
   double* d_lump_val = nullptr;
@@ -669,6 +673,32 @@ feti_status build_decomposition(feti_ctx* ctx) {
         const int g = 3 * ctx->nodes[s][d / 3] + d % 3;
         if (!is_dir[g]) gs_pos[fill2[gid[g]]++] = ctx->lay[s].voff + i;
       }
+    if (ctx->mat.kind == FETI_HGO_TWO_FIBRE) {
+      // Newton-Krylov maps: gs row -> global DOF, element DOF -> gs row (-1:
+      // Dirichlet), and per gs row its incident (element, local row) pairs
+      std::vector<int32_t> gs_gdof;
+      for (size_t g = 0; g < 3 * (size_t)N; ++g)
+        if (gid[g] >= 0) gs_gdof.push_back((int32_t)g);
+      std::vector<int32_t> elem_gs(12 * (size_t)E), inc_ptr(gs_gdof.size() + 1, 0), inc;
+      for (int e = 0; e < E; ++e)
+        for (int a = 0; a < 12; ++a) {
+          const int j = gid[3 * ctx->tets[4 * (size_t)e + a / 3] + a % 3];
+          elem_gs[12 * (size_t)e + a] = j;
+          if (j >= 0) inc_ptr[j + 1]++;
+        }
+      for (size_t j = 0; j < gs_gdof.size(); ++j) inc_ptr[j + 1] += inc_ptr[j];
+      inc.assign(inc_ptr.back(), 0);
+      std::vector<int32_t> fill3(inc_ptr.begin(), inc_ptr.end() - 1);
+      for (int e = 0; e < E; ++e)
+        for (int a = 0; a < 12; ++a) {
+          const int j = elem_gs[12 * (size_t)e + a];
+          if (j >= 0) inc[fill3[j]++] = 12 * e + a;
+        }
+      FETI_TRY(upload(ctx, &ctx->d_gs_gdof, gs_gdof));
+      FETI_TRY(upload(ctx, &ctx->d_elem_gs, elem_gs));
+      FETI_TRY(upload(ctx, &ctx->d_inc_ptr, inc_ptr));
+      FETI_TRY(upload(ctx, &ctx->d_inc, inc));
+    }
   }
   ctx->n_gs = (int)gs_ptr.size() - 1;
   ctx->U_init.assign(3 * (size_t)N, 0.0);
@@ -1405,7 +1435,7 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           ctx->tc_m[w] = 0;
           const int ntc = ctx->opt.no_tensor_cores;
           FETI_TRY(build_tensor_maps(ctx));
-          for (int variant = 1; variant <= 3; ++variant) {
+          for (int variant = 1; variant <= 5; ++variant) {
             if (ntc >= 3 && variant != ntc - 2) continue;
             FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
             feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,
@@ -1881,6 +1911,89 @@ static feti_status newton_residual(feti_ctx* ctx, const double* dU, double tau, 
   return FETI_OK;
 }
 
+// (a, b) over the non-Dirichlet global DOFs: per-CTA partials, fixed-order
+// host sum.
+static feti_status gs_dot(feti_ctx* ctx, const double* a, const double* b, double* out) {
+  const int np = feti::scatter_partials();
+  feti::launch_gs_dot(ctx->n_gs, a, b, ctx->d_partial, ctx->stream);
+  FETI_CK(cudaGetLastError());
+  ctx->h_partial.resize(np);
+  FETI_CK(cudaMemcpyAsync(ctx->h_partial.data(), ctx->d_partial, np * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  for (double v : ctx->h_partial) t += v;
+  *out = t;
+  return FETI_OK;
+}
+
+// Newton increment dU (3N, zero on Dirichlet DOFs) from the local residuals
+// d_f of the last assembly: flexible CG on the assembled tangent system
+// K dU = R over the non-Dirichlet DOFs, with the FETI solve as the
+// preconditioner (residual injected into the owner copies, dual PCG,
+// recovery, owner copies taken back) and K applied element by element from
+// the stored element tangents.  When the FETI increment is exact the first
+// iteration already meets the tolerance; when the reference rigid modes are
+// no longer exact kernels of the prestressed local tangents, the outer
+// iteration supplies what the FETI increment misses.  Stops at
+// ||R - K dU|| <= eta ||R|| or after max_it FETI solves.
+static feti_status newton_increment(feti_ctx* ctx, double eta, int max_it, int* pcg_its, double* pcg_ms,
+                                    int* krylov_its, double* krylov_rel) {
+  cudaStream_t st = ctx->stream;
+  const int n = ctx->n_gs;
+  if (!ctx->d_nk) FETI_TRY(dev_alloc(ctx, &ctx->d_nk, 5 * (size_t)std::max(n, 1)));
+  double *x = ctx->d_nk, *r = x + n, *z = r + n, *p = z + n, *q = p + n;
+  feti::launch_gs_assemble(n, ctx->d_gs_ptr, ctx->d_gs_pos, ctx->d_f, r, st);
+  FETI_CK(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
+  double bb = 0.0;
+  FETI_TRY(gs_dot(ctx, r, r, &bb));
+  const double bnorm = std::sqrt(bb);
+  double pq_prev = 0.0, rn = bnorm;
+  *krylov_its = 0;
+  for (int it = 0; it < max_it && rn > 0.0; ++it) {
+    FETI_CK(cudaMemsetAsync(ctx->d_f, 0, (size_t)ctx->nloc_total * sizeof(double), st));
+    feti::launch_gs_inject(n, ctx->d_gs_ptr, ctx->d_gs_pos, r, ctx->d_f, st);
+    feti_report rep{};
+    float ms = 0.f;
+    FETI_TRY(dual_solve(ctx, &rep, &ms));
+    *pcg_its += rep.iterations;
+    *pcg_ms += ms;
+    feti::launch_gs_take(n, ctx->d_gs_ptr, ctx->d_gs_pos, ctx->d_x, z, st);
+    if (it == 0) {
+      FETI_CK(cudaMemcpyAsync(p, z, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      double zq = 0.0;
+      FETI_TRY(gs_dot(ctx, z, q, &zq));  // q = K p of the previous direction
+      feti::launch_axpy_to(n, z, -zq / pq_prev, p, p, st);
+    }
+    feti::launch_gs_elem_matvec(n, ctx->d_inc_ptr, ctx->d_inc, ctx->d_elem_gs, ctx->d_Ke, p, q, st);
+    double pq = 0.0, pr = 0.0;
+    FETI_TRY(gs_dot(ctx, p, q, &pq));
+    FETI_TRY(gs_dot(ctx, p, r, &pr));
+    if (!(pq > 0.0) || !std::isfinite(pq)) {
+      if (it == 0) {  // tangent not positive along the FETI increment: keep that increment
+        FETI_CK(cudaMemcpyAsync(x, z, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        *krylov_its = 1;
+      }
+      break;
+    }
+    const double alpha = pr / pq;
+    feti::launch_axpy_to(n, x, alpha, p, x, st);
+    feti::launch_axpy_to(n, r, -alpha, q, r, st);
+    double rr = 0.0;
+    FETI_TRY(gs_dot(ctx, r, r, &rr));
+    rn = std::sqrt(rr);
+    *krylov_its = it + 1;
+    pq_prev = pq;
+    if (rn <= eta * bnorm) break;
+  }
+  *krylov_rel = bnorm > 0.0 ? rn / bnorm : 0.0;
+  FETI_CK(cudaMemsetAsync(ctx->d_dU, 0, 3 * (size_t)ctx->N * sizeof(double), st));
+  feti::launch_gs_to_global(n, ctx->d_gs_gdof, x, ctx->d_dU, st);
+  FETI_CK(cudaGetLastError());
+  return FETI_OK;
+}
+
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
@@ -1913,15 +2026,11 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
         if (report) { report->newton_iters = newton_total; report->newton_rel_res = rel; report->iterations = pcg_total; }
         return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "Newton reached its iteration limit at load step " + std::to_string(step));
       }
-      feti_report r{};
-      float ms = 0.f;
-      feti_status s = dual_solve(ctx, &r, &ms);
-      if (s != FETI_OK) return s;
-      pcg_total += r.iterations;
-      t_pcg += ms;
-      // increment on the global DOFs (owner rule), zero on Dirichlet DOFs
-      FETI_CK(cudaMemsetAsync(ctx->d_dU, 0, n3 * sizeof(double), st));
-      feti::launch_owner_scatter(ctx->n_own, ctx->d_own_gdof, ctx->d_own_vpos, ctx->d_x, ctx->d_dU, st);
+      int step_pcg = 0, kits = 0;
+      double krel = 0.0;
+      FETI_TRY(newton_increment(ctx, 1e-4, 12, &step_pcg, &t_pcg, &kits, &krel));
+      pcg_total += step_pcg;
+      feti_status s = FETI_OK;
       // step length: halve until the local tangents at U + a dU factorize
       double a = 1.0;
       for (;;) {
@@ -1939,8 +2048,10 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
       ++newton_total;
       FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
       if (log) {
-        std::fprintf(stderr, "feti_newton: step %d it %d pcg %d (%s, rel %.2e) step length %.4f -> rel %.3e\n", step,
-                     k + 1, r.iterations, r.converged ? "converged" : "not converged", r.rel_residual, a, rel);
+        std::fprintf(stderr,
+                     "feti_newton: step %d it %d: %d FETI solves (%d PCG iterations), increment residual %.2e, "
+                     "step length %.4f -> rel %.3e\n",
+                     step, k + 1, kits, step_pcg, krel, a, rel);
       }
     }
   }
@@ -2210,7 +2321,7 @@ feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
     out[4 + 2 * w] = ctx->cfg32[w].R;
     out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
     if (ctx->tuned_m) {
-      out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;  // 0, -1, -2: tensor-core variants
+      out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;  // 0 .. -4: tensor-core variants
       out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;
     }
   }

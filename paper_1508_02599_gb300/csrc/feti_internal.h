@@ -181,6 +181,18 @@ void launch_global_sumsq(int n, const int32_t* ptr, const int32_t* pos, const do
                          cudaStream_t st);
 // out = u + a du
 void launch_axpy_to(int n, const double* u, double a, const double* du, double* out, cudaStream_t st);
+// Newton-Krylov on the non-Dirichlet global DOFs (gs rows: local copies,
+// lowest subdomain first): assembled sum of the copies, owner injection into
+// (pre-zeroed) local vectors, owner copy back, element-wise tangent matvec
+// (node-incidence gather, deterministic), fixed-order dot partials (one per
+// CTA of scatter_partials()), and scatter to the 3N global vector.
+void launch_gs_assemble(int n, const int32_t* ptr, const int32_t* pos, const double* xloc, double* y, cudaStream_t st);
+void launch_gs_inject(int n, const int32_t* ptr, const int32_t* pos, const double* r, double* floc, cudaStream_t st);
+void launch_gs_take(int n, const int32_t* ptr, const int32_t* pos, const double* xloc, double* z, cudaStream_t st);
+void launch_gs_elem_matvec(int n, const int32_t* inc_ptr, const int32_t* inc, const int32_t* elem_gs, const double* Ke,
+                           const double* v, double* y, cudaStream_t st);
+void launch_gs_dot(int n, const double* a, const double* b, double* partial, cudaStream_t st);
+void launch_gs_to_global(int n, const int32_t* gdof, const double* x, double* out, cudaStream_t st);
 }  // namespace feti
 
 namespace feti {
@@ -238,8 +250,9 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // the 128-rows-per-CTA table; nrhs <= 16; *err is set if a bounded wait
 // timed out.
 // Tensor-core block GEMM on the FP32 copies: variant 1 register-staged,
-// 2 bulk-copy staged, 3 tensor-map (TMA) fed; tmaps = one CUtensorMap per
-// subdomain for the matrix `which` (variant 3 only).
+// 2 bulk-copy staged, 3 tensor-map (TMA) fed, 4 / 5 warp-specialised
+// TMA-fed with 3 / 2 stages; tmaps = one CUtensorMap per subdomain for the
+// matrix `which` (variants 3-5).
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
                     double* y, const int* done, int* err, int variant, const void* tmaps, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,

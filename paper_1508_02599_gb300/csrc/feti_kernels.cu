@@ -1144,6 +1144,83 @@ void launch_global_sumsq(int n, const int32_t* ptr, const int32_t* pos, const do
   k_global_sumsq<<<kPartials, kThreads, 0, st>>>(n, ptr, pos, x, partial);
 }
 
+namespace {
+// Newton-Krylov helpers on the non-Dirichlet global DOFs ("gs space": row j
+// lists the local copies gs_pos[gs_ptr[j] .. gs_ptr[j + 1]), lowest
+// subdomain first).
+__global__ void k_gs_assemble(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                              const double* __restrict__ xloc, double* __restrict__ y) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int q = ptr[j]; q < ptr[j + 1]; ++q) t += xloc[pos[q]];
+    y[j] = t;
+  }
+}
+__global__ void k_gs_inject(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                            const double* __restrict__ r, double* __restrict__ floc) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) floc[pos[ptr[j]]] = r[j];
+}
+__global__ void k_gs_take(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                          const double* __restrict__ xloc, double* __restrict__ z) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) z[j] = xloc[pos[ptr[j]]];
+}
+// y = K v with K the sum of the element tangents Ke (row-major 12x12 per
+// element): row j gathers, over its incident (element, local row) pairs
+// inc[inc_ptr[j] ..], the 12-term products with v at the element's gs DOFs
+// (-1 = Dirichlet, skipped).  Fixed order per row: deterministic.
+__global__ void k_gs_elem_matvec(int n, const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc,
+                                 const int32_t* __restrict__ elem_gs, const double* __restrict__ Ke,
+                                 const double* __restrict__ v, double* __restrict__ y) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int q = inc_ptr[j]; q < inc_ptr[j + 1]; ++q) {
+      const int ea = inc[q];
+      const int e = ea / 12, a = ea % 12;
+      const double* K = Ke + (size_t)e * 144 + a * 12;
+      const int32_t* d = elem_gs + (size_t)e * 12;
+#pragma unroll
+      for (int b = 0; b < 12; ++b) {
+        const int g = d[b];
+        if (g >= 0) t += K[b] * v[g];
+      }
+    }
+    y[j] = t;
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_gs_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                                     double* __restrict__ partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) acc += a[j] * b[j];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+__global__ void k_gs_to_global(int n, const int32_t* __restrict__ gdof, const double* __restrict__ x,
+                               double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) out[gdof[j]] = x[j];
+}
+}  // namespace
+
+void launch_gs_assemble(int n, const int32_t* ptr, const int32_t* pos, const double* xloc, double* y, cudaStream_t st) {
+  k_gs_assemble<<<grid_for(n), kThreads, 0, st>>>(n, ptr, pos, xloc, y);
+}
+void launch_gs_inject(int n, const int32_t* ptr, const int32_t* pos, const double* r, double* floc, cudaStream_t st) {
+  k_gs_inject<<<grid_for(n), kThreads, 0, st>>>(n, ptr, pos, r, floc);
+}
+void launch_gs_take(int n, const int32_t* ptr, const int32_t* pos, const double* xloc, double* z, cudaStream_t st) {
+  k_gs_take<<<grid_for(n), kThreads, 0, st>>>(n, ptr, pos, xloc, z);
+}
+void launch_gs_elem_matvec(int n, const int32_t* inc_ptr, const int32_t* inc, const int32_t* elem_gs, const double* Ke,
+                           const double* v, double* y, cudaStream_t st) {
+  k_gs_elem_matvec<<<grid_for(n), kThreads, 0, st>>>(n, inc_ptr, inc, elem_gs, Ke, v, y);
+}
+void launch_gs_dot(int n, const double* a, const double* b, double* partial, cudaStream_t st) {
+  k_gs_dot<<<kPartials, kThreads, 0, st>>>(n, a, b, partial);
+}
+void launch_gs_to_global(int n, const int32_t* gdof, const double* x, double* out, cudaStream_t st) {
+  k_gs_to_global<<<grid_for(n), kThreads, 0, st>>>(n, gdof, x, out);
+}
+
 void launch_axpy_to(int n, const double* u, double a, const double* du, double* out, cudaStream_t st) {
   k_axpy_to<<<grid_for(n), kThreads, 0, st>>>(n, u, a, du, out);
 }

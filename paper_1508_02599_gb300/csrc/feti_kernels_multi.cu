@@ -1000,6 +1000,200 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc3(const int32_t* __restrict
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC3_TCOLS) : "memory");
 }
 
+// Warp-specialised TMA-fed variant: the same stages, operands and products
+// as k_gemm_tc3, but the roles run concurrently and meet only on per-stage
+// mbarriers, with no CTA barrier per chunk: warp 0 (one lane) issues the
+// tensor-map loads as soon as a stage is free (empty), warp 1 (one lane)
+// issues the MMAs of a chunk once its tails are ready and commits them to the
+// stage's empty barrier, warps 4..7 wait for a stage's tile (full), write
+// the tails and the V tile and arrive on ready (one arrival per warp).  Any
+// bounded wait that runs out sets a shared abort flag that ends every role's
+// loop; the producer then waits (bounded) for its own loads in flight and
+// the MMA lane for its last commit before tensor memory is freed.
+constexpr int TC4_TCOLS = 64;  // three 16-column accumulators
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* b, uint32_t par, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(b, par)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > 200000000LL) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kThreads) k_gemm_tc4(const int32_t* __restrict__ blk_sub,
+                                                       const int32_t* __restrict__ blk_row0,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const CUtensorMap* __restrict__ maps, int nrhs,
+                                                       const float* __restrict__ vloc, double* __restrict__ y,
+                                                       const int* __restrict__ done, int* __restrict__ err) {
+  if (*done) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+  unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
+  __shared__ uint64_t full[NS], ready[NS], empty[NS];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int s_id = blk_sub[blockIdx.x];
+  const int r0 = blk_row0[blockIdx.x];
+  const SubLayout L = lay[s_id];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const CUtensorMap* tm = maps + s_id;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  if (which == 0 && r0 == 0)
+    for (int idx = tid; idx < L.k * nrhs; idx += blockDim.x) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(TC4_TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&ready[i], 4);
+      mbar_init(&empty[i], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  const int nk = (m + 31) / 32;
+  volatile int* ab = &abort_flag;
+  if (wid == 0) {
+    if (lane == 0) {  // producer: chunk kc -> stage kc % NS once the MMAs of chunk kc - NS are done
+      int issued = 0;
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % NS;
+        if (kc >= NS && !wait_or_abort(&empty[st], (uint32_t)((kc / NS) - 1) & 1u, ab)) break;
+        mbar_expect_tx(&full[st], (uint32_t)TC_A_BYTES);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(su32(smem + st * TC_STAGE)),
+            "l"(tm), "r"(kc * 32), "r"(r0), "r"(su32(&full[st]))
+            : "memory");
+        issued = kc + 1;
+      }
+      for (int j = max(0, issued - NS); j < issued; ++j)
+        if (!mbar_wait_bounded(&full[j % NS], (uint32_t)(j / NS) & 1u)) atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else if (wid == 1) {
+    if (lane == 0) {  // MMA issuer
+      int n_mma = 0;
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % NS;
+        if (!wait_or_abort(&ready[st], (uint32_t)(kc / NS) & 1u, ab)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* Ahi = smem + st * TC_STAGE;
+        unsigned char* Alo = Ahi + TC_A_BYTES;
+        unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+        unsigned char* Blo = Bhi + TC_B_BYTES;
+        for (int j = 0; j < 4; ++j) {
+          const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
+          const uint64_t bh = sw128_desc(Bhi + 32 * j), bl = sw128_desc(Blo + 32 * j);
+          const uint32_t f = (kc > 0 || j > 0) ? 1u : 0u;
+          tc_mma(tmem, ah, bh, idesc, f);
+          tc_mma(tmem + 16u, ah, bl, idesc, f);
+          tc_mma(tmem + 32u, al, bh, idesc, f);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&empty[st]))
+                     : "memory");
+        n_mma = kc + 1;
+      }
+      if (n_mma > 0 && !mbar_wait_bounded(&empty[(n_mma - 1) % NS], (uint32_t)((n_mma - 1) / NS) & 1u))
+        atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else if (wid >= 4) {  // tail workers (128 threads)
+    const int t = tid - 128;
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load_b = [&](int kc2) {
+      const int n = t >> 3, c = t & 7, k0 = kc2 * 32;
+      float v4[4];
+      for (int e = 0; e < 4; ++e) {
+        const int kk = k0 + 4 * c + e;
+        v4[e] = (kk < m && n < nrhs) ? vloc[(size_t)(L.boff + kk) * nrhs + n] : 0.f;
+      }
+      rb = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    };
+    if (nk > 0) load_b(0);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int st = kc % NS;
+      const float4 cb = rb;
+      if (kc + 1 < nk) load_b(kc + 1);
+      if (!wait_or_abort(&full[st], (uint32_t)(kc / NS) & 1u, ab)) break;
+      unsigned char* Ahi = smem + st * TC_STAGE;
+      unsigned char* Alo = Ahi + TC_A_BYTES;
+      unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+      unsigned char* Blo = Bhi + TC_B_BYTES;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int off = (t + q * 128) * 16;
+        const float4 x = *reinterpret_cast<const float4*>(Ahi + off);
+        *reinterpret_cast<float4*>(Alo + off) = make_float4(x.x - tf32_trunc(x.x), x.y - tf32_trunc(x.y),
+                                                            x.z - tf32_trunc(x.z), x.w - tf32_trunc(x.w));
+      }
+      {
+        const int n = t >> 3, c = t & 7;
+        *reinterpret_cast<float4*>(Bhi + sw_off(n, c)) = cb;
+        *reinterpret_cast<float4*>(Blo + sw_off(n, c)) = make_float4(
+            cb.x - tf32_trunc(cb.x), cb.y - tf32_trunc(cb.y), cb.z - tf32_trunc(cb.z), cb.w - tf32_trunc(cb.w));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&ready[st])) : "memory");
+    }
+  }
+  // the epilogue warps wait for the last MMA group (issued after every earlier one completed)
+  bool ok = true;
+  if (wid >= 4 && nk > 0) {
+    const int j = nk - 1;
+    const long long t0 = clock64();
+    while (!mbar_try(&empty[j % NS], (uint32_t)(j / NS) & 1u))
+      if (*ab || clock64() - t0 > 200000000LL) {
+        ok = false;
+        break;
+      }
+  }
+  if (*ab) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (wid >= 4) {
+    if (!ok && lane == 0) atomicExch(err, 1);
+    const int w4 = wid - 4;
+    float acc[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) acc[n] = 0.f;
+    for (int a = 0; a < 3; ++a) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(w4 * 32) << 16) + 16u * (uint32_t)a));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int n = 0; n < 16; ++n) acc[n] += __uint_as_float(r[n]);
+    }
+    const int row = r0 + w4 * 32 + lane;
+    if (row < m && ok)
+      for (int n = 0; n < nrhs; ++n) y[(size_t)(L.boff + row) * nrhs + n] = (double)acc[n];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC4_TCOLS) : "memory");
+}
+
 inline int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -1057,7 +1251,21 @@ void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const f
     cudaFuncSetAttribute(k_gemm_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
     attr = true;
   }
-  if (variant == 3)
+  if (variant == 4 || variant == 5) {
+    static bool attr4 = false;
+    if (!attr4) {
+      cudaFuncSetAttribute(k_gemm_tc4<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * TC_STAGE + 1024);
+      cudaFuncSetAttribute(k_gemm_tc4<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * TC_STAGE + 1024);
+      attr4 = true;
+    }
+    const CUtensorMap* mp = static_cast<const CUtensorMap*>(tmaps);
+    if (variant == 4)
+      k_gemm_tc4<3><<<cfg.n_blocks, kThreads, 3 * TC_STAGE + 1024, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, mp,
+                                                                        nrhs, vloc, y, done, err);
+    else
+      k_gemm_tc4<2><<<cfg.n_blocks, kThreads, 2 * TC_STAGE + 1024, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, mp,
+                                                                        nrhs, vloc, y, done, err);
+  } else if (variant == 3)
     k_gemm_tc3<<<cfg.n_blocks, kThreads, TC3_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which,
                                                          static_cast<const CUtensorMap*>(tmaps), nrhs, vloc, y, done,
                                                          err);
