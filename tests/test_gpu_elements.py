@@ -109,3 +109,39 @@ def test_full_size_hgo_elements_sampled():
     assert np.abs(fs).max() <= 1e-10 * np.abs(fe).max()
     ks = Ke.reshape(-1, 12, 4, 3).sum(axis=2)
     assert np.abs(ks).max() <= 1e-9 * np.abs(Ke).max()
+
+
+def _oracle_rel_residual(prob, U, chunk=32768):
+    """||f_int(U) - f_ext(U)|| / ||f_ext(U)|| on the free DOFs, element forces
+    from the oracle's own element route in chunks (bounded host memory)."""
+    Ur = U.reshape(-1, 3)
+    E = prob.tets.shape[0]
+    fint = np.empty((E, 12))
+    for s0 in range(0, E, chunk):
+        t = prob.tets[s0:s0 + chunk]
+        f, _, detF = fem.hgo_element(prob.coords[t], Ur[t], prob.fibres[s0:s0 + chunk], prob.material)
+        assert np.all(detF > 0.0)
+        fint[s0:s0 + chunk] = f
+    fext = fem.load_vector(prob, Ur, True)
+    R = fem.internal_force_global(prob, fint) - fext
+    free = np.ones(U.size, bool)
+    free[prob.dir_dof] = False
+    return np.linalg.norm(R[free]) / np.linalg.norm(fext[free])
+
+
+@pytest.mark.slow
+def test_full_size_newton_256_subdomains():
+    """The 24x96x48-cell tube (117,600 nodes, 663,552 tets, 256 subdomains)
+    with the Table 1 material under follower pressure, 1 mmHg in four load
+    steps, Newton with all-floating FETI to a relative residual of 1e-8.  The
+    returned displacement is checked by the oracle's element route (its own
+    stress formula and load vector), independently of the kernel's tangent,
+    of the FETI increments and of the GPU residual."""
+    from paper_1508_02599_gb300 import FetiSolver
+    prob = mesh.cylinder_problem(24, 96, 48, (4, 16, 4), material=mesh.hgo_material(), pressure=0.13332)
+    with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-10, maxit=4000, n_load_steps=4,
+                    newton_tol=1e-8, newton_maxit=25) as s:
+        U, rep = s.newton()
+    assert rep["newton_rel_res"] <= 1e-8
+    assert np.linalg.norm(U) > 0.0
+    assert _oracle_rel_residual(prob, U) <= 2e-8
