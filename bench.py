@@ -395,9 +395,13 @@ def main():
                 "local_apply_kernel_ms": mp["kern_ms"],
                 "note": "plain form: FP64, one local-apply launch per subdomain instead of one batched launch; "
                         "same kernels, graphs and schedule"},
-            "roofline": {"bound": "hbm", "kernel": "k_gemv_loc<float> (F_i apply, FP32 copy)", "achieved": gbs32,
+            "roofline": {"bound": "hbm",
+                         "kernel": ("k_symv_f32 + k_symv_fix (F_i apply, FP32 lower block-triangle)"
+                                    if m32["sched"]["fp32_F"][0] < 0 else "k_gemv_loc<float> (F_i apply, FP32 copy)"),
+                         "achieved": gbs32,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],
                          "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
+                         "bytes_note": "n(n+1)/2 distinct FP32 entries per symmetric F_i + 16 B per boundary DOF",
                          "peak_source": src},
             "clocks": m32["clocks"],
             "schedule": {"fp32_F": m32["sched"]["fp32_F"], "fp32_M": m32["sched"]["fp32_M"],

@@ -124,6 +124,9 @@ typedef struct {
                               subdomain (p launches per apply, the plain non-batched form) instead
                               of one batched launch over all subdomains; same results, for
                               measuring what batching buys */
+  int32_t symmetric;       /* FP32 single-vector local applies: 0 = the autotuner picks the
+                              symmetric kernel (reads only the lower block-triangle of F_i / S_i)
+                              when it is faster, 1 = full rows only, 2 = symmetric always */
 } feti_options;
 
 typedef struct {
@@ -245,7 +248,8 @@ feti_status feti_prepare(feti_ctx* ctx);
 /* Dominant per-iteration kernel (dense local F_i apply with fused gather):
  * its device time averaged over the launches inside the last feti_dual_apply
  * (timed by event nodes around each launch in that graph), the algorithmic
- * bytes one launch must move (each F_i entry once, gathered multipliers,
+ * bytes one launch must move (each of the n(n+1)/2 distinct entries of the
+ * symmetric F_i once, gathered multipliers,
  * local outputs) and its floating-point operations (2 per F_i entry). */
 feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv_bytes,
                               double* gemv_flops);
@@ -263,7 +267,8 @@ feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* ele
 /* Launch schedules of the dense local applies chosen by the setup-time
  * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
  * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
- * preconditioner apply, out[4..7] the same for the FP32 copies, out[8..11]
+ * preconditioner apply, out[4..7] the same for the FP32 copies (rows per warp
+ * step -G, rows 32 = symmetric panel kernel with load groups of G rows), out[8..11]
  * the FP32 block-form GEMMs (rows per warp step 0 / -1 / -2 / -3 / -4 =
  * tensor-core kernel with register-staged / bulk-copy staged / tensor-map fed
  * operands / warp-specialised 3-stage / 2-stage; both entries -1 = block form

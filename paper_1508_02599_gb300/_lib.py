@@ -42,7 +42,7 @@ class FetiOptions(C.Structure):
                 ("maxit", C.c_int32), ("chunk", C.c_int32), ("follower", C.c_int32),
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32),
-                ("per_subdomain", C.c_int32)]
+                ("per_subdomain", C.c_int32), ("symmetric", C.c_int32)]
 
 
 class FetiReport(C.Structure):

@@ -39,7 +39,7 @@ class FetiSolver:
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
-                 tensor_cores="auto", batched: bool = True):
+                 tensor_cores="auto", batched: bool = True, symmetric="auto"):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -72,7 +72,7 @@ class FetiSolver:
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
-                            int(not batched))
+                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2}[symmetric])
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

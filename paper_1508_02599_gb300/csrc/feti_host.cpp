@@ -132,7 +132,15 @@ struct feti_ctx {
   double t_setup_ms = 0.0;
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
   double elem_ms = 0.0, elem_bytes = 0.0;
-  int64_t op_elems[5] = {0, 0, 0, 0, 0};  // sizes of d_A, d_S, d_F, d_F32, d_S32 (elements)
+  // sizes (elements) of d_A, d_S, d_F, d_F32, d_S32, d_F32s, d_S32s, d_symp
+  int64_t op_elems[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // symmetric FP32 local applies: lower block-triangles, transposed-product
+  // partials, work lists, and the load-group size picked by the autotuner
+  // per matrix (0: the full-row kernel is used)
+  float *d_F32s = nullptr, *d_S32s = nullptr, *d_symp = nullptr;
+  int32_t *d_sym_sub[2] = {nullptr, nullptr}, *d_sym_panel[2] = {nullptr, nullptr};
+  int sym_n[2] = {0, 0};
+  int sym32[2] = {0, 0};
   cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
   int m_cap = 0;  // allocated nrhs capacity of the block buffers
@@ -367,7 +375,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   ctx->fix_ldof.clear();
   std::vector<std::vector<int32_t>> dense_ldof(P);  // dense index -> local DOF
   std::vector<std::vector<double>> Rd(P);           // R in dense order, n x k
-  int64_t aoff = 0, soff = 0, foff = 0, roff = 0, foff32 = 0, soff32 = 0;
+  int64_t aoff = 0, soff = 0, foff = 0, roff = 0, foff32 = 0, soff32 = 0, fsym = 0, ssym = 0, psym = 0;
   int boff = 0, voff = 0, coff = 0;
   for (int s = 0; s < P; ++s) {
     const auto& nod = ctx->nodes[s];
@@ -486,8 +494,15 @@ feti_status build_decomposition(feti_ctx* ctx) {
     L.boff = boff; L.voff = voff; L.coff = coff;
     L.aoff = aoff; L.soff = soff; L.foff = foff; L.roff = roff;
     L.foff32 = foff32; L.soff32 = soff32;
+    L.fsym32 = fsym; L.ssym32 = ssym; L.psym = psym;
     ctx->lay[s] = L;
     const int nb = nbp + k;
+    {
+      const int64_t pf = (nbp + 31) / 32, ps = (nb + 31) / 32;
+      fsym += 512 * pf * (pf + 1);
+      ssym += 512 * ps * (ps + 1);
+      psym += 16 * ps * (ps - 1);  // sized for the larger (preconditioner) block
+    }
     boff += nb;
     voff += n;
     coff += k;
@@ -836,6 +851,32 @@ feti_status build_decomposition(feti_ctx* ctx) {
   ctx->op_elems[2] = foff;
   ctx->op_elems[3] = foff32;
   ctx->op_elems[4] = ctx->opt.precond == FETI_PREC_DIRICHLET ? soff32 : 1;
+  ctx->op_elems[5] = fsym;
+  ctx->op_elems[6] = ctx->opt.precond == FETI_PREC_DIRICHLET ? ssym : 1;
+  ctx->op_elems[7] = psym;
+  for (int w = 0; w < 2; ++w) {
+    // symmetric-apply work lists: one warp per (subdomain, 32-row panel).
+    // Panel I carries I + 1 blocks, so the list runs from the longest panels
+    // to the shortest and the eight warps of a CTA take the same panel index
+    // of eight subdomains: balanced CTAs, longest work first.
+    std::vector<int32_t> ws, wp;
+    int max_np = 0;
+    for (int q = 0; q < P; ++q) {
+      const int m = w == 0 ? ctx->lay[q].nbp : ctx->lay[q].nbp + ctx->lay[q].k;
+      max_np = std::max(max_np, (m + 31) / 32);
+    }
+    for (int I = max_np - 1; I >= 0; --I)
+      for (int q = 0; q < P; ++q) {
+        const int m = w == 0 ? ctx->lay[q].nbp : ctx->lay[q].nbp + ctx->lay[q].k;
+        if (I < (m + 31) / 32) {
+          ws.push_back(q);
+          wp.push_back(I);
+        }
+      }
+    ctx->sym_n[w] = (int)ws.size();
+    FETI_TRY(upload(ctx, &ctx->d_sym_sub[w], ws));
+    FETI_TRY(upload(ctx, &ctx->d_sym_panel[w], wp));
+  }
   FETI_TRY(dev_alloc(ctx, &ctx->d_f, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x2, ctx->nloc_total));
@@ -962,6 +1003,11 @@ feti_status factorize_all(feti_ctx* ctx) {
   if (ctx->opt.precision == FETI_MIXED) {
     feti::launch_to_f32(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32, st);
     if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_to_f32(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32, st);
+    if (ctx->d_F32s) {
+      feti::launch_to_f32_sym(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32s, st);
+      if (ctx->opt.precond == FETI_PREC_DIRICHLET)
+        feti::launch_to_f32_sym(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32s, st);
+    }
   }
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_status(ctx, "local factorization"));
@@ -1036,6 +1082,12 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
   const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
                       : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
   const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+  if (f32 && ctx->sym32[which] && !ctx->opt.per_subdomain) {
+    feti::launch_symv_f32(ctx->sym32[which], ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which],
+                          ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc,
+                          ctx->d_symp, ctx->maps, done, ctx->stream);
+    return;
+  }
   if (!ctx->opt.per_subdomain) {
     feti::launch_gemv_loc(cfg, ctx->d_lay, which, M, f32, v, ctx->d_loc, ctx->max_nb, done, ctx->stream);
     return;
@@ -1119,6 +1171,31 @@ feti_status autotune(feti_ctx* ctx) {
           if (ms < best) { best = ms; bestc = c; }
         }
       (f32 ? ctx->cfg32[w] : ctx->cfg64[w]) = bestc;
+      if (f32 && ctx->d_F32s) {
+        // symmetric lower block-triangle kernel, load groups of 8 / 16 / 32 rows
+        ctx->sym32[w] = 0;
+        const int Gs[3] = {8, 16, 32};
+        const float* Ms = w == 0 ? ctx->d_F32s : ctx->d_S32s;
+        float best_sym = 1e30f;
+        int gbest = 8;
+        for (int gi = 0; gi < 3; ++gi) {
+          feti::launch_symv_f32(Gs[gi], ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
+                                ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 3; ++rep)
+            feti::launch_symv_f32(Gs[gi], ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
+                                  ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e1, st));
+          FETI_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best_sym) {
+            best_sym = ms;
+            gbest = Gs[gi];
+          }
+        }
+        if (best_sym < best || ctx->opt.symmetric == 2) ctx->sym32[w] = gbest;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1184,6 +1261,11 @@ feti_status alloc_operators(feti_ctx* ctx) {
   if (ctx->opt.precision == FETI_MIXED) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_F32, (size_t)ctx->op_elems[3]));
     FETI_TRY(dev_alloc(ctx, &ctx->d_S32, (size_t)ctx->op_elems[4]));
+    if (ctx->opt.symmetric != 1) {
+      FETI_TRY(dev_alloc(ctx, &ctx->d_F32s, (size_t)ctx->op_elems[5]));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_S32s, (size_t)ctx->op_elems[6]));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_symp, (size_t)ctx->op_elems[7] + 4));
+    }
   }
   return FETI_OK;
 }
@@ -2288,17 +2370,19 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
     kern += t;
   }
   if (ms_per_apply) *ms_per_apply = ms / n_apply;
-  double entries = 0.0, vec = 0.0;
+  double entries = 0.0, half = 0.0, vec = 0.0;
   for (const auto& L : ctx->lay) {
     entries += (double)L.nbp * L.nbp;
+    half += 0.5 * (double)L.nbp * (L.nbp + 1);
     vec += (double)L.nbp;
   }
   ctx->gemv_ms = kern / n_apply;
-  // algorithmic bytes of one F_i-apply launch: every F_i entry once (8 B in
-  // FP64, 4 B in the FP32 copy), the gathered local input once (8 B) and the
-  // local output (8 B) per boundary DOF
+  // algorithmic bytes of one F_i apply: the n(n+1)/2 distinct entries of the
+  // symmetric F_i once (8 B in FP64, 4 B in the FP32 copy), the gathered
+  // local input (8 B) and the local output (8 B) per boundary DOF; flops: 2
+  // per entry of the full matrix
   const double esz = ctx->opt.precision == FETI_MIXED ? 4.0 : 8.0;
-  ctx->gemv_bytes = entries * esz + vec * 16.0;
+  ctx->gemv_bytes = half * esz + vec * 16.0;
   ctx->gemv_flops = 2.0 * entries;
   return FETI_OK;
 }
@@ -2318,8 +2402,8 @@ feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
   for (int w = 0; w < 2; ++w) {
     out[2 * w] = ctx->cfg64[w].R;
     out[2 * w + 1] = ctx->cfg64[w].rpc;
-    out[4 + 2 * w] = ctx->cfg32[w].R;
-    out[4 + 2 * w + 1] = ctx->cfg32[w].rpc;
+    out[4 + 2 * w] = ctx->sym32[w] ? -ctx->sym32[w] : ctx->cfg32[w].R;
+    out[4 + 2 * w + 1] = ctx->sym32[w] ? 32 : ctx->cfg32[w].rpc;
     if (ctx->tuned_m) {
       out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;  // 0 .. -4: tensor-core variants
       out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;

@@ -36,6 +36,12 @@ struct SubLayout {
   int64_t roff;   // offset of R_i (n x k, row-major) in dense local order
   int64_t foff32; // offset (floats) of the FP32 copy of F_i, row stride padded to 4
   int64_t soff32; // offset (floats) of the FP32 copy of the preconditioner block
+  // FP32 lower block-triangles of the symmetric F_i and preconditioner block:
+  // 32-row panels, panel I = rows 32I..32I+31 by columns 0..32(I+1)-1,
+  // row-major, at panel offset 512 I (I + 1); zero beyond the matrix
+  int64_t fsym32;
+  int64_t ssym32;
+  int64_t psym;   // offset (floats) of the transposed-product partials: 32 I floats per panel I
 };
 
 // Element kernels ------------------------------------------------------------
@@ -145,6 +151,15 @@ struct GemvCfg {
 // preconditioner block (which 1).
 void launch_gemv_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const void* M, int f32, const void* vloc,
                      double* y, int max_m, const int* done, cudaStream_t st);
+// Symmetric FP32 apply from the lower block-triangle: one warp per (subdomain,
+// panel) of the work list, row sums into y and, for the blocks left of the
+// diagonal block, the transposed products into the partial buffer; then
+// k_symv_fix adds the partials of the panels below each row in a fixed order.
+// G = rows per load group (8, 16 or 32).
+void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
+                     const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
+                     cudaStream_t st);
+void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // FP32 signed gather (input of the FP32 apply).
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);
 void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);

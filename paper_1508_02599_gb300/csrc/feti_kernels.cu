@@ -541,6 +541,110 @@ __global__ void k_gather32(Maps mp, const double* __restrict__ x, const double* 
   }
 }
 
+// Symmetric FP32 local apply y = M v from the lower block-triangle only (half
+// the bytes of the full rows).  A warp owns one 32-row panel I and sweeps its
+// stored columns in 128-column tiles (one float4 per lane per row): each
+// lane keeps a partial row sum for all 32 rows and, per tile, the column sums
+// a_rc v_r over the panel's rows, which are the transposed products of the
+// blocks left of the diagonal block (columns < 32 I); those go to the partial
+// buffer, the row sums (after one warp reduction per row) to y.
+template <int G>
+__global__ void __launch_bounds__(kThreads, G == 32 ? 1 : 2) k_symv_f32(const int32_t* __restrict__ wsub,
+                                                       const int32_t* __restrict__ wpanel, int n_warps,
+                                                       const SubLayout* __restrict__ lay, int which,
+                                                       const float* __restrict__ M, const float* __restrict__ vloc,
+                                                       double* __restrict__ y, float* __restrict__ part,
+                                                       const int* __restrict__ done) {
+  if (*done) return;
+  const int gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= n_warps) return;
+  const int s = wsub[gw], I = wpanel[gw];
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int w = 32 * (I + 1);
+  const int r0 = 32 * I;
+  const float* Pn = M + (which == 0 ? L.fsym32 : L.ssym32) + (size_t)512 * I * (I + 1);
+  const float* v = vloc + L.boff;
+  float* Pp = part + L.psym + (size_t)16 * I * (I - 1);
+  if (which == 0 && I == 0)
+    for (int p = lane; p < L.k; p += 32) y[L.boff + L.nbp + p] = 0.0;
+  const float vrow = r0 + lane < m ? v[r0 + lane] : 0.f;
+  float acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+  for (int c0 = 0; c0 < w; c0 += 128) {
+    const int c = c0 + 4 * lane;
+    const bool ok = c < w;
+    const float4 vv = make_float4(c < m ? v[c] : 0.f, c + 1 < m ? v[c + 1] : 0.f, c + 2 < m ? v[c + 2] : 0.f,
+                                  c + 3 < m ? v[c + 3] : 0.f);
+    float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int g = 0; g < 32 / G; ++g) {
+      float4 a[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        a[j] = ok ? __ldg(reinterpret_cast<const float4*>(Pn + (size_t)(g * G + j) * w + c))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const int i = g * G + j;
+        acc[i] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
+        const float vi = __shfl_sync(0xffffffffu, vrow, i);
+        col.x += a[j].x * vi;
+        col.y += a[j].y * vi;
+        col.z += a[j].z * vi;
+        col.w += a[j].w * vi;
+      }
+    }
+    if (ok && c < r0) *reinterpret_cast<float4*>(Pp + c) = col;
+  }
+  float mine = 0.f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float t = warp_sumf(acc[i]);
+    if (lane == i) mine = t;
+  }
+  if (r0 + lane < m) y[L.boff + r0 + lane] = (double)mine;
+}
+
+// y[c] += sum over the panels I below row c (I = c/32 + 1, ..) of their
+// transposed products at column c, in that order.
+__global__ void k_symv_fix(Maps mp, const SubLayout* __restrict__ lay, int which, const float* __restrict__ part,
+                           double* __restrict__ y, const int* __restrict__ done) {
+  if (*done) return;
+  for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < mp.nb_total; gp += gridDim.x * blockDim.x) {
+    const SubLayout L = lay[mp.bpos_sub[gp]];
+    const int m = which == 0 ? L.nbp : L.nbp + L.k;
+    const int c = gp - L.boff;
+    if (c >= m) continue;
+    const int nP = (m + 31) / 32;
+    const float* ps = part + L.psym;
+    double t = 0.0;
+    for (int I = c / 32 + 1; I < nP; ++I) t += (double)ps[(size_t)16 * I * (I - 1) + c];
+    y[gp] += t;
+  }
+}
+
+// FP64 -> FP32 lower block-triangle (32-row panels) of a symmetric local operator.
+__global__ void k_to_f32_sym(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
+                             float* __restrict__ dst) {
+  const int s = blockIdx.x;
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const double* a = src + (which == 0 ? L.foff : L.soff);
+  float* b = dst + (which == 0 ? L.fsym32 : L.ssym32);
+  const int nP = (m + 31) / 32;
+  for (int I = 0; I < nP; ++I) {
+    const int w = 32 * (I + 1);
+    float* bp = b + (size_t)512 * I * (I + 1);
+    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
+      const int r = 32 * I + idx / w, c = idx % w;
+      bp[idx] = (r < m && c < m) ? (float)a[(size_t)r * m + c] : 0.0f;
+    }
+  }
+}
+
 // FP64 -> FP32 copy of the dense local operators (row stride padded to 4).
 __global__ void k_to_f32(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
                          float* __restrict__ dst) {
@@ -1068,6 +1172,23 @@ void launch_gemv_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
       default: launch_gemv_t<double, 8>(cfg.n_blocks, cfg.blk_sub, cfg.blk_row0, cfg.rpc, lay, which, Md, vd, y, max_m, done, st); break;
     }
   }
+}
+
+void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
+                     const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
+                     cudaStream_t st) {
+  const int blocks = (n_warps + kThreads / 32 - 1) / (kThreads / 32);
+  if (G == 8)
+    k_symv_f32<8><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  else if (G == 16)
+    k_symv_f32<16><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  else
+    k_symv_f32<32><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
+}
+
+void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st) {
+  k_to_f32_sym<<<P, kThreads, 0, st>>>(lay, which, src, dst);
 }
 
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st) {

@@ -275,3 +275,39 @@ def test_per_subdomain_launches_bit_identical(precision):
     o = feti.FetiOracle(prob, "af", "dirichlet")
     U_ref, _, _ = o.solve(tol=1e-12, maxit=3000)
     assert np.linalg.norm(Up - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
+
+
+@pytest.mark.parametrize("prob", [TUBE_FLOAT, mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)],
+                         ids=["tube", "jittered"])
+def test_symmetric_fp32_apply_matches_full(prob):
+    """The FP32 local applies from the lower block-triangle only (32-row
+    panels, transposed products of the blocks left of the diagonal added back
+    in a fixed order) against the full-row FP32 kernel on the same FP32
+    copies: one dual apply agrees to 1e-5 of its largest entry (FP32 sums of
+    about a thousand terms in another order, the bound the FP32-vs-FP64 apply
+    test uses); a mixed-precision solve on the symmetric kernel matches the
+    oracle to 1e-8."""
+    from paper_1508_02599_gb300 import FetiSolver
+    out = {}
+    for sym in ("off", "force"):
+        with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", symmetric=sym) as s:
+            s.prepare()
+            nl = s.sizes()["n_lambda"]
+            v = torch.tensor(np.random.default_rng(3).normal(size=nl), device="cuda", dtype=torch.float64)
+            q = torch.empty_like(v)
+            z = torch.empty_like(v)
+            s.dual_apply(v, q, z, 2)
+            torch.cuda.synchronize()
+            out[sym] = (q.cpu().numpy(), z.cpu().numpy(), s.schedule())
+    assert out["force"][2]["fp32_F"][0] < 0 and out["force"][2]["fp32_F"][1] == 32
+    assert out["off"][2]["fp32_F"][0] > 0
+    for i in range(2):
+        a, b = out["force"][i], out["off"][i]
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+    o = feti.FetiOracle(prob, "af", "dirichlet")
+    U_ref, _, _ = o.solve(tol=1e-12, maxit=3000)
+    with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-11, maxit=3000, precision="mixed",
+                    symmetric="force") as s:
+        U, rep = s.solve()
+    assert rep["converged"] == 1
+    assert np.linalg.norm(U - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
