@@ -159,6 +159,9 @@ def main():
                     help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures; "
                          "jcyl32: jittered tube, 1024 uneven subdomains; jcyl48: jittered tube, 4096 uneven "
                          "subdomains (about 180 GB of device memory)")
+    ap.add_argument("--symmetric", default="auto", choices=["auto", "off", "force"],
+                    help="FP32 local applies: autotuner choice, full rows, or the symmetric panel kernel (pin it "
+                         "for profiler runs, where serialised launches change the autotuner's timings)")
     ap.add_argument("--plain", type=int, default=1,
                     help="also time the plain FP64 form with one local-apply launch per subdomain (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -222,7 +225,8 @@ def main():
         n_apply = n_apply or args.n_apply
         steps = steps or args.steps
         solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
-                            stream=stream.cuda_stream, precision=precision, batched=batched)
+                            stream=stream.cuda_stream, precision=precision, batched=batched,
+                            symmetric=args.symmetric)
         if args.apply_only:
             solver.prepare()
             U, rep = np.zeros(3 * prob.n_nodes), {"t_pcg_ms": None, "iterations": 0, "outer_iterations": 0,

@@ -498,10 +498,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
     ctx->lay[s] = L;
     const int nb = nbp + k;
     {
-      const int64_t pf = (nbp + 31) / 32, ps = (nb + 31) / 32;
-      fsym += 512 * pf * (pf + 1);
-      ssym += 512 * ps * (ps + 1);
-      psym += 16 * ps * (ps - 1);  // sized for the larger (preconditioner) block
+      constexpr int64_t PH = feti::kSymPH;
+      const int64_t pf = (nbp + PH - 1) / PH, ps = (nb + PH - 1) / PH;
+      fsym += PH * PH / 2 * pf * (pf + 1);
+      ssym += PH * PH / 2 * ps * (ps + 1);
+      psym += PH / 2 * ps * (ps - 1);  // sized for the larger (preconditioner) block
     }
     boff += nb;
     voff += n;
@@ -855,7 +856,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   ctx->op_elems[6] = ctx->opt.precond == FETI_PREC_DIRICHLET ? ssym : 1;
   ctx->op_elems[7] = psym;
   for (int w = 0; w < 2; ++w) {
-    // symmetric-apply work lists: one warp per (subdomain, 32-row panel).
+    // symmetric-apply work lists: one warp per (subdomain, kSymPH-row panel).
     // Panel I carries I + 1 blocks, so the list runs from the longest panels
     // to the shortest and the eight warps of a CTA take the same panel index
     // of eight subdomains: balanced CTAs, longest work first.
@@ -863,12 +864,12 @@ feti_status build_decomposition(feti_ctx* ctx) {
     int max_np = 0;
     for (int q = 0; q < P; ++q) {
       const int m = w == 0 ? ctx->lay[q].nbp : ctx->lay[q].nbp + ctx->lay[q].k;
-      max_np = std::max(max_np, (m + 31) / 32);
+      max_np = std::max(max_np, (m + feti::kSymPH - 1) / feti::kSymPH);
     }
     for (int I = max_np - 1; I >= 0; --I)
       for (int q = 0; q < P; ++q) {
         const int m = w == 0 ? ctx->lay[q].nbp : ctx->lay[q].nbp + ctx->lay[q].k;
-        if (I < (m + 31) / 32) {
+        if (I < (m + feti::kSymPH - 1) / feti::kSymPH) {
           ws.push_back(q);
           wp.push_back(I);
         }
@@ -1172,9 +1173,9 @@ feti_status autotune(feti_ctx* ctx) {
         }
       (f32 ? ctx->cfg32[w] : ctx->cfg64[w]) = bestc;
       if (f32 && ctx->d_F32s) {
-        // symmetric lower block-triangle kernel, load groups of 8 / 16 / 32 rows
+        // symmetric lower block-triangle kernel, load groups of 8 / 16 / kSymPH rows
         ctx->sym32[w] = 0;
-        const int Gs[3] = {8, 16, 32};
+        const int Gs[3] = {8, 16, feti::kSymPH};
         const float* Ms = w == 0 ? ctx->d_F32s : ctx->d_S32s;
         float best_sym = 1e30f;
         int gbest = 8;
@@ -2403,7 +2404,7 @@ feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]) {
     out[2 * w] = ctx->cfg64[w].R;
     out[2 * w + 1] = ctx->cfg64[w].rpc;
     out[4 + 2 * w] = ctx->sym32[w] ? -ctx->sym32[w] : ctx->cfg32[w].R;
-    out[4 + 2 * w + 1] = ctx->sym32[w] ? 32 : ctx->cfg32[w].rpc;
+    out[4 + 2 * w + 1] = ctx->sym32[w] ? feti::kSymPH : ctx->cfg32[w].rpc;
     if (ctx->tuned_m) {
       out[8 + 2 * w] = ctx->tc_m[w] ? 1 - ctx->tc_m[w] : ctx->cfgm32[w].R;  // 0 .. -4: tensor-core variants
       out[8 + 2 * w + 1] = ctx->tc_m[w] ? 128 : ctx->cfgm32[w].rpc;

@@ -37,12 +37,14 @@ struct SubLayout {
   int64_t foff32; // offset (floats) of the FP32 copy of F_i, row stride padded to 4
   int64_t soff32; // offset (floats) of the FP32 copy of the preconditioner block
   // FP32 lower block-triangles of the symmetric F_i and preconditioner block:
-  // 32-row panels, panel I = rows 32I..32I+31 by columns 0..32(I+1)-1,
-  // row-major, at panel offset 512 I (I + 1); zero beyond the matrix
+  // panels of kSymPH rows, panel I = rows PH I .. PH I + PH - 1 by columns
+  // 0 .. PH (I + 1) - 1, row-major, at panel offset PH^2 I (I + 1) / 2; zero
+  // beyond the matrix
   int64_t fsym32;
   int64_t ssym32;
-  int64_t psym;   // offset (floats) of the transposed-product partials: 32 I floats per panel I
+  int64_t psym;   // offset (floats) of the transposed-product partials: PH I floats per panel I
 };
+constexpr int kSymPH = 32;  // panel height of the symmetric FP32 apply
 
 // Element kernels ------------------------------------------------------------
 void launch_elem_linear(int n_tets, const double* coords, const int32_t* tets, double E, double nu,

@@ -542,19 +542,18 @@ __global__ void k_gather32(Maps mp, const double* __restrict__ x, const double* 
 }
 
 // Symmetric FP32 local apply y = M v from the lower block-triangle only (half
-// the bytes of the full rows).  A warp owns one 32-row panel I and sweeps its
-// stored columns in 128-column tiles (one float4 per lane per row): each
-// lane keeps a partial row sum for all 32 rows and, per tile, the column sums
-// a_rc v_r over the panel's rows, which are the transposed products of the
-// blocks left of the diagonal block (columns < 32 I); those go to the partial
-// buffer, the row sums (after one warp reduction per row) to y.
+// the bytes of the full rows).  A warp owns one panel I of PH = kSymPH rows
+// and sweeps its stored columns in 128-column tiles (one float4 per lane per
+// row): each lane keeps a partial row sum for the PH rows and, per tile, the
+// column sums a_rc v_r over the panel's rows, which are the transposed
+// products of the blocks left of the diagonal block (columns < PH I); those
+// go to the partial buffer, the row sums (one warp reduction per row) to y.
 template <int G>
-__global__ void __launch_bounds__(kThreads, G == 32 ? 1 : 2) k_symv_f32(const int32_t* __restrict__ wsub,
-                                                       const int32_t* __restrict__ wpanel, int n_warps,
-                                                       const SubLayout* __restrict__ lay, int which,
-                                                       const float* __restrict__ M, const float* __restrict__ vloc,
-                                                       double* __restrict__ y, float* __restrict__ part,
-                                                       const int* __restrict__ done) {
+__global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
+    const int32_t* __restrict__ wsub, const int32_t* __restrict__ wpanel, int n_warps,
+    const SubLayout* __restrict__ lay, int which, const float* __restrict__ M, const float* __restrict__ vloc,
+    double* __restrict__ y, float* __restrict__ part, const int* __restrict__ done) {
+  constexpr int PH = kSymPH;
   if (*done) return;
   const int gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -562,17 +561,17 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 1 : 2) k_symv_f32(const in
   const int s = wsub[gw], I = wpanel[gw];
   const SubLayout L = lay[s];
   const int m = which == 0 ? L.nbp : L.nbp + L.k;
-  const int w = 32 * (I + 1);
-  const int r0 = 32 * I;
-  const float* Pn = M + (which == 0 ? L.fsym32 : L.ssym32) + (size_t)512 * I * (I + 1);
+  const int w = PH * (I + 1);
+  const int r0 = PH * I;
+  const float* Pn = M + (which == 0 ? L.fsym32 : L.ssym32) + (size_t)(PH * PH / 2) * I * (I + 1);
   const float* v = vloc + L.boff;
-  float* Pp = part + L.psym + (size_t)16 * I * (I - 1);
+  float* Pp = part + L.psym + (size_t)(PH / 2) * I * (I - 1);
   if (which == 0 && I == 0)
     for (int p = lane; p < L.k; p += 32) y[L.boff + L.nbp + p] = 0.0;
-  const float vrow = r0 + lane < m ? v[r0 + lane] : 0.f;
-  float acc[32];
+  const float vrow = (lane < PH && r0 + lane < m) ? v[r0 + lane] : 0.f;
+  float acc[PH];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+  for (int i = 0; i < PH; ++i) acc[i] = 0.f;
   for (int c0 = 0; c0 < w; c0 += 128) {
     const int c = c0 + 4 * lane;
     const bool ok = c < w;
@@ -580,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 1 : 2) k_symv_f32(const in
                                   c + 3 < m ? v[c + 3] : 0.f);
     float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int g = 0; g < 32 / G; ++g) {
+    for (int g = 0; g < PH / G; ++g) {
       float4 a[G];
 #pragma unroll
       for (int j = 0; j < G; ++j)
@@ -601,32 +600,43 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 1 : 2) k_symv_f32(const in
   }
   float mine = 0.f;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < PH; ++i) {
     const float t = warp_sumf(acc[i]);
     if (lane == i) mine = t;
   }
-  if (r0 + lane < m) y[L.boff + r0 + lane] = (double)mine;
+  if (lane < PH && r0 + lane < m) y[L.boff + r0 + lane] = (double)mine;
 }
 
-// y[c] += sum over the panels I below row c (I = c/32 + 1, ..) of their
-// transposed products at column c, in that order.
+// y[c] += sum over the panels I below row c (I = c/PH + 1, ..) of their
+// transposed products at column c, in that order; loads issued in groups of
+// eight independent ones (the sum stays in panel order).
 __global__ void k_symv_fix(Maps mp, const SubLayout* __restrict__ lay, int which, const float* __restrict__ part,
                            double* __restrict__ y, const int* __restrict__ done) {
+  constexpr int PH = kSymPH;
   if (*done) return;
   for (int gp = blockIdx.x * blockDim.x + threadIdx.x; gp < mp.nb_total; gp += gridDim.x * blockDim.x) {
     const SubLayout L = lay[mp.bpos_sub[gp]];
     const int m = which == 0 ? L.nbp : L.nbp + L.k;
     const int c = gp - L.boff;
     if (c >= m) continue;
-    const int nP = (m + 31) / 32;
+    const int nP = (m + PH - 1) / PH;
     const float* ps = part + L.psym;
     double t = 0.0;
-    for (int I = c / 32 + 1; I < nP; ++I) t += (double)ps[(size_t)16 * I * (I - 1) + c];
+    for (int I0 = c / PH + 1; I0 < nP; I0 += 8) {
+      float f[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int I = I0 + u;
+        f[u] = I < nP ? ps[(size_t)(PH / 2) * I * (I - 1) + c] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += (double)f[u];
+    }
     y[gp] += t;
   }
 }
 
-// FP64 -> FP32 lower block-triangle (32-row panels) of a symmetric local operator.
+// FP64 -> FP32 lower block-triangle (panels of kSymPH rows) of a symmetric local operator.
 __global__ void k_to_f32_sym(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
                              float* __restrict__ dst) {
   const int s = blockIdx.x;
@@ -634,12 +644,13 @@ __global__ void k_to_f32_sym(const SubLayout* __restrict__ lay, int which, const
   const int m = which == 0 ? L.nbp : L.nbp + L.k;
   const double* a = src + (which == 0 ? L.foff : L.soff);
   float* b = dst + (which == 0 ? L.fsym32 : L.ssym32);
-  const int nP = (m + 31) / 32;
+  constexpr int PH = kSymPH;
+  const int nP = (m + PH - 1) / PH;
   for (int I = 0; I < nP; ++I) {
-    const int w = 32 * (I + 1);
-    float* bp = b + (size_t)512 * I * (I + 1);
-    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
-      const int r = 32 * I + idx / w, c = idx % w;
+    const int w = PH * (I + 1);
+    float* bp = b + (size_t)(PH * PH / 2) * I * (I + 1);
+    for (int idx = threadIdx.x; idx < PH * w; idx += blockDim.x) {
+      const int r = PH * I + idx / w, c = idx % w;
       bp[idx] = (r < m && c < m) ? (float)a[(size_t)r * m + c] : 0.0f;
     }
   }
@@ -1178,12 +1189,12 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
                      cudaStream_t st) {
   const int blocks = (n_warps + kThreads / 32 - 1) / (kThreads / 32);
-  if (G == 8)
-    k_symv_f32<8><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
-  else if (G == 16)
+  if (G == 16)
     k_symv_f32<16><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  else if (G == 8)
+    k_symv_f32<8><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
   else
-    k_symv_f32<32><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+    k_symv_f32<kSymPH><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 

@@ -299,7 +299,7 @@ def test_symmetric_fp32_apply_matches_full(prob):
             s.dual_apply(v, q, z, 2)
             torch.cuda.synchronize()
             out[sym] = (q.cpu().numpy(), z.cpu().numpy(), s.schedule())
-    assert out["force"][2]["fp32_F"][0] < 0 and out["force"][2]["fp32_F"][1] == 32
+    assert out["force"][2]["fp32_F"][0] < 0 and out["force"][2]["fp32_F"][1] == 32  # (-G, panel height)
     assert out["off"][2]["fp32_F"][0] > 0
     for i in range(2):
         a, b = out["force"][i], out["off"][i]
