@@ -159,7 +159,7 @@ def main():
                     help="cyl16: the 64-subdomain tube; cyl8: a 32-subdomain tube for profiler captures; "
                          "jcyl32: jittered tube, 1024 uneven subdomains; jcyl48: jittered tube, 4096 uneven "
                          "subdomains (about 180 GB of device memory)")
-    ap.add_argument("--symmetric", default="auto", choices=["auto", "off", "force"],
+    ap.add_argument("--symmetric", default="auto", choices=["auto", "off", "force", "force_streamed"],
                     help="FP32 local applies: autotuner choice, full rows, or the symmetric panel kernel (pin it "
                          "for profiler runs, where serialised launches change the autotuner's timings)")
     ap.add_argument("--plain", type=int, default=1,
@@ -400,7 +400,9 @@ def main():
                 "note": "plain form: FP64, one local-apply launch per subdomain instead of one batched launch; "
                         "same kernels, graphs and schedule"},
             "roofline": {"bound": "hbm",
-                         "kernel": ("k_symv_f32 + k_symv_fix (F_i apply, FP32 lower block-triangle)"
+                         "kernel": ("k_symv2_f32 + k_symv_fix (F_i apply, FP32 lower block-triangle, streamed)"
+                                    if m32["sched"]["fp32_F"][0] == -64 else
+                                    "k_symv_f32 + k_symv_fix (F_i apply, FP32 lower block-triangle)"
                                     if m32["sched"]["fp32_F"][0] < 0 else "k_gemv_loc<float> (F_i apply, FP32 copy)"),
                          "achieved": gbs32,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],

@@ -72,7 +72,7 @@ class FetiSolver:
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
-                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2}[symmetric])
+                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3}[symmetric])
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

@@ -140,7 +140,8 @@ struct feti_ctx {
   float *d_F32s = nullptr, *d_S32s = nullptr, *d_symp = nullptr;
   int32_t *d_sym_sub[2] = {nullptr, nullptr}, *d_sym_panel[2] = {nullptr, nullptr};
   int sym_n[2] = {0, 0};
-  int sym32[2] = {0, 0};
+  int sym32[2] = {0, 0};  // 8 / 16 / 32: register-staged load groups; 64: streamed through shared memory
+  int* d_sym_err = nullptr;  // set by a streamed symmetric apply whose bounded wait ran out
   cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
   int m_cap = 0;  // allocated nrhs capacity of the block buffers
@@ -1083,6 +1084,12 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
   const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
                       : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
   const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+  if (f32 && ctx->sym32[which] == 64 && !ctx->opt.per_subdomain) {
+    feti::launch_symv2_f32(ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which], ctx->d_lay, which,
+                           which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps,
+                           done, ctx->d_sym_err, ctx->stream);
+    return;
+  }
   if (f32 && ctx->sym32[which] && !ctx->opt.per_subdomain) {
     feti::launch_symv_f32(ctx->sym32[which], ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which],
                           ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc,
@@ -1195,7 +1202,29 @@ feti_status autotune(feti_ctx* ctx) {
             gbest = Gs[gi];
           }
         }
-        if (best_sym < best || ctx->opt.symmetric == 2) ctx->sym32[w] = gbest;
+        {  // streamed variant (shared-memory ring), kept only if no bounded wait ran out
+          FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
+          feti::launch_symv2_f32(ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
+                                 ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, ctx->d_sym_err, st);
+          FETI_CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 3; ++rep)
+            feti::launch_symv2_f32(ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
+                                   ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, ctx->d_sym_err,
+                                   st);
+          FETI_CK(cudaEventRecord(e1, st));
+          FETI_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+          int herr = 0;
+          FETI_CK(cudaMemcpy(&herr, ctx->d_sym_err, sizeof(int), cudaMemcpyDeviceToHost));
+          if (herr == 0 && ms < best_sym && ctx->opt.symmetric != 3) {
+            best_sym = ms;
+            gbest = 64;
+          }
+          FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
+        }
+        if (ctx->opt.symmetric == 3) gbest = 64;
+        if (best_sym < best || ctx->opt.symmetric >= 2) ctx->sym32[w] = gbest;
       }
     }
   }
@@ -1266,6 +1295,8 @@ feti_status alloc_operators(feti_ctx* ctx) {
       FETI_TRY(dev_alloc(ctx, &ctx->d_F32s, (size_t)ctx->op_elems[5]));
       FETI_TRY(dev_alloc(ctx, &ctx->d_S32s, (size_t)ctx->op_elems[6]));
       FETI_TRY(dev_alloc(ctx, &ctx->d_symp, (size_t)ctx->op_elems[7] + 4));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_sym_err, 1));
+      FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), ctx->stream));
     }
   }
   return FETI_OK;
@@ -1428,6 +1459,15 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_x2, ctx->d_x, st);
   if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
   FETI_CK(cudaGetLastError());
+  if (ctx->d_sym_err && (ctx->sym32[0] == 64 || ctx->sym32[1] == 64)) {
+    int herr = 0;
+    FETI_CK(cudaMemcpyAsync(&herr, ctx->d_sym_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FETI_CK(cudaStreamSynchronize(st));
+    if (herr) {
+      FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
+      return fail(ctx, FETI_ERR_TIMEOUT, "streamed symmetric local apply: a bounded wait ran out");
+    }
+  }
   if (!conv) return fail(ctx, FETI_ERR_NOT_CONVERGED, "PCG reached maxit");
   return FETI_OK;
 }

@@ -161,6 +161,11 @@ void launch_gemv_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
                      cudaStream_t st);
+// The same product with each warp streaming its panel through shared memory
+// (cp.async.bulk row segments, bounded waits; a timeout sets *err).
+void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
+                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
+                      int* err, cudaStream_t st);
 void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // FP32 signed gather (input of the FP32 apply).
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);

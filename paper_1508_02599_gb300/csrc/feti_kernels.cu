@@ -607,6 +607,146 @@ __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
   if (lane < PH && r0 + lane < m) y[L.boff + r0 + lane] = (double)mine;
 }
 
+// Streamed variant of the symmetric FP32 apply: the same panels, partials
+// and fix kernel, but each warp streams its panel through a ring of SYM_NS
+// shared-memory stages of 32 rows x 64 columns (8 KB): every lane copies one
+// 256-byte row segment with cp.async.bulk (completion counted in bytes on the
+// stage's mbarrier), so the next tiles are in flight while the current one is
+// reduced, and the arithmetic reads shared memory instead of holding the
+// loads in registers (16 row accumulators per lane: half-warp h takes rows
+// 2j + h).  Warps are independent (no CTA barrier in the loop); all waits are
+// bounded, and a warp whose wait runs out flags *err, issues nothing more and
+// waits (bounded) for its copies in flight before it returns.
+constexpr int SYM_TW = 64;  // tile width (floats)
+constexpr int SYM_NS = 3;   // stages per warp
+constexpr int SYM_WPC = 4;  // warps per CTA
+constexpr int SYM_STAGE = 32 * SYM_TW * 4;  // bytes
+
+__device__ __forceinline__ uint32_t sym_su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool sym_try(uint64_t* b, uint32_t par) {
+  uint32_t ok;
+  asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+               : "=r"(ok)
+               : "r"(sym_su32(b)), "r"(par)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool sym_wait(uint64_t* b, uint32_t par) {
+  const long long t0 = clock64();
+  while (!sym_try(b, par))
+    if (clock64() - t0 > 200000000LL) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __restrict__ wsub,
+                                                           const int32_t* __restrict__ wpanel, int n_warps,
+                                                           const SubLayout* __restrict__ lay, int which,
+                                                           const float* __restrict__ M, const float* __restrict__ vloc,
+                                                           double* __restrict__ y, float* __restrict__ part,
+                                                           const int* __restrict__ done, int* __restrict__ err) {
+  if (*done) return;
+  extern __shared__ __align__(128) unsigned char sym_smem[];
+  __shared__ uint64_t full[SYM_WPC][SYM_NS];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l16 = lane & 15;
+  const int gw = blockIdx.x * SYM_WPC + wl;
+  if (gw >= n_warps) return;
+  const int s = wsub[gw], I = wpanel[gw];
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int w = 32 * (I + 1);
+  const int r0 = 32 * I;
+  const float* Pn = M + (which == 0 ? L.fsym32 : L.ssym32) + (size_t)512 * I * (I + 1);
+  const float* v = vloc + L.boff;
+  float* Pp = part + L.psym + (size_t)16 * I * (I - 1);
+  unsigned char* ring = sym_smem + (size_t)wl * SYM_NS * SYM_STAGE;
+  uint64_t* fb = full[wl];
+  if (lane == 0) {
+    for (int q = 0; q < SYM_NS; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sym_su32(&fb[q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (which == 0 && I == 0)
+    for (int p = lane; p < L.k; p += 32) y[L.boff + L.nbp + p] = 0.0;
+  const int nt = (w + SYM_TW - 1) / SYM_TW;
+  // tile t -> stage t % NS: lane i copies row i's segment of the tile
+  auto issue = [&](int t) {
+    const int st = t % SYM_NS;
+    const int c0 = t * SYM_TW;
+    const uint32_t seg = (uint32_t)min(SYM_TW, w - c0) * 4u;
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sym_su32(&fb[st])), "r"(seg * 32u)
+                   : "memory");
+    __syncwarp();
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sym_su32(ring + st * SYM_STAGE + lane * SYM_TW * 4)),
+                 "l"(Pn + (size_t)lane * w + c0), "r"(seg), "r"(sym_su32(&fb[st]))
+                 : "memory");
+  };
+  int issued = 0;
+  for (; issued < SYM_NS && issued < nt; ++issued) issue(issued);
+  const float vrow = r0 + lane < m ? v[r0 + lane] : 0.f;
+  float acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+  bool bad = false;
+  int t = 0;
+  for (; t < nt; ++t) {
+    const int st = t % SYM_NS;
+    if (!sym_wait(&fb[st], (uint32_t)(t / SYM_NS) & 1u)) bad = true;
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad) break;
+    const int c = t * SYM_TW + 4 * l16;
+    const bool ok = c < w;
+    const float4 vv = make_float4(c < m ? v[c] : 0.f, c + 1 < m ? v[c + 1] : 0.f, c + 2 < m ? v[c + 2] : 0.f,
+                                  c + 3 < m ? v[c + 3] : 0.f);
+    const float4* tile = reinterpret_cast<const float4*>(ring + st * SYM_STAGE);
+    float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int r = 2 * j + h;
+      const float4 a = ok ? tile[r * (SYM_TW / 4) + l16] : make_float4(0.f, 0.f, 0.f, 0.f);
+      acc[j] += a.x * vv.x + a.y * vv.y + a.z * vv.z + a.w * vv.w;
+      const float vi = __shfl_sync(0xffffffffu, vrow, r);
+      col.x += a.x * vi;
+      col.y += a.y * vi;
+      col.z += a.z * vi;
+      col.w += a.w * vi;
+    }
+    col.x += __shfl_xor_sync(0xffffffffu, col.x, 16);
+    col.y += __shfl_xor_sync(0xffffffffu, col.y, 16);
+    col.z += __shfl_xor_sync(0xffffffffu, col.z, 16);
+    col.w += __shfl_xor_sync(0xffffffffu, col.w, 16);
+    if (h == 0 && ok && c < r0) *reinterpret_cast<float4*>(Pp + c) = col;
+    // every lane has read the stage: order those reads before the refill
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (t + SYM_NS < nt) {
+      issue(t + SYM_NS);
+      issued = t + SYM_NS + 1;
+    }
+  }
+  if (bad) {
+    // copies in flight land before the warp leaves (fresh bounded waits)
+    for (int j = t; j < issued; ++j) sym_wait(&fb[j % SYM_NS], (uint32_t)(j / SYM_NS) & 1u);
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
+  // row 2j + h: reduce over the 16 lanes of half h
+  float mine = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    float x = acc[j];
+    x += __shfl_xor_sync(0xffffffffu, x, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    if (l16 == j) mine = x;  // lane 16 h + j holds row 2j + h
+  }
+  const int row = r0 + 2 * l16 + h;
+  if (row < m) y[L.boff + row] = (double)mine;
+}
+
 // y[c] += sum over the panels I below row c (I = c/PH + 1, ..) of their
 // transposed products at column c, in that order; loads issued in groups of
 // eight independent ones (the sum stays in panel order).
@@ -1195,6 +1335,20 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
     k_symv_f32<8><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
   else
     k_symv_f32<kSymPH><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
+}
+
+void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
+                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
+                      int* err, cudaStream_t st) {
+  const size_t smem = (size_t)SYM_WPC * SYM_NS * SYM_STAGE;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_symv2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int blocks = (n_warps + SYM_WPC - 1) / SYM_WPC;
+  k_symv2_f32<<<blocks, SYM_WPC * 32, smem, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done, err);
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 

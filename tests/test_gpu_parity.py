@@ -279,7 +279,8 @@ def test_per_subdomain_launches_bit_identical(precision):
 
 @pytest.mark.parametrize("prob", [TUBE_FLOAT, mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)],
                          ids=["tube", "jittered"])
-def test_symmetric_fp32_apply_matches_full(prob):
+@pytest.mark.parametrize("variant", ["force", "force_streamed"])
+def test_symmetric_fp32_apply_matches_full(prob, variant):
     """The FP32 local applies from the lower block-triangle only (32-row
     panels, transposed products of the blocks left of the diagonal added back
     in a fixed order) against the full-row FP32 kernel on the same FP32
@@ -289,7 +290,7 @@ def test_symmetric_fp32_apply_matches_full(prob):
     oracle to 1e-8."""
     from paper_1508_02599_gb300 import FetiSolver
     out = {}
-    for sym in ("off", "force"):
+    for sym in ("off", variant):
         with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", symmetric=sym) as s:
             s.prepare()
             nl = s.sizes()["n_lambda"]
@@ -299,15 +300,17 @@ def test_symmetric_fp32_apply_matches_full(prob):
             s.dual_apply(v, q, z, 2)
             torch.cuda.synchronize()
             out[sym] = (q.cpu().numpy(), z.cpu().numpy(), s.schedule())
-    assert out["force"][2]["fp32_F"][0] < 0 and out["force"][2]["fp32_F"][1] == 32  # (-G, panel height)
+    assert out[variant][2]["fp32_F"][0] < 0 and out[variant][2]["fp32_F"][1] == 32  # (-G, panel height)
+    if variant == "force_streamed":
+        assert out[variant][2]["fp32_F"][0] == -64
     assert out["off"][2]["fp32_F"][0] > 0
     for i in range(2):
-        a, b = out["force"][i], out["off"][i]
+        a, b = out[variant][i], out["off"][i]
         assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
     o = feti.FetiOracle(prob, "af", "dirichlet")
     U_ref, _, _ = o.solve(tol=1e-12, maxit=3000)
     with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-11, maxit=3000, precision="mixed",
-                    symmetric="force") as s:
+                    symmetric=variant) as s:
         U, rep = s.solve()
     assert rep["converged"] == 1
     assert np.linalg.norm(U - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
