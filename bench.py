@@ -414,7 +414,10 @@ def main():
                          "fp64_F": m64["sched"]["fp64_F"], "fp64_M": m64["sched"]["fp64_M"],
                          "meaning": "[rows per warp step, rows per CTA] picked by the setup-time autotuner"},
             "e2e": e2e,
-            "gpu_launches": args.steps * args.n_apply * 6,
+            # per dual apply: gather, local apply, scatter for F and for M; a symmetric
+            # local apply is two launches (panel kernel, fixed-order partial sum)
+            "gpu_launches": args.steps * args.n_apply * (6 + sum(1 for k in ("fp32_F", "fp32_M")
+                                                                 if m32["sched"][k][0] < 0)),
         }
         if b32 is not None:
             blk = {}
