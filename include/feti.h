@@ -269,8 +269,9 @@ feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* ele
  * autotuner (timed on the real operators, fastest kept): out[0..1] rows per
  * warp step and rows per CTA of the FP64 F_i apply, out[2..3] of the FP64
  * preconditioner apply, out[4..7] the same for the FP32 copies (rows per warp
- * step -G, rows 32 = symmetric kernel on 32-row panels, load groups of G rows;
- * G = 64: panels streamed through shared memory), out[8..11]
+ * step -G, rows 32 = symmetric kernel on 32-row panels, load groups of
+ * G % 100 rows with an L2 prefetch G / 100 tiles ahead; G = 64: panels
+ * streamed through shared memory), out[8..11]
  * the FP32 block-form GEMMs (rows per warp step 0 / -1 / -2 / -3 / -4 =
  * tensor-core kernel with register-staged / bulk-copy staged / tensor-map fed
  * operands / warp-specialised 3-stage / 2-stage; both entries -1 = block form

@@ -140,7 +140,9 @@ struct feti_ctx {
   float *d_F32s = nullptr, *d_S32s = nullptr, *d_symp = nullptr;
   int32_t *d_sym_sub[2] = {nullptr, nullptr}, *d_sym_panel[2] = {nullptr, nullptr};
   int sym_n[2] = {0, 0};
-  int sym32[2] = {0, 0};  // 8 / 16 / 32: register-staged load groups; 64: streamed through shared memory
+  // 8 / 16 / 32: register-staged load groups (+ 100 x L2-prefetch distance in
+  // tiles); 64: streamed through shared memory
+  int sym32[2] = {0, 0};
   int* d_sym_err = nullptr;  // set by a streamed symmetric apply whose bounded wait ran out
   cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
@@ -1180,13 +1182,14 @@ feti_status autotune(feti_ctx* ctx) {
         }
       (f32 ? ctx->cfg32[w] : ctx->cfg64[w]) = bestc;
       if (f32 && ctx->d_F32s) {
-        // symmetric lower block-triangle kernel, load groups of 8 / 16 / kSymPH rows
+        // symmetric lower block-triangle kernel: load groups of 8 / 16 / 32 rows,
+        // + 100 x (tiles of L2 prefetch ahead)
         ctx->sym32[w] = 0;
-        const int Gs[3] = {8, 16, feti::kSymPH};
+        const int Gs[6] = {8, 16, 32, 108, 132, 232};
         const float* Ms = w == 0 ? ctx->d_F32s : ctx->d_S32s;
         float best_sym = 1e30f;
         int gbest = 8;
-        for (int gi = 0; gi < 3; ++gi) {
+        for (int gi = 0; gi < 6; ++gi) {
           feti::launch_symv_f32(Gs[gi], ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
                                 ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, st);
           FETI_CK(cudaEventRecord(e0, st));

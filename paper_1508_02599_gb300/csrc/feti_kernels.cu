@@ -548,7 +548,7 @@ __global__ void k_gather32(Maps mp, const double* __restrict__ x, const double* 
 // column sums a_rc v_r over the panel's rows, which are the transposed
 // products of the blocks left of the diagonal block (columns < PH I); those
 // go to the partial buffer, the row sums (one warp reduction per row) to y.
-template <int G>
+template <int G, int PF>
 __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
     const int32_t* __restrict__ wsub, const int32_t* __restrict__ wpanel, int n_warps,
     const SubLayout* __restrict__ lay, int which, const float* __restrict__ M, const float* __restrict__ vloc,
@@ -572,7 +572,22 @@ __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
   float acc[PH];
 #pragma unroll
   for (int i = 0; i < PH; ++i) acc[i] = 0.f;
+  if (PF > 0)  // the first PF tiles of row `lane` towards L2
+    for (int q = 0; q < PF && q * 128 < w; ++q)
+      if (lane < PH) {
+        const int cq = q * 128;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Pn + (size_t)lane * w + cq),
+                     "r"((uint32_t)min(128, w - cq) * 4u)
+                     : "memory");
+      }
   for (int c0 = 0; c0 < w; c0 += 128) {
+    if (PF > 0 && lane < PH && c0 + PF * 128 < w) {
+      // row `lane`'s segment PF tiles ahead (16-byte aligned, a multiple of 128 bytes)
+      const int cq = c0 + PF * 128;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Pn + (size_t)lane * w + cq),
+                   "r"((uint32_t)min(128, w - cq) * 4u)
+                   : "memory");
+    }
     const int c = c0 + 4 * lane;
     const bool ok = c < w;
     const float4 vv = make_float4(c < m ? v[c] : 0.f, c + 1 < m ? v[c + 1] : 0.f, c + 2 < m ? v[c + 2] : 0.f,
@@ -748,8 +763,7 @@ __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __res
 }
 
 // y[c] += sum over the panels I below row c (I = c/PH + 1, ..) of their
-// transposed products at column c, in that order; loads issued in groups of
-// eight independent ones (the sum stays in panel order).
+// transposed products at column c, in that order.
 __global__ void k_symv_fix(Maps mp, const SubLayout* __restrict__ lay, int which, const float* __restrict__ part,
                            double* __restrict__ y, const int* __restrict__ done) {
   constexpr int PH = kSymPH;
@@ -761,18 +775,21 @@ __global__ void k_symv_fix(Maps mp, const SubLayout* __restrict__ lay, int which
     if (c >= m) continue;
     const int nP = (m + PH - 1) / PH;
     const float* ps = part + L.psym;
-    double t = 0.0;
-    for (int I0 = c / PH + 1; I0 < nP; I0 += 8) {
-      float f[8];
+    // FP32 sum in panel order (the partials carry the FP32 operator's rounding;
+    // FP64 adds and conversions would occupy GB300's narrow FP64 pipe), loads
+    // requested sixteen at a time, one FP64 addition to y
+    float t = 0.f;
+    for (int I0 = c / PH + 1; I0 < nP; I0 += 16) {
+      float f[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int I = I0 + u;
-        f[u] = I < nP ? ps[(size_t)(PH / 2) * I * (I - 1) + c] : 0.f;
+        f[u] = I < nP ? __ldg(ps + (size_t)(PH / 2) * I * (I - 1) + c) : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t += (double)f[u];
+      for (int u = 0; u < 16; ++u) t += f[u];
     }
-    y[gp] += t;
+    y[gp] += (double)t;
   }
 }
 
@@ -1329,12 +1346,15 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
                      cudaStream_t st) {
   const int blocks = (n_warps + kThreads / 32 - 1) / (kThreads / 32);
-  if (G == 16)
-    k_symv_f32<16><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
-  else if (G == 8)
-    k_symv_f32<8><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
-  else
-    k_symv_f32<kSymPH><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done);
+  // G: rows per load group (8, 16, 32); + 100 * PF: L2 prefetch PF tiles ahead (1, 2)
+  switch (G) {
+    case 8: k_symv_f32<8, 0><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+    case 16: k_symv_f32<16, 0><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+    case 108: k_symv_f32<8, 1><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+    case 132: k_symv_f32<32, 1><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+    case 232: k_symv_f32<32, 2><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+    default: k_symv_f32<32, 0><<<blocks, kThreads, 0, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done); break;
+  }
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 
