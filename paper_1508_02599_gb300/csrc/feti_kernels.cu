@@ -898,13 +898,14 @@ __device__ double reduce_partials(const double* partial, double* red) {
   return block_sum(t, red);
 }
 
-// G^T x split over chunks of 256 boundary positions (many CTAs per
-// subdomain): partial[c*6 + a] = sum over the chunk of R_b[p][a] (B^T x)[p].
+// G^T x split over chunks of 256 boundary positions (one CTA per chunk,
+// several per subdomain): partial[c*6 + a] = sum over the chunk of
+// R_b[p][a] (B^T x)[p].
 // With q != NULL the input is the updated residual x - alpha q, alpha =
 // rho / (p, q) evaluated by every CTA from the partial sums of (p, q) (the
 // fused CG step); CTA 0 records alpha and flags a breakdown.
 __global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict__ chunk_sub,
-                                                       const int32_t* __restrict__ chunk_p0,
+                                                       const int32_t* __restrict__ chunk_p0, int n_chunks,
                                                        const SubLayout* __restrict__ lay,
                                                        const double* __restrict__ R, Maps mp,
                                                        const double* __restrict__ x, double* __restrict__ partial,
@@ -927,11 +928,17 @@ __global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict
       alpha_hist[sc->it] = alpha;
     }
   }
+  // one position per thread (the gathers' load chains run in parallel);
+  // the six coarse columns are reduced by a transposed warp reduction (8
+  // values -> one per lane group in 9 FP64 adds instead of 6 x 5 on GB300's
+  // narrow FP64 pipe) and the eight warps' results summed in warp order
   const int c = blockIdx.x;
+  if (c >= n_chunks) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SubLayout L = lay[chunk_sub[c]];
   const int nb = L.nbp + L.k;
   const int p = chunk_p0[c] + threadIdx.x;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (p < nb) {
     const int gp = L.boff + p;
     double val = 0.0;
@@ -940,11 +947,48 @@ __global__ void __launch_bounds__(kThreads) k_gtv_part(const int32_t* __restrict
       val += mp.bt_sgn[e] * (q ? x[row] - alpha * q[row] : x[row]);
     }
     const double* Rr = R + L.roff + (size_t)(L.nI + p) * L.k;
-    for (int a = 0; a < L.k; ++a) acc[a] = Rr[a] * val;
+    for (int a = 0; a < L.k; ++a) v8[a] = Rr[a] * val;
   }
-  for (int a = 0; a < L.k; ++a) {
-    const double t = block_sum(acc[a], red);
-    if (threadIdx.x == 0) partial[6 * c + a] = t;
+  // step 16: keep half the values, add the partner's copy of that half
+  double v4[4], v2[2], v1;
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double send = up ? v8[i] : v8[i + 4];
+      const double keep = up ? v8[i + 4] : v8[i];
+      v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const double send = up ? v4[i] : v4[i + 2];
+      const double keep = up ? v4[i + 2] : v4[i];
+      v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {
+    const bool up = lane & 4;
+    const double send = up ? v2[0] : v2[1];
+    const double keep = up ? v2[1] : v2[0];
+    v1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+  v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+  // lane 4 g holds column a = 4 (g >> 2 & 1) + 2 (g >> 1 & 1) + (g & 1), g = lane / 4
+  __shared__ double wsum[kThreads / 32][8];
+  if ((lane & 3) == 0) {
+    const int g = lane >> 2;
+    const int a = 4 * ((g >> 2) & 1) + 2 * ((g >> 1) & 1) + (g & 1);
+    wsum[wid][a] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x < L.k) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += wsum[w][threadIdx.x];
+    partial[6 * c + threadIdx.x] = t;
   }
 }
 
@@ -1393,8 +1437,8 @@ void launch_gtv_part(int n_chunks, const int32_t* chunk_sub, const int32_t* chun
                      cudaStream_t st, const double* q, const double* pq_partial, PcgScalars* sc,
                      double* alpha_hist) {
   if (n_chunks <= 0) return;
-  k_gtv_part<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, x, partial, done, q, pq_partial, sc,
-                                            alpha_hist);
+  k_gtv_part<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, n_chunks, lay, R, mp, x, partial, done, q,
+                                            pq_partial, sc, alpha_hist);
 }
 
 void launch_expand_update(const Maps& mp, const SubLayout* lay, const double* R, double* r, const double* c,
