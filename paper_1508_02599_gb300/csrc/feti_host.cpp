@@ -1181,7 +1181,7 @@ feti_status autotune(feti_ctx* ctx) {
           if (ms < best) { best = ms; bestc = c; }
         }
       (f32 ? ctx->cfg32[w] : ctx->cfg64[w]) = bestc;
-      if (f32 && ctx->d_F32s) {
+      if (f32 && ctx->d_F32s && !ctx->opt.per_subdomain) {  // the plain form launches full rows
         // symmetric lower block-triangle kernel: load groups of 8 / 16 / 32 rows,
         // + 100 x (tiles of L2 prefetch ahead)
         ctx->sym32[w] = 0;
