@@ -464,6 +464,35 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
+// Transposed warp reduction of R values per lane (R = 2, 4, 8): each of the
+// log2 R halving steps keeps half of the values and adds the partner's copy of
+// that half, then plain xor steps finish; lane (32 / R) j and its group hold
+// the warp total of value j.  R - 1 + 5 - log2 R adds per lane instead of 5 R
+// (FP64 adds occupy GB300's narrow FP64 pipe).
+template <int R>
+__device__ __forceinline__ double transposed_warp_sum(const double (&v)[R], int lane) {
+  double cur[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) cur[i] = v[i];
+  int n = R;
+#pragma unroll
+  for (int m = 16; m >= 32 / R; m >>= 1) {
+    const bool up = lane & m;
+    n >>= 1;
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i)
+      if (i < n) {
+        const double send = up ? cur[i] : cur[i + n];
+        const double keep = up ? cur[i + n] : cur[i];
+        cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+  }
+  double t = cur[0];
+#pragma unroll
+  for (int m = 16 / R; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+  return t;
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreads) k_gemv_loc(const int32_t* __restrict__ blk_sub,
                                                        const int32_t* __restrict__ blk_row0, int rpc,
@@ -518,10 +547,21 @@ __global__ void __launch_bounds__(kThreads) k_gemv_loc(const int32_t* __restrict
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[j] += a[j] * vv;
       }
+      if constexpr (R >= 2) {
+        // after the halving steps on lane bits 4, 3, .. the lanes of group
+        // g = lane / (32 / R) hold the total of row g
+        double accd[R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const double t = warp_sum(acc[j]);
-        if (lane == 0 && rbase + j < rend) y[L.boff + rbase + j] = t;
+        for (int j = 0; j < R; ++j) accd[j] = acc[j];
+        const double t = transposed_warp_sum<R>(accd, lane);
+        const int g = lane / (32 / R);
+        if (lane % (32 / R) == 0 && rbase + g < rend) y[L.boff + rbase + g] = t;
+      } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const double t = warp_sum(acc[j]);
+          if (lane == 0 && rbase + j < rend) y[L.boff + rbase + j] = t;
+        }
       }
     }
   }
