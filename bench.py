@@ -218,7 +218,7 @@ def main():
     stream = torch.cuda.Stream()            # a real stream: the library captures graphs on it
     torch.cuda.set_stream(stream)
     peaks, src = _peaks()
-    fp64_peak = 1.259  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derivation in the design doc)
+    fp64_peak = 1.259  # TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
 
     def measure(precision: str, batched: bool = True, n_apply: int = 0, steps: int = 0):
         """Full solve once, then `steps` timed blocks of n_apply dual applies."""
