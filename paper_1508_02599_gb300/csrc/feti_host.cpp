@@ -990,9 +990,11 @@ feti_status factorize_all(feti_ctx* ctx) {
   std::vector<int> chunks[2];
   for (int phase = 0; phase < 2; ++phase)
     for (const auto& L : ctx->lay) {
-      const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp, na = phase == 0 ? L.n : L.ld;
+      const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp;
       for (int t = 0, kb = c0; kb < c1; ++t, kb += 32) {
         const int r0 = kb + std::min(32, c1 - kb);
+        // phase 1: only the augmentation rows of the columns eliminated so far
+        const int na = phase == 0 ? L.n : std::min(L.ld, L.n + r0 - L.nI);
         const int ch = (na - r0 + 63) / 64;
         if ((int)chunks[phase].size() <= t) chunks[phase].push_back(0);
         chunks[phase][t] = std::max(chunks[phase][t], ch);
@@ -1050,7 +1052,7 @@ feti_status coarse_setup(feti_ctx* ctx) {
   FETI_CK(cudaMemcpy2DAsync(ctx->d_Acoarse, 2 * cd * sizeof(double), ctx->d_GtG, cd * sizeof(double),
                             cd * sizeof(double), cd, cudaMemcpyDeviceToDevice, st));
   feti::launch_augment(1, ctx->d_lay_coarse, ctx->d_Acoarse, st);
-  feti::launch_dense_chol_big(ctx->d_Acoarse, 2 * (int)cd, 0, (int)cd, 2 * (int)cd, ctx->d_status, st);
+  feti::launch_dense_chol_big(ctx->d_Acoarse, 2 * (int)cd, 0, (int)cd, 2 * (int)cd, (int)cd, ctx->d_status, st);
   // extract into Ginv: F layout of the coarse "subdomain" has foff = 0
   feti::launch_extract(1, ctx->d_lay_coarse, 1, ctx->d_Acoarse, ctx->d_Ginv, st);
   FETI_CK(cudaGetLastError());

@@ -225,7 +225,7 @@ void launch_zero_list(int n, const int32_t* idx, double* x, cudaStream_t st);
 namespace feti {
 // Multi-CTA partial Cholesky of one dense lower-triangular row-major matrix
 // (leading dimension ld): columns [c0, c1), trailing update on [c1, n_act).
-void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int* status, cudaStream_t st);
+void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int aug0, int* status, cudaStream_t st);
 }  // namespace feti
 
 namespace feti {

@@ -413,7 +413,13 @@ __global__ void k_extract(const SubLayout* __restrict__ lay, int which, const do
   }
 }
 
-// x = K^+ g: forward L y = g_r (row dots), backward L^T x = y (row axpys).
+// x = K^+ g: forward L y = g_r, backward L^T x = y, both by 32-row blocks
+// with two barriers per block.  Forward: the warps form the dot products of
+// the block's rows with the part solved so far (one warp per row, lanes
+// striding the columns), then one warp solves the 32 x 32 diagonal triangle
+// with shuffles.  Backward: one warp solves the transposed diagonal triangle,
+// then every thread subtracts the block's contributions from its columns of
+// the unsolved part.  The fixing DOFs get zero.
 __global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict__ lay,
                                                     const double* __restrict__ Abase,
                                                     const double* __restrict__ gbase, double* __restrict__ xbase) {
@@ -424,26 +430,63 @@ __global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict_
   const double* g = gbase + L.voff;
   double* x = xbase + L.voff;
   const int nr = L.nI + L.nbp;
-  __shared__ double red[32];
-  __shared__ double xi;
-  for (int i = 0; i < nr; ++i) {
-    double t = 0.0;
-    for (int j = threadIdx.x; j < i; j += blockDim.x) t += A[i * ld + j] * x[j];
-    t = block_sum(t, red);
-    if (threadIdx.x == 0) x[i] = (g[i] - t) / A[i * ld + i];
-    __syncthreads();
-  }
-  for (int i = nr + threadIdx.x; i < L.n; i += blockDim.x) x[i] = 0.0;
-  __syncthreads();
-  for (int i = nr - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) {
-      xi = x[i] / A[i * ld + i];
-      x[i] = xi;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarpsPerCta = kThreads / 32;
+  __shared__ double D[32][33];
+  __shared__ double t[32];
+  __shared__ double xs[32];
+  for (int i = nr + tid; i < L.n; i += blockDim.x) x[i] = 0.0;
+  for (int I0 = 0; I0 < nr; I0 += 32) {
+    const int nb = min(32, nr - I0);
+    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx >> 5, c = idx & 31;
+      D[r][c] = (r < nb && c <= r) ? A[(size_t)(I0 + r) * ld + I0 + c] : 0.0;
+    }
+    for (int r = warp; r < nb; r += kWarpsPerCta) {
+      const double* row = A + (size_t)(I0 + r) * ld;
+      double acc = 0.0;
+#pragma unroll 4
+      for (int j = lane; j < I0; j += 32) acc += row[j] * x[j];
+      acc = warp_sum(acc);
+      if (lane == 0) t[r] = acc;
     }
     __syncthreads();
-    const double v = xi;
-    for (int j = threadIdx.x; j < i; j += blockDim.x) x[j] -= A[i * ld + j] * v;
+    if (warp == 0) {
+      double b = lane < nb ? g[I0 + lane] - t[lane] : 0.0;
+      double xv = 0.0;
+      for (int c = 0; c < nb; ++c) {
+        if (lane == c) xv = b / D[c][c];
+        const double xc = __shfl_sync(0xffffffffu, xv, c);
+        if (lane > c) b -= D[lane][c] * xc;
+      }
+      if (lane < nb) x[I0 + lane] = xv;
+    }
     __syncthreads();
+  }
+  for (int I0 = nr > 0 ? ((nr - 1) / 32) * 32 : -32; I0 >= 0; I0 -= 32) {
+    const int nb = min(32, nr - I0);
+    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx >> 5, c = idx & 31;
+      D[r][c] = (r < nb && c <= r) ? A[(size_t)(I0 + r) * ld + I0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double b = lane < nb ? x[I0 + lane] : 0.0;
+      double xv = 0.0;
+      for (int c = nb - 1; c >= 0; --c) {
+        if (lane == c) xv = b / D[c][c];
+        const double xc = __shfl_sync(0xffffffffu, xv, c);
+        if (lane < c) b -= D[c][lane] * xc;
+      }
+      if (lane < nb) x[I0 + lane] = xv;
+      xs[lane] = xv;
+    }
+    __syncthreads();
+    for (int j = tid; j < I0; j += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < nb; ++r) acc += A[(size_t)(I0 + r) * ld + j] * xs[r];
+      x[j] -= acc;
+    }
   }
 }
 
@@ -1757,16 +1800,18 @@ __global__ void __launch_bounds__(kThreads) k_big_update(double* __restrict__ A,
 }
 }  // namespace
 
-void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int* status, cudaStream_t st) {
+void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int aug0, int* status, cudaStream_t st) {
   for (int kb = c0; kb < c1; kb += NB) {
     const int nk = min(NB, c1 - kb);
     k_big_diag<<<1, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, status);
-    const int rows = n_act - (kb + nk);
+    // augmentation rows of columns not yet eliminated are still zero there
+    const int na = aug0 >= 0 ? min(n_act, aug0 + kb + nk - c0) : n_act;
+    const int rows = na - (kb + nk);
     if (rows <= 0) continue;
     const int chunks = (rows + TT - 1) / TT;
-    k_big_trsm<<<chunks, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, n_act, status);
+    k_big_trsm<<<chunks, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, na, status);
     const long tiles = (long)chunks * (chunks + 1) / 2;
-    k_big_update<<<(unsigned)tiles, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, n_act, status);
+    k_big_update<<<(unsigned)tiles, kThreads, 0, st>>>(A, (size_t)ld, kb, nk, na, status);
   }
 }
 
@@ -1815,10 +1860,17 @@ namespace {
 // interior columns [0, nI) with trailing rows/cols [.., n); phase 1 the
 // boundary columns [nI, nI + nbp) with trailing rows/cols [.., ld).
 struct PhaseRange {
-  int c0, c1, na;
+  int c0, c1;
 };
 __device__ __forceinline__ PhaseRange phase_range(const SubLayout& L, int phase) {
-  return phase == 0 ? PhaseRange{0, L.nI, L.n} : PhaseRange{L.nI, L.nI + L.nbp, L.ld};
+  return phase == 0 ? PhaseRange{0, L.nI} : PhaseRange{L.nI, L.nI + L.nbp};
+}
+// Rows that block column [kb, kb + nk) can change.  Augmentation row n + a
+// starts as the unit row of column nI + a and stays zero left of that column
+// until it is eliminated, so in phase 1 only the augmentation rows of the
+// columns eliminated so far take part; the others would receive exact zeros.
+__device__ __forceinline__ int active_rows(const SubLayout& L, int phase, int kb, int nk) {
+  return phase == 0 ? L.n : min(L.ld, L.n + kb + nk - L.nI);
 }
 
 __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
@@ -1875,9 +1927,10 @@ __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int ste
   const int kb = pr.c0 + step * NB;
   if (kb >= pr.c1) return;
   const int nk = min(NB, pr.c1 - kb);
+  const int na = active_rows(L, phase, kb, nk);
   const int base = kb + nk + blockIdx.x * TT;
-  if (base >= pr.na) return;
-  const int nr = min(TT, pr.na - base);
+  if (base >= na) return;
+  const int nr = min(TT, na - base);
   double* A = Abase + L.aoff;
   const size_t ld = L.ld;
   __shared__ double D[NB][NB + 1];
@@ -1925,7 +1978,8 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   if (kb >= pr.c1) return;
   const int nk = min(NB, pr.c1 - kb);
   const int r0 = kb + nk;
-  const int chunks = (pr.na - r0 + TT - 1) / TT;
+  const int na = active_rows(L, phase, kb, nk);
+  const int chunks = (na - r0 + TT - 1) / TT;
   const long b = blockIdx.x;
   if (b >= (long)chunks * (chunks + 1) / 2) return;
   int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
@@ -1935,7 +1989,6 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   const int ib = r0 + ti * TT, jb = r0 + tj * TT;
   double* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  const int na = pr.na;
   __shared__ double Pa[TT][NB + 1];
   __shared__ double Pb[TT][NB + 1];
   const int tid = threadIdx.x;
