@@ -130,6 +130,12 @@ struct feti_ctx {
   int pcg_graph_chunk = 0;
   bool pcg_graph_mixed = false;
   double t_setup_ms = 0.0;
+  // interior elimination restricted to the envelope: per step and subdomain
+  // the end eI of the interior rows and the count nbact of boundary rows that
+  // the step's block column can reach ([step][subdomain][2])
+  int steps0 = 0;
+  std::vector<int32_t> env0;
+  int32_t* d_env0 = nullptr;
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
   double elem_ms = 0.0, elem_bytes = 0.0;
   // sizes (elements) of d_A, d_S, d_F, d_F32, d_S32, d_F32s, d_S32s, d_symp
@@ -372,8 +378,17 @@ feti_status build_decomposition(feti_ctx* ctx) {
   for (int64_t r = 0; r < ctx->n_lambda; ++r)
     for (int e = 0; e < 2; ++e)
       if (rs[2 * r + e] >= 0) bflag[rs[2 * r + e]][rl[2 * r + e]] = 1;
+  // elements grouped by subdomain
+  std::vector<int32_t> sub_elem_ptr(P + 1, 0), sub_elems(E);
+  for (int e = 0; e < E; ++e) sub_elem_ptr[ctx->part[e] + 1]++;
+  for (int s = 0; s < P; ++s) sub_elem_ptr[s + 1] += sub_elem_ptr[s];
+  {
+    std::vector<int32_t> f2(sub_elem_ptr.begin(), sub_elem_ptr.end() - 1);
+    for (int e = 0; e < E; ++e) sub_elems[f2[ctx->part[e]]++] = e;
+  }
   // per subdomain: free DOFs, kernels, fixing DOFs, dense order
   ctx->lay.assign(P, SubLayout{});
+  std::vector<std::vector<int32_t>> env0(P);  // per interior-elimination step: (eI, nbact)
   ctx->fix_ptr.assign(P + 1, 0);
   ctx->fix_ldof.clear();
   std::vector<std::vector<int32_t>> dense_ldof(P);  // dense index -> local DOF
@@ -487,9 +502,48 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (int d = 0; d < nd; ++d)
       if (free[d] && !bflag[s][d]) dl.push_back(d);
     const int nI = (int)dl.size();
+    // Envelope of the interior columns: per local DOF, the first interior
+    // dense position it couples to through an element of this subdomain (nI
+    // if none).  Cholesky fill stays inside the envelope, so a row is zero in
+    // every interior column left of that position.
+    std::vector<int32_t> dof_first(nd, nI);
+    {
+      std::vector<int32_t> own(nl, nI), node_first(nl, nI);
+      for (int i = 0; i < nI; ++i) own[dl[i] / 3] = std::min(own[dl[i] / 3], i);
+      for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+        const int e = sub_elems[q];
+        int ln[4], m = nI;
+        for (int a = 0; a < 4; ++a) {
+          ln[a] = lnode(s, ctx->tets[4 * (size_t)e + a]);
+          m = std::min(m, own[ln[a]]);
+        }
+        for (int a = 0; a < 4; ++a) node_first[ln[a]] = std::min(node_first[ln[a]], m);
+      }
+      for (int d = 0; d < nd; ++d) dof_first[d] = node_first[d / 3];
+    }
+    // boundary DOFs (fixing DOFs excepted) by envelope start, so that the rows
+    // an interior block column can reach form a prefix of the boundary block
+    std::vector<int32_t> bsort;
     for (int d : bl)
-      if (!isfix[d]) dl.push_back(d);
+      if (!isfix[d]) bsort.push_back(d);
+    std::stable_sort(bsort.begin(), bsort.end(),
+                     [&](int32_t a, int32_t b) { return dof_first[a] < dof_first[b]; });
+    for (int d : bsort) dl.push_back(d);
     const int nbp = (int)dl.size() - nI;
+    {
+      // last[v] = the last interior row whose envelope starts left of column v
+      std::vector<int32_t> last(nI + 1, -1);
+      for (int r = 0; r < nI; ++r) last[dof_first[dl[r]] + 1] = std::max(last[dof_first[dl[r]] + 1], r);
+      for (int v = 1; v <= nI; ++v) last[v] = std::max(last[v], last[v - 1]);
+      std::vector<int32_t> bfirst(nbp);
+      for (int i = 0; i < nbp; ++i) bfirst[i] = dof_first[bsort[i]];
+      auto& ev = env0[s];
+      for (int kb = 0; kb < nI; kb += 32) {
+        const int r0 = kb + std::min(32, nI - kb);
+        ev.push_back(std::max(r0, last[r0] + 1));
+        ev.push_back((int32_t)(std::lower_bound(bfirst.begin(), bfirst.end(), r0) - bfirst.begin()));
+      }
+    }
     for (int d : fix) dl.push_back(d);
     const int n = (int)dl.size();
     SubLayout L{};
@@ -524,6 +578,16 @@ feti_status build_decomposition(feti_ctx* ctx) {
     ctx->fix_ptr[s + 1] = (int32_t)ctx->fix_ldof.size();
   }
   ctx->nb_total = boff;
+  // envelope table of the interior elimination, [step][subdomain][2]
+  ctx->steps0 = 0;
+  for (int s = 0; s < P; ++s) ctx->steps0 = std::max(ctx->steps0, (int)env0[s].size() / 2);
+  ctx->env0.assign(2 * (size_t)ctx->steps0 * P, 0);
+  for (int s = 0; s < P; ++s)
+    for (size_t t = 0; t < env0[s].size() / 2; ++t) {
+      ctx->env0[2 * (t * P + s)] = env0[s][2 * t];
+      ctx->env0[2 * (t * P + s) + 1] = env0[s][2 * t + 1];
+    }
+  FETI_TRY(upload(ctx, &ctx->d_env0, ctx->env0));
   ctx->nloc_total = voff;
   ctx->cd = coff;
   // dense position lookup per subdomain: local DOF -> dense index
@@ -564,14 +628,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   std::vector<int32_t> bpos_sub(ctx->nb_total);
   for (int s = 0; s < P; ++s)
     for (int p = 0; p < ctx->lay[s].nbp + ctx->lay[s].k; ++p) bpos_sub[ctx->lay[s].boff + p] = s;
-  // elements grouped by subdomain and their dense maps
-  std::vector<int32_t> sub_elem_ptr(P + 1, 0), sub_elems(E);
-  for (int e = 0; e < E; ++e) sub_elem_ptr[ctx->part[e] + 1]++;
-  for (int s = 0; s < P; ++s) sub_elem_ptr[s + 1] += sub_elem_ptr[s];
-  {
-    std::vector<int32_t> f2(sub_elem_ptr.begin(), sub_elem_ptr.end() - 1);
-    for (int e = 0; e < E; ++e) sub_elems[f2[ctx->part[e]]++] = e;
-  }
+  // dense maps of the elements (grouped by subdomain above)
   std::vector<int32_t> elem_dense(12 * (size_t)E);
   std::vector<double> elem_dirval;
   ctx->any_dirval = false;
@@ -991,20 +1048,29 @@ feti_status factorize_all(feti_ctx* ctx) {
   for (int phase = 0; phase < 2; ++phase)
     for (const auto& L : ctx->lay) {
       const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp;
+      const int s = (int)(&L - ctx->lay.data());
       for (int t = 0, kb = c0; kb < c1; ++t, kb += 32) {
         const int r0 = kb + std::min(32, c1 - kb);
-        // phase 1: only the augmentation rows of the columns eliminated so far
-        const int na = phase == 0 ? L.n : std::min(L.ld, L.n + r0 - L.nI);
-        const int ch = (na - r0 + 63) / 64;
+        // phase 0: the rows inside the envelope (interior rows up to eI, the
+        // first nbact boundary rows, the fixing rows); phase 1: all remaining
+        // rows plus the augmentation rows of the columns eliminated so far
+        int m;
+        if (phase == 0) {
+          const int32_t* ev = &ctx->env0[2 * ((size_t)t * ctx->P + s)];
+          m = (ev[0] - r0) + ev[1] + L.k;
+        } else {
+          m = std::min(L.ld, L.n + r0 - L.nI) - r0;
+        }
+        const int ch = (m + 63) / 64;
         if ((int)chunks[phase].size() <= t) chunks[phase].push_back(0);
         chunks[phase][t] = std::max(chunks[phase][t], ch);
       }
     }
-  feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_A, ctx->d_status,
-                            st);
+  feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0, ctx->d_A,
+                            ctx->d_status, st);
   if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
-  feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), ctx->d_A, ctx->d_status,
-                            st);
+  feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A,
+                            ctx->d_status, st);
   feti::launch_extract(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_F, st);
   if (ctx->opt.precision == FETI_MIXED) {
     feti::launch_to_f32(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32, st);

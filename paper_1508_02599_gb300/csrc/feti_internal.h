@@ -241,11 +241,15 @@ namespace feti {
 // Batched multi-CTA partial Cholesky of every subdomain's dense matrix, one
 // launch triple (diagonal block, panel solve, tiled trailing update) per
 // 32-column step; phase 0: interior columns, phase 1: boundary minus fixing
-// columns, trailing rows/cols up to n (phase 0) or ld (phase 1).  step_chunks[t] (host array, n_steps
-// entries): the largest number of 64-row trailing chunks over the subdomains
-// at step t (idle CTAs exit at once).
-void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps, double* A,
-                         int* status, cudaStream_t st);
+// columns.  Each step updates only the rows its block column can reach:
+// phase 0 the envelope given by env0 ([step][subdomain] pairs (eI, nbact):
+// interior rows up to eI, the first nbact boundary rows, the fixing rows),
+// phase 1 the remaining rows plus the augmentation rows of the columns
+// eliminated so far (env0 unused).  step_chunks[t] (host array, n_steps
+// entries): the largest number of 64-row chunks of those rows over the
+// subdomains at step t (idle CTAs exit at once).
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                         const int32_t* env0, double* A, int* status, cudaStream_t st);
 }  // namespace feti
 
 namespace feti {

@@ -1865,12 +1865,42 @@ struct PhaseRange {
 __device__ __forceinline__ PhaseRange phase_range(const SubLayout& L, int phase) {
   return phase == 0 ? PhaseRange{0, L.nI} : PhaseRange{L.nI, L.nI + L.nbp};
 }
-// Rows that block column [kb, kb + nk) can change.  Augmentation row n + a
-// starts as the unit row of column nI + a and stays zero left of that column
-// until it is eliminated, so in phase 1 only the augmentation rows of the
-// columns eliminated so far take part; the others would receive exact zeros.
-__device__ __forceinline__ int active_rows(const SubLayout& L, int phase, int kb, int nk) {
-  return phase == 0 ? L.n : min(L.ld, L.n + kb + nk - L.nI);
+// Rows that block column [kb, kb + nk) can change, as an increasing map of
+// 0 .. m - 1 onto matrix rows; the rows left out would receive exact zeros.
+// Phase 0 (envelope of the interior columns: a row is zero left of the first
+// interior column it couples to, and Cholesky fill stays inside that
+// envelope): interior rows r0 .. eI - 1, the first nbact boundary rows (the
+// boundary DOFs are ordered by envelope start) and the fixing rows, with
+// (eI, nbact) per step and subdomain from the host.  Phase 1: rows r0 .. n - 1
+// and the augmentation rows of the columns eliminated so far (augmentation
+// row n + a starts as the unit row of column nI + a and stays zero left of
+// that column until it is eliminated).
+struct ActiveRows {
+  int r0, lenA, lenB, bbase, cbase, m;
+  __device__ __forceinline__ int row(int q) const {
+    return q < lenA ? r0 + q : (q < lenA + lenB ? bbase + (q - lenA) : cbase + (q - lenA - lenB));
+  }
+};
+__device__ __forceinline__ ActiveRows active_rows(const SubLayout& L, int phase, int step, int kb, int nk,
+                                                  const int32_t* __restrict__ env0) {
+  ActiveRows a;
+  a.r0 = kb + nk;
+  if (phase == 0) {
+    const int32_t* ev = env0 + 2 * ((size_t)step * gridDim.y + blockIdx.y);
+    const int eI = min(max(ev[0], a.r0), L.nI);
+    const int nbact = min(max(ev[1], 0), L.nbp);
+    a.lenA = eI - a.r0;
+    a.lenB = nbact;
+    a.bbase = L.nI;
+    a.cbase = L.nI + L.nbp;
+    a.m = a.lenA + a.lenB + L.k;
+  } else {
+    a.lenA = min(L.ld, L.n + a.r0 - L.nI) - a.r0;
+    a.lenB = 0;
+    a.bbase = a.cbase = a.r0;
+    a.m = a.lenA;
+  }
+  return a;
 }
 
 __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
@@ -1919,18 +1949,18 @@ __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int ste
   }
 }
 
-__global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
-                           const int* status) {
+__global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int step,
+                           const int32_t* __restrict__ env0, double* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
   const int kb = pr.c0 + step * NB;
   if (kb >= pr.c1) return;
   const int nk = min(NB, pr.c1 - kb);
-  const int na = active_rows(L, phase, kb, nk);
-  const int base = kb + nk + blockIdx.x * TT;
-  if (base >= na) return;
-  const int nr = min(TT, na - base);
+  const ActiveRows ar = active_rows(L, phase, step, kb, nk, env0);
+  const int q0 = blockIdx.x * TT;
+  if (q0 >= ar.m) return;
+  const int nr = min(TT, ar.m - q0);
   double* A = Abase + L.aoff;
   const size_t ld = L.ld;
   __shared__ double D[NB][NB + 1];
@@ -1942,7 +1972,7 @@ __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int ste
   }
   for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
     const int r = idx / NB, l = idx % NB;
-    Pa[r][l] = (r < nr && l < nk) ? A[(base + r) * ld + kb + l] : 0.0;
+    Pa[r][l] = (r < nr && l < nk) ? A[(size_t)ar.row(q0 + r) * ld + kb + l] : 0.0;
   }
   __syncthreads();
   if (tid < nr) {
@@ -1965,11 +1995,12 @@ __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int ste
   __syncthreads();
   for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
     const int r = idx / NB, l = idx % NB;
-    if (r < nr && l < nk) A[(base + r) * ld + kb + l] = Pa[r][l];
+    if (r < nr && l < nk) A[(size_t)ar.row(q0 + r) * ld + kb + l] = Pa[r][l];
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __restrict__ lay, int phase, int step,
+                                                         const int32_t* __restrict__ env0,
                                                          double* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
@@ -1977,16 +2008,16 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   const int kb = pr.c0 + step * NB;
   if (kb >= pr.c1) return;
   const int nk = min(NB, pr.c1 - kb);
-  const int r0 = kb + nk;
-  const int na = active_rows(L, phase, kb, nk);
-  const int chunks = (na - r0 + TT - 1) / TT;
+  const ActiveRows ar = active_rows(L, phase, step, kb, nk, env0);
+  const int m = ar.m;
+  const int chunks = (m + TT - 1) / TT;
   const long b = blockIdx.x;
   if (b >= (long)chunks * (chunks + 1) / 2) return;
   int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
   while ((long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
   while ((long)ti * (ti + 1) / 2 > b) --ti;
   const int tj = (int)(b - (long)ti * (ti + 1) / 2);
-  const int ib = r0 + ti * TT, jb = r0 + tj * TT;
+  const int ib = ti * TT, jb = tj * TT;  // positions in the active-row list
   double* A = Abase + L.aoff;
   const size_t ld = L.ld;
   __shared__ double Pa[TT][NB + 1];
@@ -1994,8 +2025,8 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   const int tid = threadIdx.x;
   for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
     const int r = idx / NB, l = idx % NB;
-    Pa[r][l] = (ib + r < na && l < nk) ? A[(ib + r) * ld + kb + l] : 0.0;
-    Pb[r][l] = (jb + r < na && l < nk) ? A[(jb + r) * ld + kb + l] : 0.0;
+    Pa[r][l] = (ib + r < m && l < nk) ? A[(size_t)ar.row(ib + r) * ld + kb + l] : 0.0;
+    Pb[r][l] = (jb + r < m && l < nk) ? A[(size_t)ar.row(jb + r) * ld + kb + l] : 0.0;
   }
   __syncthreads();
   const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
@@ -2020,21 +2051,21 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int i = ib + tr + a, j = jb + tc + c;
-      if (i < na && j < na && j <= i) A[i * ld + j] -= acc[a][c];
+      const int qi = ib + tr + a, qj = jb + tc + c;  // increasing map: qj <= qi <=> j <= i
+      if (qi < m && qj < m && qj <= qi) A[(size_t)ar.row(qi) * ld + ar.row(qj)] -= acc[a][c];
     }
 }
 }  // namespace
 
-void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps, double* A,
-                         int* status, cudaStream_t st) {
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                         const int32_t* env0, double* A, int* status, cudaStream_t st) {
   for (int t = 0; t < n_steps; ++t) {
     const int chunks = step_chunks[t];
     k_bat_diag<<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
     if (chunks <= 0) continue;
-    k_bat_trsm<<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    k_bat_trsm<<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
     const long tiles = (long)chunks * (chunks + 1) / 2;
-    k_bat_update<<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    k_bat_update<<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
   }
 }
 
