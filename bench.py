@@ -41,6 +41,22 @@ def _dist():
     return rank, world, local
 
 
+def _max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (every rank calls it); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
 
@@ -257,18 +273,14 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        ms = ev0.elapsed_time(ev1)
+        ms = _max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
         clk = clocks.stop()
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         ks = solver.kernel_stats()
         sched = solver.schedule()
         kern = statistics.mean(kern_ms)
         solver.close()
         return {"U": U, "rep": rep, "sizes": sizes, "ms": ms, "kern_ms": kern, "ks": ks, "clocks": clk, "sched": sched,
-                "value": steps * n_apply * world / (ms / 1e3), "steps": steps}
+                "value": _job_rate(steps * n_apply, world, ms / 1e3), "steps": steps}
 
     def measure_block(precision: str, nrhs: int = 16):
         """Block form: nrhs load cases p_k ~ U[8, 16] x the reference pressure (seeded), one block
@@ -358,6 +370,8 @@ def main():
     # problem) + solve (mixed form) + D2H of the displacement, per step
     e2e_steps = args.e2e_steps
     u_host = torch.empty(3 * prob.n_nodes, dtype=torch.float64).pin_memory()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     its = 0
     for _ in range(e2e_steps):
@@ -366,9 +380,12 @@ def main():
             r2 = s2.solve_host(u_host)
             its += r2["iterations"] + r2["outer_iterations"] + 2
     e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    e2e_dt = _max_over_ranks(e2e_dt, world, "cuda")
     h2d = (prob.coords.nbytes + prob.tets.nbytes + prob.part.nbytes + prob.dir_dof.nbytes + prob.dir_val.nbytes
            + prob.press_tri.nbytes + prob.press_owner.nbytes)
-    e2e = {"value": its * world / e2e_dt if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": _job_rate(its, world, e2e_dt) if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(u_host.numel() * 8),
            "note": "dual applies of complete FP32-local solves (create + setup + PCG to 1e-8 + recovery) per "
                    "second of wall time, problem arrays from host, displacement back to pinned host"}
