@@ -233,8 +233,12 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
  * that every GPU loading the library keeps until process exit.
  *  - Limit: a decomposition needs about 2.5 x (sum of boundary DOFs) doubles;
  *    larger ones are rejected with FETI_ERR_INVALID_ARG and a message.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Set-up happens in feti_create, with the context's device current: it
+ *    looks up the array's device address (cudaGetSymbolAddress), which also
+ *    makes the runtime load the module holding the array there, so no call of
+ *    this function loads code or reserves memory.  Call it with the same
+ *    device current (another device: FETI_ERR_INVALID_ARG).  An error left
+ *    pending by earlier CUDA work is reported (FETI_ERR_CUDA), not cleared.
  *  - The work is enqueued on the context's stream and the call returns
  *    without waiting.  All calls share the array: calls whose work overlaps
  *    on the GPU (other streams, other contexts) race on it.  Every scratch

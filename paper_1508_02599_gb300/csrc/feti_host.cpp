@@ -54,6 +54,12 @@ struct feti_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
+  int device = -1;  // the CUDA device current at feti_create
+  // static scratch of feti_dual_apply_noalloc on that device (looked up at
+  // feti_create), its capacity in doubles, and the lookup's error if it failed
+  double* noalloc_scratch = nullptr;
+  size_t noalloc_cap = 0;
+  std::string noalloc_err;
 
   // decomposition (host)
   std::vector<std::vector<int32_t>> nodes;
@@ -1925,18 +1931,36 @@ namespace feti {
 
 feti_status set_error(feti_ctx* ctx, feti_status st, const std::string& msg) { return fail(ctx, st, msg); }
 
-feti_status dual_apply_with_scratch(feti_ctx* ctx, const double* v, double* q, double* z, double* scratch,
-                                    size_t capacity) {
+feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z) {
   if (!v || !q || !z) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_dual_apply_noalloc: null vector");
+  if (!ctx->noalloc_scratch)
+    return fail(ctx, FETI_ERR_CUDA, "feti_dual_apply_noalloc: static scratch unavailable (" + ctx->noalloc_err + ")");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(ctx, FETI_ERR_CUDA, "feti_dual_apply_noalloc: no current CUDA device");
+  }
+  if (dev != ctx->device)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "feti_dual_apply_noalloc: current device " + std::to_string(dev) +
+                                               " is not the context's device " + std::to_string(ctx->device));
+  double* scratch = ctx->noalloc_scratch;
+  const size_t capacity = ctx->noalloc_cap;
   // scratch: local input (doubles, or floats for the FP32 copies) + local output
   const size_t nb = (size_t)ctx->nb_total;
   const size_t need = nb + (nb + 7) / 2 + 4 + nb;
   if (need > capacity)
     return fail(ctx, FETI_ERR_INVALID_ARG,
                 "feti_dual_apply_noalloc: this decomposition needs " + std::to_string(need) +
-                    " doubles of scratch (3 per boundary DOF), the static scratch holds " + std::to_string(capacity));
+                    " doubles of scratch (about 2.5 per boundary DOF), the static scratch holds " +
+                    std::to_string(capacity));
   if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
-  (void)cudaGetLastError();
+  {
+    // an error left pending by earlier work is reported, not cleared
+    const cudaError_t pend = cudaPeekAtLastError();
+    if (pend != cudaSuccess)
+      return fail(ctx, FETI_ERR_CUDA, std::string("feti_dual_apply_noalloc: pending CUDA error: ") +
+                                          cudaGetErrorString(pend));
+  }
   cudaStream_t st = ctx->stream;
   const int* zero = ctx->d_zero;
   double* vloc = scratch;                                          // nb doubles
@@ -2043,6 +2067,16 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   } else {
     FETI_CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
     ctx->own_stream = true;
+  }
+  FETI_CK(cudaGetDevice(&ctx->device));
+  {
+    // set-up of feti_dual_apply_noalloc on this device: the static scratch's
+    // device address (this loads its module here, not in a later call)
+    const cudaError_t e = feti::noalloc_scratch_lookup(&ctx->noalloc_scratch, &ctx->noalloc_cap);
+    if (e != cudaSuccess) {
+      ctx->noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      (void)cudaGetLastError();
+    }
   }
   return build_decomposition(ctx);
 }

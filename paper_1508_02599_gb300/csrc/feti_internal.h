@@ -305,9 +305,11 @@ void launch_col_set(int n, int nrhs, int k, double scale, const double* v, doubl
 namespace feti {
 // Records msg as the context's last error and returns st.
 feti_status set_error(feti_ctx* ctx, feti_status st, const std::string& msg);
-// q = F v, z = M^-1 q with the local scratch vectors placed in the caller's
-// device buffer `scratch` (capacity in doubles) instead of context memory;
-// enqueued on the context's stream, no allocation, no graph, no event.
-feti_status dual_apply_with_scratch(feti_ctx* ctx, const double* v, double* q, double* z, double* scratch,
-                                    size_t capacity);
+// Device address and capacity (doubles) of the static no-alloc scratch on the
+// current device (cudaGetSymbolAddress; loads the module that holds it).
+cudaError_t noalloc_scratch_lookup(double** out, size_t* capacity);
+// q = F v, z = M^-1 q with the local scratch vectors placed in the static
+// scratch looked up at feti_create instead of context memory; enqueued on the
+// context's stream, no allocation, no graph, no event.
+feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z);
 }  // namespace feti

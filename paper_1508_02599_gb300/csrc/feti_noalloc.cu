@@ -10,10 +10,16 @@
 // implicit device synchronisation cudaMalloc may cause in a latency-critical
 // loop, and code that issues work while some other component holds the
 // allocator (for example while a stream is being captured).
+//
+// Set-up: feti_create calls noalloc_scratch_lookup with the context's device
+// current.  The lookup (cudaGetSymbolAddress) makes the runtime load this
+// file's device module -- and so reserve the array -- at that point, never
+// inside a later feti_dual_apply_noalloc call; the context keeps the address
+// and the device it belongs to.
 #include "feti.h"
 #include "feti_internal.h"
 
-#include <cstdio>
+#include <string>
 
 namespace {
 
@@ -23,29 +29,29 @@ constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;
 
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
-// Device address of the array, looked up once per device (host code may not
-// use the symbol itself as a device pointer).
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
-
 }  // namespace
+
+namespace feti {
+
+// Device address of the static scratch on the current device.  Host code may
+// not use the symbol itself as a device pointer: in host code the name
+// stands for a host-side shadow, not for device memory.
+cudaError_t noalloc_scratch_lookup(double** out, size_t* capacity) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    *out = nullptr;
+    *capacity = 0;
+    return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+  }
+  *out = static_cast<double*>(p);
+  *capacity = kNoAllocScratchDoubles;
+  return cudaSuccess;
+}
+
+}  // namespace feti
 
 extern "C" feti_status feti_dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    (void)cudaGetLastError();
-    return feti::set_error(ctx, FETI_ERR_CUDA, "feti_dual_apply_noalloc: no current CUDA device");
-  }
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      (void)cudaGetLastError();
-      return feti::set_error(ctx, FETI_ERR_CUDA, std::string("feti_dual_apply_noalloc: cudaGetSymbolAddress: ") +
-                                                     cudaGetErrorString(e));
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  return feti::dual_apply_with_scratch(ctx, v, q, z, g_scratch_addr[dev], kNoAllocScratchDoubles);
+  return feti::dual_apply_noalloc(ctx, v, q, z);
 }

@@ -6,7 +6,9 @@ cudaMalloc's implicit synchronisation, or a phase in which another component
 owns the allocator).  They call feti_dual_apply_noalloc, which keeps its
 scratch in a static device array.  This file runs last in the suite so that a
 failure here never hides the other tests; it passes in a fresh process and
-after the rest of the suite alike.  Tolerance: the same kernels run on the
+after the rest of the suite alike.  Around every allocation-free call the
+device's free memory (cudaMemGetInfo) must stay the same: the static array and
+its module are set up by feti_create, not by the call.  Tolerance: the same kernels run on the
 same data, so results agree to 1e-12 relative (the bound the other operator
 tests use).  The allocation-free apply uses the full-row local kernels, so the
 solver here keeps its FP32 applies on full rows too (symmetric="off"); with
@@ -42,8 +44,12 @@ def test_noalloc_apply_matches_dual_apply_twice(precision, precond):
             q_ref, z_ref = torch.empty_like(v), torch.empty_like(v)
             s.dual_apply(v, q_ref, z_ref, 1)
             q, z = torch.full_like(v, np.nan), torch.full_like(v, np.nan)
+            torch.cuda.synchronize()
+            free0, _ = torch.cuda.mem_get_info()
             s.dual_apply_noalloc(v, q, z)
             torch.cuda.synchronize()
+            free1, _ = torch.cuda.mem_get_info()
+            assert free1 == free0, (call, free0 - free1)
             assert torch.isfinite(q).all() and torch.isfinite(z).all()
             assert (q - q_ref).abs().max().item() <= 1e-12 * q_ref.abs().max().item(), call
             assert (z - z_ref).abs().max().item() <= 1e-12 * z_ref.abs().max().item(), call
