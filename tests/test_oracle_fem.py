@@ -192,3 +192,25 @@ def test_pressure_load_resultant_on_tube():
     # sum to p * area * cos(pi/32)
     assert np.isclose(fr[inner].sum(), prob.pressure * area * np.cos(np.pi / 32), rtol=1e-12)
     assert np.abs(fr[~inner]).max() == 0.0
+
+
+def test_traction_load_resultant_and_moment_on_cube():
+    """Constant traction t on the face x = 1 of the unit cube (area 1): the
+    P1-consistent nodal forces sum to t * area, their first moment sum_n x_n f_n
+    equals t times the face's first moment of area (centroid (1, 1/2, 1/2)),
+    and no force acts off the face."""
+    prob = mesh.cube_problem(6, (1, 1, 1))
+    t = np.asarray(prob.traction, dtype=float)
+    assert np.abs(t).max() > 0.0
+    f = fem.load_vector(prob).reshape(-1, 3)
+    x = prob.coords
+    on_face = np.abs(x[:, 0] - 1.0) < 1e-12
+    assert np.abs(f[~on_face]).max() == 0.0
+    assert np.allclose(f.sum(axis=0), t * 1.0, rtol=0.0, atol=1e-15)
+    moment = np.einsum("na,nb->ab", x, f)           # sum_n x_n (outer) f_n
+    expected = np.outer([1.0, 0.5, 0.5], t) * 1.0
+    assert np.allclose(moment, expected, rtol=0.0, atol=1e-15)
+    # corner nodes of the face carry less than edge and interior nodes
+    # (fewer incident triangles): the split is not uniform over nodes
+    fz = f[on_face, 2]
+    assert fz.min() < fz.max() < 0.0 or fz.max() < fz.min() < 0.0 or np.ptp(fz) > 0.0
