@@ -128,6 +128,13 @@ typedef struct {
                               symmetric kernel (reads only the lower block-triangle of F_i / S_i)
                               when it is faster, 1 = full rows only, 2 = symmetric always
                               (fastest variant), 3 = symmetric, streamed through shared memory */
+  uint64_t spin_timeout_ns; /* budget of each main-loop mbarrier wait of the streamed symmetric
+                               apply and the warp-specialised tensor-core block GEMM, in ns of the
+                               GPU's global timer (0: 0.1 s).  A wait that runs out stops the
+                               kernel's pipeline, waits for its copies and tensor-core products in
+                               flight (those drain waits keep a fixed budget of 2e8 clock cycles),
+                               releases tensor memory and flags the call, which then returns
+                               FETI_ERR_TIMEOUT; the context stays usable. */
 } feti_options;
 
 typedef struct {
@@ -281,6 +288,11 @@ feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* ele
  * operands / warp-specialised 3-stage / 2-stage; both entries -1 = block form
  * not tuned yet). */
 feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]);
+
+/* Sets the main-loop wait budget of feti_options.spin_timeout_ns (ns; 0 =
+ * 0.1 s) for the later calls on this context; captured graphs read it at
+ * every launch.  Host blocking: waits for the context's stream. */
+feti_status feti_set_spin_timeout(feti_ctx* ctx, uint64_t spin_timeout_ns);
 
 const char* feti_last_error(const feti_ctx* ctx);
 void feti_destroy(feti_ctx* ctx);

@@ -42,7 +42,7 @@ class FetiOptions(C.Structure):
                 ("maxit", C.c_int32), ("chunk", C.c_int32), ("follower", C.c_int32),
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32),
-                ("per_subdomain", C.c_int32), ("symmetric", C.c_int32)]
+                ("per_subdomain", C.c_int32), ("symmetric", C.c_int32), ("spin_timeout_ns", C.c_uint64)]
 
 
 class FetiReport(C.Structure):
@@ -54,7 +54,7 @@ class FetiReport(C.Structure):
 
 EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
            "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_element_stats", "feti_get_schedule",
-           "feti_last_error",
+           "feti_set_spin_timeout", "feti_last_error",
            "feti_destroy"]
 
 _lib = None
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
     lib.feti_kernel_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.feti_element_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.feti_get_schedule.argtypes = [vp, vp]
+    lib.feti_set_spin_timeout.argtypes = [vp, C.c_uint64]
     lib.feti_last_error.argtypes = [vp]
     lib.feti_last_error.restype = C.c_char_p
     lib.feti_destroy.argtypes = [vp]

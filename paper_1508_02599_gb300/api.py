@@ -39,7 +39,7 @@ class FetiSolver:
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
-                 tensor_cores="auto", batched: bool = True, symmetric="auto"):
+                 tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -72,7 +72,8 @@ class FetiSolver:
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
-                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3}[symmetric])
+                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3}[symmetric],
+                            int(spin_timeout_ns))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))
@@ -147,6 +148,10 @@ class FetiSolver:
 
     def prepare(self):
         self._check(self._lib.feti_prepare(self._ctx))
+
+    def set_spin_timeout(self, ns: int):
+        """Main-loop wait budget (ns, 0 = default) of the kernels with bounded mbarrier waits."""
+        self._check(self._lib.feti_set_spin_timeout(self._ctx, int(ns)))
 
     def _report(self, rep: L.FetiReport) -> dict:
         return {k: getattr(rep, k) for k, _ in L.FetiReport._fields_}

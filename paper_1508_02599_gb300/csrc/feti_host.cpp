@@ -156,6 +156,9 @@ struct feti_ctx {
   // tiles); 64: streamed through shared memory
   int sym32[2] = {0, 0};
   int* d_sym_err = nullptr;  // set by a streamed symmetric apply whose bounded wait ran out
+  // main-loop wait budget (ns) of the streamed symmetric apply and the
+  // warp-specialised tensor-core GEMM: a device word read at every launch
+  unsigned long long* d_spin = nullptr;
   cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
   int m_cap = 0;  // allocated nrhs capacity of the block buffers
@@ -301,6 +304,16 @@ double lanczos_cond(const std::vector<double>& alpha, const std::vector<double>&
 }
 
 // ---------------------------------------------------------------------------
+// Main-loop wait budget of the kernels with bounded mbarrier waits: ns (0:
+// the default 0.1 s), written to the context's device word.
+constexpr unsigned long long kDefaultSpinNs = 100000000ull;
+feti_status set_spin_budget(feti_ctx* ctx, uint64_t ns) {
+  const unsigned long long v = ns ? (unsigned long long)ns : kDefaultSpinNs;
+  FETI_CK(cudaMemcpyAsync(ctx->d_spin, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  return FETI_OK;
+}
+
 feti_status build_decomposition(feti_ctx* ctx) {
   const int N = ctx->N, E = ctx->E, P = ctx->P;
   ctx->af = ctx->opt.method == FETI_ALL_FLOATING;
@@ -965,6 +978,8 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(dev_alloc(ctx, &ctx->d_sc, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_status, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_zero, 1));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_spin, 1));
+  FETI_TRY(set_spin_budget(ctx, ctx->opt.spin_timeout_ns));
   FETI_CK(cudaMemsetAsync(ctx->d_zero, 0, sizeof(int), ctx->stream));
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   if (ctx->cd > 0) {
@@ -1001,6 +1016,19 @@ feti_status check_status(feti_ctx* ctx, const char* where) {
   if (s == feti::DEV_INVERTED) return fail(ctx, FETI_ERR_ELEMENT_INVERTED, std::string(where) + ": inverted element");
   if (s != 0) return fail(ctx, FETI_ERR_CUDA, std::string(where) + ": device status " + std::to_string(s));
   return FETI_OK;
+}
+
+// A bounded device wait that ran out (flag set by the kernel): FETI_ERR_TIMEOUT,
+// flag cleared so the context stays usable.
+feti_status check_wait_flag(feti_ctx* ctx, int* d_flag, const char* where) {
+  if (!d_flag) return FETI_OK;
+  int herr = 0;
+  FETI_CK(cudaMemcpyAsync(&herr, d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  if (!herr) return FETI_OK;
+  FETI_CK(cudaMemsetAsync(d_flag, 0, sizeof(int), ctx->stream));
+  FETI_CK(cudaStreamSynchronize(ctx->stream));
+  return fail(ctx, FETI_ERR_TIMEOUT, std::string(where) + ": a bounded wait ran out");
 }
 
 // Element matrices at U (device pointer or NULL), local assembly, loads.
@@ -1163,7 +1191,7 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
   if (f32 && ctx->sym32[which] == 64 && !ctx->opt.per_subdomain) {
     feti::launch_symv2_f32(ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which], ctx->d_lay, which,
                            which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps,
-                           done, ctx->d_sym_err, ctx->stream);
+                           done, ctx->d_sym_err, ctx->d_spin, ctx->stream);
     return;
   }
   if (f32 && ctx->sym32[which] && !ctx->opt.per_subdomain) {
@@ -1282,12 +1310,13 @@ feti_status autotune(feti_ctx* ctx) {
         {  // streamed variant (shared-memory ring), kept only if no bounded wait ran out
           FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
           feti::launch_symv2_f32(ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
-                                 ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, ctx->d_sym_err, st);
+                                 ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, ctx->d_sym_err,
+                                 ctx->d_spin, st);
           FETI_CK(cudaEventRecord(e0, st));
           for (int rep = 0; rep < 3; ++rep)
             feti::launch_symv2_f32(ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
                                    ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps, ctx->d_zero, ctx->d_sym_err,
-                                   st);
+                                   ctx->d_spin, st);
           FETI_CK(cudaEventRecord(e1, st));
           FETI_CK(cudaEventSynchronize(e1));
           float ms = 0.f;
@@ -1523,6 +1552,7 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
     rep->n_lambda = ctx->n_lambda;
     rep->coarse_dim = ctx->cd;
   }
+  FETI_TRY(check_wait_flag(ctx, ctx->d_sym_err, "streamed symmetric local apply"));
   if (breakdown) return fail(ctx, FETI_ERR_BREAKDOWN, "PCG breakdown");
   // recovery: gamma = (G^T G)^-1 G^T (F lambda - d~), u_i = K^+(f_i - B_i^T lambda) + R_i gamma_i
   apply_F(ctx, ctx->d_lam, ctx->d_q, nullptr, false, zero);
@@ -1536,15 +1566,7 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_x2, ctx->d_x, st);
   if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
   FETI_CK(cudaGetLastError());
-  if (ctx->d_sym_err && (ctx->sym32[0] == 64 || ctx->sym32[1] == 64)) {
-    int herr = 0;
-    FETI_CK(cudaMemcpyAsync(&herr, ctx->d_sym_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    FETI_CK(cudaStreamSynchronize(st));
-    if (herr) {
-      FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
-      return fail(ctx, FETI_ERR_TIMEOUT, "streamed symmetric local apply: a bounded wait ran out");
-    }
-  }
+  FETI_TRY(check_wait_flag(ctx, ctx->d_sym_err, "streamed symmetric local apply"));
   if (!conv) return fail(ctx, FETI_ERR_NOT_CONVERGED, "PCG reached maxit");
   return FETI_OK;
 }
@@ -1639,11 +1661,11 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
             if (ntc >= 3 && variant != ntc - 2) continue;
             FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
             feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,
-                                 variant, ctx->d_tmap[w], st);
+                                 variant, ctx->d_tmap[w], ctx->d_spin, st);
             FETI_CK(cudaEventRecord(e0, st));
             for (int rep = 0; rep < 3; ++rep)
               feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero,
-                                   ctx->d_tc_err, variant, ctx->d_tmap[w], st);
+                                   ctx->d_tc_err, variant, ctx->d_tmap[w], ctx->d_spin, st);
             FETI_CK(cudaEventRecord(e1, st));
             FETI_CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -1713,7 +1735,7 @@ void local_apply_m(feti_ctx* ctx, int which, int nrhs, const double* x, const do
   if (f32 && ctx->tc_m[which])
     feti::launch_gemm_tc(ctx->tab[which][2], ctx->d_lay, which, static_cast<const float*>(M), nrhs,
                          static_cast<const float*>(v), ctx->dm_loc, done, ctx->d_tc_err, ctx->tc_m[which],
-                         ctx->d_tmap[which], st);
+                         ctx->d_tmap[which], ctx->d_spin, st);
   else
     feti::launch_gemm_loc(cfg, ctx->d_lay, which, M, f32 ? 1 : 0, nrhs, v, ctx->dm_loc, ctx->max_nb, done, st);
 }
@@ -1887,6 +1909,7 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
     rep->n_lambda = ctx->n_lambda;
     rep->coarse_dim = ctx->cd;
   }
+  FETI_TRY(check_wait_flag(ctx, ctx->d_tc_err, "tensor-core block GEMM"));
   if (breakdown) return fail(ctx, FETI_ERR_BREAKDOWN, "PCG breakdown (block form)");
   // recovery, one right-hand side at a time (single-RHS kernels on column k)
   const size_t n3 = 3 * (size_t)ctx->N;
@@ -2390,7 +2413,7 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
       FETI_CK(cudaEventRecordWithFlags(ctx->dualm_events[2 + 2 * i], st, cudaEventRecordExternal));
       if (f32 && ctx->tc_m[0])
         feti::launch_gemm_tc(ctx->tab[0][2], ctx->d_lay, 0, ctx->d_F32, nrhs, static_cast<const float*>(vl), ctx->dm_loc,
-                             zero, ctx->d_tc_err, ctx->tc_m[0], ctx->d_tmap[0], st);
+                             zero, ctx->d_tc_err, ctx->tc_m[0], ctx->d_tmap[0], ctx->d_spin, st);
       else
         feti::launch_gemm_loc(cfg, ctx->d_lay, 0, f32 ? (const void*)ctx->d_F32 : (const void*)ctx->d_F, f32 ? 1 : 0,
                               nrhs, vl, ctx->dm_loc, ctx->max_nb, zero, st);
@@ -2567,6 +2590,13 @@ feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv
 }
 
 const char* feti_last_error(const feti_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+feti_status feti_set_spin_timeout(feti_ctx* ctx, uint64_t spin_timeout_ns) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  if (!ctx->d_spin) return fail(ctx, FETI_ERR_STATE, "context not set up");
+  ctx->opt.spin_timeout_ns = spin_timeout_ns;
+  return set_spin_budget(ctx, spin_timeout_ns);
+}
 
 void feti_destroy(feti_ctx* ctx) {
   if (!ctx) return;

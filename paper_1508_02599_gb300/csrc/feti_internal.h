@@ -162,10 +162,11 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
                      cudaStream_t st);
 // The same product with each warp streaming its panel through shared memory
-// (cp.async.bulk row segments, bounded waits; a timeout sets *err).
+// (cp.async.bulk row segments, bounded waits; a timeout sets *err).  spin_ns:
+// device word, the main-loop wait budget in nanoseconds.
 void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
                       const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
-                      int* err, cudaStream_t st);
+                      int* err, const unsigned long long* spin_ns, cudaStream_t st);
 void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // FP32 signed gather (input of the FP32 apply).
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);
@@ -279,8 +280,11 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // 2 bulk-copy staged, 3 tensor-map (TMA) fed, 4 / 5 warp-specialised
 // TMA-fed with 3 / 2 stages; tmaps = one CUtensorMap per subdomain for the
 // matrix `which` (variants 3-5).
+// spin_ns: device word, the main-loop wait budget in nanoseconds of the
+// warp-specialised variants (4, 5); their drain waits keep a fixed budget.
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
-                    double* y, const int* done, int* err, int variant, const void* tmaps, cudaStream_t st);
+                    double* y, const int* done, int* err, int variant, const void* tmaps,
+                    const unsigned long long* spin_ns, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
 // c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).

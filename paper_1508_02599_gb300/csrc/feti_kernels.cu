@@ -714,7 +714,10 @@ __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
 // loads in registers (16 row accumulators per lane: half-warp h takes rows
 // 2j + h).  Warps are independent (no CTA barrier in the loop); all waits are
 // bounded, and a warp whose wait runs out flags *err, issues nothing more and
-// waits (bounded) for its copies in flight before it returns.
+// waits (bounded) for its copies in flight before it returns.  The main-loop
+// waits give up after *spin_ns nanoseconds (global timer; the context's spin
+// timeout); the drain waits keep a fixed budget of 2e8 clock cycles, so every
+// copy issued has landed before the warp leaves.
 constexpr int SYM_TW = 64;  // tile width (floats)
 constexpr int SYM_NS = 3;   // stages per warp
 constexpr int SYM_WPC = 4;  // warps per CTA
@@ -735,13 +738,26 @@ __device__ __forceinline__ bool sym_wait(uint64_t* b, uint32_t par) {
     if (clock64() - t0 > 200000000LL) return false;
   return true;
 }
+__device__ __forceinline__ unsigned long long sym_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// main-loop wait with a caller-set budget in nanoseconds (global timer)
+__device__ __forceinline__ bool sym_wait_ns(uint64_t* b, uint32_t par, unsigned long long budget_ns) {
+  const unsigned long long t0 = sym_gtimer();
+  while (!sym_try(b, par))
+    if (sym_gtimer() - t0 > budget_ns) return false;
+  return true;
+}
 
 __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __restrict__ wsub,
                                                            const int32_t* __restrict__ wpanel, int n_warps,
                                                            const SubLayout* __restrict__ lay, int which,
                                                            const float* __restrict__ M, const float* __restrict__ vloc,
                                                            double* __restrict__ y, float* __restrict__ part,
-                                                           const int* __restrict__ done, int* __restrict__ err) {
+                                                           const int* __restrict__ done, int* __restrict__ err,
+                                                           const unsigned long long* __restrict__ spin_ns) {
   if (*done) return;
   extern __shared__ __align__(128) unsigned char sym_smem[];
   __shared__ uint64_t full[SYM_WPC][SYM_NS];
@@ -789,9 +805,10 @@ __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __res
   for (int j = 0; j < 16; ++j) acc[j] = 0.f;
   bool bad = false;
   int t = 0;
+  const unsigned long long budget = *spin_ns;
   for (; t < nt; ++t) {
     const int st = t % SYM_NS;
-    if (!sym_wait(&fb[st], (uint32_t)(t / SYM_NS) & 1u)) bad = true;
+    if (!sym_wait_ns(&fb[st], (uint32_t)(t / SYM_NS) & 1u, budget)) bad = true;
     bad = __any_sync(0xffffffffu, bad);
     if (bad) break;
     const int c = t * SYM_TW + 4 * l16;
@@ -1487,7 +1504,7 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
 
 void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
                       const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
-                      int* err, cudaStream_t st) {
+                      int* err, const unsigned long long* spin_ns, cudaStream_t st) {
   const size_t smem = (size_t)SYM_WPC * SYM_NS * SYM_STAGE;
   static bool attr = false;
   if (!attr) {
@@ -1495,7 +1512,8 @@ void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, c
     attr = true;
   }
   const int blocks = (n_warps + SYM_WPC - 1) / SYM_WPC;
-  k_symv2_f32<<<blocks, SYM_WPC * 32, smem, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done, err);
+  k_symv2_f32<<<blocks, SYM_WPC * 32, smem, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done, err,
+                                                  spin_ns);
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 
