@@ -378,6 +378,8 @@ def config_problem(name: str) -> Problem:
         return cylinder_problem(24, 96, 48, (4, 16, 4), material=hgo_material(), pressure=16.0)
     if name == "jcyl32":          # 274,560 nodes, 1024 uneven subdomains
         return jittered_cylinder_problem(32, 128, 64, 1024, 1508, 2599)
+    if name == "jcyl16":          # 35,904 nodes, 128 uneven subdomains (jcyl32's subdomain sizes)
+        return jittered_cylinder_problem(16, 64, 32, 128, 1510, 2601)
     if name == "jcyl48":          # 912,576 nodes, 4096 uneven subdomains
         return jittered_cylinder_problem(48, 192, 96, 4096, 1509, 2600)
     raise KeyError(name)

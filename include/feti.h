@@ -44,7 +44,8 @@ typedef enum {
   FETI_ERR_TIMEOUT = 9,          /* a bounded device wait gave up */
   FETI_ERR_OOM = 10,             /* device allocation failed */
   FETI_ERR_CUDA = 11,            /* any other CUDA runtime error */
-  FETI_ERR_STATE = 12            /* call made in the wrong order */
+  FETI_ERR_STATE = 12,           /* call made in the wrong order */
+  FETI_ERR_IO = 13               /* checkpoint file not writable, unreadable or corrupt */
 } feti_status;
 
 enum { FETI_LINEAR_ISO = 0, FETI_HGO_TWO_FIBRE = 1 };          /* feti_material.kind */
@@ -53,8 +54,13 @@ enum { FETI_PREC_IDENTITY = 0, FETI_PREC_LUMPED = 1, FETI_PREC_DIRICHLET = 2 };
 /* feti_options.precision: FETI_FP64 -- every operator in FP64; FETI_MIXED --
  * FP32 copies of the dense local operators F_i and S_i inside the PCG,
  * FP64 vectors, dot products, projection, coarse solve and an FP64 outer
- * residual (iterative refinement on the dual problem). */
-enum { FETI_FP64 = 0, FETI_MIXED = 1 };
+ * residual (iterative refinement on the dual problem);
+ * FETI_MIXED_F32FACTOR -- as FETI_MIXED, but the local factorizations
+ * themselves run in FP32 (F_i and S_i come out of the FP32 elimination), and
+ * every FP64-accurate use of K_i^+ (dual right-hand side, outer residual,
+ * recovery) is an FP32 triangular solve refined against the FP64 element
+ * matrices (mixed-precision iterative refinement); linear solves only. */
+enum { FETI_FP64 = 0, FETI_MIXED = 1, FETI_MIXED_F32FACTOR = 2 };
 
 /* Mesh T_N of Sec. 3.2 (P1 tetrahedra) and its non-overlapping decomposition
  * (Sec. 4, Eq. decomposition).  coords: [n_nodes*3] reference coordinates;
@@ -105,7 +111,7 @@ typedef struct {
 typedef struct {
   int32_t method;      /* FETI_CLASSICAL or FETI_ALL_FLOATING */
   int32_t precond;     /* FETI_PREC_* */
-  int32_t precision;   /* FETI_FP64 */
+  int32_t precision;   /* FETI_FP64, FETI_MIXED or FETI_MIXED_F32FACTOR */
   double tol;          /* stop when ||P r_k||_2 <= tol ||P r_0||_2 */
   int32_t maxit;       /* PCG iteration limit */
   int32_t chunk;       /* PCG iterations per CUDA-graph launch (0: default 16) */
@@ -127,10 +133,13 @@ typedef struct {
   int32_t symmetric;       /* FP32 single-vector local applies: 0 = the autotuner picks the
                               symmetric kernel (reads only the lower block-triangle of F_i / S_i)
                               when it is faster, 1 = full rows only, 2 = symmetric always
-                              (fastest variant), 3 = symmetric, streamed through shared memory */
+                              (fastest variant), 3 = symmetric, streamed through shared memory,
+                              4 = symmetric, one CTA per subdomain (transposed partial sums
+                              reduced in shared memory, no second pass) */
   uint64_t spin_timeout_ns; /* budget of each main-loop mbarrier wait of the streamed symmetric
-                               apply and the warp-specialised tensor-core block GEMM, in ns of the
-                               GPU's global timer (0: 0.1 s).  A wait that runs out stops the
+                               apply and the warp-specialised tensor-core block GEMM, in ns,
+                               counted as SM clock cycles at the device's maximum clock
+                               (0: 0.1 s).  A wait that runs out stops the
                                kernel's pipeline, waits for its copies and tensor-core products in
                                flight (those drain waits keep a fixed budget of 2e8 clock cycles),
                                releases tensor memory and flags the call, which then returns
@@ -182,6 +191,42 @@ feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nr
  * Newton with one FETI solve per step until ||R|| <= newton_tol ||tau f_ext||.
  * Requires FETI_HGO_TWO_FIBRE.  Writes U [n_nodes*3] like feti_solve. */
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report);
+
+/* Load steps first_step .. last_step (1 <= first_step <= last_step <=
+ * n_load_steps) of the load-stepped Newton method of feti_newton, starting
+ * from U_start [n_nodes*3] -- the displacement after load step first_step - 1
+ * (NULL: zero, the unloaded state; first_step = 1 with NULL is feti_newton).
+ * U_start and u_out are host or device pointers as u_on_device says.  The
+ * continuation of a long run from a checkpoint (Sec. 5.3 runs hundreds of
+ * load steps).  pcg_per_step / newton_per_step (host arrays of
+ * last_step - first_step + 1 entries, may be NULL) receive the PCG iterations
+ * (summed over the FETI solves of the step) and the Newton iterations each
+ * load step took. */
+feti_status feti_newton_steps(feti_ctx* ctx, const double* U_start, int32_t first_step, int32_t last_step,
+                              double* u_out, int32_t u_on_device, int32_t* pcg_per_step, int32_t* newton_per_step,
+                              feti_report* report);
+
+/* Checkpoint of a load-stepped run: the state after load step `step` of
+ * n_load_steps, tau = step / n_load_steps (Eq. loadStepping), and U [n_dofs]
+ * (host array).  Binary file: magic "FETICKP1", n_dofs (int64), step,
+ * n_load_steps (int32), tau (double), U (n_dofs doubles), FNV-1a 64-bit hash
+ * of all preceding bytes; native byte order.  Written to "<path>.tmp" and
+ * renamed over path.  Host-only (no CUDA call, no context); FETI_ERR_IO when the
+ * file cannot be written. */
+typedef struct {
+  int64_t n_dofs;
+  int32_t step;
+  int32_t n_load_steps;
+  double tau;
+} feti_checkpoint_info;
+feti_status feti_checkpoint_write(const char* path, const double* U, int64_t n_dofs, int32_t step,
+                                  int32_t n_load_steps, double tau);
+/* Reads a checkpoint: header into *info (may be NULL) and, with U != NULL,
+ * the displacement into U (capacity doubles; too small: FETI_ERR_INVALID_ARG).
+ * U == NULL reads the header only.  FETI_ERR_IO for a missing, truncated or
+ * corrupt file (bad magic, sizes or hash); U is written only after the hash
+ * matched. */
+feti_status feti_checkpoint_read(const char* path, double* U, int64_t capacity, feti_checkpoint_info* info);
 
 /* Element level of Sec. 3.2 (Eq. Tangent and the residual K(U)): for every
  * tetrahedron the 12x12 tangent K_e (row-major, local DOF 3 * vertex +
@@ -282,16 +327,28 @@ feti_status feti_element_stats(const feti_ctx* ctx, double* elem_ms, double* ele
  * preconditioner apply, out[4..7] the same for the FP32 copies (rows per warp
  * step -G, rows 32 = symmetric kernel on 32-row panels, load groups of
  * G % 100 rows with an L2 prefetch G / 100 tiles ahead; G = 64: panels
- * streamed through shared memory), out[8..11]
+ * streamed through shared memory; G = 300 + g: one CTA per subdomain, load
+ * groups of g rows), out[8..11]
  * the FP32 block-form GEMMs (rows per warp step 0 / -1 / -2 / -3 / -4 =
  * tensor-core kernel with register-staged / bulk-copy staged / tensor-map fed
  * operands / warp-specialised 3-stage / 2-stage; both entries -1 = block form
  * not tuned yet). */
 feti_status feti_get_schedule(const feti_ctx* ctx, int32_t out[12]);
 
-/* Sets the main-loop wait budget of feti_options.spin_timeout_ns (ns; 0 =
- * 0.1 s) for the later calls on this context; captured graphs read it at
- * every launch.  Host blocking: waits for the context's stream. */
+/* FETI_MIXED_F32FACTOR: the number of FP64 refinement corrections each
+ * application of K_i^+ takes (chosen at setup: corrections are added while
+ * the largest relative residual ||g - K_rr x|| / ||g|| over the subdomains,
+ * on a fixed pseudo-random g, still halves and exceeds 1e-14; at most 12) and
+ * that residual.  Zeros for the other forms or before setup. */
+feti_status feti_get_refinement(const feti_ctx* ctx, int32_t* steps, double* residual);
+
+/* Sets the main-loop wait budget of feti_options.spin_timeout_ns for the
+ * later calls on this context, in ns taken literally (100000000 = the default
+ * 0.1 s); a budget below one clock cycle, e.g. 0, makes every main-loop wait
+ * give up at its first check (the pipelines then always stop, drain and
+ * report FETI_ERR_TIMEOUT: a way to exercise that path).  Captured graphs
+ * read the budget at every launch.  Host blocking: waits for the context's
+ * stream. */
 feti_status feti_set_spin_timeout(feti_ctx* ctx, uint64_t spin_timeout_ns);
 
 const char* feti_last_error(const feti_ctx* ctx);

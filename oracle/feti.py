@@ -541,3 +541,40 @@ def newton_solve(prob, method: str = ALL_FLOATING, precond: str = "dirichlet",
             its.append((rel, res.iterations, a))
         log.append(its)
     return U, log
+
+
+def monolithic_newton(prob, n_load_steps: int = 1, follower: bool = True, tol: float = 1e-10,
+                      maxit: int = 30):
+    """Load-stepped Newton on the assembled global system (the plain definition).
+
+    tau = s / n_load_steps (Eq. loadStepping); per step, Newton on
+    R(U) = f_int(U) - tau f_ext(U) over the non-Dirichlet DOFs with the
+    assembled element tangents (Sec. 3.2, Eq. NewtonRecursion) and a sparse
+    direct solve, until ||R|| <= tol ||tau f_ext|| or maxit iterations (the
+    follower pressure's load stiffness is left out, as in the paper, so the
+    convergence is linear rather than quadratic in follower mode).  Returns
+    (U, history) with the relative residuals of every step.
+    """
+    import scipy.sparse.linalg as spla
+    N = prob.n_nodes
+    U = np.zeros(3 * N)
+    free = np.ones(3 * N, bool)
+    free[prob.dir_dof] = False
+    idx = np.nonzero(free)[0]
+    hist = []
+    for s in range(1, n_load_steps + 1):
+        tau = s / n_load_steps
+        h = []
+        for _ in range(maxit):
+            Ke, fint = fem.element_matrices(prob, U.reshape(-1, 3))
+            fext = fem.load_vector(prob, U.reshape(-1, 3), follower)
+            R = fem.internal_force_global(prob, fint) - tau * fext
+            h.append(np.linalg.norm(R[free]) / np.linalg.norm(tau * fext[free]))
+            if h[-1] <= tol:
+                break
+            K = fem.assemble_global(prob, Ke)
+            dU = np.zeros(3 * N)
+            dU[idx] = spla.spsolve(K[idx][:, idx].tocsc(), -R[idx])
+            U = U + dU
+        hist.append(h)
+    return U, hist

@@ -10,12 +10,12 @@ LIB_PATH = os.path.join(HERE, "libfeti.so")
 FETI_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PARTITION", 3: "ELEMENT_INVERTED", 4: "LOCAL_SINGULAR",
                 5: "KERNEL_DETECT", 6: "BREAKDOWN", 7: "NOT_CONVERGED", 8: "NEWTON_DIVERGED", 9: "TIMEOUT",
-                10: "OOM", 11: "CUDA", 12: "STATE"}
+                10: "OOM", 11: "CUDA", 12: "STATE", 13: "IO"}
 
 LINEAR_ISO, HGO_TWO_FIBRE = 0, 1
 CLASSICAL, ALL_FLOATING = 0, 1
 PREC_IDENTITY, PREC_LUMPED, PREC_DIRICHLET = 0, 1, 2
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_F32FACTOR = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -45,6 +45,10 @@ class FetiOptions(C.Structure):
                 ("per_subdomain", C.c_int32), ("symmetric", C.c_int32), ("spin_timeout_ns", C.c_uint64)]
 
 
+class FetiCheckpointInfo(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("step", C.c_int32), ("n_load_steps", C.c_int32), ("tau", C.c_double)]
+
+
 class FetiReport(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
                 ("cond_est", C.c_double), ("t_setup_ms", C.c_double), ("t_pcg_ms", C.c_double),
@@ -52,9 +56,10 @@ class FetiReport(C.Structure):
                 ("newton_iters", C.c_int32), ("newton_rel_res", C.c_double), ("outer_iterations", C.c_int32)]
 
 
-EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
+EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_newton_steps",
+           "feti_checkpoint_write", "feti_checkpoint_read", "feti_elements", "feti_get_sizes", "feti_get_index_maps",
            "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_element_stats", "feti_get_schedule",
-           "feti_set_spin_timeout", "feti_last_error",
+           "feti_set_spin_timeout", "feti_get_refinement", "feti_last_error",
            "feti_destroy"]
 
 _lib = None
@@ -74,6 +79,9 @@ def load(path: str = LIB_PATH):
                                 C.POINTER(FetiOptions), vp]
     lib.feti_solve.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_newton.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
+    lib.feti_newton_steps.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(FetiReport)]
+    lib.feti_checkpoint_write.argtypes = [C.c_char_p, vp, C.c_int64, C.c_int32, C.c_int32, C.c_double]
+    lib.feti_checkpoint_read.argtypes = [C.c_char_p, vp, C.c_int64, C.POINTER(FetiCheckpointInfo)]
     lib.feti_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.feti_elements.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32]
     lib.feti_get_index_maps.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -87,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.feti_element_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.feti_get_schedule.argtypes = [vp, vp]
     lib.feti_set_spin_timeout.argtypes = [vp, C.c_uint64]
+    lib.feti_get_refinement.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.feti_last_error.argtypes = [vp]
     lib.feti_last_error.restype = C.c_char_p
     lib.feti_destroy.argtypes = [vp]

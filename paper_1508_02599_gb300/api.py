@@ -66,13 +66,13 @@ class FetiSolver:
         bc = L.FetiBC(dd.size, _ptr(dd, C.c_int32), _ptr(dv, C.c_double), pt.shape[0], _ptr(pt, C.c_int32),
                       _ptr(po, C.c_int32), float(prob.pressure), tt.shape[0], _ptr(tt, C.c_int32),
                       _ptr(to, C.c_int32), (C.c_double * 3)(*[float(v) for v in prob.traction]))
-        prec = {"fp64": L.FP64, "mixed": L.MIXED}[precision]
+        prec = {"fp64": L.FP64, "mixed": L.MIXED, "mixed_f32factor": L.MIXED_F32FACTOR}[precision]
         opt = L.FetiOptions(_METHODS[method], _PRECONDS[precond], prec, float(tol), int(maxit), int(chunk),
                             int(bool(follower)), int(n_load_steps), float(newton_tol), int(newton_maxit),
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
-                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3}[symmetric],
+                            int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
                             int(spin_timeout_ns))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
@@ -149,8 +149,15 @@ class FetiSolver:
     def prepare(self):
         self._check(self._lib.feti_prepare(self._ctx))
 
+    def refinement(self) -> dict:
+        """FP32-factor form: refinement corrections per K^+ application and the residual they reach."""
+        n, r = C.c_int32(), C.c_double()
+        self._check(self._lib.feti_get_refinement(self._ctx, C.byref(n), C.byref(r)))
+        return {"steps": n.value, "residual": r.value}
+
     def set_spin_timeout(self, ns: int):
-        """Main-loop wait budget (ns, 0 = default) of the kernels with bounded mbarrier waits."""
+        """Main-loop wait budget (ns, literal; 100_000_000 = the default; 0 = give up at once) of the
+        kernels with bounded mbarrier waits."""
         self._check(self._lib.feti_set_spin_timeout(self._ctx, int(ns)))
 
     def _report(self, rep: L.FetiReport) -> dict:
@@ -215,6 +222,20 @@ class FetiSolver:
             self._check(self._lib.feti_newton(self._ctx, C.c_void_p(out.data_ptr()), 1, C.byref(rep)))
         return u, self._report(rep)
 
+    def newton_steps(self, first: int, last: int, U_start=None):
+        """Load steps first..last of the load-stepped Newton method from U_start (host array
+        [3N] or None = unloaded); returns (U, report, pcg_per_step, newton_per_step)."""
+        n = last - first + 1
+        pcg = np.zeros(max(n, 1), np.int32)
+        nwt = np.zeros(max(n, 1), np.int32)
+        u = np.empty(3 * self.n_nodes, np.float64)
+        u0 = None if U_start is None else np.ascontiguousarray(U_start, dtype=np.float64).ravel()
+        rep = L.FetiReport()
+        self._check(self._lib.feti_newton_steps(self._ctx, None if u0 is None else u0.ctypes.data, int(first),
+                                                int(last), u.ctypes.data, 0, pcg.ctypes.data, nwt.ctypes.data,
+                                                C.byref(rep)))
+        return u, self._report(rep), pcg[:n], nwt[:n]
+
     def dual_apply(self, v, q, z, n_apply: int) -> float:
         """q = F v, z = M^-1 q, n_apply times on device tensors; returns ms per apply."""
         ms = C.c_double()
@@ -238,3 +259,27 @@ class FetiSolver:
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         self._check(self._lib.feti_kernel_stats(self._ctx, C.byref(a), C.byref(b), C.byref(c)))
         return {"gemv_ms": a.value, "gemv_bytes": b.value, "gemv_flops": c.value}
+
+
+def checkpoint_write(path: str, U, step: int, n_load_steps: int, tau: float) -> None:
+    """feti_checkpoint_write: the state (U, step, tau) of a load-stepped run (host-only call)."""
+    lib = L.load()
+    u = np.ascontiguousarray(U, dtype=np.float64).ravel()
+    st = lib.feti_checkpoint_write(str(path).encode(), u.ctypes.data, u.size, int(step), int(n_load_steps),
+                                   float(tau))
+    if st != L.FETI_OK:
+        raise FetiError(st, f"checkpoint_write {path}")
+
+
+def checkpoint_read(path: str):
+    """feti_checkpoint_read: returns (U, step, n_load_steps, tau); raises FetiError on a bad file."""
+    lib = L.load()
+    info = L.FetiCheckpointInfo()
+    st = lib.feti_checkpoint_read(str(path).encode(), None, 0, C.byref(info))
+    if st != L.FETI_OK:
+        raise FetiError(st, f"checkpoint_read {path}")
+    u = np.empty(info.n_dofs, np.float64)
+    st = lib.feti_checkpoint_read(str(path).encode(), u.ctypes.data, u.size, C.byref(info))
+    if st != L.FETI_OK:
+        raise FetiError(st, f"checkpoint_read {path}")
+    return u, info.step, info.n_load_steps, info.tau

@@ -1,0 +1,303 @@
+// FP32 local factorizations with FP64 iterative refinement of K^+.
+//
+// In the FETI_MIXED_F32FACTOR form the dense local elimination of Sec. 4.3 /
+// 4.4 (K_rr = L L^T with the interior columns first, the Schur complement S_i
+// as its trailing block, F_i = (S_i[b',b'])^-1 through an identity
+// augmentation) runs in FP32 (the batched Cholesky kernels instantiated for
+// float).  The FP32 explicit operators F_i and S_i drive the inner PCG as in
+// the mixed form; every FP64-accurate use of the generalized inverse (the
+// dual right-hand side d~, the outer dual residual, the recovery of u_i)
+// goes through K^+ refined in FP64 (classical mixed-precision iterative
+// refinement, Moler 1967):
+//   x = L^-T L^-1 g (FP32 sweeps);  repeat: r = g - K_rr x (FP64, from the
+//   element matrices);  x += L^-T L^-1 r,
+// with zero on the fixing DOFs, which is K^+ g of the fixing-DOF generalized
+// inverse of Sec. 5.2 ("regularization by fixing nodes").
+#include "feti_internal.h"
+
+#include <algorithm>
+
+namespace feti {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ float f32_warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32 workspace -> padded FP32 operator copies (row stride padded to 4):
+// which 0: the preconditioner block S_i (trailing block after the interior
+// elimination), which 1: F_i = minus the eliminated augmentation block.
+__global__ void k_extract32(const SubLayout* __restrict__ lay, int which, const float* __restrict__ Abase,
+                            float* __restrict__ out) {
+  const SubLayout L = lay[blockIdx.x];
+  const float* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  if (which == 0) {
+    const int nb = L.nbp + L.k, ldo = (nb + 3) & ~3;
+    float* S = out + L.soff32;
+    for (int idx = threadIdx.x; idx < nb * ldo; idx += blockDim.x) {
+      const int i = idx / ldo, j = idx % ldo;
+      const int ii = max(i, j), jj = min(i, j);
+      S[idx] = j < nb ? A[(size_t)(L.nI + ii) * ld + L.nI + jj] : 0.0f;
+    }
+  } else {
+    const int m = L.nbp, ldo = (m + 3) & ~3;
+    float* F = out + L.foff32;
+    for (int idx = threadIdx.x; idx < m * ldo; idx += blockDim.x) {
+      const int i = idx / ldo, j = idx % ldo;
+      const int ii = max(i, j), jj = min(i, j);
+      F[idx] = j < m ? -A[(size_t)(L.n + ii) * ld + L.n + jj] : 0.0f;
+    }
+  }
+}
+
+// Padded FP32 copy -> lower block-triangle panels of the symmetric apply
+// (which 0: F_i, which 1: preconditioner block; the layout of k_symv_f32).
+__global__ void k_pad_to_sym(const SubLayout* __restrict__ lay, int which, const float* __restrict__ src,
+                             float* __restrict__ dst) {
+  const SubLayout L = lay[blockIdx.x];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int lds = (m + 3) & ~3;
+  const float* a = src + (which == 0 ? L.foff32 : L.soff32);
+  float* b = dst + (which == 0 ? L.fsym32 : L.ssym32);
+  constexpr int PH = kSymPH;
+  const int nP = (m + PH - 1) / PH;
+  for (int I = 0; I < nP; ++I) {
+    const int w = PH * (I + 1);
+    float* bp = b + (size_t)(PH * PH / 2) * I * (I + 1);
+    for (int idx = threadIdx.x; idx < PH * w; idx += blockDim.x) {
+      const int r = PH * I + idx / w, c = idx % w;
+      bp[idx] = (r < m && c < m) ? a[(size_t)r * lds + c] : 0.0f;
+    }
+  }
+}
+
+// x (+)= L^-T L^-1 r on the rows [0, nr) of every subdomain, nr = nI + nbp,
+// with L the FP32 Cholesky factor of K_rr in the leading block of the FP32
+// workspace: one CTA per subdomain, the right-hand side and the solution in
+// shared memory (FP32), 32-row blocks.  Forward: the warps form the dot
+// products of the block's rows with the solved part (one warp per row, lanes
+// striding the columns), one warp solves the 32 x 32 diagonal triangle with
+// shuffles.  Backward: one warp solves the transposed diagonal triangle, then
+// every thread subtracts the block's contributions from its columns of the
+// unsolved part.  init: x = correction, and zero on the fixing DOFs; else
+// x += correction (the fixing DOFs keep their value).
+__global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
+                                                  const double* __restrict__ rbase, double* __restrict__ xbase,
+                                                  int init) {
+  extern __shared__ float ys[];
+  const SubLayout L = lay[blockIdx.x];
+  const float* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  const double* r = rbase + L.voff;
+  double* x = xbase + L.voff;
+  const int nr = L.nI + L.nbp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kT / 32;
+  __shared__ float D[32][33];
+  __shared__ float t[32];
+  __shared__ float xs[32];
+  for (int i = tid; i < nr; i += kT) ys[i] = (float)r[i];
+  if (init)
+    for (int i = nr + tid; i < L.n; i += kT) x[i] = 0.0;
+  __syncthreads();
+  for (int I0 = 0; I0 < nr; I0 += 32) {
+    const int nb = min(32, nr - I0);
+    for (int idx = tid; idx < 32 * 32; idx += kT) {
+      const int rr = idx >> 5, c = idx & 31;
+      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
+    }
+    {
+      // warp w: rows w, w + 8, w + 16, w + 24 of the block together, so each
+      // lane keeps four independent loads in flight per column step
+      const float* rp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rp[q] = A + (size_t)(I0 + min(warp + kW * q, nb - 1)) * ld;
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+      for (int j = lane; j < I0; j += 32) {
+        const float yv = ys[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += rp[q][j] * yv;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float v = f32_warp_sum(acc[q]);
+        if (lane == 0 && warp + kW * q < nb) t[warp + kW * q] = v;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float b = lane < nb ? ys[I0 + lane] - t[lane] : 0.0f;
+      float xv = 0.0f;
+      for (int c = 0; c < nb; ++c) {
+        if (lane == c) xv = b / D[c][c];
+        const float xc = __shfl_sync(0xffffffffu, xv, c);
+        if (lane > c) b -= D[lane][c] * xc;
+      }
+      if (lane < nb) ys[I0 + lane] = xv;
+    }
+    __syncthreads();
+  }
+  for (int I0 = nr > 0 ? ((nr - 1) / 32) * 32 : -32; I0 >= 0; I0 -= 32) {
+    const int nb = min(32, nr - I0);
+    for (int idx = tid; idx < 32 * 32; idx += kT) {
+      const int rr = idx >> 5, c = idx & 31;
+      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float b = lane < nb ? ys[I0 + lane] : 0.0f;
+      float xv = 0.0f;
+      for (int c = nb - 1; c >= 0; --c) {
+        if (lane == c) xv = b / D[c][c];
+        const float xc = __shfl_sync(0xffffffffu, xv, c);
+        if (lane < c) b -= D[c][lane] * xc;
+      }
+      if (lane < nb) ys[I0 + lane] = xv;
+      xs[lane] = lane < nb ? xv : 0.0f;
+    }
+    __syncthreads();
+    // full 32-row panels: 16 independent loads per thread in flight
+    if (nb == 32) {
+      for (int j = tid; j < I0; j += kT) {
+        const float* col = A + (size_t)I0 * ld + j;
+        float acc = 0.0f;
+#pragma unroll 16
+        for (int rr = 0; rr < 32; ++rr) acc += col[(size_t)rr * ld] * xs[rr];
+        ys[j] -= acc;
+      }
+    } else {
+      for (int j = tid; j < I0; j += kT) {
+        float acc = 0.0f;
+        for (int rr = 0; rr < nb; ++rr) acc += A[(size_t)(I0 + rr) * ld + j] * xs[rr];
+        ys[j] -= acc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nr; i += kT) x[i] = (init ? 0.0 : x[i]) + (double)ys[i];
+}
+
+// r = g - K_rr x in FP64 on the rows [0, nr) (zero on the fixing rows), K_i
+// applied element by element from the FP64 element matrices: row i sums, in
+// a fixed order, the rows a of the elements listed for it (kinc: 12 e + a),
+// columns through the element's dense map (negative: an eliminated DOF).
+__global__ void __launch_bounds__(128) k_kresid(const SubLayout* __restrict__ lay, const int32_t* __restrict__ kinc_ptr,
+                                               const int32_t* __restrict__ kinc, const int32_t* __restrict__ elem_dense,
+                                               const double* __restrict__ Ke, const double* __restrict__ gbase,
+                                               const double* __restrict__ xbase, double* __restrict__ rbase) {
+  const SubLayout L = lay[blockIdx.x];
+  const int nr = L.nI + L.nbp;
+  const double* x = xbase + L.voff;
+  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+    const int gi = L.voff + i;
+    double acc = 0.0;
+    if (i < nr) {
+      acc = gbase[gi];
+      for (int q = kinc_ptr[gi]; q < kinc_ptr[gi + 1]; ++q) {
+        const int ea = kinc[q];
+        const int e = ea / 12, a = ea - 12 * e;
+        const double* ke = Ke + (size_t)e * 144 + a * 12;
+        const int32_t* dm = elem_dense + 12 * (size_t)e;
+#pragma unroll
+        for (int b = 0; b < 12; ++b) {
+          const int c = dm[b];
+          if (c >= 0) acc -= ke[b] * x[c];
+        }
+      }
+    }
+    rbase[gi] = acc;
+  }
+}
+
+// out (full local vectors) = the boundary vector loc at the boundary
+// positions [nI, n), zero on the interior.
+__global__ void k_place(const SubLayout* __restrict__ lay, const double* __restrict__ loc, double* __restrict__ out) {
+  const SubLayout L = lay[blockIdx.x];
+  for (int i = threadIdx.x; i < L.n; i += blockDim.x)
+    out[L.voff + i] = i < L.nI ? 0.0 : loc[L.boff + i - L.nI];
+}
+
+// Per subdomain: out[2 s] = sum of r_i^2, out[2 s + 1] = sum of g_i^2 over [0, nr).
+__global__ void k_sub_norm2(const SubLayout* __restrict__ lay, const double* __restrict__ r,
+                            const double* __restrict__ g, double* __restrict__ out) {
+  const SubLayout L = lay[blockIdx.x];
+  const int nr = L.nI + L.nbp;
+  __shared__ double sr[kT / 32], sg[kT / 32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nr; i += kT) {
+    a += r[L.voff + i] * r[L.voff + i];
+    b += g[L.voff + i] * g[L.voff + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = a;
+    sg[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < kT / 32; ++w) {
+      ta += sr[w];
+      tb += sg[w];
+    }
+    out[2 * blockIdx.x] = ta;
+    out[2 * blockIdx.x + 1] = tb;
+  }
+}
+
+// Deterministic test vector in [-1, 1) from a 64-bit mix of the index
+// (splitmix64 finaliser).
+__global__ void k_fill_mix(long n, double* __restrict__ x) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+}  // namespace
+
+void launch_extract32(int P, const SubLayout* lay, int which, const float* A, float* out, cudaStream_t st) {
+  k_extract32<<<P, kT, 0, st>>>(lay, which, A, out);
+}
+
+void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src, float* dst, cudaStream_t st) {
+  k_pad_to_sym<<<P, kT, 0, st>>>(lay, which, src, dst);
+}
+
+void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double* r, double* x, int init, int max_nr,
+                       cudaStream_t st) {
+  const size_t smem = (size_t)max_nr * sizeof(float);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kplus_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_kplus_corr<<<P, kT, smem, st>>>(lay, A, r, x, init);
+}
+
+void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
+                   const double* Ke, const double* g, const double* x, double* r, cudaStream_t st) {
+  k_kresid<<<P, 128, 0, st>>>(lay, kinc_ptr, kinc, elem_dense, Ke, g, x, r);
+}
+
+void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st) {
+  k_place<<<P, kT, 0, st>>>(lay, loc, out);
+}
+
+void launch_sub_norm2(int P, const SubLayout* lay, const double* r, const double* g, double* out, cudaStream_t st) {
+  k_sub_norm2<<<P, kT, 0, st>>>(lay, r, g, out);
+}
+
+void launch_fill_mix(long n, double* x, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill_mix<<<(unsigned)std::min<long>((n + kT - 1) / kT, 4096), kT, 0, st>>>(n, x);
+}
+
+}  // namespace feti

@@ -21,6 +21,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <unordered_map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -53,6 +55,14 @@ struct feti_ctx {
   feti_options opt{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the coarse-problem setup runs on a second stream, overlapping the local
+  // factorizations: stream, completion event, its own device status word and
+  // its workspace (freed once joined)
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_coarse = nullptr;
+  int* d_status2 = nullptr;
+  void* coarse_ws[2] = {nullptr, nullptr};
+  bool coarse_pending = false;
   std::string err;
   int device = -1;  // the CUDA device current at feti_create
   // static scratch of feti_dual_apply_noalloc on that device (looked up at
@@ -151,14 +161,31 @@ struct feti_ctx {
   // per matrix (0: the full-row kernel is used)
   float *d_F32s = nullptr, *d_S32s = nullptr, *d_symp = nullptr;
   int32_t *d_sym_sub[2] = {nullptr, nullptr}, *d_sym_panel[2] = {nullptr, nullptr};
+  // subdomain-per-CTA symmetric apply: subdomains by operator size, largest
+  // first, and the largest size, per matrix
+  int32_t* d_sym_order[2] = {nullptr, nullptr};
+  int sym_max_m[2] = {0, 0};
   int sym_n[2] = {0, 0};
   // 8 / 16 / 32: register-staged load groups (+ 100 x L2-prefetch distance in
   // tiles); 64: streamed through shared memory
   int sym32[2] = {0, 0};
   int* d_sym_err = nullptr;  // set by a streamed symmetric apply whose bounded wait ran out
-  // main-loop wait budget (ns) of the streamed symmetric apply and the
-  // warp-specialised tensor-core GEMM: a device word read at every launch
+  // main-loop wait budget (SM clock cycles) of the streamed symmetric apply
+  // and the warp-specialised tensor-core GEMM: a device word read at every launch
   unsigned long long* d_spin = nullptr;
+  // FP32-factor form: FP32 elimination workspace (same offsets as d_A), per
+  // local row its (element, element row) incidences for the FP64 residual of
+  // the refined K^+, refinement scratch, per-subdomain norms, and the number
+  // of refinement corrections chosen at setup (with the residual they reach)
+  float* d_A32 = nullptr;
+  int32_t *d_kinc_ptr = nullptr, *d_kinc = nullptr;
+  double *d_kr = nullptr, *d_kg = nullptr, *d_knorm = nullptr;
+  int refine_steps = 0;
+  // Newton preconditioner: relative diagonal shift of the local tangents of
+  // the last assembly (0 = exact local tangents)
+  double shift = 0.0;
+  double refine_res = 0.0;
+  int max_nr = 0;
   cudaEvent_t elem_ev[2] = {nullptr, nullptr};
   // block form (several right-hand sides)
   int m_cap = 0;  // allocated nrhs capacity of the block buffers
@@ -207,6 +234,12 @@ feti_status fail(feti_ctx* ctx, feti_status st, const std::string& msg) {
   ctx->err = msg;
   return st;
 }
+
+// Precision forms: FP32 elimination (refined K^+); FP32 operators inside the
+// PCG (both mixed forms); FP64 explicit F_i and S_i (FP64 and mixed forms).
+bool f32_factor(const feti_ctx* ctx) { return ctx->opt.precision == FETI_MIXED_F32FACTOR; }
+bool f32_ops(const feti_ctx* ctx) { return ctx->opt.precision != FETI_FP64; }
+bool fp64_ops(const feti_ctx* ctx) { return ctx->opt.precision != FETI_MIXED_F32FACTOR; }
 
 template <class T>
 feti_status dev_alloc(feti_ctx* ctx, T** out, size_t count) {
@@ -304,17 +337,43 @@ double lanczos_cond(const std::vector<double>& alpha, const std::vector<double>&
 }
 
 // ---------------------------------------------------------------------------
-// Main-loop wait budget of the kernels with bounded mbarrier waits: ns (0:
-// the default 0.1 s), written to the context's device word.
+// FETI_LOG=2 (or more) in the environment: wall time of each setup stage on
+// stderr (the stream is synchronised after each stage, only then).
+struct StageLog {
+  feti_ctx* ctx;
+  bool on;
+  std::chrono::steady_clock::time_point t;
+  explicit StageLog(feti_ctx* c) : ctx(c) {
+    const char* e = std::getenv("FETI_LOG");
+    on = e && e[0] >= '2' && e[0] <= '9';
+    t = std::chrono::steady_clock::now();
+  }
+  void mark(const char* what) {
+    if (!on) return;
+    cudaStreamSynchronize(ctx->stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "feti: %-28s %9.2f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
+// Main-loop wait budget of the kernels with bounded mbarrier waits: ns,
+// converted to SM clock cycles at the device's maximum clock (rounded down)
+// and written to the context's device word; 0 cycles = give up at the first
+// check.
 constexpr unsigned long long kDefaultSpinNs = 100000000ull;
 feti_status set_spin_budget(feti_ctx* ctx, uint64_t ns) {
-  const unsigned long long v = ns ? (unsigned long long)ns : kDefaultSpinNs;
+  int khz = 0;
+  FETI_CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
+  const double cyc = (double)ns * (khz > 0 ? khz : 2000000) * 1e-6;
+  const unsigned long long v = cyc > 9.0e18 ? 9000000000000000000ull : (unsigned long long)cyc;
   FETI_CK(cudaMemcpyAsync(ctx->d_spin, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
   FETI_CK(cudaStreamSynchronize(ctx->stream));
   return FETI_OK;
 }
 
 feti_status build_decomposition(feti_ctx* ctx) {
+  StageLog lg(ctx);
   const int N = ctx->N, E = ctx->E, P = ctx->P;
   ctx->af = ctx->opt.method == FETI_ALL_FLOATING;
   // local nodes per subdomain
@@ -337,12 +396,19 @@ feti_status build_decomposition(feti_ctx* ctx) {
   for (int s = 0; s < P; ++s)
     for (int n : ctx->nodes[s]) nptr[n + 1]++;
   for (int n = 0; n < N; ++n) nptr[n + 1] += nptr[n];
-  std::vector<int32_t> nsub(nptr[N]), fill(nptr.begin(), nptr.end() - 1);
+  // nsub[a]: the subdomains of each node (ascending); lcopy[a]: the node's
+  // local index in subdomain nsub[a]
+  std::vector<int32_t> nsub(nptr[N]), lcopy(nptr[N]), fill(nptr.begin(), nptr.end() - 1);
   for (int s = 0; s < P; ++s)
-    for (int n : ctx->nodes[s]) nsub[fill[n]++] = s;
+    for (size_t l = 0; l < ctx->nodes[s].size(); ++l) {
+      const int n = ctx->nodes[s][l];
+      lcopy[fill[n]] = (int32_t)l;
+      nsub[fill[n]++] = s;
+    }
   auto lnode = [&](int s, int n) {
-    const auto& v = ctx->nodes[s];
-    return (int)(std::lower_bound(v.begin(), v.end(), n) - v.begin());
+    for (int a = nptr[n]; a < nptr[n + 1]; ++a)
+      if (nsub[a] == s) return (int)lcopy[a];
+    return -1;
   };
   std::vector<char> is_dir(3 * (size_t)N, 0);
   std::vector<double> dval(3 * (size_t)N, 0.0);
@@ -369,7 +435,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
         for (int b = a + 1; b < nptr[n + 1]; ++b) {
           const int i = nsub[a], j = nsub[b];
           rs.push_back(i); rs.push_back(j);
-          rl.push_back(3 * lnode(i, n) + c); rl.push_back(3 * lnode(j, n) + c);
+          rl.push_back(3 * lcopy[a] + c); rl.push_back(3 * lcopy[b] + c);
           rg.push_back(1); rg.push_back(-1);
           rw.push_back(w);
           rb.push_back(0.0);
@@ -382,13 +448,14 @@ feti_status build_decomposition(feti_ctx* ctx) {
       for (int a = nptr[n]; a < nptr[n + 1]; ++a) {
         const int i = nsub[a];
         rs.push_back(i); rs.push_back(-1);
-        rl.push_back(3 * lnode(i, n) + c); rl.push_back(-1);
+        rl.push_back(3 * lcopy[a] + c); rl.push_back(-1);
         rg.push_back(1); rg.push_back(0);
         rw.push_back(1.0);
         rb.push_back(ctx->dir_val[q]);
       }
     }
   }
+  lg.mark("create: local nodes, multipliers");
   ctx->n_lambda = (int64_t)rw.size();
   if (ctx->n_lambda == 0) return fail(ctx, FETI_ERR_PARTITION, "decomposition has no multipliers");
   // boundary flags per subdomain local DOF
@@ -596,6 +663,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (int d : fix) ctx->fix_ldof.push_back(d);
     ctx->fix_ptr[s + 1] = (int32_t)ctx->fix_ldof.size();
   }
+  lg.mark("create: kernels, fixing, dense order");
   ctx->nb_total = boff;
   // envelope table of the interior elimination, [step][subdomain][2]
   ctx->steps0 = 0;
@@ -665,6 +733,30 @@ feti_status build_decomposition(feti_ctx* ctx) {
         if (ctx->any_dirval && is_dir[3 * (size_t)n + c]) elem_dirval[12 * (size_t)e + 3 * a + c] = dval[3 * (size_t)n + c];
       }
     }
+  }
+  // FP32-factor form: per local row (global local index voff + dense row) the
+  // (element, element row) pairs of its subdomain's elements, ascending
+  if (ctx->opt.precision == FETI_MIXED_F32FACTOR) {
+    std::vector<int32_t> kptr(voff + 1, 0);
+    for (int e = 0; e < E; ++e) {
+      const SubLayout& L = ctx->lay[ctx->part[e]];
+      for (int a = 0; a < 12; ++a) {
+        const int r = elem_dense[12 * (size_t)e + a];
+        if (r >= 0) kptr[L.voff + r + 1]++;
+      }
+    }
+    for (int i = 0; i < voff; ++i) kptr[i + 1] += kptr[i];
+    std::vector<int32_t> kinc(kptr[voff]), kf(kptr.begin(), kptr.end() - 1);
+    for (int e = 0; e < E; ++e) {      // element order: each row's list ascends in 12 e + a
+      const SubLayout& L = ctx->lay[ctx->part[e]];
+      for (int a = 0; a < 12; ++a) {
+        const int r = elem_dense[12 * (size_t)e + a];
+        if (r >= 0) kinc[kf[L.voff + r]++] = 12 * e + a;
+      }
+    }
+    FETI_TRY(upload(ctx, &ctx->d_kinc_ptr, kptr));
+    FETI_TRY(upload(ctx, &ctx->d_kinc, kinc));
+    for (const auto& L : ctx->lay) ctx->max_nr = std::max(ctx->max_nr, L.nI + L.nbp);
   }
   // lumped preconditioner: CSR pattern of K_bb over the global boundary
   // positions, from the boundary DOF pairs that share an element
@@ -799,32 +891,59 @@ feti_status build_decomposition(feti_ctx* ctx) {
   ctx->U_init.assign(3 * (size_t)N, 0.0);
   if (!af)
     for (size_t i = 0; i < ctx->dir_dof.size(); ++i) ctx->U_init[ctx->dir_dof[i]] = ctx->dir_val[i];
-  // coarse G^T G pair blocks
-  std::map<std::pair<int, int>, std::vector<int32_t>> blocks;
-  for (int64_t r = 0; r < ctx->n_lambda; ++r) {
-    int ss[2];
-    int cnt = 0;
-    for (int e = 0; e < 2; ++e) {
-      const int s = rs[2 * r + e];
-      if (s >= 0 && ctx->lay[s].k > 0) ss[cnt++] = s;
-    }
-    if (cnt >= 1) blocks[{ss[0], ss[0]}].push_back((int32_t)r);
-    if (cnt == 2) {
-      blocks[{ss[1], ss[1]}].push_back((int32_t)r);
-      blocks[{std::min(ss[0], ss[1]), std::max(ss[0], ss[1])}].push_back((int32_t)r);
-    }
-  }
+  // coarse G^T G pair blocks (i <= j, ascending), each with the multiplier
+  // rows that couple them, ascending: two passes over the rows, blocks found
+  // through a hash of the pair
   std::vector<int32_t> gi, gj, gptr(1, 0), grows;
-  for (auto& kv : blocks) {
-    gi.push_back(kv.first.first);
-    gj.push_back(kv.first.second);
-    auto& v = kv.second;
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-    grows.insert(grows.end(), v.begin(), v.end());
-    gptr.push_back((int32_t)grows.size());
+  {
+    auto pairs_of = [&](int64_t r, uint64_t out[3]) {
+      int ss[2], cnt = 0;
+      for (int e = 0; e < 2; ++e) {
+        const int s = rs[2 * r + e];
+        if (s >= 0 && ctx->lay[s].k > 0) ss[cnt++] = s;
+      }
+      int m = 0;
+      if (cnt >= 1) out[m++] = (uint64_t)ss[0] * P + ss[0];
+      if (cnt == 2) {
+        out[m++] = (uint64_t)ss[1] * P + ss[1];
+        out[m++] = (uint64_t)std::min(ss[0], ss[1]) * P + std::max(ss[0], ss[1]);
+      }
+      return m;
+    };
+    std::unordered_map<uint64_t, int32_t> id;
+    std::vector<uint64_t> keys;
+    std::vector<int32_t> cnt;
+    uint64_t k3[3];
+    for (int64_t r = 0; r < ctx->n_lambda; ++r) {
+      const int m = pairs_of(r, k3);
+      for (int q = 0; q < m; ++q) {
+        auto it = id.find(k3[q]);
+        if (it == id.end()) {
+          it = id.emplace(k3[q], (int32_t)keys.size()).first;
+          keys.push_back(k3[q]);
+          cnt.push_back(0);
+        }
+        cnt[it->second]++;
+      }
+    }
+    std::vector<int32_t> order(keys.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return keys[a] < keys[b]; });
+    std::vector<int32_t> start(keys.size());
+    for (int32_t o : order) {
+      start[o] = gptr.back();
+      gi.push_back((int32_t)(keys[o] / P));
+      gj.push_back((int32_t)(keys[o] % P));
+      gptr.push_back(gptr.back() + cnt[o]);
+    }
+    grows.assign(gptr.back(), 0);
+    for (int64_t r = 0; r < ctx->n_lambda; ++r) {  // rows in increasing order within each block
+      const int m = pairs_of(r, k3);
+      for (int q = 0; q < m; ++q) grows[start[id[k3[q]]]++] = (int32_t)r;
+    }
   }
   ctx->n_gtg = (int)gi.size();
+  lg.mark("create: maps, coarse blocks");
   // gemv block tables
   std::vector<int32_t> tab_sub[2][3], tab_row[2][3];
   const int rpcs[3] = {32, 64, 128};
@@ -850,6 +969,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   std::vector<double> Rall(roff);
   for (int s = 0; s < P; ++s) std::copy(Rd[s].begin(), Rd[s].end(), Rall.begin() + ctx->lay[s].roff);
 
+  lg.mark("create: tables");
   // ---- uploads and allocations
   FETI_TRY(upload(ctx, &ctx->d_coords, ctx->coords));
   FETI_TRY(upload(ctx, &ctx->d_tets, ctx->tets));
@@ -956,6 +1076,12 @@ feti_status build_decomposition(feti_ctx* ctx) {
     ctx->sym_n[w] = (int)ws.size();
     FETI_TRY(upload(ctx, &ctx->d_sym_sub[w], ws));
     FETI_TRY(upload(ctx, &ctx->d_sym_panel[w], wp));
+    std::vector<int32_t> ord(P);
+    std::iota(ord.begin(), ord.end(), 0);
+    auto msz = [&](int q) { return w == 0 ? ctx->lay[q].nbp : ctx->lay[q].nbp + ctx->lay[q].k; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return msz(a) > msz(b); });
+    ctx->sym_max_m[w] = P > 0 ? msz(ord[0]) : 0;
+    FETI_TRY(upload(ctx, &ctx->d_sym_order[w], ord));
   }
   FETI_TRY(dev_alloc(ctx, &ctx->d_f, ctx->nloc_total));
   FETI_TRY(dev_alloc(ctx, &ctx->d_x, ctx->nloc_total));
@@ -979,7 +1105,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(dev_alloc(ctx, &ctx->d_status, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_zero, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_spin, 1));
-  FETI_TRY(set_spin_budget(ctx, ctx->opt.spin_timeout_ns));
+  FETI_TRY(set_spin_budget(ctx, ctx->opt.spin_timeout_ns ? ctx->opt.spin_timeout_ns : kDefaultSpinNs));
   FETI_CK(cudaMemsetAsync(ctx->d_zero, 0, sizeof(int), ctx->stream));
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   if (ctx->cd > 0) {
@@ -1044,10 +1170,18 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
   FETI_CK(cudaGetLastError());
   size_t abytes = 0;
   for (const auto& L : ctx->lay) abytes += (size_t)L.ld * L.ld;
-  FETI_CK(cudaMemsetAsync(ctx->d_A, 0, abytes * sizeof(double), st));
-  feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
-                        ctx->d_A, st);
-  feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A, st);
+  if (f32_factor(ctx)) {
+    FETI_CK(cudaMemsetAsync(ctx->d_A32, 0, abytes * sizeof(float), st));
+    feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
+                          ctx->d_A32, st);
+    feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A32, st);
+  } else {
+    FETI_CK(cudaMemsetAsync(ctx->d_A, 0, abytes * sizeof(double), st));
+    feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
+                          ctx->d_A, st);
+    if (ctx->shift > 0.0) feti::launch_shift_diag(ctx->P, ctx->d_lay, ctx->d_A, ctx->shift, st);
+    feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A, st);
+  }
   // face forces (grouped order; kind per face)
   const int nf = ctx->n_press + ctx->n_trac;
   if (nf > 0) {
@@ -1072,11 +1206,89 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
   return check_status(ctx, "element/assembly");
 }
 
+// x = K^+ g on full local vectors (zero on the fixing DOFs): FP64 sweeps on the
+// FP64 factor, or, in the FP32-factor form, FP32 sweeps refined against the
+// FP64 element matrices (refine_steps corrections; d_kr is scratch).
+void kplus(feti_ctx* ctx, const double* g, double* x) {
+  cudaStream_t st = ctx->stream;
+  if (!f32_factor(ctx)) {
+    feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, g, x, st);
+    return;
+  }
+  feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, g, x, 1, ctx->max_nr, st);
+  for (int k = 1; k < ctx->refine_steps; ++k) {
+    feti::launch_kresid(ctx->P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, g, x,
+                        ctx->d_kr, st);
+    feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, ctx->d_kr, x, 0, ctx->max_nr, st);
+  }
+}
+
+// Number of refinement corrections of the FP32-factor K^+: applied to a fixed
+// pseudo-random vector, corrections are added while the largest relative
+// residual over the subdomains, ||g - K_rr x|| / ||g||, still falls by at
+// least half and is above 1e-14 (at most 12).
+feti_status tune_refinement(feti_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const int P = ctx->P;
+  feti::launch_fill_mix(ctx->nloc_total, ctx->d_kg, st);
+  feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kg, ctx->d_x2, 1, ctx->max_nr, st);
+  std::vector<double> nrm(2 * (size_t)P);
+  double prev = 1e300;
+  int steps = 1;
+  for (; steps <= 12; ++steps) {
+    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->d_kg,
+                        ctx->d_x2, ctx->d_kr, st);
+    feti::launch_sub_norm2(P, ctx->d_lay, ctx->d_kr, ctx->d_kg, ctx->d_knorm, st);
+    FETI_CK(cudaGetLastError());
+    FETI_CK(cudaMemcpyAsync(nrm.data(), ctx->d_knorm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FETI_CK(cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int q = 0; q < P; ++q)
+      if (nrm[2 * q + 1] > 0.0) worst = std::max(worst, std::sqrt(nrm[2 * q] / nrm[2 * q + 1]));
+    if (!std::isfinite(worst)) return fail(ctx, FETI_ERR_LOCAL_SINGULAR, "FP32 factor: refinement diverged");
+    ctx->refine_res = worst;
+    if (worst <= 1e-14 || worst > 0.5 * prev || steps == 12) break;
+    prev = worst;
+    feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kr, ctx->d_x2, 0, ctx->max_nr, st);
+  }
+  if (ctx->refine_res > 1e-6)
+    return fail(ctx, FETI_ERR_LOCAL_SINGULAR, "FP32 factor: refinement does not converge (residual " +
+                                                  std::to_string(ctx->refine_res) + ")");
+  ctx->refine_steps = steps;
+  const char* e = std::getenv("FETI_LOG");
+  if (e && e[0] >= '2' && e[0] <= '9') {  // one correction and one residual, timed
+    cudaEvent_t a, b, c;
+    FETI_CK(cudaEventCreate(&a));
+    FETI_CK(cudaEventCreate(&b));
+    FETI_CK(cudaEventCreate(&c));
+    FETI_CK(cudaEventRecord(a, st));
+    feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kr, ctx->d_x2, 0, ctx->max_nr, st);
+    FETI_CK(cudaEventRecord(b, st));
+    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->d_kg,
+                        ctx->d_x2, ctx->d_kr, st);
+    FETI_CK(cudaEventRecord(c, st));
+    FETI_CK(cudaEventSynchronize(c));
+    float t1 = 0.f, t2 = 0.f;
+    FETI_CK(cudaEventElapsedTime(&t1, a, b));
+    FETI_CK(cudaEventElapsedTime(&t2, b, c));
+    std::fprintf(stderr, "feti: refinement %d corrections, residual %.2e; correction %.3f ms, residual %.3f ms\n",
+                 steps, ctx->refine_res, t1, t2);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaEventDestroy(c);
+  }
+  return FETI_OK;
+}
+
 // Local factorizations, dense local operators, coarse problem.
 feti_status factorize_all(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
-  if (ctx->opt.precond == FETI_PREC_LUMPED)
-    feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
+  if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    if (f32_factor(ctx))
+      feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A32, ctx->d_lump_val, st);
+    else
+      feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
+  }
   // per step, the largest trailing chunk count over the subdomains
   std::vector<int> chunks[2];
   for (int phase = 0; phase < 2; ++phase)
@@ -1100,6 +1312,25 @@ feti_status factorize_all(feti_ctx* ctx) {
         chunks[phase][t] = std::max(chunks[phase][t], ch);
       }
     }
+  if (f32_factor(ctx)) {
+    // FP32 elimination; S_i and F_i go straight into the FP32 operator layouts
+    feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0,
+                              ctx->d_A32, ctx->d_status, st);
+    if (ctx->opt.precond == FETI_PREC_DIRICHLET)
+      feti::launch_extract32(ctx->P, ctx->d_lay, 0, ctx->d_A32, ctx->d_S32, st);
+    feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A32,
+                              ctx->d_status, st);
+    feti::launch_extract32(ctx->P, ctx->d_lay, 1, ctx->d_A32, ctx->d_F32, st);
+    if (ctx->d_F32s) {
+      feti::launch_pad_to_sym(ctx->P, ctx->d_lay, 0, ctx->d_F32, ctx->d_F32s, st);
+      if (ctx->opt.precond == FETI_PREC_DIRICHLET)
+        feti::launch_pad_to_sym(ctx->P, ctx->d_lay, 1, ctx->d_S32, ctx->d_S32s, st);
+    }
+    FETI_CK(cudaGetLastError());
+    FETI_TRY(check_status(ctx, "local factorization (FP32)"));
+    if (ctx->refine_steps == 0) FETI_TRY(tune_refinement(ctx));
+    return FETI_OK;
+  }
   feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0, ctx->d_A,
                             ctx->d_status, st);
   if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
@@ -1120,45 +1351,68 @@ feti_status factorize_all(feti_ctx* ctx) {
   return FETI_OK;
 }
 
-// G^T G and the elimination workspace (5 cd^2 doubles) exist only during
-// this call; the context keeps (G^T G)^-1.
-feti_status coarse_setup(feti_ctx* ctx) {
+// Coarse problem, enqueued on the second stream (it needs only R_i and the
+// multiplier maps, not the local factorizations, so it overlaps them; the
+// FP64 elimination and an FP32 local factorization use different pipes).
+// G^T G and the elimination workspace (5 cd^2 doubles) exist until
+// coarse_join; the context keeps (G^T G)^-1.
+feti_status coarse_begin(feti_ctx* ctx) {
   if (ctx->cd == 0) return FETI_OK;
-  cudaStream_t st = ctx->stream;
   const size_t cd = ctx->cd;
-  struct Scratch {
-    void* p[2] = {nullptr, nullptr};
-    ~Scratch() {
-      for (void* q : p)
-        if (q) cudaFree(q);
-    }
-  } scratch;
+  if (!ctx->stream2) {
+    FETI_CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+    FETI_CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    FETI_CK(cudaEventCreateWithFlags(&ctx->ev_coarse, cudaEventDisableTiming));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_status2, 1));
+  }
   {
-    cudaError_t e = cudaMalloc(&scratch.p[0], cd * cd * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&scratch.p[1], 4 * cd * cd * sizeof(double));
+    cudaError_t e = cudaMalloc(&ctx->coarse_ws[0], cd * cd * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->coarse_ws[1], 4 * cd * cd * sizeof(double));
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
+      for (void*& q : ctx->coarse_ws)
+        if (q) { cudaFree(q); q = nullptr; }
       return fail(ctx, e == cudaErrorMemoryAllocation ? FETI_ERR_OOM : FETI_ERR_CUDA,
                   std::string("coarse workspace: ") + cudaGetErrorString(e));
     }
   }
-  ctx->d_GtG = static_cast<double*>(scratch.p[0]);
-  ctx->d_Acoarse = static_cast<double*>(scratch.p[1]);
-  FETI_CK(cudaMemsetAsync(ctx->d_GtG, 0, cd * cd * sizeof(double), st));
+  cudaStream_t st = ctx->stream2;
+  FETI_CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  FETI_CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+  double* GtG = static_cast<double*>(ctx->coarse_ws[0]);
+  double* Ac = static_cast<double*>(ctx->coarse_ws[1]);
+  FETI_CK(cudaMemsetAsync(ctx->d_status2, 0, sizeof(int), st));
+  FETI_CK(cudaMemsetAsync(GtG, 0, cd * cd * sizeof(double), st));
   feti::launch_gtg(ctx->n_gtg, ctx->d_gtg_i, ctx->d_gtg_j, ctx->d_gtg_ptr, ctx->d_gtg_rows, ctx->d_lay, ctx->d_R,
-                   ctx->maps, (int)cd, ctx->d_GtG, st);
+                   ctx->maps, (int)cd, GtG, st);
   // [[G^T G, I], [I, 0]] eliminated over the first cd columns leaves -(G^T G)^-1
-  FETI_CK(cudaMemsetAsync(ctx->d_Acoarse, 0, 4 * cd * cd * sizeof(double), st));
-  FETI_CK(cudaMemcpy2DAsync(ctx->d_Acoarse, 2 * cd * sizeof(double), ctx->d_GtG, cd * sizeof(double),
-                            cd * sizeof(double), cd, cudaMemcpyDeviceToDevice, st));
-  feti::launch_augment(1, ctx->d_lay_coarse, ctx->d_Acoarse, st);
-  feti::launch_dense_chol_big(ctx->d_Acoarse, 2 * (int)cd, 0, (int)cd, 2 * (int)cd, (int)cd, ctx->d_status, st);
+  FETI_CK(cudaMemsetAsync(Ac, 0, 4 * cd * cd * sizeof(double), st));
+  FETI_CK(cudaMemcpy2DAsync(Ac, 2 * cd * sizeof(double), GtG, cd * sizeof(double), cd * sizeof(double), cd,
+                            cudaMemcpyDeviceToDevice, st));
+  feti::launch_augment(1, ctx->d_lay_coarse, Ac, st);
+  feti::launch_dense_chol_big(Ac, 2 * (int)cd, 0, (int)cd, 2 * (int)cd, (int)cd, ctx->d_status2, st);
   // extract into Ginv: F layout of the coarse "subdomain" has foff = 0
-  feti::launch_extract(1, ctx->d_lay_coarse, 1, ctx->d_Acoarse, ctx->d_Ginv, st);
+  feti::launch_extract(1, ctx->d_lay_coarse, 1, Ac, ctx->d_Ginv, st);
   FETI_CK(cudaGetLastError());
-  const feti_status status = check_status(ctx, "coarse factorization");  // synchronises the stream
-  ctx->d_GtG = ctx->d_Acoarse = nullptr;
-  return status;
+  FETI_CK(cudaEventRecord(ctx->ev_coarse, st));
+  ctx->coarse_pending = true;
+  return FETI_OK;
+}
+
+// Joins the coarse setup into the context's stream, checks its status and
+// frees its workspace.
+feti_status coarse_join(feti_ctx* ctx) {
+  if (!ctx->coarse_pending) return FETI_OK;
+  ctx->coarse_pending = false;
+  FETI_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_coarse, 0));
+  int h = 0;
+  FETI_CK(cudaMemcpyAsync(&h, ctx->d_status2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream2));
+  FETI_CK(cudaStreamSynchronize(ctx->stream2));
+  for (void*& q : ctx->coarse_ws)
+    if (q) { cudaFree(q); q = nullptr; }
+  if (h == feti::DEV_LOCAL_SINGULAR) return fail(ctx, FETI_ERR_KERNEL_DETECT, "coarse factorization: G^T G not positive definite");
+  if (h != 0) return fail(ctx, FETI_ERR_CUDA, "coarse factorization: device status " + std::to_string(h));
+  return FETI_OK;
 }
 
 // P v -> out (with optional partial dot with a, or the squared norm, into
@@ -1192,6 +1446,12 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
     feti::launch_symv2_f32(ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which], ctx->d_lay, which,
                            which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps,
                            done, ctx->d_sym_err, ctx->d_spin, ctx->stream);
+    return;
+  }
+  if (f32 && ctx->sym32[which] >= 300 && !ctx->opt.per_subdomain) {
+    feti::launch_symv3_f32(ctx->sym32[which] - 300, ctx->P, ctx->d_sym_order[which], ctx->sym_max_m[which],
+                           ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc,
+                           done, ctx->stream);
     return;
   }
   if (f32 && ctx->sym32[which] && !ctx->opt.per_subdomain) {
@@ -1230,6 +1490,17 @@ void local_apply(feti_ctx* ctx, int which, const double* x, const double* wv, co
 // optional partial dot with a.  f32 selects the FP32 copies of F_i.
 void apply_F(feti_ctx* ctx, const double* x, double* q, const double* a, bool with_dot, const int* done,
              bool f32 = false) {
+  if (!f32 && f32_factor(ctx)) {
+    // FP64-accurate F x without FP64 explicit operators: B K^+ B^T x with the
+    // refined K^+ on full local vectors (boundary values placed, interior zero)
+    feti::launch_gather(ctx->maps, x, nullptr, ctx->d_loc, done, ctx->stream);
+    feti::launch_place(ctx->P, ctx->d_lay, ctx->d_loc, ctx->d_kg, ctx->stream);
+    kplus(ctx, ctx->d_kg, ctx->d_x2);
+    feti::launch_take_boundary(ctx->P, ctx->d_lay, ctx->d_x2, ctx->d_loc, ctx->stream);
+    feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, a, with_dot ? ctx->d_partial : nullptr, done,
+                         ctx->stream);
+    return;
+  }
   local_apply(ctx, 0, x, nullptr, done, f32);
   feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, a, with_dot ? ctx->d_partial : nullptr, done, ctx->stream);
 }
@@ -1250,16 +1521,91 @@ void apply_M(feti_ctx* ctx, const double* w, double* z, const int* done, bool f3
 
 // Autotuner: times every (rows per warp step, rows per CTA) schedule of the
 // dense local applies on the real operators and keeps the fastest.
+feti_status autotune_run(feti_ctx* ctx);
+
+// Schedules picked by the autotuner, remembered per process for decompositions
+// with the same signature (sizes of every subdomain layout, options that
+// change the operators), so that a new context on the same mesh and
+// partition skips the timing runs.
+struct TunedPick {
+  int t64[2], r64[2], t32[2], r32[2], sym[2];
+};
+std::mutex g_tune_mu;
+std::unordered_map<uint64_t, TunedPick> g_tune_cache;
+
+uint64_t tune_signature(const feti_ctx* ctx) {
+  uint64_t h = 1469598103934665603ull;
+  auto add = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  add(ctx->P);
+  add(ctx->n_lambda);
+  add(ctx->nb_total);
+  add(ctx->opt.precision);
+  add(ctx->opt.precond);
+  add(ctx->opt.symmetric);
+  add(ctx->opt.per_subdomain);
+  add(ctx->device);
+  for (const auto& L : ctx->lay) {
+    add(L.n);
+    add(L.nI);
+    add(L.nbp);
+    add(L.k);
+  }
+  return h;
+}
+
+int tab_index(const feti_ctx* ctx, int w, const feti::GemvCfg& c) {
+  for (int t = 0; t < 3; ++t)
+    if (ctx->tab[w][t].blk_sub == c.blk_sub) return t;
+  return 0;
+}
+
 feti_status autotune(feti_ctx* ctx) {
+  const uint64_t sig = tune_signature(ctx);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      const TunedPick& tp = it->second;
+      for (int w = 0; w < 2; ++w) {
+        ctx->cfg64[w] = ctx->tab[w][tp.t64[w]];
+        ctx->cfg64[w].R = tp.r64[w];
+        ctx->cfg32[w] = ctx->tab[w][tp.t32[w]];
+        ctx->cfg32[w].R = tp.r32[w];
+        ctx->sym32[w] = tp.sym[w];
+      }
+      ctx->tuned = true;
+      return FETI_OK;
+    }
+  }
+  FETI_TRY(autotune_run(ctx));
+  TunedPick tp{};
+  for (int w = 0; w < 2; ++w) {
+    tp.t64[w] = tab_index(ctx, w, ctx->cfg64[w]);
+    tp.r64[w] = ctx->cfg64[w].R;
+    tp.t32[w] = tab_index(ctx, w, ctx->cfg32[w]);
+    tp.r32[w] = ctx->cfg32[w].R;
+    tp.sym[w] = ctx->sym32[w];
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[sig] = tp;
+  return FETI_OK;
+}
+
+feti_status autotune_run(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   cudaEvent_t e0, e1;
   FETI_CK(cudaEventCreate(&e0));
   FETI_CK(cudaEventCreate(&e1));
   const int Rs[3] = {2, 4, 8};
-  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  const bool mixed = f32_ops(ctx);
   FETI_CK(cudaMemsetAsync(ctx->d_vloc, 0, ctx->nb_total * sizeof(double), st));
   FETI_CK(cudaMemsetAsync(ctx->d_vloc32, 0, ctx->nb_total * sizeof(float), st));
-  for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
+  for (int prec = fp64_ops(ctx) ? 0 : 1; prec < (mixed ? 2 : 1); ++prec) {
     const bool f32 = prec == 1;
     for (int w = 0; w < 2; ++w) {
       if (w == 1 && ctx->opt.precond != FETI_PREC_DIRICHLET) continue;
@@ -1307,6 +1653,22 @@ feti_status autotune(feti_ctx* ctx) {
             gbest = Gs[gi];
           }
         }
+        for (int g3 : {8, 16, 32}) {  // subdomain-per-CTA variant (no second pass)
+          feti::launch_symv3_f32(g3, ctx->P, ctx->d_sym_order[w], ctx->sym_max_m[w], ctx->d_lay, w, Ms,
+                                 ctx->d_vloc32, ctx->d_loc, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 3; ++rep)
+            feti::launch_symv3_f32(g3, ctx->P, ctx->d_sym_order[w], ctx->sym_max_m[w], ctx->d_lay, w, Ms,
+                                   ctx->d_vloc32, ctx->d_loc, ctx->d_zero, st);
+          FETI_CK(cudaEventRecord(e1, st));
+          FETI_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best_sym) {
+            best_sym = ms;
+            gbest = 300 + g3;
+          }
+        }
         {  // streamed variant (shared-memory ring), kept only if no bounded wait ran out
           FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
           feti::launch_symv2_f32(ctx->sym_n[w], ctx->d_sym_sub[w], ctx->d_sym_panel[w], ctx->d_lay, w, Ms,
@@ -1330,6 +1692,22 @@ feti_status autotune(feti_ctx* ctx) {
           FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), st));
         }
         if (ctx->opt.symmetric == 3) gbest = 64;
+        if (ctx->opt.symmetric == 4 && gbest < 300) {  // fastest subdomain-per-CTA load group
+          float b3 = 1e30f;
+          for (int g3 : {8, 16, 32}) {
+            FETI_CK(cudaEventRecord(e0, st));
+            feti::launch_symv3_f32(g3, ctx->P, ctx->d_sym_order[w], ctx->sym_max_m[w], ctx->d_lay, w, Ms,
+                                   ctx->d_vloc32, ctx->d_loc, ctx->d_zero, st);
+            FETI_CK(cudaEventRecord(e1, st));
+            FETI_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FETI_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < b3) {
+              b3 = ms;
+              gbest = 300 + g3;
+            }
+          }
+        }
         if (best_sym < best || ctx->opt.symmetric >= 2) ctx->sym32[w] = gbest;
       }
     }
@@ -1390,11 +1768,18 @@ feti_status build_pcg_graph(feti_ctx* ctx, int chunk, bool mixed) {
 
 // Dense local matrices (factorized in place), S_i, F_i and their FP32 copies.
 feti_status alloc_operators(feti_ctx* ctx) {
-  if (ctx->d_A) return FETI_OK;
-  FETI_TRY(dev_alloc(ctx, &ctx->d_A, (size_t)ctx->op_elems[0]));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_S, (size_t)ctx->op_elems[1]));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_F, (size_t)ctx->op_elems[2]));
-  if (ctx->opt.precision == FETI_MIXED) {
+  if (ctx->d_A || ctx->d_A32) return FETI_OK;
+  if (f32_factor(ctx)) {
+    FETI_TRY(dev_alloc(ctx, &ctx->d_A32, (size_t)ctx->op_elems[0]));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kr, (size_t)ctx->nloc_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kg, (size_t)ctx->nloc_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_knorm, 2 * (size_t)ctx->P));
+  } else {
+    FETI_TRY(dev_alloc(ctx, &ctx->d_A, (size_t)ctx->op_elems[0]));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_S, (size_t)ctx->op_elems[1]));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_F, (size_t)ctx->op_elems[2]));
+  }
+  if (f32_ops(ctx)) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_F32, (size_t)ctx->op_elems[3]));
     FETI_TRY(dev_alloc(ctx, &ctx->d_S32, (size_t)ctx->op_elems[4]));
     if (ctx->opt.symmetric != 1) {
@@ -1410,11 +1795,20 @@ feti_status alloc_operators(feti_ctx* ctx) {
 
 // Setup: element matrices through the coarse inverse.
 feti_status prepare(feti_ctx* ctx, const double* dU, double tau) {
+  StageLog lg(ctx);
   FETI_TRY(alloc_operators(ctx));
+  lg.mark("setup: allocation");
   FETI_TRY(assemble_all(ctx, dU, tau));
-  FETI_TRY(factorize_all(ctx));
-  if (!ctx->prepared) FETI_TRY(coarse_setup(ctx));
+  lg.mark("setup: elements + assembly");
+  if (!ctx->prepared) FETI_TRY(coarse_begin(ctx));
+  feti_status fs = factorize_all(ctx);
+  lg.mark("setup: local factorization");
+  const feti_status cs = coarse_join(ctx);
+  FETI_TRY(fs);
+  FETI_TRY(cs);
+  lg.mark("setup: coarse problem (joined)");
   if (!ctx->tuned) FETI_TRY(autotune(ctx));
+  lg.mark("setup: autotuning");
   ctx->prepared = true;
   return FETI_OK;
 }
@@ -1462,7 +1856,7 @@ feti_status rhs_setup(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const int nl = (int)ctx->n_lambda;
   const int* zero = ctx->d_zero;
-  feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_f, ctx->d_x, st);
+  kplus(ctx, ctx->d_f, ctx->d_x);
   feti::launch_take_boundary(ctx->P, ctx->d_lay, ctx->d_x, ctx->d_loc, st);
   feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, ctx->d_q, nullptr, nullptr, zero, st);
   feti::launch_vsub(nl, ctx->d_q, ctx->d_b, ctx->d_d, st);
@@ -1482,7 +1876,7 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   cudaStream_t st = ctx->stream;
   const int nl = (int)ctx->n_lambda;
   const int* zero = ctx->d_zero;
-  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  const bool mixed = f32_ops(ctx);
   FETI_TRY(rhs_setup(ctx));
   cudaEvent_t e0, e1;
   FETI_CK(cudaEventCreate(&e0));
@@ -1563,7 +1957,7 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   }
   feti::launch_gather(ctx->maps, ctx->d_lam, nullptr, ctx->d_loc, zero, st);
   feti::launch_local_sub(ctx->P, ctx->d_lay, ctx->d_f, ctx->d_loc, ctx->d_x2, st);
-  feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_x2, ctx->d_x, st);
+  kplus(ctx, ctx->d_x2, ctx->d_x);
   if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_wait_flag(ctx, ctx->d_sym_err, "streamed symmetric local apply"));
@@ -1618,11 +2012,11 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
   cudaEvent_t e0, e1;
   FETI_CK(cudaEventCreate(&e0));
   FETI_CK(cudaEventCreate(&e1));
-  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  const bool mixed = f32_ops(ctx);
   FETI_CK(cudaMemsetAsync(ctx->dm_vloc, 0, (size_t)ctx->nb_total * nrhs * sizeof(double), st));
   FETI_CK(cudaMemsetAsync(ctx->dm_vloc32, 0, (size_t)ctx->nb_total * nrhs * sizeof(float), st));
   const int Rs[3] = {1, 2, 4};
-  for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
+  for (int prec = fp64_ops(ctx) ? 0 : 1; prec < (mixed ? 2 : 1); ++prec) {
     const bool f32 = prec == 1;
     for (int w = 0; w < 2; ++w) {
       feti::GemvCfg best = ctx->tab[w][0];
@@ -1831,7 +2225,7 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
   cudaStream_t st = ctx->stream;
   const int nl = (int)ctx->n_lambda;
   const int* zero = ctx->d_zero;
-  const bool mixed = ctx->opt.precision == FETI_MIXED;
+  const bool mixed = f32_ops(ctx);
   FETI_TRY(alloc_multi(ctx, nrhs));
   FETI_TRY(rhs_setup(ctx));
   for (int k = 0; k < nrhs; ++k) {
@@ -1863,7 +2257,15 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
     const double inner_tol = ctx->opt.inner_tol > 0.0 ? ctx->opt.inner_tol : 1e-4;
     const int max_outer = ctx->opt.max_outer > 0 ? ctx->opt.max_outer : 20;
     for (;;) {
-      apply_F_m(ctx, nrhs, ctx->dm_lam, ctx->dm_q, nullptr, nullptr, zero, false);   // FP64 residuals
+      if (f32_factor(ctx)) {   // FP64 residuals by the refined K^+, one right-hand side at a time
+        for (int k = 0; k < nrhs; ++k) {
+          feti::launch_col_get(nl, nrhs, k, ctx->dm_lam, ctx->d_lam, st);
+          apply_F(ctx, ctx->d_lam, ctx->d_q, nullptr, false, zero);
+          feti::launch_col_set(nl, nrhs, k, 1.0, ctx->d_q, ctx->dm_q, st);
+        }
+      } else {
+        apply_F_m(ctx, nrhs, ctx->dm_lam, ctx->dm_q, nullptr, nullptr, zero, false);   // FP64 residuals
+      }
       feti::launch_vsub(nlb, ctx->dm_d, ctx->dm_q, ctx->dm_r, st);
       std::vector<int> none;
       FETI_TRY(start_pcg_m(ctx, nrhs, tolv.data(), none, std::max(1, ctx->opt.maxit - total_it)));
@@ -1924,7 +2326,7 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
     feti::launch_gather(ctx->maps, ctx->d_lam, nullptr, ctx->d_loc, zero, st);
     feti::launch_axpy_to((int)ctx->nloc_total, ctx->d_f, scale[k] - 1.0, ctx->d_f, ctx->d_x2, st);   // scale_k f
     feti::launch_local_sub(ctx->P, ctx->d_lay, ctx->d_x2, ctx->d_loc, ctx->d_x2, st);
-    feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_x2, ctx->d_x, st);
+    kplus(ctx, ctx->d_x2, ctx->d_x);
     if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
     FETI_CK(cudaGetLastError());
     double* out_k = u_out + k * n3;
@@ -1990,7 +2392,7 @@ feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double
   float* vloc32 = reinterpret_cast<float*>(scratch + nb);          // nb floats, 16-byte aligned
   double* loc = scratch + nb + (nb + 7) / 2 + 4;                   // nb doubles
   vloc32 = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(vloc32 + 3) & ~uintptr_t(15));
-  const bool f32 = ctx->opt.precision == FETI_MIXED;
+  const bool f32 = f32_ops(ctx);
   // q = F v
   if (f32) {
     feti::launch_gather32(ctx->maps, v, nullptr, vloc32, zero, st);
@@ -2036,7 +2438,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown method");
   if (opt->precond < FETI_PREC_IDENTITY || opt->precond > FETI_PREC_DIRICHLET)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown preconditioner");
-  if (opt->precision != FETI_FP64 && opt->precision != FETI_MIXED)
+  if (opt->precision != FETI_FP64 && opt->precision != FETI_MIXED && opt->precision != FETI_MIXED_F32FACTOR)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported precision");
   if (!(opt->tol > 0.0) || opt->maxit <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "tol and maxit must be positive");
   if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE)
@@ -2091,6 +2493,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
     FETI_CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
     ctx->own_stream = true;
   }
+  StageLog lg(ctx);
   FETI_CK(cudaGetDevice(&ctx->device));
   {
     // set-up of feti_dual_apply_noalloc on this device: the static scratch's
@@ -2101,13 +2504,17 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
       (void)cudaGetLastError();
     }
   }
-  return build_decomposition(ctx);
+  lg.mark("create: arguments");
+  const feti_status st = build_decomposition(ctx);
+  lg.mark("create: decomposition + upload");
+  return st;
 }
 
 feti_status feti_prepare(feti_ctx* ctx) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
   (void)cudaGetLastError();  // drop a non-sticky error left by an earlier, unrelated runtime call
   auto t0 = std::chrono::steady_clock::now();
+  ctx->shift = 0.0;  // exact local operators (a Newton run may have left a shift)
   FETI_TRY(prepare(ctx, nullptr, 1.0));
   ctx->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return FETI_OK;
@@ -2245,30 +2652,62 @@ static feti_status newton_increment(feti_ctx* ctx, double eta, int max_it, int* 
   return FETI_OK;
 }
 
-feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
-  if (!ctx) return FETI_ERR_INVALID_ARG;
+// Setup of a Newton iteration at U: element tangents, local assembly and
+// factorization.  A local tangent that is not positive definite (possible
+// under prestress: rigid rotations stop being kernel vectors of a
+// subdomain's tangent, and its quadratic form along them can turn negative)
+// is shifted, A_ii += delta max_j A_jj with delta = 1e-6, 1e-5, .. 1e-1, until
+// every local Cholesky factorization succeeds; the FETI solve is then only
+// the preconditioner of the flexible CG on the exact element-assembled
+// tangent (newton_increment), which still converges to the Newton increment.
+static feti_status prepare_newton(feti_ctx* ctx, const double* dU, double tau, bool log) {
+  ctx->shift = 0.0;
+  feti_status s = prepare(ctx, dU, tau);
+  for (double d = 1e-6; s == FETI_ERR_LOCAL_SINGULAR && d <= 0.11; d *= 10.0) {
+    ctx->shift = d;
+    if (log) std::fprintf(stderr, "feti_newton: local tangent not positive definite; shift %.0e\n", d);
+    s = prepare(ctx, dU, tau);
+  }
+  return s;
+}
+
+// Load steps first..last of the load-stepped Newton method (Sec. 3.2, Eq.
+// loadStepping: tau = s / n_load_steps), starting from U_start (device, host
+// or NULL = zero) -- the state after load step first - 1.
+static feti_status newton_run(feti_ctx* ctx, const double* U_start, int32_t u_start_on_device, int first, int last,
+                              double* u_out, int32_t u_on_device, int32_t* pcg_per_step, int32_t* newton_per_step,
+                              feti_report* report) {
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
   (void)cudaGetLastError();
   if (ctx->mat.kind != FETI_HGO_TWO_FIBRE) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton needs HGO_TWO_FIBRE");
+  if (f32_factor(ctx))
+    return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton: FETI_MIXED_F32FACTOR is for linear solves");
   for (double v : ctx->dir_val)
     if (v != 0.0) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton needs homogeneous Dirichlet data");
+  const int nsteps = ctx->opt.n_load_steps > 0 ? ctx->opt.n_load_steps : 1;
+  if (first < 1 || last > nsteps || first > last)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "load steps must satisfy 1 <= first <= last <= n_load_steps");
   if (report) std::memset(report, 0, sizeof(*report));
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = ctx->stream;
   const int n3 = 3 * ctx->N;
-  const int nsteps = ctx->opt.n_load_steps > 0 ? ctx->opt.n_load_steps : 1;
   const int maxit = ctx->opt.newton_maxit > 0 ? ctx->opt.newton_maxit : 25;
   const double ntol = ctx->opt.newton_tol > 0 ? ctx->opt.newton_tol : 1e-8;
-  FETI_CK(cudaMemsetAsync(ctx->d_U, 0, n3 * sizeof(double), st));
+  if (U_start)
+    FETI_CK(cudaMemcpyAsync(ctx->d_U, U_start, n3 * sizeof(double),
+                            u_start_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  else
+    FETI_CK(cudaMemsetAsync(ctx->d_U, 0, n3 * sizeof(double), st));
   // FETI_LOG=1 in the environment prints one line per Newton iteration to stderr
   const char* log_env = std::getenv("FETI_LOG");
   const bool log = log_env && log_env[0] && log_env[0] != '0';
   int newton_total = 0, pcg_total = 0;
   double rel = 0.0;
   double t_pcg = 0.0;
-  for (int step = 1; step <= nsteps; ++step) {
+  for (int step = first; step <= last; ++step) {
     const double tau = (double)step / nsteps;
-    FETI_TRY(prepare(ctx, ctx->d_U, tau));
+    int step_newton = 0, step_pcg_total = 0;
+    FETI_TRY(prepare_newton(ctx, ctx->d_U, tau, log));
     FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
     if (log) std::fprintf(stderr, "feti_newton: load step %d tau %.4f start rel %.3e\n", step, tau, rel);
     for (int k = 0;; ++k) {
@@ -2281,22 +2720,38 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
       double krel = 0.0;
       FETI_TRY(newton_increment(ctx, 1e-4, 12, &step_pcg, &t_pcg, &kits, &krel));
       pcg_total += step_pcg;
+      step_pcg_total += step_pcg;
       feti_status s = FETI_OK;
       // step length: halve until the local tangents at U + a dU factorize
+      // (down to 1/64).  Where they stop being positive definite -- the
+      // current state already needed a shift, or no step length keeps them
+      // definite -- a shifted trial is accepted once the residual falls (or
+      // at the smallest step length).
+      const bool state_shifted = ctx->shift > 0.0;
       double a = 1.0;
       for (;;) {
         feti::launch_axpy_to(n3, ctx->d_U, a, ctx->d_dU, ctx->d_Utrial, st);
         feti::launch_zero_list((int)ctx->dir_dof.size(), ctx->d_dir_dof, ctx->d_Utrial, st);
+        ctx->shift = 0.0;
         s = prepare(ctx, ctx->d_Utrial, tau);
         if (s == FETI_OK) break;
         if (log) std::fprintf(stderr, "feti_newton: step %d it %d step length %.4f rejected (%s)\n", step, k + 1, a,
                               ctx->err.c_str());
         if (s != FETI_ERR_LOCAL_SINGULAR && s != FETI_ERR_ELEMENT_INVERTED) return s;
+        if (s == FETI_ERR_LOCAL_SINGULAR && (state_shifted || a < 1.0 / 32)) {
+          FETI_TRY(prepare_newton(ctx, ctx->d_Utrial, tau, log));
+          double rel_trial = 0.0;
+          FETI_TRY(newton_residual(ctx, ctx->d_Utrial, tau, &rel_trial));
+          if (rel_trial < rel || a < 1.0 / 32) break;
+          if (log) std::fprintf(stderr, "feti_newton: step %d it %d shifted step %.4f: residual %.3e >= %.3e\n", step,
+                                k + 1, a, rel_trial, rel);
+        }
         a *= 0.5;
-        if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "no step keeps the local tangents positive definite");
+        if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "no step length is acceptable");
       }
       FETI_CK(cudaMemcpyAsync(ctx->d_U, ctx->d_Utrial, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
       ++newton_total;
+      ++step_newton;
       FETI_TRY(newton_residual(ctx, ctx->d_U, tau, &rel));
       if (log) {
         std::fprintf(stderr,
@@ -2305,6 +2760,8 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
                      step, k + 1, kits, step_pcg, krel, a, rel);
       }
     }
+    if (pcg_per_step) pcg_per_step[step - first] = step_pcg_total;
+    if (newton_per_step) newton_per_step[step - first] = step_newton;
   }
   FETI_CK(cudaMemcpyAsync(u_out, ctx->d_U, n3 * sizeof(double), u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   FETI_CK(cudaStreamSynchronize(st));
@@ -2319,6 +2776,20 @@ feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_
     report->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return FETI_OK;
+}
+
+feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  const int nsteps = ctx->opt.n_load_steps > 0 ? ctx->opt.n_load_steps : 1;
+  return newton_run(ctx, nullptr, 0, 1, nsteps, u_out, u_on_device, nullptr, nullptr, report);
+}
+
+feti_status feti_newton_steps(feti_ctx* ctx, const double* U_start, int32_t first_step, int32_t last_step,
+                              double* u_out, int32_t u_on_device, int32_t* pcg_per_step, int32_t* newton_per_step,
+                              feti_report* report) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  return newton_run(ctx, U_start, u_on_device, first_step, last_step, u_out, u_on_device, pcg_per_step,
+                    newton_per_step, report);
 }
 
 feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, double* Ke_out, double* fe_out,
@@ -2396,7 +2867,7 @@ feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, dou
   FETI_TRY(alloc_multi(ctx, nrhs));
   cudaStream_t st = ctx->stream;
   const int* zero = ctx->d_zero;
-  const bool f32 = ctx->opt.precision == FETI_MIXED;
+  const bool f32 = f32_ops(ctx);
   if (!(ctx->dualm_graph && ctx->dualm_v == v && ctx->dualm_q == q && ctx->dualm_z == z && ctx->dualm_n == n_apply &&
         ctx->dualm_nrhs == nrhs)) {
     if (ctx->dualm_graph) cudaGraphExecDestroy(ctx->dualm_graph);
@@ -2505,7 +2976,7 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
     // dominant kernel is timed inside the same run as the whole apply.
     cudaGraph_t g = nullptr;
     FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const bool f32 = ctx->opt.precision == FETI_MIXED;
+    const bool f32 = f32_ops(ctx);
     for (int i = 0; i < n_apply; ++i) {
       if (f32)
         feti::launch_gather32(ctx->maps, v, nullptr, ctx->d_vloc32, zero, st);
@@ -2550,7 +3021,7 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
   // symmetric F_i once (8 B in FP64, 4 B in the FP32 copy), the gathered
   // local input (8 B) and the local output (8 B) per boundary DOF; flops: 2
   // per entry of the full matrix
-  const double esz = ctx->opt.precision == FETI_MIXED ? 4.0 : 8.0;
+  const double esz = f32_ops(ctx) ? 4.0 : 8.0;
   ctx->gemv_bytes = half * esz + vec * 16.0;
   ctx->gemv_flops = 2.0 * entries;
   return FETI_OK;
@@ -2591,15 +3062,22 @@ feti_status feti_kernel_stats(const feti_ctx* ctx, double* gemv_ms, double* gemv
 
 const char* feti_last_error(const feti_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+feti_status feti_get_refinement(const feti_ctx* ctx, int32_t* steps, double* residual) {
+  if (!ctx) return FETI_ERR_INVALID_ARG;
+  if (steps) *steps = ctx->refine_steps;
+  if (residual) *residual = ctx->refine_res;
+  return FETI_OK;
+}
+
 feti_status feti_set_spin_timeout(feti_ctx* ctx, uint64_t spin_timeout_ns) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
   if (!ctx->d_spin) return fail(ctx, FETI_ERR_STATE, "context not set up");
-  ctx->opt.spin_timeout_ns = spin_timeout_ns;
   return set_spin_budget(ctx, spin_timeout_ns);
 }
 
 void feti_destroy(feti_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->coarse_pending && ctx->stream2) cudaStreamSynchronize(ctx->stream2);
   if (ctx->pcg_graph) cudaGraphExecDestroy(ctx->pcg_graph);
   if (ctx->dual_graph) cudaGraphExecDestroy(ctx->dual_graph);
   for (auto ev : ctx->dual_events) cudaEventDestroy(ev);
@@ -2613,6 +3091,11 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  for (void* q : ctx->coarse_ws)
+    if (q) cudaFree(q);
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_coarse) cudaEventDestroy(ctx->ev_coarse);
   delete ctx;
 }
 

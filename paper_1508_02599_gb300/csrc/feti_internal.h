@@ -63,8 +63,15 @@ void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_pt
                          const double* fe, double tau, double* f, cudaStream_t st);
 void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, const double* U,
                         int kind, double scale, const double* traction, double* out, cudaStream_t st);
+// The same into the FP32 workspace of the FP32-factor form (entries summed in FP32).
+void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                     const int32_t* elem_dense, const double* Ke, float* A, cudaStream_t st);
+// A_ii += delta * (largest diagonal entry of K_rr) on the K_rr rows of every
+// subdomain's FP64 workspace.
+void launch_shift_diag(int P, const SubLayout* lay, double* A, double delta, cudaStream_t st);
 // Writes the identity coupling of the augmentation block and zeros the rest of it.
 void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st);
+void launch_augment(int P, const SubLayout* lay, float* A, cudaStream_t st);
 // Copies the trailing boundary block (nb x nb at [nI, nI)) into S (which=0),
 // or minus the augmentation block into F (which=1).
 void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st);
@@ -162,11 +169,16 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
                      const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
                      cudaStream_t st);
 // The same product with each warp streaming its panel through shared memory
-// (cp.async.bulk row segments, bounded waits; a timeout sets *err).  spin_ns:
-// device word, the main-loop wait budget in nanoseconds.
+// (cp.async.bulk row segments, bounded waits; a timeout sets *err).
+// spin_cycles: device word, the main-loop wait budget in SM clock cycles.
 void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
                       const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
-                      int* err, const unsigned long long* spin_ns, cudaStream_t st);
+                      int* err, const unsigned long long* spin_cycles, cudaStream_t st);
+// The same product with one CTA per subdomain (order: subdomains largest
+// first) and the transposed partial sums reduced in shared memory, no second
+// pass; max_m: the largest operator size.  G = 8, 16 or 32.
+void launch_symv3_f32(int G, int P, const int32_t* order, int max_m, const SubLayout* lay, int which,
+                      const float* Msym, const float* vloc, double* y, const int* done, cudaStream_t st);
 void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // FP32 signed gather (input of the FP32 apply).
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);
@@ -234,6 +246,7 @@ namespace feti {
 // boundary positions: values gathered from the assembled local matrices,
 // then y = K_bb v (one warp per row).
 void launch_lump_fill(long nnz, const int64_t* src, const double* A, double* val, cudaStream_t st);
+void launch_lump_fill(long nnz, const int64_t* src, const float* A, double* val, cudaStream_t st);
 void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const double* val, const double* v,
                       double* y, const int* done, cudaStream_t st);
 }  // namespace feti
@@ -251,6 +264,31 @@ namespace feti {
 // subdomains at step t (idle CTAs exit at once).
 void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
                          const int32_t* env0, double* A, int* status, cudaStream_t st);
+// The same steps on the FP32 workspace (FP32 factorization).
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                         const int32_t* env0, float* A, int* status, cudaStream_t st);
+}  // namespace feti
+
+namespace feti {
+// ---- FP32 factorization with FP64-refined K^+ (feti_factor32.cu) ----
+// FP32 workspace -> padded FP32 copies: which 0 the preconditioner block
+// (S_i), which 1 F_i (minus the eliminated augmentation block).
+void launch_extract32(int P, const SubLayout* lay, int which, const float* A, float* out, cudaStream_t st);
+// Padded FP32 copy -> symmetric-apply panels (which 0: F_i, 1: preconditioner block).
+void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src, float* dst, cudaStream_t st);
+// x (+)= L^-T L^-1 r on rows [0, nI + nbp) (FP32 sweeps, FP64 vectors); init:
+// x = correction and zero on the fixing DOFs.  max_nr: largest nI + nbp.
+void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double* r, double* x, int init, int max_nr,
+                       cudaStream_t st);
+// r = g - K_rr x (FP64, element by element; zero on the fixing rows).
+void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
+                   const double* Ke, const double* g, const double* x, double* r, cudaStream_t st);
+// out = boundary vector loc placed at the boundary positions, zero interior.
+void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st);
+// out[2 s], out[2 s + 1] = squared norms of r and g over rows [0, nI + nbp) of subdomain s.
+void launch_sub_norm2(int P, const SubLayout* lay, const double* r, const double* g, double* out, cudaStream_t st);
+// x[i] = deterministic pseudo-random value in [-1, 1).
+void launch_fill_mix(long n, double* x, cudaStream_t st);
 }  // namespace feti
 
 namespace feti {
@@ -280,11 +318,11 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // 2 bulk-copy staged, 3 tensor-map (TMA) fed, 4 / 5 warp-specialised
 // TMA-fed with 3 / 2 stages; tmaps = one CUtensorMap per subdomain for the
 // matrix `which` (variants 3-5).
-// spin_ns: device word, the main-loop wait budget in nanoseconds of the
+// spin_cycles: device word, the main-loop wait budget (SM clock cycles) of the
 // warp-specialised variants (4, 5); their drain waits keep a fixed budget.
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
                     double* y, const int* done, int* err, int variant, const void* tmaps,
-                    const unsigned long long* spin_ns, cudaStream_t st);
+                    const unsigned long long* spin_cycles, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
 // c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).

@@ -293,18 +293,21 @@ __global__ void __launch_bounds__(64) k_elem_hgo(int n_tets, const double* __res
 }
 
 // ---------------------------------------------------------------------------
+// T = double (FP64 factorization) or float (FP32 factorization: each entry
+// is summed in FP32 in element order).
+template <typename T>
 __global__ void k_assemble(const SubLayout* __restrict__ lay, const int32_t* __restrict__ sub_elem_ptr,
                            const int32_t* __restrict__ sub_elems, const int32_t* __restrict__ elem_dense,
-                           const double* __restrict__ Ke, double* __restrict__ Abase) {
+                           const double* __restrict__ Ke, T* __restrict__ Abase) {
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
-  double* A = Abase + L.aoff;
+  T* A = Abase + L.aoff;
   const int t = threadIdx.x;
   for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
     const int e = sub_elems[q];
     if (t < 144) {
       const int r = elem_dense[12 * e + t / 12], c = elem_dense[12 * e + t % 12];
-      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += Ke[(size_t)e * 144 + t];
+      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += (T)Ke[(size_t)e * 144 + t];
     }
     __syncthreads();
   }
@@ -377,11 +380,12 @@ __global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t*
   }
 }
 
-__global__ void k_augment(const SubLayout* __restrict__ lay, double* __restrict__ Abase) {
+template <typename T>
+__global__ void k_augment(const SubLayout* __restrict__ lay, T* __restrict__ Abase) {
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
-  double* A = Abase + L.aoff;
-  for (int j = threadIdx.x; j < L.nbp; j += blockDim.x) A[(size_t)(L.n + j) * L.ld + L.nI + j] = 1.0;
+  T* A = Abase + L.aoff;
+  for (int j = threadIdx.x; j < L.nbp; j += blockDim.x) A[(size_t)(L.n + j) * L.ld + L.nI + j] = (T)1;
 }
 
 // Block sizes of the dense Cholesky kernels: 32-column panels, 64x64 update tiles.
@@ -705,6 +709,102 @@ __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
   if (lane < PH && r0 + lane < m) y[L.boff + r0 + lane] = (double)mine;
 }
 
+// Subdomain-per-CTA variant of the symmetric FP32 apply, with no second
+// pass: CTA b takes subdomain order[b] (largest first), its eight warps take
+// the panels in a snake order (w, 15 - w, 16 + w, ..), each warp sweeps its
+// panel exactly as k_symv_f32 does, keeps the panel's row sums in shared
+// memory (one owner per row) and adds the transposed products of the blocks
+// left of the diagonal into its own shared-memory column buffer.  After a
+// barrier every row c gets row sum + the eight warps' column sums in warp
+// order (deterministic, no atomics).
+template <int G>
+__global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv3_f32(const int32_t* __restrict__ order,
+                                                          const SubLayout* __restrict__ lay, int which,
+                                                          const float* __restrict__ M,
+                                                          const float* __restrict__ vloc, double* __restrict__ y,
+                                                          const int* __restrict__ done) {
+  constexpr int PH = kSymPH;
+  constexpr int W = kThreads / 32;
+  if (*done) return;
+  extern __shared__ float s3[];
+  const int s = order[blockIdx.x];
+  const SubLayout L = lay[s];
+  const int m = which == 0 ? L.nbp : L.nbp + L.k;
+  const int mp = (m + 3) & ~3;
+  float* rowsum = s3;               // [mp]
+  float* colsum = s3 + mp;          // [W][mp]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < (W + 1) * mp; i += kThreads) s3[i] = 0.f;
+  if (which == 0)
+    for (int p = threadIdx.x; p < L.k; p += kThreads) y[L.boff + L.nbp + p] = 0.0;
+  __syncthreads();
+  const float* Mbase = M + (which == 0 ? L.fsym32 : L.ssym32);
+  const float* v = vloc + L.boff;
+  float* cs = colsum + (size_t)warp * mp;
+  const int nP = (m + PH - 1) / PH;
+  for (int q = 0;; ++q) {
+    const int base = (q >> 1) * 2 * W;
+    const int I = (q & 1) ? base + 2 * W - 1 - warp : base + warp;
+    if (base >= nP) break;
+    if (I >= nP) continue;
+    const int w = PH * (I + 1);
+    const int r0 = PH * I;
+    const float* Pn = Mbase + (size_t)(PH * PH / 2) * I * (I + 1);
+    const float vrow = (r0 + lane < m) ? v[r0 + lane] : 0.f;
+    float acc[PH];
+#pragma unroll
+    for (int i = 0; i < PH; ++i) acc[i] = 0.f;
+    for (int c0 = 0; c0 < w; c0 += 128) {
+      const int c = c0 + 4 * lane;
+      const bool ok = c < w;
+      const float4 vv = make_float4(c < m ? v[c] : 0.f, c + 1 < m ? v[c + 1] : 0.f, c + 2 < m ? v[c + 2] : 0.f,
+                                    c + 3 < m ? v[c + 3] : 0.f);
+      float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < PH / G; ++g) {
+        float4 a[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+          a[j] = ok ? __ldg(reinterpret_cast<const float4*>(Pn + (size_t)(g * G + j) * w + c))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int i = g * G + j;
+          acc[i] += a[j].x * vv.x + a[j].y * vv.y + a[j].z * vv.z + a[j].w * vv.w;
+          const float vi = __shfl_sync(0xffffffffu, vrow, i);
+          col.x += a[j].x * vi;
+          col.y += a[j].y * vi;
+          col.z += a[j].z * vi;
+          col.w += a[j].w * vi;
+        }
+      }
+      if (ok && c < r0) {
+        float4* d = reinterpret_cast<float4*>(cs + c);
+        float4 t = *d;
+        t.x += col.x;
+        t.y += col.y;
+        t.z += col.z;
+        t.w += col.w;
+        *d = t;
+      }
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int i = 0; i < PH; ++i) {
+      const float t = warp_sumf(acc[i]);
+      if (lane == i) mine = t;
+    }
+    if (r0 + lane < m) rowsum[r0 + lane] = mine;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += kThreads) {
+    float t = rowsum[c];
+#pragma unroll
+    for (int q = 0; q < W; ++q) t += colsum[(size_t)q * mp + c];
+    y[L.boff + c] = (double)t;
+  }
+}
+
 // Streamed variant of the symmetric FP32 apply: the same panels, partials
 // and fix kernel, but each warp streams its panel through a ring of SYM_NS
 // shared-memory stages of 32 rows x 64 columns (8 KB): every lane copies one
@@ -715,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, G == kSymPH ? 1 : 2) k_symv_f32(
 // 2j + h).  Warps are independent (no CTA barrier in the loop); all waits are
 // bounded, and a warp whose wait runs out flags *err, issues nothing more and
 // waits (bounded) for its copies in flight before it returns.  The main-loop
-// waits give up after *spin_ns nanoseconds (global timer; the context's spin
+// waits give up after *spin_cycles SM clock cycles (the context's spin
 // timeout); the drain waits keep a fixed budget of 2e8 clock cycles, so every
 // copy issued has landed before the warp leaves.
 constexpr int SYM_TW = 64;  // tile width (floats)
@@ -738,17 +838,14 @@ __device__ __forceinline__ bool sym_wait(uint64_t* b, uint32_t par) {
     if (clock64() - t0 > 200000000LL) return false;
   return true;
 }
-__device__ __forceinline__ unsigned long long sym_gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// main-loop wait with a caller-set budget in nanoseconds (global timer)
-__device__ __forceinline__ bool sym_wait_ns(uint64_t* b, uint32_t par, unsigned long long budget_ns) {
-  const unsigned long long t0 = sym_gtimer();
-  while (!sym_try(b, par))
-    if (sym_gtimer() - t0 > budget_ns) return false;
-  return true;
+// main-loop wait with a caller-set budget in SM clock cycles, checked before
+// every try (a zero budget gives up at once)
+__device__ __forceinline__ bool sym_wait_cycles(uint64_t* b, uint32_t par, long long budget) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (clock64() - t0 >= budget) return false;
+    if (sym_try(b, par)) return true;
+  }
 }
 
 __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __restrict__ wsub,
@@ -757,7 +854,7 @@ __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __res
                                                            const float* __restrict__ M, const float* __restrict__ vloc,
                                                            double* __restrict__ y, float* __restrict__ part,
                                                            const int* __restrict__ done, int* __restrict__ err,
-                                                           const unsigned long long* __restrict__ spin_ns) {
+                                                           const unsigned long long* __restrict__ spin_cycles) {
   if (*done) return;
   extern __shared__ __align__(128) unsigned char sym_smem[];
   __shared__ uint64_t full[SYM_WPC][SYM_NS];
@@ -805,10 +902,10 @@ __global__ void __launch_bounds__(SYM_WPC * 32) k_symv2_f32(const int32_t* __res
   for (int j = 0; j < 16; ++j) acc[j] = 0.f;
   bool bad = false;
   int t = 0;
-  const unsigned long long budget = *spin_ns;
+  const long long budget = (long long)*spin_cycles;
   for (; t < nt; ++t) {
     const int st = t % SYM_NS;
-    if (!sym_wait_ns(&fb[st], (uint32_t)(t / SYM_NS) & 1u, budget)) bad = true;
+    if (!sym_wait_cycles(&fb[st], (uint32_t)(t / SYM_NS) & 1u, budget)) bad = true;
     bad = __any_sync(0xffffffffu, bad);
     if (bad) break;
     const int c = t * SYM_TW + 4 * l16;
@@ -1364,7 +1461,12 @@ void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, cons
 
 void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
                      const int32_t* elem_dense, const double* Ke, double* A, cudaStream_t st) {
-  k_assemble<<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
+  k_assemble<double><<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
+}
+
+void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                     const int32_t* elem_dense, const double* Ke, float* A, cudaStream_t st) {
+  k_assemble<float><<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
 }
 
 void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_ptr, const int32_t* face_dense,
@@ -1381,8 +1483,36 @@ void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, c
   k_face_forces<<<(n_faces + 127) / 128, 128, 0, st>>>(n_faces, tri, coords, U, kind, scale, traction, out);
 }
 
+namespace {
+// A_ii += delta * max_j A_jj over the rows [0, nI + nbp) of K_rr in each
+// subdomain's dense workspace (a Levenberg-type shift of the local tangent).
+__global__ void k_shift_diag(const SubLayout* __restrict__ lay, double* __restrict__ Abase, double delta) {
+  const SubLayout L = lay[blockIdx.x];
+  double* A = Abase + L.aoff;
+  const int nr = L.nI + L.nbp;
+  __shared__ double wmax[kThreads / 32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) m = fmax(m, A[(size_t)i * L.ld + i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double mm = 0.0;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmax(mm, wmax[w]);
+  const double sh = delta * mm;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) A[(size_t)i * L.ld + i] += sh;
+}
+}  // namespace
+
+void launch_shift_diag(int P, const SubLayout* lay, double* A, double delta, cudaStream_t st) {
+  k_shift_diag<<<P, kThreads, 0, st>>>(lay, A, delta);
+}
+
 void launch_augment(int P, const SubLayout* lay, double* A, cudaStream_t st) {
-  k_augment<<<P, kThreads, 0, st>>>(lay, A);
+  k_augment<double><<<P, kThreads, 0, st>>>(lay, A);
+}
+
+void launch_augment(int P, const SubLayout* lay, float* A, cudaStream_t st) {
+  k_augment<float><<<P, kThreads, 0, st>>>(lay, A);
 }
 
 void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st) {
@@ -1502,9 +1632,25 @@ void launch_symv_f32(int G, int n_warps, const int32_t* wsub, const int32_t* wpa
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 
+void launch_symv3_f32(int G, int P, const int32_t* order, int max_m, const SubLayout* lay, int which,
+                      const float* Msym, const float* vloc, double* y, const int* done, cudaStream_t st) {
+  const size_t smem = (size_t)(kThreads / 32 + 1) * (((size_t)max_m + 3) & ~(size_t)3) * sizeof(float);
+  static size_t attr[3] = {0, 0, 0};
+  const int gi = G == 8 ? 0 : (G == 16 ? 1 : 2);
+  if (smem > 48 * 1024 && smem > attr[gi]) {
+    if (G == 8) cudaFuncSetAttribute(k_symv3_f32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (G == 16) cudaFuncSetAttribute(k_symv3_f32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else cudaFuncSetAttribute(k_symv3_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr[gi] = smem;
+  }
+  if (G == 8) k_symv3_f32<8><<<P, kThreads, smem, st>>>(order, lay, which, Msym, vloc, y, done);
+  else if (G == 16) k_symv3_f32<16><<<P, kThreads, smem, st>>>(order, lay, which, Msym, vloc, y, done);
+  else k_symv3_f32<32><<<P, kThreads, smem, st>>>(order, lay, which, Msym, vloc, y, done);
+}
+
 void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, const SubLayout* lay, int which,
                       const float* Msym, const float* vloc, double* y, float* part, const Maps& mp, const int* done,
-                      int* err, const unsigned long long* spin_ns, cudaStream_t st) {
+                      int* err, const unsigned long long* spin_cycles, cudaStream_t st) {
   const size_t smem = (size_t)SYM_WPC * SYM_NS * SYM_STAGE;
   static bool attr = false;
   if (!attr) {
@@ -1513,7 +1659,7 @@ void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, c
   }
   const int blocks = (n_warps + SYM_WPC - 1) / SYM_WPC;
   k_symv2_f32<<<blocks, SYM_WPC * 32, smem, st>>>(wsub, wpanel, n_warps, lay, which, Msym, vloc, y, part, done, err,
-                                                  spin_ns);
+                                                  spin_cycles);
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 
@@ -1836,7 +1982,8 @@ void launch_dense_chol_big(double* A, int ld, int c0, int c1, int n_act, int aug
 namespace {
 // Lumped preconditioner block K_bb in CSR over the boundary positions:
 // values gathered from the assembled (unfactorized) local matrices.
-__global__ void k_lump_fill(long nnz, const int64_t* __restrict__ src, const double* __restrict__ A,
+template <typename T>
+__global__ void k_lump_fill(long nnz, const int64_t* __restrict__ src, const T* __restrict__ A,
                             double* __restrict__ val) {
   for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < nnz; j += (long)gridDim.x * blockDim.x)
     val[j] = A[src[j]];
@@ -1863,7 +2010,12 @@ __global__ void __launch_bounds__(kThreads) k_spmv_lump(int n_rows, const int32_
 
 void launch_lump_fill(long nnz, const int64_t* src, const double* A, double* val, cudaStream_t st) {
   if (nnz <= 0) return;
-  k_lump_fill<<<grid_for(nnz), kThreads, 0, st>>>(nnz, src, A, val);
+  k_lump_fill<double><<<grid_for(nnz), kThreads, 0, st>>>(nnz, src, A, val);
+}
+
+void launch_lump_fill(long nnz, const int64_t* src, const float* A, double* val, cudaStream_t st) {
+  if (nnz <= 0) return;
+  k_lump_fill<float><<<grid_for(nnz), kThreads, 0, st>>>(nnz, src, A, val);
 }
 
 void launch_spmv_lump(int n_rows, const int32_t* ptr, const int32_t* col, const double* val, const double* v,
@@ -1921,29 +2073,30 @@ __device__ __forceinline__ ActiveRows active_rows(const SubLayout& L, int phase,
   return a;
 }
 
-__global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, double* __restrict__ Abase,
+template <typename T>
+__global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, T* __restrict__ Abase,
                            int* status) {
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
   const int kb = pr.c0 + step * NB;
   if (kb >= pr.c1) return;
   const int nk = min(NB, pr.c1 - kb);
-  double* A = Abase + L.aoff;
+  T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ double D[NB][NB + 1];
+  __shared__ T D[NB][NB + 1];
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
-    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : (T)0;
   }
   __syncthreads();
   if (tid < 32) {
     const int i = tid;
     for (int j = 0; j < nk; ++j) {
       if (i == j) {
-        const double d = D[j][j];
+        const T d = D[j][j];
         if (!(d > 0.0) || !isfinite(d)) bad = 1;
         D[j][j] = sqrt(d);
       }
@@ -1967,8 +2120,9 @@ __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int ste
   }
 }
 
+template <typename T>
 __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int step,
-                           const int32_t* __restrict__ env0, double* __restrict__ Abase, const int* status) {
+                           const int32_t* __restrict__ env0, T* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
@@ -1979,28 +2133,28 @@ __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int ste
   const int q0 = blockIdx.x * TT;
   if (q0 >= ar.m) return;
   const int nr = min(TT, ar.m - q0);
-  double* A = Abase + L.aoff;
+  T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ double D[NB][NB + 1];
-  __shared__ double Pa[TT][NB + 1];
+  __shared__ T D[NB][NB + 1];
+  __shared__ T Pa[TT][NB + 1];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
-    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : 0.0;
+    D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : (T)0;
   }
   for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
     const int r = idx / NB, l = idx % NB;
-    Pa[r][l] = (r < nr && l < nk) ? A[(size_t)ar.row(q0 + r) * ld + kb + l] : 0.0;
+    Pa[r][l] = (r < nr && l < nk) ? A[(size_t)ar.row(q0 + r) * ld + kb + l] : (T)0;
   }
   __syncthreads();
   if (tid < nr) {
-    double xr[NB];
+    T xr[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if (j < nk) {
-        double v = xr[j];
+        T v = xr[j];
 #pragma unroll
         for (int l = 0; l < NB; ++l)
           if (l < j) v -= xr[l] * D[j][l];
@@ -2017,9 +2171,10 @@ __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int ste
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __restrict__ lay, int phase, int step,
                                                          const int32_t* __restrict__ env0,
-                                                         double* __restrict__ Abase, const int* status) {
+                                                         T* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
@@ -2036,25 +2191,25 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   while ((long)ti * (ti + 1) / 2 > b) --ti;
   const int tj = (int)(b - (long)ti * (ti + 1) / 2);
   const int ib = ti * TT, jb = tj * TT;  // positions in the active-row list
-  double* A = Abase + L.aoff;
+  T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ double Pa[TT][NB + 1];
-  __shared__ double Pb[TT][NB + 1];
+  __shared__ T Pa[TT][NB + 1];
+  __shared__ T Pb[TT][NB + 1];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
     const int r = idx / NB, l = idx % NB;
-    Pa[r][l] = (ib + r < m && l < nk) ? A[(size_t)ar.row(ib + r) * ld + kb + l] : 0.0;
-    Pb[r][l] = (jb + r < m && l < nk) ? A[(size_t)ar.row(jb + r) * ld + kb + l] : 0.0;
+    Pa[r][l] = (ib + r < m && l < nk) ? A[(size_t)ar.row(ib + r) * ld + kb + l] : (T)0;
+    Pb[r][l] = (jb + r < m && l < nk) ? A[(size_t)ar.row(jb + r) * ld + kb + l] : (T)0;
   }
   __syncthreads();
   const int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (int c = 0; c < 4; ++c) acc[a][c] = (T)0;
   for (int l = 0; l < nk; ++l) {
-    double av[4], bv[4];
+    T av[4], bv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       av[a] = Pa[tr + a][l];
@@ -2075,16 +2230,27 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
 }
 }  // namespace
 
-void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
-                         const int32_t* env0, double* A, int* status, cudaStream_t st) {
+template <typename T>
+void chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                  const int32_t* env0, T* A, int* status, cudaStream_t st) {
   for (int t = 0; t < n_steps; ++t) {
     const int chunks = step_chunks[t];
-    k_bat_diag<<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    k_bat_diag<T><<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
     if (chunks <= 0) continue;
-    k_bat_trsm<<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
+    k_bat_trsm<T><<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
     const long tiles = (long)chunks * (chunks + 1) / 2;
-    k_bat_update<<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
+    k_bat_update<T><<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
   }
+}
+
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                         const int32_t* env0, double* A, int* status, cudaStream_t st) {
+  chol_batched<double>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
+}
+
+void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
+                         const int32_t* env0, float* A, int* status, cudaStream_t st) {
+  chol_batched<float>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
 }
 
 }  // namespace feti

@@ -1010,30 +1010,24 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc3(const int32_t* __restrict
 // bounded wait that runs out sets a shared abort flag that ends every role's
 // loop; the producer then waits (bounded) for its own loads in flight and
 // the MMA lane for its last commit before tensor memory is freed.  The
-// main-loop waits give up after *spin_ns nanoseconds (the context's spin
-// timeout); those drain waits keep a fixed 2e8-cycle budget, so every load
-// and MMA issued has completed before tensor memory is released.
+// main-loop waits give up after *spin_cycles SM clock cycles (the context's
+// spin timeout); those drain waits keep a fixed 2e8-cycle budget, so every
+// load and MMA issued has completed before tensor memory is released.
 constexpr int TC4_TCOLS = 64;  // three 16-column accumulators
 
-__device__ __forceinline__ unsigned long long tc_gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Main-loop wait: gives up after budget_ns nanoseconds of the global timer
-// (the context's spin timeout) or when another role has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* b, uint32_t par, volatile int* abort_flag,
-                                              unsigned long long budget_ns) {
-  const unsigned long long t0 = tc_gtimer();
-  while (!mbar_try(b, par)) {
+// Main-loop wait: gives up after `budget` SM clock cycles (the context's spin
+// timeout; checked before every try, so a zero budget gives up at once) or
+// when another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* b, uint32_t par, volatile int* abort_flag, long long budget) {
+  const long long t0 = clock64();
+  for (;;) {
     if (*abort_flag) return false;
-    if (tc_gtimer() - t0 > budget_ns) {
+    if (clock64() - t0 >= budget) {
       *abort_flag = 1;
       return false;
     }
+    if (mbar_try(b, par)) return true;
   }
-  return true;
 }
 
 template <int NS>
@@ -1043,7 +1037,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc4(const int32_t* __restrict
                                                        const CUtensorMap* __restrict__ maps, int nrhs,
                                                        const float* __restrict__ vloc, double* __restrict__ y,
                                                        const int* __restrict__ done, int* __restrict__ err,
-                                                       const unsigned long long* __restrict__ spin_ns) {
+                                                       const unsigned long long* __restrict__ spin_cycles) {
   if (*done) return;
   extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
   unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
@@ -1081,7 +1075,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc4(const int32_t* __restrict
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
   const int nk = (m + 31) / 32;
   volatile int* ab = &abort_flag;
-  const unsigned long long budget = *spin_ns;
+  const long long budget = (long long)*spin_cycles;
   if (wid == 0) {
     if (lane == 0) {  // producer: chunk kc -> stage kc % NS once the MMAs of chunk kc - NS are done
       int issued = 0;
@@ -1258,7 +1252,7 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
                     double* y, const int* done, int* err, int variant, const void* tmaps,
-                    const unsigned long long* spin_ns, cudaStream_t st) {
+                    const unsigned long long* spin_cycles, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -1276,10 +1270,10 @@ void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const f
     const CUtensorMap* mp = static_cast<const CUtensorMap*>(tmaps);
     if (variant == 4)
       k_gemm_tc4<3><<<cfg.n_blocks, kThreads, 3 * TC_STAGE + 1024, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, mp,
-                                                                        nrhs, vloc, y, done, err, spin_ns);
+                                                                        nrhs, vloc, y, done, err, spin_cycles);
     else
       k_gemm_tc4<2><<<cfg.n_blocks, kThreads, 2 * TC_STAGE + 1024, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which, mp,
-                                                                        nrhs, vloc, y, done, err, spin_ns);
+                                                                        nrhs, vloc, y, done, err, spin_cycles);
   } else if (variant == 3)
     k_gemm_tc3<<<cfg.n_blocks, kThreads, TC3_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, lay, which,
                                                          static_cast<const CUtensorMap*>(tmaps), nrhs, vloc, y, done,

@@ -4,10 +4,10 @@ The streamed symmetric FP32 apply and the warp-specialised tensor-core block
 GEMM wait on mbarriers for their bulk / tensor-map copies and tensor-core
 products.  Their main-loop waits give up after the context's spin timeout
 (feti_options.spin_timeout_ns, feti_set_spin_timeout).  Here that budget is
-set to 1 ns after set-up, so the waits run out on copies that are still in
-flight; each kernel then stops its pipeline, waits for what it issued (those
-drain waits keep their full budget), releases tensor memory and flags the
-call.  The solve must return FETI_ERR_TIMEOUT (9), and the next solve on the
+set to zero after set-up, so every main-loop wait gives up at its first check
+while the copies it waits for are still in flight; each kernel then stops its
+pipeline, waits for what it issued (those drain waits keep their full
+budget), releases tensor memory and flags the call.  The solve must return FETI_ERR_TIMEOUT (9), and the next solve on the
 same context, with the default budget again, must match the FP64 oracle.
 Nothing traps, faults or spins without a bound.
 """
@@ -47,11 +47,11 @@ def test_streamed_symmetric_apply_times_out_then_recovers(case):
                     tol=1e-10, maxit=60) as s:
         s.prepare()
         assert s.schedule()["fp32_F"][0] == -64          # the streamed kernel is the one in use
-        s.set_spin_timeout(1)
+        s.set_spin_timeout(0)
         with pytest.raises(FetiError) as ei:
             s.solve()
         assert ei.value.status == 9 and "bounded wait" in str(ei.value)
-        s.set_spin_timeout(0)
+        s.set_spin_timeout(100_000_000)
         U, rep = s.solve()
         assert rep["converged"] == 1
         assert _rel(U, U_ref) <= 1e-8
@@ -65,11 +65,11 @@ def test_tensor_core_block_gemm_times_out_then_recovers(case):
                     tol=1e-10, maxit=60) as s:
         U, _ = s.solve_multi(scales)                     # tunes the block schedules with the default budget
         assert s.schedule()["block_fp32_F"][0] == -3     # warp-specialised 3-stage kernel
-        s.set_spin_timeout(1)
+        s.set_spin_timeout(0)
         with pytest.raises(FetiError) as ei:
             s.solve_multi(scales)
         assert ei.value.status == 9 and "bounded wait" in str(ei.value)
-        s.set_spin_timeout(0)
+        s.set_spin_timeout(100_000_000)
         U, rep = s.solve_multi(scales)
         assert rep["converged"] == 1
         for k, sc in enumerate(scales):

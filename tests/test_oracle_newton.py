@@ -10,29 +10,7 @@ def _small_tube(pressure=0.13332):   # 1 mmHg, as in Tables 4-7
 
 
 def _monolithic_newton(prob, steps, follower, tol=1e-10):
-    N = prob.n_nodes
-    U = np.zeros(3 * N)
-    free = np.ones(3 * N, bool)
-    free[prob.dir_dof] = False
-    hist = []
-    for s in range(1, steps + 1):
-        tau = s / steps
-        h = []
-        for _ in range(30):
-            Ke, fint = fem.element_matrices(prob, U.reshape(-1, 3))
-            fext = fem.load_vector(prob, U.reshape(-1, 3), follower)
-            R = fem.internal_force_global(prob, fint) - tau * fext
-            h.append(np.linalg.norm(R[free]) / np.linalg.norm(tau * fext[free]))
-            if h[-1] <= tol:
-                break
-            K = fem.assemble_global(prob, Ke)
-            dU = np.zeros(3 * N)
-            idx = np.nonzero(free)[0]
-            import scipy.sparse.linalg as spla
-            dU[idx] = spla.spsolve(K[idx][:, idx].tocsc(), -R[idx])
-            U = U + dU
-        hist.append(h)
-    return U, hist
+    return feti.monolithic_newton(prob, steps, follower, tol)
 
 
 def test_dead_load_newton_converges_quadratically():
