@@ -20,6 +20,7 @@ _PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 
 LINEAR_ISO = 0
 HGO_TWO_FIBRE = 1
+LINEAR_ISO_P0 = 2
 
 # Table 1 of the paper: matrix and fibre parameters of the media (kPa).
 TABLE1_C = 3.0
@@ -126,8 +127,9 @@ def _empty_tri():
     return np.zeros((0, 3), dtype=np.int32), np.zeros(0, dtype=np.int32)
 
 
-def linear_material(E: float = 1.0, nu: float = 0.3) -> dict:
-    return {"kind": LINEAR_ISO, "E": float(E), "nu": float(nu),
+def linear_material(E: float = 1.0, nu: float = 0.3, p0: bool = False) -> dict:
+    """Hooke's law; p0: volumetric part condensed to a piecewise-constant pressure (P2-P0 on P2 meshes)."""
+    return {"kind": LINEAR_ISO_P0 if p0 else LINEAR_ISO, "E": float(E), "nu": float(nu),
             "c": 0.0, "k1": 0.0, "k2": 0.0, "kappa": 0.0}
 
 
@@ -366,6 +368,89 @@ def jittered_cylinder_problem(nr: int, nt: int, nz: int, n_parts: int, mesh_seed
         meta={"cells": (nr, nt, nz), "parts": n_parts, "mesh_seed": mesh_seed,
               "part_seed": part_seed, "jitter": jitter, "cut_jitter": cut_jitter,
               "r_in": r_in, "r_out": r_out, "length": length})
+
+
+# Edges of a tetrahedron in the P2 node order: nodes 4..9 are the midpoints of
+# the vertex pairs (0,1), (0,2), (0,3), (1,2), (1,3), (2,3).
+P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+
+
+def p2_problem(prob: Problem, dirichlet=None) -> Problem:
+    """The same problem on 10-node (P2) tetrahedra: the P1 mesh's vertices keep
+    their numbers, each edge gets a midpoint node numbered after them (edges in
+    order of their sorted vertex pairs), tets become [E, 10] (vertices, then the
+    midpoints of P2_EDGES) and loaded triangles [T, 6] (vertices v0 v1 v2, then
+    the midpoints of (v0,v1), (v1,v2), (v2,v0)).  dirichlet(coords) -> (dofs,
+    values) recomputes the Dirichlet data on the new node set (default: a DOF is
+    prescribed iff both end vertices of its edge carry that DOF, with the mean
+    of their values -- exact for homogeneous and affine data)."""
+    N = prob.n_nodes
+    t = prob.tets.astype(np.int64)
+    pairs = np.concatenate([np.sort(t[:, [a, b]], axis=1) for a, b in P2_EDGES], axis=0)
+    key = pairs[:, 0] * N + pairs[:, 1]
+    uniq, inv = np.unique(key, return_inverse=True)
+    ea, eb = uniq // N, uniq % N
+    coords = np.concatenate([prob.coords, 0.5 * (prob.coords[ea] + prob.coords[eb])], axis=0)
+    E = t.shape[0]
+    mid = (N + inv).reshape(6, E).T
+    tets10 = np.concatenate([t, mid], axis=1).astype(np.int32)
+    edge_id = dict(zip(uniq.tolist(), range(uniq.size)))
+
+    def midpoint(a, b):
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        return N + np.array([edge_id[k] for k in (lo * N + hi).tolist()], dtype=np.int64)
+
+    def faces6(tri):
+        if tri.shape[0] == 0:
+            return np.zeros((0, 6), np.int32)
+        tri = tri.astype(np.int64)
+        m01 = midpoint(tri[:, 0], tri[:, 1])
+        m12 = midpoint(tri[:, 1], tri[:, 2])
+        m20 = midpoint(tri[:, 2], tri[:, 0])
+        return np.concatenate([tri, m01[:, None], m12[:, None], m20[:, None]], axis=1).astype(np.int32)
+
+    if dirichlet is not None:
+        dir_dof, dir_val = dirichlet(coords)
+    else:
+        pres = np.zeros(3 * N, bool)
+        val = np.zeros(3 * N)
+        pres[prob.dir_dof] = True
+        val[prob.dir_dof] = prob.dir_val
+        d, v = [prob.dir_dof.astype(np.int64)], [prob.dir_val]
+        for c in range(3):
+            both = pres[3 * ea + c] & pres[3 * eb + c]
+            idx = np.nonzero(both)[0]
+            d.append(3 * (N + idx) + c)
+            v.append(0.5 * (val[3 * ea[idx] + c] + val[3 * eb[idx] + c]))
+        d, v = np.concatenate(d), np.concatenate(v)
+        order = np.argsort(d)
+        dir_dof, dir_val = d[order], v[order]
+    meta = dict(prob.meta)
+    meta["order"] = 2
+    return Problem(name=prob.name + "_p2", coords=coords, tets=tets10, part=prob.part.copy(), n_parts=prob.n_parts,
+                   dir_dof=np.asarray(dir_dof, dtype=np.int32), dir_val=np.asarray(dir_val, dtype=np.float64),
+                   press_tri=faces6(prob.press_tri), press_owner=prob.press_owner.copy(), pressure=prob.pressure,
+                   trac_tri=faces6(prob.trac_tri), trac_owner=prob.trac_owner.copy(), traction=prob.traction.copy(),
+                   material=dict(prob.material), fibres=None if prob.fibres is None else prob.fibres.copy(), meta=meta)
+
+
+def kelvin_cube_problem_p2(n: int = 4, parts=(2, 2, 2), E: float = 210.0, nu: float = 0.45,
+                           x_star=(-0.5, -0.5, -0.5)) -> Problem:
+    """Kelvin-solution cube on P2 tetrahedra (the quadratic study of Sec. 5.1,
+    Table 3): Dirichlet data of Kelvin's solution at every boundary node,
+    vertices and edge midpoints."""
+    base = kelvin_cube_problem(n, parts, E=E, nu=nu, x_star=x_star)
+
+    def kelvin_data(coords):
+        tol = 1e-12
+        on_b = np.any((coords < tol) | (coords > 1.0 - tol), axis=1)
+        bn = np.nonzero(on_b)[0]
+        uD = kelvin_displacement(coords[bn], E, nu, x_star)
+        dof = (3 * bn[:, None] + np.arange(3)[None, :]).ravel()
+        order = np.argsort(dof)
+        return dof[order], uD.ravel()[order]
+
+    return p2_problem(base, kelvin_data)
 
 
 def config_problem(name: str) -> Problem:

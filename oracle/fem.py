@@ -1,4 +1,4 @@
-"""FP64 finite-element building blocks of the oracle (P1 tetrahedra).
+"""FP64 finite-element building blocks of the oracle (P1 and P2-P0 tetrahedra).
 
 Follows Sec. 3 (kinematics, Eq. for F, C, J and the Flory split; the energy of
 Eq. (isoaniso) with the volumetric penalty, neo-Hooke matrix and the two
@@ -33,6 +33,7 @@ import scipy.sparse.linalg as spla
 
 LINEAR_ISO = 0
 HGO_TWO_FIBRE = 1
+LINEAR_ISO_P0 = 2   # Hooke's law with the volumetric part condensed to a piecewise-constant pressure
 FIBRE_ACTIVE_EPS = 1e-12
 
 # Derivatives of the P1 shape functions w.r.t. barycentric reference coords.
@@ -65,6 +66,72 @@ def linear_element(X: np.ndarray, E: float, nu: float) -> np.ndarray:
          + mu * np.einsum("eaj,ebi->eaibj", g, g))
     K *= V[:, None, None, None, None]
     return K.reshape(-1, 12, 12)
+
+
+# P2-P0 tetrahedra (Sec. 3.2, static condensation; Sec. 5.1, Table 3).
+# Ten nodes: the vertices, then the midpoints of the edges (0,1), (0,2), (0,3),
+# (1,2), (1,3), (2,3).  In barycentric coordinates L_0..L_3 the shape
+# functions are N_a = L_a (2 L_a - 1) at a vertex and N_ab = 4 L_a L_b at the
+# midpoint of edge (a, b).
+P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+# Degree-2 Gauss rule on the tetrahedron: the four points with barycentric
+# coordinates (alpha, beta, beta, beta) and permutations, equal weights 1/4
+# (alpha = (5 + 3 sqrt 5) / 20, beta = (5 - sqrt 5) / 20).
+_Q2_ALPHA = (5.0 + 3.0 * np.sqrt(5.0)) / 20.0
+_Q2_BETA = (5.0 - np.sqrt(5.0)) / 20.0
+Q2_POINTS = np.array([[_Q2_ALPHA if j == i else _Q2_BETA for j in range(4)] for i in range(4)])
+Q2_WEIGHTS = np.full(4, 0.25)
+
+
+def p2_shape_values(Lq: np.ndarray) -> np.ndarray:
+    """P2 shape function values [Q, 10] at barycentric points Lq [Q, 4]."""
+    N = np.empty((Lq.shape[0], 10))
+    for a in range(4):
+        N[:, a] = Lq[:, a] * (2.0 * Lq[:, a] - 1.0)
+    for e, (a, b) in enumerate(P2_EDGES):
+        N[:, 4 + e] = 4.0 * Lq[:, a] * Lq[:, b]
+    return N
+
+
+def p2_shape_gradients(X: np.ndarray, Lq: np.ndarray = Q2_POINTS):
+    """Gradients [E, Q, 10, 3] of the P2 shape functions at the barycentric
+    points Lq and the volume [E] (straight-sided tetrahedra: X [E, >=4, 3],
+    the vertices first).  grad N_a = (4 L_a - 1) grad L_a,
+    grad N_ab = 4 (L_a grad L_b + L_b grad L_a)."""
+    gL, V = shape_gradients(X[:, :4])           # gradients of the barycentric coordinates
+    Q = Lq.shape[0]
+    g = np.empty((X.shape[0], Q, 10, 3))
+    for a in range(4):
+        g[:, :, a, :] = (4.0 * Lq[None, :, a, None] - 1.0) * gL[:, None, a, :]
+    for e, (a, b) in enumerate(P2_EDGES):
+        g[:, :, 4 + e, :] = 4.0 * (Lq[None, :, a, None] * gL[:, None, b, :] + Lq[None, :, b, None] * gL[:, None, a, :])
+    return g, V
+
+
+def linear_p2_element(X: np.ndarray, E: float, nu: float, p0: bool = False) -> np.ndarray:
+    """P2 element matrices K_e [E, 30, 30] (dof = 3 * node + comp) for Hooke's law.
+
+    p0 = False: the displacement element of the linear cube study (Table 3),
+    K[a i, b j] = int lambda g_a,i g_b,j + mu (delta_ij g_a . g_b + g_a,j g_b,i).
+    p0 = True: P2-P0, the volumetric part carried by a piecewise-constant
+    pressure p and condensed out element by element (Sec. 3.2, static
+    condensation): with int q (div u - p / lambda) = 0, p = lambda (int div u) / V,
+    so the lambda term becomes lambda V bbar_a,i bbar_b,j, bbar_a = (int g_a) / V.
+    The integrands are of degree 2 in the coordinates, exact with the degree-2
+    Gauss rule.
+    """
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    g, V = p2_shape_gradients(X)
+    w = Q2_WEIGHTS
+    gg = np.einsum("q,eqak,eqbk->eab", w, g, g)
+    K = mu * (np.einsum("ij,eab->eaibj", np.eye(3), gg) + np.einsum("q,eqaj,eqbi->eaibj", w, g, g))
+    if p0:
+        bbar = np.einsum("q,eqai->eai", w, g)
+        K = K + lam * np.einsum("eai,ebj->eaibj", bbar, bbar)
+    else:
+        K = K + lam * np.einsum("q,eqai,eqbj->eaibj", w, g, g)
+    return (K * V[:, None, None, None, None]).reshape(-1, 30, 30)
 
 
 def hgo_energy(C: np.ndarray, a1: np.ndarray, a2: np.ndarray, mat: dict) -> np.ndarray:
@@ -156,7 +223,11 @@ def element_matrices(prob, U: np.ndarray | None = None):
     """
     X = prob.coords[prob.tets]
     mat = prob.material
-    if mat["kind"] == LINEAR_ISO:
+    if prob.tets.shape[1] == 10:
+        if mat["kind"] not in (LINEAR_ISO, LINEAR_ISO_P0):
+            raise NotImplementedError("P2 elements are built for the linear material")
+        return linear_p2_element(X, mat["E"], mat["nu"], p0=mat["kind"] == LINEAR_ISO_P0), None
+    if mat["kind"] in (LINEAR_ISO, LINEAR_ISO_P0):   # on P1 the element mean of div u is div u itself
         return linear_element(X, mat["E"], mat["nu"]), None
     if U is None:
         U = np.zeros_like(prob.coords)
@@ -167,11 +238,39 @@ def element_matrices(prob, U: np.ndarray | None = None):
 
 
 def surface_loads(prob, U: np.ndarray | None = None, follower: bool = True):
-    """P1-consistent nodal loads per loaded triangle.
+    """Consistent nodal loads per loaded triangle.
 
-    Returns (owner tet [T], vertices [T,3], force per vertex [T,3]) for the
-    pressure and traction triangles together.
+    Returns (owner tet [T], nodes [T,3] or [T,6], force per node [T,3] or
+    [T,6,3]) for the pressure and traction triangles together.  P1 (3-node)
+    triangles: a third of the force to each vertex.  P2 (6-node, flat)
+    triangles under a constant load: int N = 0 at the vertices and A/3 at the
+    edge midpoints.
     """
+    if prob.trac_tri.shape[1:] == (6,) or prob.press_tri.shape[1:] == (6,):
+        owners, nodes, forces = [], [], []
+        if prob.press_tri.shape[0]:
+            if U is not None and follower:
+                raise NotImplementedError("follower pressure on P2 faces")
+            x = prob.coords
+            t = prob.press_tri
+            av = 0.5 * np.cross(x[t[:, 1]] - x[t[:, 0]], x[t[:, 2]] - x[t[:, 0]])
+            f = np.zeros((t.shape[0], 6, 3))
+            f[:, 3:, :] = (prob.pressure * av / 3.0)[:, None, :]
+            owners.append(prob.press_owner)
+            nodes.append(t)
+            forces.append(f)
+        if prob.trac_tri.shape[0]:
+            x = prob.coords
+            t = prob.trac_tri
+            area = 0.5 * np.linalg.norm(np.cross(x[t[:, 1]] - x[t[:, 0]], x[t[:, 2]] - x[t[:, 0]]), axis=1)
+            f = np.zeros((t.shape[0], 6, 3))
+            f[:, 3:, :] = (area[:, None] * prob.traction[None, :] / 3.0)[:, None, :]
+            owners.append(prob.trac_owner)
+            nodes.append(t)
+            forces.append(f)
+        if not owners:
+            return np.zeros(0, np.int64), np.zeros((0, 6), np.int64), np.zeros((0, 6, 3))
+        return np.concatenate(owners), np.concatenate(nodes), np.concatenate(forces)
     owners, verts, forces = [], [], []
     if prob.press_tri.shape[0]:
         x = prob.coords.copy()
@@ -196,9 +295,10 @@ def surface_loads(prob, U: np.ndarray | None = None, follower: bool = True):
 
 def assemble_global(prob, Ke: np.ndarray) -> sp.csr_matrix:
     """Global stiffness K'[i,j] (Sec. 3.2) as a sparse matrix on all 3N DOFs."""
-    dofs = (3 * prob.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
-    rows = np.repeat(dofs, 12, axis=1).ravel()
-    cols = np.tile(dofs, (1, 12)).ravel()
+    nd = 3 * prob.tets.shape[1]
+    dofs = (3 * prob.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, nd)
+    rows = np.repeat(dofs, nd, axis=1).ravel()
+    cols = np.tile(dofs, (1, nd)).ravel()
     n = 3 * prob.n_nodes
     return sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
 
@@ -207,6 +307,10 @@ def load_vector(prob, U=None, follower=True) -> np.ndarray:
     """Global external load vector on all 3N DOFs."""
     _, verts, forces = surface_loads(prob, U, follower)
     f = np.zeros(3 * prob.n_nodes)
+    if verts.shape[1:] == (6,):
+        for v in range(6):
+            np.add.at(f, (3 * verts[:, v][:, None] + np.arange(3)[None, :]).ravel(), forces[:, v, :].ravel())
+        return f
     for v in range(3):
         np.add.at(f, (3 * verts[:, v][:, None] + np.arange(3)[None, :]).ravel(), forces.ravel())
     return f

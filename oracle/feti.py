@@ -267,21 +267,27 @@ class FetiOracle:
         Ke, fint = fem.element_matrices(prob, None if U is None else U.reshape(-1, 3))
         owners, verts, forces = fem.surface_loads(prob, None if U is None else U.reshape(-1, 3), follower)
         tri_part = prob.part[owners] if owners.size else np.zeros(0, np.int64)
+        nd = 3 * prob.tets.shape[1]
         for s, sd in enumerate(self.subs):
             nod = sd.nodes
             ndof = 3 * nod.size
             els = np.nonzero(prob.part == s)[0]
             ln = np.searchsorted(nod, prob.tets[els])
-            ld = (3 * ln[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
+            ld = (3 * ln[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, nd)
             Kfull = np.zeros((ndof, ndof))
             np.add.at(Kfull, (ld[:, :, None], ld[:, None, :]), Ke[els])
             ffull = np.zeros(ndof)
             tri = np.nonzero(tri_part == s)[0]
             if tri.size:
                 lt = np.searchsorted(nod, verts[tri])
-                for v in range(3):
-                    np.add.at(ffull, (3 * lt[:, v][:, None] + np.arange(3)[None, :]).ravel(),
-                              (tau * forces[tri]).ravel())
+                if verts.shape[1] == 6:       # P2 faces: a force per face node
+                    for v in range(6):
+                        np.add.at(ffull, (3 * lt[:, v][:, None] + np.arange(3)[None, :]).ravel(),
+                                  (tau * forces[tri][:, v, :]).ravel())
+                else:
+                    for v in range(3):
+                        np.add.at(ffull, (3 * lt[:, v][:, None] + np.arange(3)[None, :]).ravel(),
+                                  (tau * forces[tri]).ravel())
             if fint is not None:
                 np.add.at(ffull, ld.ravel(), -fint[els].ravel())
             gdof = (3 * nod[:, None] + np.arange(3)[None, :]).ravel()
