@@ -331,9 +331,12 @@ class FetiOracle:
         return x
 
     def _coarse(self):
-        cols = [sd.B @ sd.R for sd in self.subs if sd.R.shape[1]]
-        self.G = np.hstack(cols) if cols else np.zeros((self.n_lambda, 0))
-        self.GtG = self.G.T @ self.G
+        """G = [B_1 R_1, ..., B_p R_p] (Sec. 4.3, read as column blocks), kept
+        sparse: block i is nonzero only on the multiplier rows of subdomain i;
+        G^T G is dense (cd x cd) and factored by Cholesky."""
+        cols = [sp.csc_matrix(sd.B @ sd.R) for sd in self.subs if sd.R.shape[1]]
+        self.G = sp.hstack(cols, format="csr") if cols else sp.csr_matrix((self.n_lambda, 0))
+        self.GtG = (self.G.T @ self.G).toarray()
         self.GtG_chol = sla.cho_factor(self.GtG, lower=True) if self.G.shape[1] else None
 
     # ---- dual operators (Sec. 4.3) --------------------------------------
