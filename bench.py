@@ -112,6 +112,14 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# DRAM bytes per F_i apply of the dominant FP32 kernel, from the ncu capture in
+# profiles/k_symv3_f32_traffic_jittered_tube_16x64x32_128sub.md (128 subdomains
+# of the same size mix, dram__bytes_read.sum + dram__bytes_write.sum of the
+# second F_i launch = 1.075 x the algorithmic bytes there), scaled by the
+# algorithmic bytes of the workload; only for the kernel variant captured.
+TRAFFIC_RATIO = {"k_symv3_f32<32>": 1.075}
+
+
 def cpu_baseline(prob, n_apply: int, budget_s: float = 20.0) -> dict:
     """The FP64 oracle's dual apply on the host cores (bounded sample)."""
     import numpy as np
@@ -471,7 +479,13 @@ def main():
                                     if m32["sched"]["fp32_F"][0] < 0 else "k_gemv_loc<float> (F_i apply, FP32 copy)"),
                          "achieved": gbs32,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs32 / peaks["hbm_gbs"],
-                         "traffic": None, "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
+                         "traffic": (TRAFFIC_RATIO["k_symv3_f32<32>"] * ks32["gemv_bytes"]
+                                     if m32["sched"]["fp32_F"][0] == -332 else None),
+                         "traffic_note": "dram read+write per launch from an ncu capture of the same kernel on "
+                                         "128 subdomains of the same size mix, scaled by algorithmic bytes "
+                                         "(profiles/k_symv3_f32_traffic_jittered_tube_16x64x32_128sub.md); null "
+                                         "for a kernel variant that was not captured",
+                         "kernel_ms": m32["kern_ms"], "algorithmic_bytes": ks32["gemv_bytes"],
                          "bytes_note": "n(n+1)/2 distinct FP32 entries per symmetric F_i + 16 B per boundary DOF",
                          "peak_source": src},
             "clocks": m32["clocks"],

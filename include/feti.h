@@ -48,7 +48,13 @@ typedef enum {
   FETI_ERR_IO = 13               /* checkpoint file not writable, unreadable or corrupt */
 } feti_status;
 
-enum { FETI_LINEAR_ISO = 0, FETI_HGO_TWO_FIBRE = 1 };          /* feti_material.kind */
+/* feti_material.kind: FETI_LINEAR_ISO -- Hooke's law (E, nu); FETI_HGO_TWO_FIBRE
+ * -- the two-fibre hyperelastic energy (P1 only); FETI_LINEAR_ISO_P0 -- Hooke's
+ * law with the volumetric part carried by a piecewise-constant pressure that
+ * is condensed out element by element (Sec. 3.2, static condensation): the
+ * P2-P0 element on 10-node meshes; on 4-node meshes identical to
+ * FETI_LINEAR_ISO (the element mean of div u is div u itself). */
+enum { FETI_LINEAR_ISO = 0, FETI_HGO_TWO_FIBRE = 1, FETI_LINEAR_ISO_P0 = 2 };
 enum { FETI_CLASSICAL = 0, FETI_ALL_FLOATING = 1 };             /* feti_options.method */
 enum { FETI_PREC_IDENTITY = 0, FETI_PREC_LUMPED = 1, FETI_PREC_DIRICHLET = 2 };
 /* feti_options.precision: FETI_FP64 -- every operator in FP64; FETI_MIXED --
@@ -62,10 +68,13 @@ enum { FETI_PREC_IDENTITY = 0, FETI_PREC_LUMPED = 1, FETI_PREC_DIRICHLET = 2 };
  * matrices (mixed-precision iterative refinement); linear solves only. */
 enum { FETI_FP64 = 0, FETI_MIXED = 1, FETI_MIXED_F32FACTOR = 2 };
 
-/* Mesh T_N of Sec. 3.2 (P1 tetrahedra) and its non-overlapping decomposition
- * (Sec. 4, Eq. decomposition).  coords: [n_nodes*3] reference coordinates;
- * tets: [n_tets*4] node ids, positive orientation; part: [n_tets] subdomain
- * id in [0, n_parts).  Every subdomain must own at least one tetrahedron. */
+/* Mesh T_N of Sec. 3.2 and its non-overlapping decomposition (Sec. 4, Eq.
+ * decomposition).  coords: [n_nodes*3] reference coordinates; tets:
+ * [n_tets*nodes_per_tet] node ids, positive orientation; part: [n_tets]
+ * subdomain id in [0, n_parts).  Every subdomain must own at least one
+ * tetrahedron.  nodes_per_tet: 4 (P1; 0 is read as 4) or 10 (P2, straight
+ * edges: the four vertices, then the midpoints of the edges (0,1), (0,2),
+ * (0,3), (1,2), (1,3), (2,3); linear materials only; Sec. 5.1, Table 3). */
 typedef struct {
   int32_t n_nodes;
   const double* coords;
@@ -73,6 +82,7 @@ typedef struct {
   const int32_t* tets;
   const int32_t* part;
   int32_t n_parts;
+  int32_t nodes_per_tet;
 } feti_mesh;
 
 /* Material of Sec. 3.1.  LINEAR_ISO: Hooke with (E, nu).  HGO_TWO_FIBRE:
@@ -93,7 +103,11 @@ typedef struct {
  * into the solid, press_owner: [n_press] the tetrahedron owning each face;
  * a pressure p pushes along that area vector (P1-consistent: a third of the
  * force to each vertex).  trac_tri/trac_owner likewise, with the constant
- * traction vector traction[3] per unit reference area. */
+ * traction vector traction[3] per unit reference area.  On 10-node meshes the
+ * faces have 6 nodes (v0, v1, v2, then the midpoints of (v0,v1), (v1,v2),
+ * (v2,v0)) and the consistent load of a flat face goes a third to each edge
+ * midpoint (the vertex shape functions integrate to zero); a pressure there
+ * does not follow the deformation. */
 typedef struct {
   int32_t n_dir;
   const int32_t* dir_dof;
@@ -229,10 +243,11 @@ feti_status feti_checkpoint_write(const char* path, const double* U, int64_t n_d
 feti_status feti_checkpoint_read(const char* path, double* U, int64_t capacity, feti_checkpoint_info* info);
 
 /* Element level of Sec. 3.2 (Eq. Tangent and the residual K(U)): for every
- * tetrahedron the 12x12 tangent K_e (row-major, local DOF 3 * vertex +
- * component, vertices in tets order) into Ke_out [n_tets*144], and for the
+ * tetrahedron the 12x12 tangent K_e (30x30 on 10-node meshes; row-major,
+ * local DOF 3 * node + component, nodes in tets order) into Ke_out
+ * [n_tets*144] ([n_tets*900]), and for the
  * hyperelastic material the internal force f_e = V (F S grad N_a) into
- * fe_out [n_tets*12] (may be NULL; unused for LINEAR_ISO), at the
+ * fe_out [n_tets*12] (may be NULL; unused for the linear materials), at the
  * displacement U [n_nodes*3] (NULL = zero).  U and the outputs are host or
  * device pointers as u_on_device / out_on_device say.  Fails with
  * FETI_ERR_ELEMENT_INVERTED if det F <= 0 anywhere. */

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PARTITION", 3: "ELEMENT_INVERTED"
                 5: "KERNEL_DETECT", 6: "BREAKDOWN", 7: "NOT_CONVERGED", 8: "NEWTON_DIVERGED", 9: "TIMEOUT",
                 10: "OOM", 11: "CUDA", 12: "STATE", 13: "IO"}
 
-LINEAR_ISO, HGO_TWO_FIBRE = 0, 1
+LINEAR_ISO, HGO_TWO_FIBRE, LINEAR_ISO_P0 = 0, 1, 2
 CLASSICAL, ALL_FLOATING = 0, 1
 PREC_IDENTITY, PREC_LUMPED, PREC_DIRICHLET = 0, 1, 2
 FP64, MIXED, MIXED_F32FACTOR = 0, 1, 2
@@ -23,7 +23,7 @@ _ip = C.POINTER(C.c_int32)
 
 class FetiMesh(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("coords", _dp), ("n_tets", C.c_int32), ("tets", _ip),
-                ("part", _ip), ("n_parts", C.c_int32)]
+                ("part", _ip), ("n_parts", C.c_int32), ("nodes_per_tet", C.c_int32)]
 
 
 class FetiMaterial(C.Structure):

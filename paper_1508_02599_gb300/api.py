@@ -49,8 +49,9 @@ class FetiSolver:
         part = np.ascontiguousarray(prob.part, dtype=np.int32); keep(part)
         self.n_nodes = coords.shape[0]
         self._n_tets = tets.shape[0]
+        self._npe = tets.shape[1]
         mesh = L.FetiMesh(coords.shape[0], _ptr(coords, C.c_double), tets.shape[0], _ptr(tets, C.c_int32),
-                          _ptr(part, C.c_int32), int(prob.n_parts))
+                          _ptr(part, C.c_int32), int(prob.n_parts), int(self._npe))
         m = prob.material
         fib = None
         if getattr(prob, "fibres", None) is not None:
@@ -59,9 +60,10 @@ class FetiSolver:
                              float(m["k2"]), float(m["kappa"]), _ptr(fib, C.c_double))
         dd = np.ascontiguousarray(prob.dir_dof, dtype=np.int32); keep(dd)
         dv = np.ascontiguousarray(prob.dir_val, dtype=np.float64); keep(dv)
-        pt = np.ascontiguousarray(prob.press_tri, dtype=np.int32).reshape(-1, 3); keep(pt)
+        fpn = 6 if tets.shape[1] == 10 else 3
+        pt = np.ascontiguousarray(prob.press_tri, dtype=np.int32).reshape(-1, fpn); keep(pt)
         po = np.ascontiguousarray(prob.press_owner, dtype=np.int32); keep(po)
-        tt = np.ascontiguousarray(prob.trac_tri, dtype=np.int32).reshape(-1, 3); keep(tt)
+        tt = np.ascontiguousarray(prob.trac_tri, dtype=np.int32).reshape(-1, fpn); keep(tt)
         to = np.ascontiguousarray(prob.trac_owner, dtype=np.int32); keep(to)
         bc = L.FetiBC(dd.size, _ptr(dd, C.c_int32), _ptr(dv, C.c_double), pt.shape[0], _ptr(pt, C.c_int32),
                       _ptr(po, C.c_int32), float(prob.pressure), tt.shape[0], _ptr(tt, C.c_int32),
@@ -133,14 +135,15 @@ class FetiSolver:
         of those shapes, U must be a torch CUDA tensor (or None) and the
         results stay on the device."""
         E = n_tets if n_tets is not None else self._n_tets
+        nd = 3 * self._npe
         if out is not None:
             Ke, fe = out
             up = None if U is None else C.c_void_p(U.data_ptr())
             self._check(self._lib.feti_elements(self._ctx, up, 1, C.c_void_p(Ke.data_ptr()),
                                                 C.c_void_p(fe.data_ptr()), 1))
             return Ke, fe
-        Ke = np.empty((E, 12, 12), np.float64)
-        fe = np.empty((E, 12), np.float64)
+        Ke = np.empty((E, nd, nd), np.float64)
+        fe = np.empty((E, nd), np.float64)
         Uc = None if U is None else np.ascontiguousarray(U, dtype=np.float64).ravel()
         self._check(self._lib.feti_elements(self._ctx, None if Uc is None else Uc.ctypes.data, 0, Ke.ctypes.data,
                                             fe.ctypes.data, 0))

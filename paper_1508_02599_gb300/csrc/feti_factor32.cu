@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restric
 
 // r = g - K_rr x in FP64 on the rows [0, nr) (zero on the fixing rows), K_i
 // applied element by element from the FP64 element matrices: row i sums, in
-// a fixed order, the rows a of the elements listed for it (kinc: 12 e + a),
+// a fixed order, the rows a of the elements listed for it (kinc: nde e + a),
 // columns through the element's dense map (negative: an eliminated DOF).
 __global__ void __launch_bounds__(128) k_kresid(const SubLayout* __restrict__ lay, const int32_t* __restrict__ kinc_ptr,
                                                const int32_t* __restrict__ kinc, const int32_t* __restrict__ elem_dense,
-                                               const double* __restrict__ Ke, const double* __restrict__ gbase,
+                                               const double* __restrict__ Ke, int nde, const double* __restrict__ gbase,
                                                const double* __restrict__ xbase, double* __restrict__ rbase) {
   const SubLayout L = lay[blockIdx.x];
   const int nr = L.nI + L.nbp;
@@ -200,11 +200,10 @@ __global__ void __launch_bounds__(128) k_kresid(const SubLayout* __restrict__ la
       acc = gbase[gi];
       for (int q = kinc_ptr[gi]; q < kinc_ptr[gi + 1]; ++q) {
         const int ea = kinc[q];
-        const int e = ea / 12, a = ea - 12 * e;
-        const double* ke = Ke + (size_t)e * 144 + a * 12;
-        const int32_t* dm = elem_dense + 12 * (size_t)e;
-#pragma unroll
-        for (int b = 0; b < 12; ++b) {
+        const int e = ea / nde, a = ea - nde * e;
+        const double* ke = Ke + (size_t)e * nde * nde + (size_t)a * nde;
+        const int32_t* dm = elem_dense + (size_t)nde * e;
+        for (int b = 0; b < nde; ++b) {
           const int c = dm[b];
           if (c >= 0) acc -= ke[b] * x[c];
         }
@@ -283,8 +282,8 @@ void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double
 }
 
 void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
-                   const double* Ke, const double* g, const double* x, double* r, cudaStream_t st) {
-  k_kresid<<<P, 128, 0, st>>>(lay, kinc_ptr, kinc, elem_dense, Ke, g, x, r);
+                   const double* Ke, int nde, const double* g, const double* x, double* r, cudaStream_t st) {
+  k_kresid<<<P, 128, 0, st>>>(lay, kinc_ptr, kinc, elem_dense, Ke, nde, g, x, r);
 }
 
 void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st) {

@@ -41,6 +41,8 @@ struct DevBuf {
 struct feti_ctx {
   // problem (host copies)
   int N = 0, E = 0, P = 0;
+  // nodes per element (4: P1, 10: P2), DOFs per element, nodes per loaded face
+  int npe = 4, nde = 12, fpn = 3;
   std::vector<double> coords;
   std::vector<int32_t> tets, part;
   feti_material mat{};
@@ -382,10 +384,10 @@ feti_status build_decomposition(feti_ctx* ctx) {
   for (int e = 0; e < E; ++e) ecount[ctx->part[e]]++;
   for (int s = 0; s < P; ++s) {
     if (ecount[s] == 0) return fail(ctx, FETI_ERR_PARTITION, "subdomain " + std::to_string(s) + " has no elements");
-    ctx->nodes[s].reserve(4 * ecount[s]);
+    ctx->nodes[s].reserve((size_t)ctx->npe * ecount[s]);
   }
   for (int e = 0; e < E; ++e)
-    for (int a = 0; a < 4; ++a) ctx->nodes[ctx->part[e]].push_back(ctx->tets[4 * e + a]);
+    for (int a = 0; a < ctx->npe; ++a) ctx->nodes[ctx->part[e]].push_back(ctx->tets[(size_t)ctx->npe * e + a]);
   for (int s = 0; s < P; ++s) {
     auto& v = ctx->nodes[s];
     std::sort(v.begin(), v.end());
@@ -598,12 +600,12 @@ feti_status build_decomposition(feti_ctx* ctx) {
       for (int i = 0; i < nI; ++i) own[dl[i] / 3] = std::min(own[dl[i] / 3], i);
       for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
         const int e = sub_elems[q];
-        int ln[4], m = nI;
-        for (int a = 0; a < 4; ++a) {
-          ln[a] = lnode(s, ctx->tets[4 * (size_t)e + a]);
+        int ln[10], m = nI;
+        for (int a = 0; a < ctx->npe; ++a) {
+          ln[a] = lnode(s, ctx->tets[(size_t)ctx->npe * e + a]);
           m = std::min(m, own[ln[a]]);
         }
-        for (int a = 0; a < 4; ++a) node_first[ln[a]] = std::min(node_first[ln[a]], m);
+        for (int a = 0; a < ctx->npe; ++a) node_first[ln[a]] = std::min(node_first[ln[a]], m);
       }
       for (int d = 0; d < nd; ++d) dof_first[d] = node_first[d / 3];
     }
@@ -716,32 +718,34 @@ feti_status build_decomposition(feti_ctx* ctx) {
   for (int s = 0; s < P; ++s)
     for (int p = 0; p < ctx->lay[s].nbp + ctx->lay[s].k; ++p) bpos_sub[ctx->lay[s].boff + p] = s;
   // dense maps of the elements (grouped by subdomain above)
-  std::vector<int32_t> elem_dense(12 * (size_t)E);
+  const int npe = ctx->npe, nde = ctx->nde, fpn = ctx->fpn;
+  std::vector<int32_t> elem_dense((size_t)nde * E);
   std::vector<double> elem_dirval;
   ctx->any_dirval = false;
   if (!af)
     for (double v : ctx->dir_val)
       if (v != 0.0) ctx->any_dirval = true;
-  if (ctx->any_dirval) elem_dirval.assign(12 * (size_t)E, 0.0);
+  if (ctx->any_dirval) elem_dirval.assign((size_t)nde * E, 0.0);
   for (int e = 0; e < E; ++e) {
     const int s = ctx->part[e];
-    for (int a = 0; a < 4; ++a) {
-      const int n = ctx->tets[4 * e + a];
+    for (int a = 0; a < npe; ++a) {
+      const int n = ctx->tets[(size_t)npe * e + a];
       const int l = lnode(s, n);
       for (int c = 0; c < 3; ++c) {
-        elem_dense[12 * (size_t)e + 3 * a + c] = pos_of[s][3 * l + c];
-        if (ctx->any_dirval && is_dir[3 * (size_t)n + c]) elem_dirval[12 * (size_t)e + 3 * a + c] = dval[3 * (size_t)n + c];
+        elem_dense[(size_t)nde * e + 3 * a + c] = pos_of[s][3 * l + c];
+        if (ctx->any_dirval && is_dir[3 * (size_t)n + c]) elem_dirval[(size_t)nde * e + 3 * a + c] = dval[3 * (size_t)n + c];
       }
     }
   }
   // FP32-factor form: per local row (global local index voff + dense row) the
   // (element, element row) pairs of its subdomain's elements, ascending
+  // (encoded nde e + a)
   if (ctx->opt.precision == FETI_MIXED_F32FACTOR) {
     std::vector<int32_t> kptr(voff + 1, 0);
     for (int e = 0; e < E; ++e) {
       const SubLayout& L = ctx->lay[ctx->part[e]];
-      for (int a = 0; a < 12; ++a) {
-        const int r = elem_dense[12 * (size_t)e + a];
+      for (int a = 0; a < nde; ++a) {
+        const int r = elem_dense[(size_t)nde * e + a];
         if (r >= 0) kptr[L.voff + r + 1]++;
       }
     }
@@ -749,9 +753,9 @@ feti_status build_decomposition(feti_ctx* ctx) {
     std::vector<int32_t> kinc(kptr[voff]), kf(kptr.begin(), kptr.end() - 1);
     for (int e = 0; e < E; ++e) {      // element order: each row's list ascends in 12 e + a
       const SubLayout& L = ctx->lay[ctx->part[e]];
-      for (int a = 0; a < 12; ++a) {
-        const int r = elem_dense[12 * (size_t)e + a];
-        if (r >= 0) kinc[kf[L.voff + r]++] = 12 * e + a;
+      for (int a = 0; a < nde; ++a) {
+        const int r = elem_dense[(size_t)nde * e + a];
+        if (r >= 0) kinc[kf[L.voff + r]++] = nde * e + a;
       }
     }
     FETI_TRY(upload(ctx, &ctx->d_kinc_ptr, kptr));
@@ -766,9 +770,9 @@ feti_status build_decomposition(feti_ctx* ctx) {
     std::vector<std::vector<int32_t>> rows(ctx->nb_total);
     for (int e = 0; e < E; ++e) {
       const SubLayout& L = ctx->lay[ctx->part[e]];
-      int bp[12], nbq = 0;
-      for (int a = 0; a < 12; ++a) {
-        const int di = elem_dense[12 * (size_t)e + a];
+      int bp[30], nbq = 0;
+      for (int a = 0; a < nde; ++a) {
+        const int di = elem_dense[(size_t)nde * e + a];
         if (di >= L.nI) bp[nbq++] = di - L.nI;
       }
       for (int x = 0; x < nbq; ++x)
@@ -794,7 +798,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   // faces grouped by owning subdomain
   const int nf = ctx->n_press + ctx->n_trac;
-  std::vector<int32_t> sub_face_ptr(P + 1, 0), face_order(nf), face_dense(9 * (size_t)nf, -1);
+  std::vector<int32_t> sub_face_ptr(P + 1, 0), face_order(nf), face_dense(3 * (size_t)fpn * nf, -1);
   for (int f = 0; f < nf; ++f) sub_face_ptr[ctx->part[ctx->face_owner[f]] + 1]++;
   for (int s = 0; s < P; ++s) sub_face_ptr[s + 1] += sub_face_ptr[s];
   {
@@ -802,19 +806,19 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (int f = 0; f < nf; ++f) face_order[f2[ctx->part[ctx->face_owner[f]]]++] = f;
   }
   // face_dense indexed by the grouped position; face forces are permuted to it
-  std::vector<int32_t> face_tri_grouped(3 * (size_t)nf);
+  std::vector<int32_t> face_tri_grouped((size_t)fpn * nf);
   std::vector<int32_t> face_kind(nf);
   for (int q = 0; q < nf; ++q) {
     const int f = face_order[q];
     const int s = ctx->part[ctx->face_owner[f]];
-    for (int v = 0; v < 3; ++v) {
-      const int n = ctx->face_tri[3 * f + v];
+    for (int v = 0; v < fpn; ++v) {
+      const int n = ctx->face_tri[(size_t)fpn * f + v];
       const auto& nod = ctx->nodes[s];
       auto it = std::lower_bound(nod.begin(), nod.end(), n);
       if (it == nod.end() || *it != n) return fail(ctx, FETI_ERR_INVALID_ARG, "loaded face not on its owner element");
       const int l = (int)(it - nod.begin());
-      for (int c = 0; c < 3; ++c) face_dense[9 * (size_t)q + 3 * v + c] = pos_of[s][3 * l + c];
-      face_tri_grouped[3 * (size_t)q + v] = n;
+      for (int c = 0; c < 3; ++c) face_dense[3 * (size_t)fpn * q + 3 * v + c] = pos_of[s][3 * l + c];
+      face_tri_grouped[(size_t)fpn * q + v] = n;
     }
     face_kind[q] = f < ctx->n_press ? 0 : 1;
   }
@@ -1035,8 +1039,8 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_Uinit, ctx->U_init));
   FETI_TRY(dev_alloc(ctx, &ctx->d_Uout, 3 * (size_t)N));
   ctx->face_kind.swap(face_kind);
-  FETI_TRY(dev_alloc(ctx, &ctx->d_face_force, 9 * (size_t)std::max(nf, 1)));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_Ke, 144 * (size_t)E));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_face_force, 3 * (size_t)fpn * std::max(nf, 1)));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_Ke, (size_t)nde * nde * E));
   if (ctx->mat.kind == FETI_HGO_TWO_FIBRE) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_fe, 12 * (size_t)E));
     FETI_TRY(dev_alloc(ctx, &ctx->d_U, 3 * (size_t)N));
@@ -1158,27 +1162,38 @@ feti_status check_wait_flag(feti_ctx* ctx, int* d_flag, const char* where) {
 }
 
 // Element matrices at U (device pointer or NULL), local assembly, loads.
-feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
+// Element matrices at dU (device or NULL): the two-fibre tangent and force,
+// Hooke P1 (linear, and P2-P0 on P1 where the element mean of div u is div u),
+// or Hooke P2 / P2-P0 on 10-node tetrahedra.
+void launch_elements(feti_ctx* ctx, const double* dU) {
   cudaStream_t st = ctx->stream;
-  const bool hgo = ctx->mat.kind == FETI_HGO_TWO_FIBRE;
-  if (hgo)
+  if (ctx->mat.kind == FETI_HGO_TWO_FIBRE)
     feti::launch_elem_hgo(ctx->E, ctx->d_coords, ctx->d_tets, dU, ctx->d_fibres, ctx->mat.c, ctx->mat.k1,
                           ctx->mat.k2, ctx->mat.kappa, ctx->d_Ke, ctx->d_fe, ctx->d_status, st);
+  else if (ctx->npe == 10)
+    feti::launch_elem_linear_p2(ctx->E, ctx->d_coords, ctx->d_tets, ctx->mat.E, ctx->mat.nu,
+                                ctx->mat.kind == FETI_LINEAR_ISO_P0 ? 1 : 0, ctx->d_Ke, ctx->d_status, st);
   else
     feti::launch_elem_linear(ctx->E, ctx->d_coords, ctx->d_tets, ctx->mat.E, ctx->mat.nu, ctx->d_Ke,
                              ctx->d_status, st);
+}
+
+feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
+  cudaStream_t st = ctx->stream;
+  const bool hgo = ctx->mat.kind == FETI_HGO_TWO_FIBRE;
+  launch_elements(ctx, dU);
   FETI_CK(cudaGetLastError());
   size_t abytes = 0;
   for (const auto& L : ctx->lay) abytes += (size_t)L.ld * L.ld;
   if (f32_factor(ctx)) {
     FETI_CK(cudaMemsetAsync(ctx->d_A32, 0, abytes * sizeof(float), st));
     feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
-                          ctx->d_A32, st);
+                          ctx->nde, ctx->d_A32, st);
     feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A32, st);
   } else {
     FETI_CK(cudaMemsetAsync(ctx->d_A, 0, abytes * sizeof(double), st));
     feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
-                          ctx->d_A, st);
+                          ctx->nde, ctx->d_A, st);
     if (ctx->shift > 0.0) feti::launch_shift_diag(ctx->P, ctx->d_lay, ctx->d_A, ctx->shift, st);
     feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A, st);
   }
@@ -1192,16 +1207,15 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
       const int kind = ctx->face_kind[q];
       int q1 = q;
       while (q1 < nf && ctx->face_kind[q1] == kind) ++q1;
-      feti::launch_face_forces(q1 - q, ctx->d_face_tri + 3 * (size_t)q, ctx->d_coords,
-                               (hgo && ctx->opt.follower) ? dU : nullptr, kind,
-                               kind == 0 ? ctx->pressure : 1.0, ctx->d_traction, ctx->d_face_force + 9 * (size_t)q,
-                               st);
+      feti::launch_face_forces(q1 - q, ctx->fpn, ctx->d_face_tri + (size_t)ctx->fpn * q, ctx->d_coords,
+                               (hgo && ctx->opt.follower) ? dU : nullptr, kind, kind == 0 ? ctx->pressure : 1.0,
+                               ctx->d_traction, ctx->d_face_force + 3 * (size_t)ctx->fpn * q, st);
       q = q1;
     }
   }
   feti::launch_assemble_rhs(ctx->P, ctx->d_lay, ctx->d_sub_face_ptr, ctx->d_face_dense, ctx->d_face_force,
-                            ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_elem_dirval,
-                            ctx->d_Ke, hgo ? ctx->d_fe : nullptr, tau, ctx->d_f, st);
+                            3 * ctx->fpn, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense,
+                            ctx->d_elem_dirval, ctx->d_Ke, hgo ? ctx->d_fe : nullptr, ctx->nde, tau, ctx->d_f, st);
   FETI_CK(cudaGetLastError());
   return check_status(ctx, "element/assembly");
 }
@@ -1217,7 +1231,7 @@ void kplus(feti_ctx* ctx, const double* g, double* x) {
   }
   feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, g, x, 1, ctx->max_nr, st);
   for (int k = 1; k < ctx->refine_steps; ++k) {
-    feti::launch_kresid(ctx->P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, g, x,
+    feti::launch_kresid(ctx->P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, g, x,
                         ctx->d_kr, st);
     feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, ctx->d_kr, x, 0, ctx->max_nr, st);
   }
@@ -1236,7 +1250,7 @@ feti_status tune_refinement(feti_ctx* ctx) {
   double prev = 1e300;
   int steps = 1;
   for (; steps <= 12; ++steps) {
-    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->d_kg,
+    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, ctx->d_kg,
                         ctx->d_x2, ctx->d_kr, st);
     feti::launch_sub_norm2(P, ctx->d_lay, ctx->d_kr, ctx->d_kg, ctx->d_knorm, st);
     FETI_CK(cudaGetLastError());
@@ -1264,7 +1278,7 @@ feti_status tune_refinement(feti_ctx* ctx) {
     FETI_CK(cudaEventRecord(a, st));
     feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kr, ctx->d_x2, 0, ctx->max_nr, st);
     FETI_CK(cudaEventRecord(b, st));
-    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->d_kg,
+    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, ctx->d_kg,
                         ctx->d_x2, ctx->d_kr, st);
     FETI_CK(cudaEventRecord(c, st));
     FETI_CK(cudaEventSynchronize(c));
@@ -2441,14 +2455,20 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   if (opt->precision != FETI_FP64 && opt->precision != FETI_MIXED && opt->precision != FETI_MIXED_F32FACTOR)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported precision");
   if (!(opt->tol > 0.0) || opt->maxit <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "tol and maxit must be positive");
-  if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE)
+  if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE && mat->kind != FETI_LINEAR_ISO_P0)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown material");
   if (mat->kind == FETI_HGO_TWO_FIBRE && !mat->fibres) return fail(ctx, FETI_ERR_INVALID_ARG, "fibres required");
   ctx->N = mesh->n_nodes;
   ctx->E = mesh->n_tets;
   ctx->P = mesh->n_parts;
   ctx->coords.assign(mesh->coords, mesh->coords + 3 * (size_t)ctx->N);
-  ctx->tets.assign(mesh->tets, mesh->tets + 4 * (size_t)ctx->E);
+  ctx->npe = mesh->nodes_per_tet == 0 ? 4 : mesh->nodes_per_tet;
+  if (ctx->npe != 4 && ctx->npe != 10) return fail(ctx, FETI_ERR_INVALID_ARG, "nodes_per_tet must be 4 or 10");
+  ctx->nde = 3 * ctx->npe;
+  ctx->fpn = ctx->npe == 10 ? 6 : 3;
+  if (ctx->npe == 10 && mat->kind == FETI_HGO_TWO_FIBRE)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "10-node tetrahedra are built for the linear materials");
+  ctx->tets.assign(mesh->tets, mesh->tets + (size_t)ctx->npe * ctx->E);
   ctx->part.assign(mesh->part, mesh->part + ctx->E);
   for (int32_t v : ctx->tets)
     if (v < 0 || v >= ctx->N) return fail(ctx, FETI_ERR_INVALID_ARG, "tetrahedron node out of range");
@@ -2472,8 +2492,8 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   for (int i = 0; i < 3; ++i) ctx->traction[i] = bc->traction[i];
   if ((bc->n_press && (!bc->press_tri || !bc->press_owner)) || (bc->n_trac && (!bc->trac_tri || !bc->trac_owner)))
     return fail(ctx, FETI_ERR_INVALID_ARG, "missing face arrays");
-  ctx->face_tri.assign(bc->press_tri, bc->press_tri + 3 * (size_t)bc->n_press);
-  ctx->face_tri.insert(ctx->face_tri.end(), bc->trac_tri, bc->trac_tri + 3 * (size_t)bc->n_trac);
+  ctx->face_tri.assign(bc->press_tri, bc->press_tri + (size_t)ctx->fpn * bc->n_press);
+  ctx->face_tri.insert(ctx->face_tri.end(), bc->trac_tri, bc->trac_tri + (size_t)ctx->fpn * bc->n_trac);
   ctx->face_owner.assign(bc->press_owner, bc->press_owner + bc->n_press);
   ctx->face_owner.insert(ctx->face_owner.end(), bc->trac_owner, bc->trac_owner + bc->n_trac);
   for (int32_t v : ctx->face_owner)
@@ -2526,7 +2546,7 @@ feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_r
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
   auto t0 = std::chrono::steady_clock::now();
   if (report) std::memset(report, 0, sizeof(*report));
-  if (ctx->mat.kind != FETI_LINEAR_ISO) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve needs a linear material");
+  if (ctx->mat.kind == FETI_HGO_TWO_FIBRE) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve needs a linear material");
   FETI_TRY(feti_prepare(ctx));
   float pcg_ms = 0.f;
   feti_status s = dual_solve(ctx, report, &pcg_ms);
@@ -2561,8 +2581,8 @@ static feti_status newton_residual(feti_ctx* ctx, const double* dU, double tau, 
   double rn = 0.0, fn = 0.0;
   FETI_TRY(global_norm(ctx, ctx->d_f, &rn));
   feti::launch_assemble_rhs(ctx->P, ctx->d_lay, ctx->d_sub_face_ptr, ctx->d_face_dense, ctx->d_face_force,
-                            ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, nullptr, ctx->d_Ke, nullptr,
-                            tau, ctx->d_fl, ctx->stream);
+                            3 * ctx->fpn, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, nullptr,
+                            ctx->d_Ke, nullptr, ctx->nde, tau, ctx->d_fl, ctx->stream);
   FETI_TRY(global_norm(ctx, ctx->d_fl, &fn));
   (void)dU;
   *rel = fn > 0.0 ? rn / fn : rn;
@@ -2613,7 +2633,13 @@ static feti_status newton_increment(feti_ctx* ctx, double eta, int max_it, int* 
     feti::launch_gs_inject(n, ctx->d_gs_ptr, ctx->d_gs_pos, r, ctx->d_f, st);
     feti_report rep{};
     float ms = 0.f;
-    FETI_TRY(dual_solve(ctx, &rep, &ms));
+    {
+      // the FETI solve is only the preconditioner here: an inner PCG that
+      // stops at maxit (possible on shifted local tangents) still gives a
+      // usable direction for the flexible CG
+      const feti_status ds = dual_solve(ctx, &rep, &ms);
+      if (ds != FETI_OK && ds != FETI_ERR_NOT_CONVERGED) return ds;
+    }
     *pcg_its += rep.iterations;
     *pcg_ms += ms;
     feti::launch_gs_take(n, ctx->d_gs_ptr, ctx->d_gs_pos, ctx->d_x, z, st);
@@ -2680,6 +2706,7 @@ static feti_status newton_run(feti_ctx* ctx, const double* U_start, int32_t u_st
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
   (void)cudaGetLastError();
   if (ctx->mat.kind != FETI_HGO_TWO_FIBRE) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton needs HGO_TWO_FIBRE");
+  if (ctx->npe != 4) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton is built for 4-node tetrahedra");
   if (f32_factor(ctx))
     return fail(ctx, FETI_ERR_INVALID_ARG, "feti_newton: FETI_MIXED_F32FACTOR is for linear solves");
   for (double v : ctx->dir_val)
@@ -2722,32 +2749,21 @@ static feti_status newton_run(feti_ctx* ctx, const double* U_start, int32_t u_st
       pcg_total += step_pcg;
       step_pcg_total += step_pcg;
       feti_status s = FETI_OK;
-      // step length: halve until the local tangents at U + a dU factorize
-      // (down to 1/64).  Where they stop being positive definite -- the
-      // current state already needed a shift, or no step length keeps them
-      // definite -- a shifted trial is accepted once the residual falls (or
-      // at the smallest step length).
-      const bool state_shifted = ctx->shift > 0.0;
+      // the full Newton step (Sec. 3.2, Eq. NewtonRecursion); the step is
+      // halved only while an element inverts (down to 1/64).  Local tangents
+      // that are not positive definite at the new state are shifted for the
+      // FETI preconditioner (prepare_newton).
       double a = 1.0;
       for (;;) {
         feti::launch_axpy_to(n3, ctx->d_U, a, ctx->d_dU, ctx->d_Utrial, st);
         feti::launch_zero_list((int)ctx->dir_dof.size(), ctx->d_dir_dof, ctx->d_Utrial, st);
-        ctx->shift = 0.0;
-        s = prepare(ctx, ctx->d_Utrial, tau);
+        s = prepare_newton(ctx, ctx->d_Utrial, tau, log);
         if (s == FETI_OK) break;
         if (log) std::fprintf(stderr, "feti_newton: step %d it %d step length %.4f rejected (%s)\n", step, k + 1, a,
                               ctx->err.c_str());
-        if (s != FETI_ERR_LOCAL_SINGULAR && s != FETI_ERR_ELEMENT_INVERTED) return s;
-        if (s == FETI_ERR_LOCAL_SINGULAR && (state_shifted || a < 1.0 / 32)) {
-          FETI_TRY(prepare_newton(ctx, ctx->d_Utrial, tau, log));
-          double rel_trial = 0.0;
-          FETI_TRY(newton_residual(ctx, ctx->d_Utrial, tau, &rel_trial));
-          if (rel_trial < rel || a < 1.0 / 32) break;
-          if (log) std::fprintf(stderr, "feti_newton: step %d it %d shifted step %.4f: residual %.3e >= %.3e\n", step,
-                                k + 1, a, rel_trial, rel);
-        }
+        if (s != FETI_ERR_ELEMENT_INVERTED) return s;
         a *= 0.5;
-        if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "no step length is acceptable");
+        if (a < 1.0 / 64) return fail(ctx, FETI_ERR_NEWTON_DIVERGED, "every step length inverts an element");
       }
       FETI_CK(cudaMemcpyAsync(ctx->d_U, ctx->d_Utrial, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
       ++newton_total;
@@ -2812,11 +2828,7 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
     FETI_CK(cudaEventCreate(&ctx->elem_ev[1]));
   }
   FETI_CK(cudaEventRecord(ctx->elem_ev[0], st));
-  if (hgo)
-    feti::launch_elem_hgo(ctx->E, ctx->d_coords, ctx->d_tets, dU, ctx->d_fibres, ctx->mat.c, ctx->mat.k1, ctx->mat.k2,
-                          ctx->mat.kappa, ctx->d_Ke, ctx->d_fe, ctx->d_status, st);
-  else
-    feti::launch_elem_linear(ctx->E, ctx->d_coords, ctx->d_tets, ctx->mat.E, ctx->mat.nu, ctx->d_Ke, ctx->d_status, st);
+  launch_elements(ctx, dU);
   FETI_CK(cudaGetLastError());
   FETI_CK(cudaEventRecord(ctx->elem_ev[1], st));
   FETI_TRY(check_status(ctx, "element matrices"));
@@ -2826,12 +2838,13 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
     ctx->elem_ms = ms;
     // connectivity, fibres (hyperelastic), packed symmetric tangent and force
     // per element; coordinates (+ displacement) per node
-    const double per_elem = 16.0 + 78.0 * 8.0 + (hgo ? 48.0 + 12.0 * 8.0 : 0.0);
+    const double nd = ctx->nde;
+    const double per_elem = 4.0 * ctx->npe + nd * (nd + 1) / 2 * 8.0 + (hgo ? 48.0 + 12.0 * 8.0 : 0.0);
     const double per_node = hgo ? 48.0 : 24.0;
     ctx->elem_bytes = per_elem * (double)ctx->E + per_node * (double)ctx->N;
   }
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  FETI_CK(cudaMemcpyAsync(Ke_out, ctx->d_Ke, 144 * (size_t)ctx->E * sizeof(double), kind, st));
+  FETI_CK(cudaMemcpyAsync(Ke_out, ctx->d_Ke, (size_t)ctx->nde * ctx->nde * ctx->E * sizeof(double), kind, st));
   if (fe_out && hgo) FETI_CK(cudaMemcpyAsync(fe_out, ctx->d_fe, 12 * (size_t)ctx->E * sizeof(double), kind, st));
   FETI_CK(cudaStreamSynchronize(st));
   return FETI_OK;
@@ -2844,7 +2857,8 @@ feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nr
   if (nrhs < 1 || nrhs > feti::kMaxRhs) return fail(ctx, FETI_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
   (void)cudaGetLastError();
   if (report) std::memset(report, 0, sizeof(*report));
-  if (ctx->mat.kind != FETI_LINEAR_ISO) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve_multi needs a linear material");
+  if (ctx->mat.kind == FETI_HGO_TWO_FIBRE)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve_multi needs a linear material");
   for (double v : ctx->dir_val)
     if (v != 0.0) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_solve_multi needs homogeneous Dirichlet data");
   auto t0 = std::chrono::steady_clock::now();

@@ -53,19 +53,26 @@ void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, cons
                      const double* fibres, double c, double k1, double k2, double kappa,
                      double* Ke, double* fe, int* status, cudaStream_t st);
 
-// Local assembly: one CTA per subdomain walks its elements in order (no atomics).
+// P2 (10-node) linear element matrices [n_tets * 900] (tets: [n_tets * 10]);
+// p0: volumetric part condensed to a piecewise-constant pressure (P2-P0).
+void launch_elem_linear_p2(int n_tets, const double* coords, const int32_t* tets, double E, double nu, int p0,
+                           double* Ke, int* status, cudaStream_t st);
+// Local assembly: one CTA per subdomain walks its elements in order (no
+// atomics); nde = DOFs per element (12 for P1, 30 for P2), Ke stride nde^2.
 void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
-                     const int32_t* elem_dense, const double* Ke, double* A, cudaStream_t st);
-// Local load vectors: surface loads (+ -f_int) (- K_iD u_D).
+                     const int32_t* elem_dense, const double* Ke, int nde, double* A, cudaStream_t st);
+// Local load vectors: surface loads (+ -f_int) (- K_iD u_D); fdn = DOFs per
+// loaded face (9 or 18).
 void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_ptr, const int32_t* face_dense,
-                         const double* face_force, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                         const double* face_force, int fdn, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
                          const int32_t* elem_dense, const double* elem_dirval, const double* Ke,
-                         const double* fe, double tau, double* f, cudaStream_t st);
-void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, const double* U,
+                         const double* fe, int nde, double tau, double* f, cudaStream_t st);
+// fpn = nodes per loaded face (3, or 6 for P2 faces).
+void launch_face_forces(int n_faces, int fpn, const int32_t* tri, const double* coords, const double* U,
                         int kind, double scale, const double* traction, double* out, cudaStream_t st);
 // The same into the FP32 workspace of the FP32-factor form (entries summed in FP32).
 void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
-                     const int32_t* elem_dense, const double* Ke, float* A, cudaStream_t st);
+                     const int32_t* elem_dense, const double* Ke, int nde, float* A, cudaStream_t st);
 // A_ii += delta * (largest diagonal entry of K_rr) on the K_rr rows of every
 // subdomain's FP64 workspace.
 void launch_shift_diag(int P, const SubLayout* lay, double* A, double delta, cudaStream_t st);
@@ -282,7 +289,7 @@ void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double
                        cudaStream_t st);
 // r = g - K_rr x (FP64, element by element; zero on the fixing rows).
 void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
-                   const double* Ke, const double* g, const double* x, double* r, cudaStream_t st);
+                   const double* Ke, int nde, const double* g, const double* x, double* r, cudaStream_t st);
 // out = boundary vector loc placed at the boundary positions, zero interior.
 void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st);
 // out[2 s], out[2 s + 1] = squared norms of r and g over rows [0, nI + nbp) of subdomain s.

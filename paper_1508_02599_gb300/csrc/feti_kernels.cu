@@ -107,6 +107,75 @@ __global__ void k_elem_linear(int n_tets, const double* __restrict__ coords, con
     }
 }
 
+// P2 element (10-node tetrahedron, straight edges; nodes: the vertices, then
+// the midpoints of the edges (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)) for Hooke's
+// law, one warp per element: every lane evaluates the gradients of the
+// barycentric coordinates, then takes node-pair blocks (a, b) = lane, lane +
+// 32, .. of the 10 x 10 block grid and writes their 3 x 3 entries.  The
+// gradients of N_a = L_a (2 L_a - 1) and N_ab = 4 L_a L_b are linear, so the
+// degree-2 Gauss rule (four points (alpha, beta, beta, beta) and permutations,
+// weights 1/4) integrates the stiffness exactly.  p0: the lambda term is
+// carried by a piecewise-constant pressure condensed out of the element
+// (Sec. 3.2, static condensation): lambda V bbar_a,i bbar_b,j with bbar_a the
+// element mean of grad N_a, instead of the integral of lambda g_a,i g_b,j.
+__device__ __forceinline__ void p2_grad(const double gL[4][3], const double Lq[4], int a, double g[3]) {
+  if (a < 4) {
+    const double f = 4.0 * Lq[a] - 1.0;
+    g[0] = f * gL[a][0];
+    g[1] = f * gL[a][1];
+    g[2] = f * gL[a][2];
+    return;
+  }
+  const int ea[6] = {0, 0, 0, 1, 1, 2}, eb[6] = {1, 2, 3, 2, 3, 3};
+  const int u = ea[a - 4], v = eb[a - 4];
+  for (int i = 0; i < 3; ++i) g[i] = 4.0 * (Lq[u] * gL[v][i] + Lq[v] * gL[u][i]);
+}
+
+__global__ void k_elem_linear_p2(int n_tets, const double* __restrict__ coords, const int32_t* __restrict__ tets,
+                                 double E, double nu, int p0, double* __restrict__ Ke, int* status) {
+  const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= n_tets) return;
+  double x[4][3], gL[4][3], V;
+  for (int a = 0; a < 4; ++a) {
+    const int n = tets[10 * (size_t)e + a];
+    for (int i = 0; i < 3; ++i) x[a][i] = coords[3 * (size_t)n + i];
+  }
+  if (!p1_gradients(x, gL, V)) {
+    if (lane == 0) set_status(status, DEV_INVERTED);
+    return;
+  }
+  const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = E / (2.0 * (1.0 + nu));
+  const double al = (5.0 + 3.0 * sqrt(5.0)) / 20.0, be = (5.0 - sqrt(5.0)) / 20.0;
+  double* K = Ke + (size_t)e * 900;
+  for (int blk = lane; blk < 100; blk += 32) {
+    const int a = blk / 10, b = blk % 10;
+    double k9[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double ma[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
+    for (int q = 0; q < 4; ++q) {
+      double Lq[4];
+      for (int c = 0; c < 4; ++c) Lq[c] = c == q ? al : be;
+      double ga[3], gb[3];
+      p2_grad(gL, Lq, a, ga);
+      p2_grad(gL, Lq, b, gb);
+      const double gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+      for (int i = 0; i < 3; ++i) {
+        ma[i] += 0.25 * ga[i];
+        mb[i] += 0.25 * gb[i];
+        for (int j = 0; j < 3; ++j) {
+          double v = mu * ga[j] * gb[i] + (p0 ? 0.0 : lam * ga[i] * gb[j]);
+          if (i == j) v += mu * gab;
+          k9[i][j] += 0.25 * v;
+        }
+      }
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        K[(3 * a + i) * 30 + 3 * b + j] = V * (k9[i][j] + (p0 ? lam * ma[i] * mb[j] : 0.0));
+  }
+}
+
 // Two-fibre hyperelastic element (Sec. 3.1 energy, Sec. 3.2 tangent), one
 // thread per element, evaluated in the current configuration.
 //
@@ -298,29 +367,34 @@ __global__ void __launch_bounds__(64) k_elem_hgo(int n_tets, const double* __res
 template <typename T>
 __global__ void k_assemble(const SubLayout* __restrict__ lay, const int32_t* __restrict__ sub_elem_ptr,
                            const int32_t* __restrict__ sub_elems, const int32_t* __restrict__ elem_dense,
-                           const double* __restrict__ Ke, T* __restrict__ Abase) {
+                           const double* __restrict__ Ke, int nde, T* __restrict__ Abase) {
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
   T* A = Abase + L.aoff;
-  const int t = threadIdx.x;
+  const int kes = nde * nde;
   for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
     const int e = sub_elems[q];
-    if (t < 144) {
-      const int r = elem_dense[12 * e + t / 12], c = elem_dense[12 * e + t % 12];
-      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += (T)Ke[(size_t)e * 144 + t];
+    for (int t = threadIdx.x; t < kes; t += blockDim.x) {
+      const int r = elem_dense[(size_t)nde * e + t / nde], c = elem_dense[(size_t)nde * e + t % nde];
+      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += (T)Ke[(size_t)e * kes + t];
     }
     __syncthreads();
   }
 }
 
-__global__ void k_face_forces(int n_faces, const int32_t* __restrict__ tri, const double* __restrict__ coords,
+// Consistent nodal loads of one loaded face under constant pressure (kind 0,
+// along the area vector) or traction (kind 1).  3-node faces: a third of the
+// force to each vertex; 6-node (P2, flat) faces: the vertex shape functions
+// integrate to zero and the midpoint ones to A/3, so a third of the force to
+// each edge midpoint (nodes 3..5) and none to the vertices.
+__global__ void k_face_forces(int n_faces, int fpn, const int32_t* __restrict__ tri, const double* __restrict__ coords,
                               const double* __restrict__ U, int kind, double scale,
                               const double* __restrict__ traction, double* __restrict__ out) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n_faces) return;
   double x[3][3];
   for (int v = 0; v < 3; ++v) {
-    const int n = tri[3 * f + v];
+    const int n = tri[(size_t)fpn * f + v];
     for (int i = 0; i < 3; ++i) x[v][i] = coords[3 * n + i] + (U ? U[3 * n + i] : 0.0);
   }
   double e1[3], e2[3], av[3];
@@ -338,15 +412,16 @@ __global__ void k_face_forces(int n_faces, const int32_t* __restrict__ tri, cons
     const double area = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
     for (int i = 0; i < 3; ++i) force[i] = scale * area * traction[i] / 3.0;
   }
-  for (int v = 0; v < 3; ++v)
-    for (int i = 0; i < 3; ++i) out[9 * (size_t)f + 3 * v + i] = force[i];
+  for (int v = 0; v < fpn; ++v)
+    for (int i = 0; i < 3; ++i)
+      out[3 * (size_t)fpn * f + 3 * v + i] = (fpn == 3 || v >= 3) ? force[i] : 0.0;
 }
 
 __global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t* __restrict__ sub_face_ptr,
-                               const int32_t* __restrict__ face_dense, const double* __restrict__ face_force,
+                               const int32_t* __restrict__ face_dense, const double* __restrict__ face_force, int fdn,
                                const int32_t* __restrict__ sub_elem_ptr, const int32_t* __restrict__ sub_elems,
                                const int32_t* __restrict__ elem_dense, const double* __restrict__ elem_dirval,
-                               const double* __restrict__ Ke, const double* __restrict__ fe, double tau,
+                               const double* __restrict__ Ke, const double* __restrict__ fe, int nde, double tau,
                                double* __restrict__ fbase) {
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
@@ -355,22 +430,23 @@ __global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t*
   for (int i = t; i < L.n; i += blockDim.x) f[i] = 0.0;
   __syncthreads();
   for (int q = sub_face_ptr[s]; q < sub_face_ptr[s + 1]; ++q) {
-    if (t < 9) {
-      const int r = face_dense[9 * q + t];
-      if (r >= 0) f[r] += tau * face_force[9 * (size_t)q + t];
+    if (t < fdn) {
+      const int r = face_dense[(size_t)fdn * q + t];
+      if (r >= 0) f[r] += tau * face_force[(size_t)fdn * q + t];
     }
     __syncthreads();
   }
+  const int kes = nde * nde;
   for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
     const int e = sub_elems[q];
-    if (t < 12) {
-      const int r = elem_dense[12 * e + t];
+    if (t < nde) {
+      const int r = elem_dense[(size_t)nde * e + t];
       if (r >= 0) {
-        double v = fe ? -fe[(size_t)e * 12 + t] : 0.0;
+        double v = fe ? -fe[(size_t)e * nde + t] : 0.0;
         if (elem_dirval) {
-          for (int b = 0; b < 12; ++b) {
-            const double ud = elem_dirval[12 * (size_t)e + b];
-            if (ud != 0.0) v -= Ke[(size_t)e * 144 + t * 12 + b] * ud;
+          for (int b = 0; b < nde; ++b) {
+            const double ud = elem_dirval[(size_t)nde * e + b];
+            if (ud != 0.0) v -= Ke[(size_t)e * kes + t * nde + b] * ud;
           }
         }
         f[r] += v;
@@ -1460,27 +1536,34 @@ void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, cons
 }
 
 void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
-                     const int32_t* elem_dense, const double* Ke, double* A, cudaStream_t st) {
-  k_assemble<double><<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
+                     const int32_t* elem_dense, const double* Ke, int nde, double* A, cudaStream_t st) {
+  k_assemble<double><<<P, nde > 12 ? 256 : 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, nde, A);
 }
 
 void launch_assemble(int P, const SubLayout* lay, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
-                     const int32_t* elem_dense, const double* Ke, float* A, cudaStream_t st) {
-  k_assemble<float><<<P, 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, A);
+                     const int32_t* elem_dense, const double* Ke, int nde, float* A, cudaStream_t st) {
+  k_assemble<float><<<P, nde > 12 ? 256 : 160, 0, st>>>(lay, sub_elem_ptr, sub_elems, elem_dense, Ke, nde, A);
 }
 
 void launch_assemble_rhs(int P, const SubLayout* lay, const int32_t* sub_face_ptr, const int32_t* face_dense,
-                         const double* face_force, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
+                         const double* face_force, int fdn, const int32_t* sub_elem_ptr, const int32_t* sub_elems,
                          const int32_t* elem_dense, const double* elem_dirval, const double* Ke, const double* fe,
-                         double tau, double* f, cudaStream_t st) {
-  k_assemble_rhs<<<P, 128, 0, st>>>(lay, sub_face_ptr, face_dense, face_force, sub_elem_ptr, sub_elems,
-                                     elem_dense, elem_dirval, Ke, fe, tau, f);
+                         int nde, double tau, double* f, cudaStream_t st) {
+  k_assemble_rhs<<<P, 128, 0, st>>>(lay, sub_face_ptr, face_dense, face_force, fdn, sub_elem_ptr, sub_elems,
+                                     elem_dense, elem_dirval, Ke, fe, nde, tau, f);
 }
 
-void launch_face_forces(int n_faces, const int32_t* tri, const double* coords, const double* U, int kind,
+void launch_face_forces(int n_faces, int fpn, const int32_t* tri, const double* coords, const double* U, int kind,
                         double scale, const double* traction, double* out, cudaStream_t st) {
   if (n_faces <= 0) return;
-  k_face_forces<<<(n_faces + 127) / 128, 128, 0, st>>>(n_faces, tri, coords, U, kind, scale, traction, out);
+  k_face_forces<<<(n_faces + 127) / 128, 128, 0, st>>>(n_faces, fpn, tri, coords, U, kind, scale, traction, out);
+}
+
+void launch_elem_linear_p2(int n_tets, const double* coords, const int32_t* tets, double E, double nu, int p0,
+                           double* Ke, int* status, cudaStream_t st) {
+  if (n_tets <= 0) return;
+  const long threads = 32L * n_tets;
+  k_elem_linear_p2<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n_tets, coords, tets, E, nu, p0, Ke, status);
 }
 
 namespace {
