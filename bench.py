@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--plain", type=int, default=1,
                     help="also time the plain FP64 form with one local-apply launch per subdomain (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--coarse", default="auto", choices=["auto", "dense", "sparse"],
+                    help="coarse problem: dense inverse, supernodal sparse Cholesky, or automatic")
     ap.add_argument("--fp32-form", default="mixed", choices=["mixed", "f32factor"],
                     help="precision form of the timed FP32-local applies: FP64 factors rounded to FP32 operators "
                          "(mixed, default) or FP32 factorizations (f32factor: half the device memory, for profiler "
@@ -262,7 +264,7 @@ def main():
         """Full solve once, then `steps` timed blocks of n_apply dual applies."""
         n_apply = n_apply or args.n_apply
         steps = steps or args.steps
-        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000, coarse=args.coarse,
                             stream=stream.cuda_stream, precision=precision, batched=batched,
                             symmetric=args.symmetric)
         if args.apply_only:
@@ -272,6 +274,7 @@ def main():
         else:
             U, rep = solver.solve()      # full hot path once: setup + PCG + recovery
         sizes = solver.sizes()
+        sizes["coarse"] = solver.coarse_info()
         nl = sizes["n_lambda"]
         g = torch.Generator(device="cuda").manual_seed(1234 + rank)
         v = torch.randn(nl, dtype=torch.float64, device="cuda", generator=g)
@@ -311,7 +314,7 @@ def main():
         PCG to 1e-8, then timed blocks of block dual applies (RHS-applies/s)."""
         rng = np.random.Generator(np.random.PCG64(16))
         scales = rng.uniform(8.0, 16.0, size=nrhs)
-        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000, coarse=args.coarse,
                             stream=stream.cuda_stream, precision=precision)
         U, rep = solver.solve_multi(scales)
         nl = solver.sizes()["n_lambda"]
@@ -378,7 +381,7 @@ def main():
     def measure_f32factor():
         """FP32 local factorizations with FP64-refined K^+: setup and PCG to 1e-8 (the dual applies
         run the same FP32 operator kernels as the FP32-local form)."""
-        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+        solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000, coarse=args.coarse,
                             stream=stream.cuda_stream, precision="mixed_f32factor", symmetric=args.symmetric)
         U, rep = solver.solve()
         ref = solver.refinement()
@@ -412,7 +415,7 @@ def main():
         t0 = time.perf_counter()
         its = 0
         for _ in range(e2e_steps):
-            with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000,
+            with FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000, coarse=args.coarse,
                             stream=stream.cuda_stream, precision=precision) as s2:
                 r2 = s2.solve_host(u_host)
                 its += r2["iterations"] + r2["outer_iterations"] + 2
@@ -443,7 +446,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": dict(workload_cfg, precision="FP32 local operators, FP64 vectors/projection/coarse/outer "
                                                     "residual", n_apply_per_step=args.n_apply,
-                           n_lambda=m32["sizes"]["n_lambda"], coarse_dim=m32["sizes"]["coarse_dim"]),
+                           n_lambda=m32["sizes"]["n_lambda"], coarse_dim=m32["sizes"]["coarse_dim"],
+                           coarse=m32["sizes"]["coarse"]),
             "pcg": {"tol": 1e-8,
                     "fp32_local": {"time_to_tol_ms": r32["t_pcg_ms"], "inner_iterations": r32["iterations"],
                                    "outer_iterations": r32["outer_iterations"], "rel_err_vs_fp64": err},

@@ -157,7 +157,15 @@ typedef struct {
                                kernel's pipeline, waits for its copies and tensor-core products in
                                flight (those drain waits keep a fixed budget of 2e8 clock cycles),
                                releases tensor memory and flags the call, which then returns
-                               FETI_ERR_TIMEOUT; the context stays usable. */
+                               FETI_ERR_TIMEOUT; the context stays usable.  The same budget bounds
+                               each dependency wait of the sparse coarse solve. */
+  int32_t coarse_form;      /* the coarse problem (G^T G)^-1 of the projection (Sec. 4.3):
+                               0 = automatic (sparse from 1536 coarse columns on), 1 = dense
+                               explicit inverse (block elimination; each projection a dense
+                               matvec), 2 = sparse: supernodal Cholesky over a nested-dissection
+                               order of the subdomain graph (fronts eliminated level by level),
+                               each projection a forward and a backward sweep over the supernodes
+                               run as one task-graph kernel whose waits are bounded as above */
 } feti_options;
 
 typedef struct {
@@ -257,6 +265,15 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
 /* Sizes of the decomposition: out[0] n_lambda, out[1] coarse_dim, out[2]
  * sum of local DOFs, out[3] sum of boundary DOFs, out[4] n_parts. */
 feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]);
+
+/* Form of the coarse problem (G^T G)^-1 (Sec. 4.3) chosen at feti_create:
+ * out[0] 0 no coarse space, 1 dense explicit inverse, 2 sparse supernodal
+ * Cholesky; for the sparse form out[1] supernodes, out[2] height of the
+ * assembly tree, out[3] entries of the factor (lower triangle of each
+ * diagonal block plus its panel), out[4] tasks of one forward + backward
+ * sweep, out[5] doubles of the factorization workspace (held only during
+ * set-up); for the dense form out[3] = coarse_dim^2. */
+feti_status feti_get_coarse_info(const feti_ctx* ctx, int64_t out[6]);
 
 /* Multiplier rows in canonical order (Sec. 4.1, Fig. 3a, fully redundant):
  * interface rows by (global node, component, subdomain pair i<j) with +1 on

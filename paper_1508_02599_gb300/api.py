@@ -39,7 +39,8 @@ class FetiSolver:
                  maxit: int = 1000, chunk: int = 16, stream=None, follower: bool = True,
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
-                 tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0):
+                 tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0,
+                 coarse: str = "auto"):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -75,7 +76,7 @@ class FetiSolver:
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7}[tensor_cores],
                             int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
-                            int(spin_timeout_ns))
+                            int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse])
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))
@@ -108,6 +109,16 @@ class FetiSolver:
         out = (C.c_int64 * 5)()
         self._check(self._lib.feti_get_sizes(self._ctx, out))
         return dict(zip(["n_lambda", "coarse_dim", "n_local", "n_boundary", "n_parts"], list(out)))
+
+    def coarse_info(self) -> dict:
+        """Form of the coarse problem: 'none', 'dense' or 'sparse', with the
+        sparse factor's supernodes, assembly-tree height, factor entries,
+        sweep tasks and set-up workspace (doubles)."""
+        out = (C.c_int64 * 6)()
+        self._check(self._lib.feti_get_coarse_info(self._ctx, out))
+        v = list(out)
+        return {"form": ["none", "dense", "sparse"][v[0]], "supernodes": v[1], "height": v[2],
+                "factor_entries": v[3], "tasks": v[4], "workspace": v[5]}
 
     def index_maps(self) -> dict:
         n = self.sizes()["n_lambda"]

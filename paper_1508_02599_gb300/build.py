@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfeti.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["feti_kernels.cu", "feti_kernels_multi.cu", "feti_factor32.cu", "feti_noalloc.cu", "feti_host.cpp", "feti_checkpoint.cpp"]
+SOURCES = ["feti_kernels.cu", "feti_kernels_multi.cu", "feti_factor32.cu", "feti_coarse.cu", "feti_noalloc.cu", "feti_host.cpp",
+           "feti_coarse_plan.cpp", "feti_checkpoint.cpp"]
 
 
 def nvcc() -> str:

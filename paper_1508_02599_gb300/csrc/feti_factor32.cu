@@ -201,11 +201,11 @@ __global__ void __launch_bounds__(128) k_kresid(const SubLayout* __restrict__ la
       for (int q = kinc_ptr[gi]; q < kinc_ptr[gi + 1]; ++q) {
         const int ea = kinc[q];
         const int e = ea / nde, a = ea - nde * e;
-        const double* ke = Ke + (size_t)e * nde * nde + (size_t)a * nde;
+        const double* ke = Ke + (size_t)e * ke_packed(nde);
         const int32_t* dm = elem_dense + (size_t)nde * e;
         for (int b = 0; b < nde; ++b) {
           const int c = dm[b];
-          if (c >= 0) acc -= ke[b] * x[c];
+          if (c >= 0) acc -= ke[ke_idx(nde, a, b)] * x[c];
         }
       }
     }

@@ -129,6 +129,13 @@ struct feti_ctx {
   int n_gtg = 0;
   double *d_GtG = nullptr, *d_Ginv = nullptr, *d_Acoarse = nullptr;
   SubLayout* d_lay_coarse = nullptr;
+  // sparse coarse problem (supernodal Cholesky of G^T G) in place of the
+  // dense inverse: plan, device views, and the flag of its bounded waits
+  bool coarse_sparse = false;
+  feti::CoarsePlan cplan;
+  feti::CoarseDev cdev{};
+  feti::CoarseDag cdag{};
+  int* d_coarse_err = nullptr;
   int32_t *d_own_gdof = nullptr, *d_own_vpos = nullptr;
   int n_own = 0;
   std::vector<double> U_init;  // classical: Dirichlet values at their DOFs
@@ -364,6 +371,80 @@ struct StageLog {
 // and written to the context's device word; 0 cycles = give up at the first
 // check.
 constexpr unsigned long long kDefaultSpinNs = 100000000ull;
+
+// Sparse coarse problem: used from this many coarse columns on (automatic
+// form); supernodes of at most kCoarseLeaf subdomains below the separators;
+// a front with at most kCoarseMergeBytes of factor per sweep runs each sweep
+// as one task, larger fronts in row tasks of about kCoarseTaskBytes.
+constexpr int64_t kCoarseSparseMin = 1536;
+constexpr int kCoarseLeaf = 8;
+constexpr int kCoarseTaskBytes = 49152;
+constexpr int kCoarseMergeBytes = 98304;
+
+// Uploads the coarse plan and allocates the factor, the sweep scratch (for up
+// to kMaxRhs vectors), the task flags and counters (zero) and the wait flag.
+feti_status upload_coarse(feti_ctx* ctx) {
+  const feti::CoarsePlan& cp = ctx->cplan;
+  std::vector<int32_t> lvl;
+  ctx->cdev.lvl_off.clear();
+  for (const auto& L : cp.level_fronts) {
+    ctx->cdev.lvl_off.push_back((int64_t)lvl.size());
+    lvl.insert(lvl.end(), L.begin(), L.end());
+  }
+  feti::CoarseFront* fr = nullptr;
+  feti::CoarseChild* ch = nullptr;
+  feti::CoarseTask* tk = nullptr;
+  feti::CoarsePlace* pl = nullptr;
+  int32_t *map = nullptr, *nat = nullptr, *dep = nullptr, *dlvl = nullptr, *gptr = nullptr, *gsrc = nullptr;
+  FETI_TRY(upload(ctx, &fr, cp.fronts));
+  FETI_TRY(upload(ctx, &ch, cp.child));
+  FETI_TRY(upload(ctx, &map, cp.map));
+  FETI_TRY(upload(ctx, &nat, cp.nat));
+  FETI_TRY(upload(ctx, &tk, cp.tasks));
+  FETI_TRY(upload(ctx, &dep, cp.dep));
+  FETI_TRY(upload(ctx, &pl, cp.place));
+  FETI_TRY(upload(ctx, &dlvl, lvl));
+  FETI_TRY(upload(ctx, &gptr, cp.gptr));
+  FETI_TRY(upload(ctx, &gsrc, cp.gsrc));
+  double *Dm = nullptr, *Lm = nullptr, *yt = nullptr, *out = nullptr;
+  unsigned *flag = nullptr, *ctr = nullptr;
+  FETI_TRY(dev_alloc(ctx, &Dm, cp.nD));
+  FETI_TRY(dev_alloc(ctx, &Lm, cp.nL));
+  FETI_TRY(dev_alloc(ctx, &yt, (size_t)ctx->cd * feti::kMaxRhs));
+  FETI_TRY(dev_alloc(ctx, &out, (size_t)std::max<int32_t>(cp.n_out, 1) * feti::kMaxRhs));
+  FETI_TRY(dev_alloc(ctx, &flag, cp.tasks.size()));
+  FETI_TRY(dev_alloc(ctx, &ctr, 3));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_coarse_err, 1));
+  FETI_CK(cudaMemsetAsync(flag, 0, std::max<size_t>(cp.tasks.size(), 1) * sizeof(unsigned), ctx->stream));
+  FETI_CK(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned), ctx->stream));
+  FETI_CK(cudaMemsetAsync(ctx->d_coarse_err, 0, sizeof(int), ctx->stream));
+  ctx->cdev.fr = fr;
+  ctx->cdev.child = ch;
+  ctx->cdev.map = map;
+  ctx->cdev.place = pl;
+  ctx->cdev.lvl = dlvl;
+  ctx->cdev.Dm = Dm;
+  ctx->cdev.Lm = Lm;
+  feti::CoarseDag& d = ctx->cdag;
+  d.fr = fr;
+  d.child = ch;
+  d.map = map;
+  d.nat = nat;
+  d.task = tk;
+  d.dep = dep;
+  d.gptr = gptr;
+  d.gsrc = gsrc;
+  d.Dm = Dm;
+  d.Lm = Lm;
+  d.yt = yt;
+  d.out = out;
+  d.flag = flag;
+  d.ctr = ctr;
+  d.n_tasks = (int)cp.tasks.size();
+  d.smem1 = cp.smem1;
+  d.smem16 = cp.smem16;
+  return FETI_OK;
+}
 feti_status set_spin_budget(feti_ctx* ctx, uint64_t ns) {
   int khz = 0;
   FETI_CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
@@ -948,6 +1029,22 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   ctx->n_gtg = (int)gi.size();
   lg.mark("create: maps, coarse blocks");
+  {
+    const int form = ctx->opt.coarse_form;
+    ctx->coarse_sparse = ctx->cd > 0 && (form == 2 || (form == 0 && ctx->cd >= kCoarseSparseMin));
+    if (ctx->coarse_sparse) {
+      std::vector<int32_t> kk(P), co(P);
+      for (int s = 0; s < P; ++s) {
+        kk[s] = ctx->lay[s].k;
+        co[s] = ctx->lay[s].coff;
+      }
+      std::string e;
+      if (!feti::coarse_plan(P, kk.data(), co.data(), gi, gj, kCoarseLeaf, kCoarseTaskBytes, kCoarseMergeBytes,
+                              &ctx->cplan, &e))
+        return fail(ctx, FETI_ERR_PARTITION, e);
+      lg.mark("create: coarse ordering and supernodes");
+    }
+  }
   // gemv block tables
   std::vector<int32_t> tab_sub[2][3], tab_row[2][3];
   const int rpcs[3] = {32, 64, 128};
@@ -1024,6 +1121,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(upload(ctx, &ctx->d_gtg_j, gj));
   FETI_TRY(upload(ctx, &ctx->d_gtg_ptr, gptr));
   FETI_TRY(upload(ctx, &ctx->d_gtg_rows, grows));
+  if (ctx->coarse_sparse) FETI_TRY(upload_coarse(ctx));
   FETI_TRY(upload(ctx, &ctx->d_R, Rall));
   FETI_TRY(upload(ctx, &ctx->d_own_gdof, own_gdof));
   FETI_TRY(upload(ctx, &ctx->d_gs_ptr, gs_ptr));
@@ -1040,7 +1138,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(dev_alloc(ctx, &ctx->d_Uout, 3 * (size_t)N));
   ctx->face_kind.swap(face_kind);
   FETI_TRY(dev_alloc(ctx, &ctx->d_face_force, 3 * (size_t)fpn * std::max(nf, 1)));
-  FETI_TRY(dev_alloc(ctx, &ctx->d_Ke, (size_t)nde * nde * E));
+  FETI_TRY(dev_alloc(ctx, &ctx->d_Ke, (size_t)feti::ke_packed(nde) * E));
   if (ctx->mat.kind == FETI_HGO_TWO_FIBRE) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_fe, 12 * (size_t)E));
     FETI_TRY(dev_alloc(ctx, &ctx->d_U, 3 * (size_t)N));
@@ -1112,7 +1210,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(set_spin_budget(ctx, ctx->opt.spin_timeout_ns ? ctx->opt.spin_timeout_ns : kDefaultSpinNs));
   FETI_CK(cudaMemsetAsync(ctx->d_zero, 0, sizeof(int), ctx->stream));
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  if (ctx->cd > 0) {
+  if (ctx->cd > 0 && !ctx->coarse_sparse) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_Ginv, (size_t)ctx->cd * ctx->cd));
     SubLayout Lc{};
     Lc.n = (int)ctx->cd; Lc.nI = 0; Lc.nbp = (int)ctx->cd; Lc.k = 0; Lc.ld = 2 * (int)ctx->cd;
@@ -1379,6 +1477,27 @@ feti_status coarse_begin(feti_ctx* ctx) {
     FETI_CK(cudaEventCreateWithFlags(&ctx->ev_coarse, cudaEventDisableTiming));
     FETI_TRY(dev_alloc(ctx, &ctx->d_status2, 1));
   }
+  if (ctx->coarse_sparse) {
+    // supernodal factorization: fronts workspace only until joined
+    cudaError_t e = cudaMalloc(&ctx->coarse_ws[0], std::max<int64_t>(ctx->cplan.ws, 1) * sizeof(double));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      ctx->coarse_ws[0] = nullptr;
+      return fail(ctx, e == cudaErrorMemoryAllocation ? FETI_ERR_OOM : FETI_ERR_CUDA,
+                  std::string("coarse workspace: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t st = ctx->stream2;
+    FETI_CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    FETI_CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+    FETI_CK(cudaMemsetAsync(ctx->d_status2, 0, sizeof(int), st));
+    feti::launch_coarse_factor(ctx->cplan, ctx->cdev, ctx->d_gtg_i, ctx->d_gtg_j, ctx->d_gtg_ptr, ctx->d_gtg_rows,
+                               ctx->n_gtg, ctx->d_lay, ctx->d_R, ctx->maps, static_cast<double*>(ctx->coarse_ws[0]),
+                               ctx->d_status2, st);
+    FETI_CK(cudaGetLastError());
+    FETI_CK(cudaEventRecord(ctx->ev_coarse, st));
+    ctx->coarse_pending = true;
+    return FETI_OK;
+  }
   {
     cudaError_t e = cudaMalloc(&ctx->coarse_ws[0], cd * cd * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->coarse_ws[1], 4 * cd * cd * sizeof(double));
@@ -1429,6 +1548,25 @@ feti_status coarse_join(feti_ctx* ctx) {
   return FETI_OK;
 }
 
+// c = (G^T G)^-1 g (one vector): dense inverse or sparse sweeps.
+void coarse_apply_g(feti_ctx* ctx, const double* g, double* c, const int* done) {
+  if (ctx->coarse_sparse)
+    feti::launch_coarse_solve(ctx->cdag, 1, g, nullptr, ctx->d_sub_chunk_ptr, ctx->d_col_sub, ctx->d_lay, c, done,
+                              ctx->d_coarse_err, ctx->d_spin, ctx->stream);
+  else
+    feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, g, c, done, ctx->stream);
+}
+
+// d_c = (G^T G)^-1 G^T x from the chunk partials in d_gpart.
+void coarse_apply_part(feti_ctx* ctx, const int* done) {
+  if (ctx->coarse_sparse)
+    feti::launch_coarse_solve(ctx->cdag, 1, nullptr, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub, ctx->d_lay,
+                              ctx->d_c, done, ctx->d_coarse_err, ctx->d_spin, ctx->stream);
+  else
+    feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
+                                   ctx->d_lay, ctx->d_c, done, ctx->stream);
+}
+
 // P v -> out (with optional partial dot with a, or the squared norm, into
 // partial, by default d_partial)
 void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool with_dot, const int* done,
@@ -1442,8 +1580,7 @@ void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool 
   }
   feti::launch_gtv_part(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_lay, ctx->d_R, ctx->maps, v,
                         ctx->d_gpart, done, st);
-  feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
-                                 ctx->d_lay, ctx->d_c, done, st);
+  coarse_apply_part(ctx, done);
   feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, v, ctx->d_c, out, a, partial, with_dot, done, st);
 }
 
@@ -1753,8 +1890,7 @@ void pcg_iteration(feti_ctx* ctx, double* lam, bool f32) {
     feti::launch_gtv_part(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_lay, ctx->d_R, ctx->maps,
                           ctx->d_r, ctx->d_gpart, done, st, ctx->d_q, ctx->d_partial_pq, ctx->d_sc,
                           ctx->d_alpha_hist);
-    feti::launch_coarse_apply_part((int)ctx->cd, ctx->d_Ginv, ctx->d_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
-                                   ctx->d_lay, ctx->d_c, done, st);
+    coarse_apply_part(ctx, done);
   }
   feti::launch_expand_update(ctx->maps, ctx->d_lay, ctx->d_R, ctx->d_r, ctx->d_c, ctx->d_w, ctx->d_partial, lam,
                              ctx->d_p, ctx->d_q, ctx->d_partial_pq, ctx->d_sc, ctx->d_alpha_hist, st);
@@ -1878,7 +2014,7 @@ feti_status rhs_setup(feti_ctx* ctx) {
   FETI_CK(cudaMemsetAsync(ctx->d_lam, 0, nl * sizeof(double), st));
   if (ctx->cd > 0) {
     feti::launch_rtx(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_f, -1.0, ctx->d_e, st);
-    feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, ctx->d_e, ctx->d_c, zero, st);
+    coarse_apply_g(ctx, ctx->d_e, ctx->d_c, zero);
     feti::launch_expand(ctx->maps, ctx->d_lay, ctx->d_R, ctx->d_lam, ctx->d_c, ctx->d_lam, nullptr, nullptr, 0,
                         zero, st);
   }
@@ -1961,13 +2097,14 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
     rep->coarse_dim = ctx->cd;
   }
   FETI_TRY(check_wait_flag(ctx, ctx->d_sym_err, "streamed symmetric local apply"));
+  FETI_TRY(check_wait_flag(ctx, ctx->d_coarse_err, "sparse coarse solve"));
   if (breakdown) return fail(ctx, FETI_ERR_BREAKDOWN, "PCG breakdown");
   // recovery: gamma = (G^T G)^-1 G^T (F lambda - d~), u_i = K^+(f_i - B_i^T lambda) + R_i gamma_i
   apply_F(ctx, ctx->d_lam, ctx->d_q, nullptr, false, zero);
   feti::launch_vsub(nl, ctx->d_q, ctx->d_d, ctx->d_z, st);
   if (ctx->cd > 0) {
     feti::launch_gtv(ctx->P, ctx->d_lay, ctx->d_R, ctx->maps, ctx->d_z, ctx->d_g, zero, st);
-    feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, ctx->d_g, ctx->d_c, zero, st);
+    coarse_apply_g(ctx, ctx->d_g, ctx->d_c, zero);
   }
   feti::launch_gather(ctx->maps, ctx->d_lam, nullptr, ctx->d_loc, zero, st);
   feti::launch_local_sub(ctx->P, ctx->d_lay, ctx->d_f, ctx->d_loc, ctx->d_x2, st);
@@ -1975,6 +2112,7 @@ feti_status dual_solve(feti_ctx* ctx, feti_report* rep, float* pcg_ms) {
   if (ctx->cd > 0) feti::launch_add_kernel(ctx->P, ctx->d_lay, ctx->d_R, ctx->d_c, ctx->d_x, st);
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_wait_flag(ctx, ctx->d_sym_err, "streamed symmetric local apply"));
+  FETI_TRY(check_wait_flag(ctx, ctx->d_coarse_err, "sparse coarse solve"));
   if (!conv) return fail(ctx, FETI_ERR_NOT_CONVERGED, "PCG reached maxit");
   return FETI_OK;
 }
@@ -2163,10 +2301,16 @@ void apply_M_m(feti_ctx* ctx, int nrhs, const double* w, double* z, const int* d
 void project_m(feti_ctx* ctx, int nrhs, const double* v, double* out, const double* a, double* partial,
                double* r_upd, double* lam, const double* p, const double* q, const int* done) {
   const bool coarse = ctx->cd > 0;
-  if (coarse)
+  if (coarse) {
+    // dense: G^T x partials, their sums, Ginv G; sparse: G^T x partials, then the sweeps
     feti::launch_project_m(ctx->n_chunks, ctx->d_chunk_sub, ctx->d_chunk_p0, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
-                           ctx->d_lay, ctx->d_R, ctx->maps, nrhs, (int)ctx->cd, ctx->d_Ginv, r_upd ? r_upd : v,
-                           r_upd ? q : nullptr, ctx->dm_sc, ctx->dm_gpart, ctx->dm_g, ctx->dm_c, done, ctx->stream);
+                           ctx->d_lay, ctx->d_R, ctx->maps, nrhs, (int)ctx->cd,
+                           ctx->coarse_sparse ? nullptr : ctx->d_Ginv, r_upd ? r_upd : v, r_upd ? q : nullptr,
+                           ctx->dm_sc, ctx->dm_gpart, ctx->dm_g, ctx->dm_c, done, ctx->stream);
+    if (ctx->coarse_sparse)
+      feti::launch_coarse_solve(ctx->cdag, nrhs, nullptr, ctx->dm_gpart, ctx->d_sub_chunk_ptr, ctx->d_col_sub,
+                                ctx->d_lay, ctx->dm_c, done, ctx->d_coarse_err, ctx->d_spin, ctx->stream);
+  }
   feti::launch_expand_m(ctx->maps, ctx->d_lay, ctx->d_R, nrhs, coarse ? 1 : 0, v, ctx->dm_c, out, a, partial, r_upd,
                         lam, p, q, ctx->dm_sc, done, ctx->stream);
 }
@@ -2326,6 +2470,7 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
     rep->coarse_dim = ctx->cd;
   }
   FETI_TRY(check_wait_flag(ctx, ctx->d_tc_err, "tensor-core block GEMM"));
+  FETI_TRY(check_wait_flag(ctx, ctx->d_coarse_err, "sparse coarse solve"));
   if (breakdown) return fail(ctx, FETI_ERR_BREAKDOWN, "PCG breakdown (block form)");
   // recovery, one right-hand side at a time (single-RHS kernels on column k)
   const size_t n3 = 3 * (size_t)ctx->N;
@@ -2335,7 +2480,7 @@ feti_status dual_solve_multi(feti_ctx* ctx, const double* scale, int nrhs, doubl
     feti::launch_axpy_to(nl, ctx->d_q, -scale[k], ctx->d_d, ctx->d_z, st);       // F lambda_k - d~_k
     if (ctx->cd > 0) {
       feti::launch_gtv(ctx->P, ctx->d_lay, ctx->d_R, ctx->maps, ctx->d_z, ctx->d_g, zero, st);
-      feti::launch_coarse_apply((int)ctx->cd, ctx->d_Ginv, ctx->d_g, ctx->d_c, zero, st);
+      coarse_apply_g(ctx, ctx->d_g, ctx->d_c, zero);
     }
     feti::launch_gather(ctx->maps, ctx->d_lam, nullptr, ctx->d_loc, zero, st);
     feti::launch_axpy_to((int)ctx->nloc_total, ctx->d_f, scale[k] - 1.0, ctx->d_f, ctx->d_x2, st);   // scale_k f
@@ -2454,6 +2599,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown preconditioner");
   if (opt->precision != FETI_FP64 && opt->precision != FETI_MIXED && opt->precision != FETI_MIXED_F32FACTOR)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported precision");
+  if (opt->coarse_form < 0 || opt->coarse_form > 2) return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported coarse_form");
   if (!(opt->tol > 0.0) || opt->maxit <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "tol and maxit must be positive");
   if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE && mat->kind != FETI_LINEAR_ISO_P0)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown material");
@@ -2844,7 +2990,20 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
     ctx->elem_bytes = per_elem * (double)ctx->E + per_node * (double)ctx->N;
   }
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  FETI_CK(cudaMemcpyAsync(Ke_out, ctx->d_Ke, (size_t)ctx->nde * ctx->nde * ctx->E * sizeof(double), kind, st));
+  // full nde x nde copies of the packed (upper-triangle) element matrices
+  const size_t full = (size_t)ctx->nde * ctx->nde * ctx->E;
+  if (out_on_device) {
+    feti::launch_ke_unpack(ctx->E, ctx->nde, ctx->d_Ke, Ke_out, st);
+    FETI_CK(cudaGetLastError());
+  } else {
+    double* tmp = nullptr;
+    FETI_CK(cudaMalloc(&tmp, std::max<size_t>(full, 1) * sizeof(double)));
+    feti::launch_ke_unpack(ctx->E, ctx->nde, ctx->d_Ke, tmp, st);
+    cudaError_t e = cudaMemcpyAsync(Ke_out, tmp, full * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    FETI_CK(e);
+  }
   if (fe_out && hgo) FETI_CK(cudaMemcpyAsync(fe_out, ctx->d_fe, 12 * (size_t)ctx->E * sizeof(double), kind, st));
   FETI_CK(cudaStreamSynchronize(st));
   return FETI_OK;
@@ -2948,6 +3107,24 @@ feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]) {
   out[2] = ctx->nloc_total;
   out[3] = ctx->nb_total;
   out[4] = ctx->P;
+  return FETI_OK;
+}
+
+feti_status feti_get_coarse_info(const feti_ctx* ctx, int64_t out[6]) {
+  if (!ctx || !out) return FETI_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i) out[i] = 0;
+  if (ctx->cd == 0) return FETI_OK;
+  out[0] = ctx->coarse_sparse ? 2 : 1;
+  if (!ctx->coarse_sparse) {
+    out[3] = ctx->cd * ctx->cd;
+    return FETI_OK;
+  }
+  const feti::CoarsePlan& cp = ctx->cplan;
+  out[1] = (int64_t)cp.fronts.size();
+  out[2] = cp.height;
+  for (const auto& F : cp.fronts) out[3] += (int64_t)F.w * (F.w + 1) / 2 + (int64_t)F.w * F.p;
+  out[4] = (int64_t)cp.tasks.size();
+  out[5] = cp.ws;
   return FETI_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "feti.h"
@@ -47,6 +48,15 @@ struct SubLayout {
 constexpr int kSymPH = 32;  // panel height of the symmetric FP32 apply
 
 // Element kernels ------------------------------------------------------------
+// Element matrices are symmetric and stored as their upper triangle, row by
+// row: ke_packed(nde) doubles per element, entry (i, j) at ke_idx(nde, i, j).
+__host__ __device__ constexpr int ke_packed(int nde) { return nde * (nde + 1) / 2; }
+__host__ __device__ inline int ke_idx(int nde, int i, int j) {
+  const int a = i < j ? i : j, b = i < j ? j : i;
+  return a * nde - a * (a - 1) / 2 + (b - a);
+}
+// Full (nde x nde, row-major) copies of the packed element matrices.
+void launch_ke_unpack(int n_el, int nde, const double* Kp, double* K, cudaStream_t st);
 void launch_elem_linear(int n_tets, const double* coords, const int32_t* tets, double E, double nu,
                         double* Ke, int* status, cudaStream_t st);
 void launch_elem_hgo(int n_tets, const double* coords, const int32_t* tets, const double* U,
@@ -332,7 +342,8 @@ void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const f
                     const unsigned long long* spin_cycles, cudaStream_t st);
 void launch_scatter_m(const Maps& mp, int nrhs, const double* y, const double* wv, double* q, const double* a,
                       double* partial, const int* done, cudaStream_t st);
-// c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update).
+// c = (G^T G)^-1 G^T (x - alpha q), q optional (fused CG update); with
+// Ginv == NULL only the chunk partials of G^T (x - alpha q) into gpart.
 void launch_project_m(int n_chunks, const int32_t* chunk_sub, const int32_t* chunk_p0, const int32_t* sub_chunk_ptr,
                       const int32_t* col_sub, const SubLayout* lay, const double* R, const Maps& mp, int nrhs, int cd,
                       const double* Ginv, const double* x, const double* q, const PcgScalarsM* sc, double* gpart,
@@ -361,4 +372,120 @@ cudaError_t noalloc_scratch_lookup(double** out, size_t* capacity);
 // scratch looked up at feti_create instead of context memory; enqueued on the
 // context's stream, no allocation, no graph, no event.
 feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z);
+}  // namespace feti
+
+namespace feti {
+// ---- sparse coarse problem: supernodal Cholesky of G^T G (Sec. 4.3) ----
+// Dynamic shared memory a sweep task may use (doubles, 224 KiB).
+constexpr int64_t kCoarseSmemDoubles = 224 * 1024 / 8;
+// Row stride of a staged factor block in shared memory: odd, so that rows
+// read column by column by neighbouring threads fall in different banks.
+__host__ __device__ constexpr int64_t coarse_odd(int64_t n) { return n | 1; }
+// Front of a supernode: its own coarse columns (w), then its panel rows (p),
+// as natural coarse indices nat[nat .. nat + w + p).
+struct CoarseFront {
+  int32_t w, p;
+  int32_t parent;  // -1: root of the assembly tree
+  int32_t level;   // height in the assembly tree (leaves 0)
+  int32_t nat;     // offset of the front's natural indices
+  int32_t out;     // first row of the update vector in the out scratch (p rows)
+  int32_t ch0, ch1;  // children: range of the child list
+  int32_t gofs;    // gather lists of the front rows: gptr[gofs .. gofs + w + p]
+                   // bound the children's update rows (gsrc, rows of the out
+                   // scratch) that add into each front row, children in order
+  int32_t pad;
+  int64_t off;     // numeric workspace, (f + w) x f row-major (f = w + p); the
+                   // last w rows start as the identity on the own columns
+  int64_t doff;    // L_ss^-1 (w x w, lower) then L_ss^-T (w x w, upper), row-major
+  int64_t loff;    // L_ps (p x w) then L_ps^T (w x p), row-major
+};
+// A child of a front: its p front indices in the parent's front start at
+// map; the first n_own of them are own columns of the parent.
+struct CoarseChild {
+  int32_t c, map, n_own, pad;
+};
+// One task of the triangular sweeps: rows [r0, r1) of kind 0 (forward:
+// y = L_ss^-1 t on own rows), 1 (forward: update vector on panel rows),
+// 2 (backward: t = y - L_ps^T x_panel on own rows), 3 (backward:
+// x = L_ss^-T t on own rows), or a whole front: 4 (kinds 0 and 1), 5
+// (kinds 2 and 3); it waits for the ticket ranges dep[2 d], dep[2 d + 1]
+// (first, count) for d in [dep0, dep1).
+struct CoarseTask {
+  int32_t s, kind, r0, r1, dep0, dep1;
+};
+// Destination of a G^T G pair block (blk_i <= blk_j natural subdomain
+// numbers) in a front: rows row0.., columns col0..; swap: the blk_i columns
+// are the front's columns.
+struct CoarsePlace {
+  int64_t off;
+  int32_t ld, row0, col0, swap;
+};
+struct CoarsePlan {
+  std::vector<CoarseFront> fronts;
+  std::vector<CoarseChild> child;
+  std::vector<int32_t> map, nat, dep, gptr, gsrc;
+  std::vector<CoarseTask> tasks;
+  std::vector<CoarsePlace> place;
+  std::vector<std::vector<int32_t>> level_fronts;
+  int64_t ws = 0, nD = 0, nL = 0;
+  int32_t n_out = 0;
+  int max_w = 0, max_p = 0, max_children = 0, height = 0;
+  // shared memory of the largest task (doubles: its staged factor block plus
+  // its vectors) for one and for kMaxRhs right-hand sides
+  int64_t smem1 = 1, smem16 = 1;
+  double flops = 0.0;
+};
+// Nested-dissection order of the subdomain graph (pair blocks gi[b] <= gj[b]
+// of the subdomains with k > 0), supernodes of at most leaf_max subdomains
+// below the separators, fronts, child maps, block placements and the task
+// graph of the sweeps (a front of at most merge_bytes of factor per sweep as
+// one task, larger ones in row tasks of about task_bytes).  Host only.
+bool coarse_plan(int P, const int32_t* k, const int32_t* coff, const std::vector<int32_t>& gi,
+                 const std::vector<int32_t>& gj, int leaf_max, int task_bytes, int merge_bytes, CoarsePlan* out,
+                 std::string* err);
+}  // namespace feti
+
+namespace feti {
+// Device views of a coarse plan (feti_coarse.cu).
+struct CoarseDag {
+  const CoarseFront* fr;
+  const CoarseChild* child;
+  const int32_t* map;
+  const int32_t* nat;
+  const CoarseTask* task;
+  const int32_t* dep;
+  const int32_t* gptr;
+  const int32_t* gsrc;
+  const double* Dm;  // L_ss^-1, L_ss^-T per front
+  const double* Lm;  // L_ps, L_ps^T per front
+  double* yt;        // y, then t, by natural coarse index (cd x nrhs)
+  double* out;       // update vectors (n_out x nrhs)
+  unsigned* flag;    // per task: epoch of its last completion
+  unsigned* ctr;     // ticket counter, completed count, epoch
+  int n_tasks;
+  int64_t smem1, smem16;  // dynamic shared memory (doubles) for 1 and up to kMaxRhs vectors
+};
+struct CoarseDev {
+  const CoarseFront* fr;
+  const CoarseChild* child;
+  const int32_t* map;
+  const CoarsePlace* place;
+  const int32_t* lvl;            // level lists, concatenated
+  std::vector<int64_t> lvl_off;  // host: start of each level list
+  double* Dm;
+  double* Lm;
+};
+// Numeric multifrontal factorization of G^T G into dv.Dm / dv.Lm (workspace
+// ws of cp.ws doubles, pair blocks as for launch_gtg); a non-positive pivot
+// sets DEV_LOCAL_SINGULAR in *status.
+void launch_coarse_factor(const CoarsePlan& cp, const CoarseDev& dv, const int32_t* blk_i, const int32_t* blk_j,
+                          const int32_t* blk_ptr, const int32_t* blk_rows, int n_blocks, const SubLayout* lay,
+                          const double* R, const Maps& mp, double* ws, int* status, cudaStream_t st);
+// c = (G^T G)^-1 g for nrhs vectors ([j][k] layout, natural coarse index j):
+// g given, or (g == NULL) summed from the chunk partials of the G^T x
+// kernels (partial[(chunk * 6 + a) * nrhs + k]).  One launch of dag.n_tasks
+// CTAs; a wait that exceeds *spin_cycles sets *err.
+void launch_coarse_solve(const CoarseDag& dag, int nrhs, const double* g, const double* partial,
+                         const int32_t* sub_chunk_ptr, const int32_t* col_sub, const SubLayout* lay, double* c,
+                         const int* done, int* err, const unsigned long long* spin_cycles, cudaStream_t st);
 }  // namespace feti

@@ -94,15 +94,15 @@ __global__ void k_elem_linear(int n_tets, const double* __restrict__ coords, con
   }
   const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   const double mu = E / (2.0 * (1.0 + nu));
-  double* K = Ke + (size_t)e * 144;
+  double* K = Ke + (size_t)e * ke_packed(12);
   for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) {
+    for (int b = a; b < 4; ++b) {
       const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
       for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
+        for (int j = (a == b ? i : 0); j < 3; ++j) {
           double v = lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i];
           if (i == j) v += mu * gab;
-          K[(3 * a + i) * 12 + 3 * b + j] = V * v;
+          K[ke_idx(12, 3 * a + i, 3 * b + j)] = V * v;
         }
     }
 }
@@ -148,9 +148,10 @@ __global__ void k_elem_linear_p2(int n_tets, const double* __restrict__ coords, 
   const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   const double mu = E / (2.0 * (1.0 + nu));
   const double al = (5.0 + 3.0 * sqrt(5.0)) / 20.0, be = (5.0 - sqrt(5.0)) / 20.0;
-  double* K = Ke + (size_t)e * 900;
+  double* K = Ke + (size_t)e * ke_packed(30);
   for (int blk = lane; blk < 100; blk += 32) {
     const int a = blk / 10, b = blk % 10;
+    if (b < a) continue;  // upper triangle of node blocks
     double k9[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     double ma[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
     for (int q = 0; q < 4; ++q) {
@@ -171,8 +172,8 @@ __global__ void k_elem_linear_p2(int n_tets, const double* __restrict__ coords, 
       }
     }
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        K[(3 * a + i) * 30 + 3 * b + j] = V * (k9[i][j] + (p0 ? lam * ma[i] * mb[j] : 0.0));
+      for (int j = (a == b ? i : 0); j < 3; ++j)
+        K[ke_idx(30, 3 * a + i, 3 * b + j)] = V * (k9[i][j] + (p0 ? lam * ma[i] * mb[j] : 0.0));
   }
 }
 
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(64) k_elem_hgo(int n_tets, const double* __res
   }
   // diagonal-in-(i,j) part: D_ab = V ((c_Q/2) h_a.h_b + h_a.tau h_b)
   const double hq = 0.5 * cQ * V;
-  double* Kout = Ke + (size_t)e * 144;
+  double* Kout = Ke + (size_t)e * ke_packed(12);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -349,8 +350,7 @@ __global__ void __launch_bounds__(64) k_elem_hgo(int n_tets, const double* __res
           double v = Pv[a][i] * h[b][j] + h[a][i] * P[b][j] + hq * h[a][j] * h[b][i] + r[0][a][i] * r[0][b][j] +
                      r[1][a][i] * r[1][b][j];
           if (i == j) v += D;
-          Kout[(3 * a + i) * 12 + 3 * b + j] = v;
-          Kout[(3 * b + j) * 12 + 3 * a + i] = v;
+          Kout[ke_idx(12, 3 * a + i, 3 * b + j)] = v;
         }
     }
   if (fe) {
@@ -371,12 +371,23 @@ __global__ void k_assemble(const SubLayout* __restrict__ lay, const int32_t* __r
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
   T* A = Abase + L.aoff;
-  const int kes = nde * nde;
+  const int kes = ke_packed(nde);
   for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
     const int e = sub_elems[q];
     for (int t = threadIdx.x; t < kes; t += blockDim.x) {
-      const int r = elem_dense[(size_t)nde * e + t / nde], c = elem_dense[(size_t)nde * e + t % nde];
-      if (r >= 0 && c >= 0) A[(size_t)r * L.ld + c] += (T)Ke[(size_t)e * kes + t];
+      // packed entry t -> (i, j), i <= j; both (i, j) and (j, i) of the local matrix
+      int i = 0, rem = t;
+      while (rem >= nde - i) {
+        rem -= nde - i;
+        ++i;
+      }
+      const int j = i + rem;
+      const int r = elem_dense[(size_t)nde * e + i], c = elem_dense[(size_t)nde * e + j];
+      if (r >= 0 && c >= 0) {
+        const T v = (T)Ke[(size_t)e * kes + t];
+        A[(size_t)r * L.ld + c] += v;
+        if (i != j) A[(size_t)c * L.ld + r] += v;
+      }
     }
     __syncthreads();
   }
@@ -436,7 +447,7 @@ __global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t*
     }
     __syncthreads();
   }
-  const int kes = nde * nde;
+  const int kes = ke_packed(nde);
   for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
     const int e = sub_elems[q];
     if (t < nde) {
@@ -446,7 +457,7 @@ __global__ void k_assemble_rhs(const SubLayout* __restrict__ lay, const int32_t*
         if (elem_dirval) {
           for (int b = 0; b < nde; ++b) {
             const double ud = elem_dirval[(size_t)nde * e + b];
-            if (ud != 0.0) v -= Ke[(size_t)e * kes + t * nde + b] * ud;
+            if (ud != 0.0) v -= Ke[(size_t)e * kes + ke_idx(nde, t, b)] * ud;
           }
         }
         f[r] += v;
@@ -1856,12 +1867,12 @@ __global__ void k_gs_elem_matvec(int n, const int32_t* __restrict__ inc_ptr, con
     for (int q = inc_ptr[j]; q < inc_ptr[j + 1]; ++q) {
       const int ea = inc[q];
       const int e = ea / 12, a = ea % 12;
-      const double* K = Ke + (size_t)e * 144 + a * 12;
+      const double* K = Ke + (size_t)e * ke_packed(12);
       const int32_t* d = elem_gs + (size_t)e * 12;
 #pragma unroll
       for (int b = 0; b < 12; ++b) {
         const int g = d[b];
-        if (g >= 0) t += K[b] * v[g];
+        if (g >= 0) t += K[ke_idx(12, a, b)] * v[g];
       }
     }
     y[j] = t;
@@ -2334,6 +2345,25 @@ void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step
 void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
                          const int32_t* env0, float* A, int* status, cudaStream_t st) {
   chol_batched<float>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
+}
+
+namespace {
+__global__ void k_ke_unpack(long n, int nde, const double* __restrict__ Kp, double* __restrict__ K) {
+  const int kes = nde * nde;
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < n; x += (long)gridDim.x * blockDim.x) {
+    const long e = x / kes;
+    const int t = (int)(x - e * kes);
+    K[x] = Kp[e * ke_packed(nde) + ke_idx(nde, t / nde, t % nde)];
+  }
+}
+}  // namespace
+
+void launch_ke_unpack(int n_el, int nde, const double* Kp, double* K, cudaStream_t st) {
+  const long n = (long)n_el * nde * nde;
+  if (n <= 0) return;
+  long b = (n + kThreads - 1) / kThreads;
+  if (b > 65535) b = 65535;
+  k_ke_unpack<<<(int)b, kThreads, 0, st>>>(n, nde, Kp, K);
 }
 
 }  // namespace feti

@@ -1297,6 +1297,7 @@ void launch_project_m(int n_chunks, const int32_t* chunk_sub, const int32_t* chu
                       double* g, double* c, const int* done, cudaStream_t st) {
   if (cd <= 0 || n_chunks <= 0) return;
   k_gtv_part_m<<<n_chunks, kThreads, 0, st>>>(chunk_sub, chunk_p0, lay, R, mp, nrhs, x, gpart, q, sc, done);
+  if (!Ginv) return;  // sparse coarse problem: the caller solves from the partials
   k_gsum_m<<<grid_for((long)cd * nrhs), kThreads, 0, st>>>(cd, nrhs, gpart, sub_chunk_ptr, col_sub, lay, g, done);
   const int warps = cd < 2432 ? cd : 2432;
   k_coarse_gemm_m<<<(warps * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(cd, nrhs, Ginv, g, c, done);
