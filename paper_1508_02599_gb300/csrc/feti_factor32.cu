@@ -111,17 +111,32 @@ __global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restric
       D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
     }
     {
-      // warp w: rows w, w + 8, w + 16, w + 24 of the block together, so each
-      // lane keeps four independent loads in flight per column step
-      const float* rp[4];
+      // warp w: rows w, w + 8, w + 16, w + 24 of the block together, four
+      // column strides at a time, so each lane keeps 16 independent loads in
+      // flight (the sweep is bound by the latency of these loads)
+      const float* rp = A + (size_t)I0 * ld;
+      int ro[4];  // row offsets within the 32-row block (< 32 ld)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) rp[q] = A + (size_t)(I0 + min(warp + kW * q, nb - 1)) * ld;
+      for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nb - 1) * (int)ld;
       float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 2
-      for (int j = lane; j < I0; j += 32) {
+      int j = lane;
+      for (; j + 96 < I0; j += 128) {
+        float a[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float yv = ys[j + 32 * u];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
+        }
+      }
+      for (; j < I0; j += 32) {
         const float yv = ys[j];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += rp[q][j] * yv;
+        for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

@@ -21,7 +21,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <numeric>
 #include <string>
@@ -348,6 +350,32 @@ double lanczos_cond(const std::vector<double>& alpha, const std::vector<double>&
 // ---------------------------------------------------------------------------
 // FETI_LOG=2 (or more) in the environment: wall time of each setup stage on
 // stderr (the stream is synchronised after each stage, only then).
+// Runs f(i) for i in [0, n) on up to 16 host threads, chunks taken in order
+// from a shared counter.  Every caller writes only the slots of its own
+// index, so the result does not depend on the number of threads.
+template <class F>
+void par_for(int64_t n, int64_t chunk, F&& f) {
+  const int64_t nchunks = (n + chunk - 1) / std::max<int64_t>(chunk, 1);
+  int T = (int)std::min<int64_t>(nchunks, std::min(16u, std::max(1u, std::thread::hardware_concurrency())));
+  if (T <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const int64_t c = next.fetch_add(1);
+      if (c >= nchunks) break;
+      const int64_t e = std::min(n, (c + 1) * chunk);
+      for (int64_t i = c * chunk; i < e; ++i) f(i);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+}
+
 struct StageLog {
   feti_ctx* ctx;
   bool on;
@@ -459,21 +487,28 @@ feti_status build_decomposition(feti_ctx* ctx) {
   StageLog lg(ctx);
   const int N = ctx->N, E = ctx->E, P = ctx->P;
   ctx->af = ctx->opt.method == FETI_ALL_FLOATING;
-  // local nodes per subdomain
-  ctx->nodes.assign(P, {});
-  std::vector<int32_t> ecount(P, 0);
-  for (int e = 0; e < E; ++e) ecount[ctx->part[e]]++;
+  // elements grouped by subdomain (ascending), then the local nodes of each
+  // subdomain (ascending), subdomains in parallel
+  std::vector<int32_t> sub_elem_ptr(P + 1, 0), sub_elems(E);
+  for (int e = 0; e < E; ++e) sub_elem_ptr[ctx->part[e] + 1]++;
   for (int s = 0; s < P; ++s) {
-    if (ecount[s] == 0) return fail(ctx, FETI_ERR_PARTITION, "subdomain " + std::to_string(s) + " has no elements");
-    ctx->nodes[s].reserve((size_t)ctx->npe * ecount[s]);
+    if (sub_elem_ptr[s + 1] == 0) return fail(ctx, FETI_ERR_PARTITION, "subdomain " + std::to_string(s) + " has no elements");
+    sub_elem_ptr[s + 1] += sub_elem_ptr[s];
   }
-  for (int e = 0; e < E; ++e)
-    for (int a = 0; a < ctx->npe; ++a) ctx->nodes[ctx->part[e]].push_back(ctx->tets[(size_t)ctx->npe * e + a]);
-  for (int s = 0; s < P; ++s) {
+  {
+    std::vector<int32_t> f2(sub_elem_ptr.begin(), sub_elem_ptr.end() - 1);
+    for (int e = 0; e < E; ++e) sub_elems[f2[ctx->part[e]]++] = e;
+  }
+  ctx->nodes.assign(P, {});
+  par_for(P, 4, [&](int64_t s) {
     auto& v = ctx->nodes[s];
+    v.reserve((size_t)ctx->npe * (sub_elem_ptr[s + 1] - sub_elem_ptr[s]));
+    for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q)
+      for (int a = 0; a < ctx->npe; ++a) v.push_back(ctx->tets[(size_t)ctx->npe * sub_elems[q] + a]);
     std::sort(v.begin(), v.end());
     v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
+  });
+  lg.mark("create:   local node lists");
   // node -> subdomains (ascending)
   std::vector<int32_t> nptr(N + 1, 0);
   for (int s = 0; s < P; ++s)
@@ -493,6 +528,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
       if (nsub[a] == s) return (int)lcopy[a];
     return -1;
   };
+  lg.mark("create:   node -> subdomains");
   std::vector<char> is_dir(3 * (size_t)N, 0);
   std::vector<double> dval(3 * (size_t)N, 0.0);
   for (size_t i = 0; i < ctx->dir_dof.size(); ++i) {
@@ -547,14 +583,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   for (int64_t r = 0; r < ctx->n_lambda; ++r)
     for (int e = 0; e < 2; ++e)
       if (rs[2 * r + e] >= 0) bflag[rs[2 * r + e]][rl[2 * r + e]] = 1;
-  // elements grouped by subdomain
-  std::vector<int32_t> sub_elem_ptr(P + 1, 0), sub_elems(E);
-  for (int e = 0; e < E; ++e) sub_elem_ptr[ctx->part[e] + 1]++;
-  for (int s = 0; s < P; ++s) sub_elem_ptr[s + 1] += sub_elem_ptr[s];
-  {
-    std::vector<int32_t> f2(sub_elem_ptr.begin(), sub_elem_ptr.end() - 1);
-    for (int e = 0; e < E; ++e) sub_elems[f2[ctx->part[e]]++] = e;
-  }
+  lg.mark("create:   boundary flags, element groups");
   // per subdomain: free DOFs, kernels, fixing DOFs, dense order
   ctx->lay.assign(P, SubLayout{});
   std::vector<std::vector<int32_t>> env0(P);  // per interior-elimination step: (eI, nbact)
@@ -564,7 +593,17 @@ feti_status build_decomposition(feti_ctx* ctx) {
   std::vector<std::vector<double>> Rd(P);           // R in dense order, n x k
   int64_t aoff = 0, soff = 0, foff = 0, roff = 0, foff32 = 0, soff32 = 0, fsym = 0, ssym = 0, psym = 0;
   int boff = 0, voff = 0, coff = 0;
-  for (int s = 0; s < P; ++s) {
+  // per subdomain (in parallel): free DOFs, kernel basis, fixing DOFs, dense
+  // order, envelope and R in dense order; sizes and offsets after
+  struct SubInfo {
+    int k = 0, nI = 0, nbp = 0, n = 0;
+    std::vector<int32_t> fix;
+    feti_status err = FETI_OK;
+    const char* msg = nullptr;
+  };
+  std::vector<SubInfo> info(P);
+  par_for(P, 1, [&](int64_t s) {
+    SubInfo& si = info[s];
     const auto& nod = ctx->nodes[s];
     const int nl = (int)nod.size(), nd = 3 * nl;
     std::vector<char> free(nd, 1);
@@ -634,7 +673,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
       if (free[d] && bflag[s][d]) bl.push_back(d);
     std::vector<int32_t> fix;
     if (k > 0) {
-      if ((int)bl.size() < k) return fail(ctx, FETI_ERR_KERNEL_DETECT, "too few boundary DOFs to fix the kernel");
+      if ((int)bl.size() < k) {
+        si.err = FETI_ERR_KERNEL_DETECT;
+        si.msg = "too few boundary DOFs to fix the kernel";
+        return;
+      }
       std::vector<double> W((size_t)bl.size() * k);
       for (size_t i = 0; i < bl.size(); ++i)
         for (int a = 0; a < k; ++a) W[i * k + a] = Rl[(size_t)bl[i] * k + a];
@@ -652,7 +695,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
         size_t j = 0;
         for (size_t i = 0; i < bl.size(); ++i)
           if (!chosen[i] && nrm[i] >= top * (1.0 - 1e-10)) { j = i; break; }
-        if (!(top > 0.0)) return fail(ctx, FETI_ERR_KERNEL_DETECT, "kernel basis vanishes on the boundary");
+        if (!(top > 0.0)) {
+          si.err = FETI_ERR_KERNEL_DETECT;
+          si.msg = "kernel basis vanishes on the boundary";
+          return;
+        }
         chosen[j] = 1;
         fix.push_back(bl[j]);
         std::vector<double> qv(k);
@@ -715,6 +762,20 @@ feti_status build_decomposition(feti_ctx* ctx) {
     }
     for (int d : fix) dl.push_back(d);
     const int n = (int)dl.size();
+    Rd[s].assign((size_t)n * k, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < k; ++a) Rd[s][(size_t)i * k + a] = Rl[(size_t)dl[i] * k + a];
+    si.k = k;
+    si.nI = nI;
+    si.nbp = nbp;
+    si.n = n;
+    si.fix = std::move(fix);
+  });
+  for (int s = 0; s < P; ++s)
+    if (info[s].err != FETI_OK) return fail(ctx, info[s].err, info[s].msg);
+  for (int s = 0; s < P; ++s) {
+    const SubInfo& si = info[s];
+    const int n = si.n, nI = si.nI, nbp = si.nbp, k = si.k;
     SubLayout L{};
     L.n = n; L.nI = nI; L.nbp = nbp; L.k = k; L.ld = n + nbp;
     L.boff = boff; L.voff = voff; L.coff = coff;
@@ -740,10 +801,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     foff32 += (int64_t)nbp * ((nbp + 3) & ~3);
     soff32 += (int64_t)nb * ((nb + 3) & ~3);
     ctx->max_nb = std::max(ctx->max_nb, nb);
-    Rd[s].assign((size_t)n * k, 0.0);
-    for (int i = 0; i < n; ++i)
-      for (int a = 0; a < k; ++a) Rd[s][(size_t)i * k + a] = Rl[(size_t)dl[i] * k + a];
-    for (int d : fix) ctx->fix_ldof.push_back(d);
+    for (int d : si.fix) ctx->fix_ldof.push_back(d);
     ctx->fix_ptr[s + 1] = (int32_t)ctx->fix_ldof.size();
   }
   lg.mark("create: kernels, fixing, dense order");
@@ -766,6 +824,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     pos_of[s].assign(3 * ctx->nodes[s].size(), -1);
     for (size_t i = 0; i < dense_ldof[s].size(); ++i) pos_of[s][dense_ldof[s][i]] = (int32_t)i;
   }
+  lg.mark("create:   dense positions");
   // device maps
   std::vector<int32_t> row_pos(2 * ctx->n_lambda, -1);
   std::vector<double> row_sgn(2 * ctx->n_lambda, 0.0);
@@ -798,6 +857,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   std::vector<int32_t> bpos_sub(ctx->nb_total);
   for (int s = 0; s < P; ++s)
     for (int p = 0; p < ctx->lay[s].nbp + ctx->lay[s].k; ++p) bpos_sub[ctx->lay[s].boff + p] = s;
+  lg.mark("create:   multiplier maps");
   // dense maps of the elements (grouped by subdomain above)
   const int npe = ctx->npe, nde = ctx->nde, fpn = ctx->fpn;
   std::vector<int32_t> elem_dense((size_t)nde * E);
@@ -807,7 +867,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (double v : ctx->dir_val)
       if (v != 0.0) ctx->any_dirval = true;
   if (ctx->any_dirval) elem_dirval.assign((size_t)nde * E, 0.0);
-  for (int e = 0; e < E; ++e) {
+  par_for(E, 4096, [&](int64_t e) {
     const int s = ctx->part[e];
     for (int a = 0; a < npe; ++a) {
       const int n = ctx->tets[(size_t)npe * e + a];
@@ -817,32 +877,43 @@ feti_status build_decomposition(feti_ctx* ctx) {
         if (ctx->any_dirval && is_dir[3 * (size_t)n + c]) elem_dirval[(size_t)nde * e + 3 * a + c] = dval[3 * (size_t)n + c];
       }
     }
-  }
+  });
+  lg.mark("create:   element dense maps");
   // FP32-factor form: per local row (global local index voff + dense row) the
   // (element, element row) pairs of its subdomain's elements, ascending
   // (encoded nde e + a)
   if (ctx->opt.precision == FETI_MIXED_F32FACTOR) {
+    // a subdomain's rows are touched only by its own elements: count and fill
+    // per subdomain in parallel, elements ascending (each row's list ascends
+    // in nde e + a)
     std::vector<int32_t> kptr(voff + 1, 0);
-    for (int e = 0; e < E; ++e) {
-      const SubLayout& L = ctx->lay[ctx->part[e]];
-      for (int a = 0; a < nde; ++a) {
-        const int r = elem_dense[(size_t)nde * e + a];
-        if (r >= 0) kptr[L.voff + r + 1]++;
+    par_for(P, 4, [&](int64_t s) {
+      const SubLayout& L = ctx->lay[s];
+      for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+        const int e = sub_elems[q];
+        for (int a = 0; a < nde; ++a) {
+          const int r = elem_dense[(size_t)nde * e + a];
+          if (r >= 0) kptr[L.voff + r + 1]++;
+        }
       }
-    }
+    });
     for (int i = 0; i < voff; ++i) kptr[i + 1] += kptr[i];
     std::vector<int32_t> kinc(kptr[voff]), kf(kptr.begin(), kptr.end() - 1);
-    for (int e = 0; e < E; ++e) {      // element order: each row's list ascends in 12 e + a
-      const SubLayout& L = ctx->lay[ctx->part[e]];
-      for (int a = 0; a < nde; ++a) {
-        const int r = elem_dense[(size_t)nde * e + a];
-        if (r >= 0) kinc[kf[L.voff + r]++] = nde * e + a;
+    par_for(P, 4, [&](int64_t s) {
+      const SubLayout& L = ctx->lay[s];
+      for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+        const int e = sub_elems[q];
+        for (int a = 0; a < nde; ++a) {
+          const int r = elem_dense[(size_t)nde * e + a];
+          if (r >= 0) kinc[kf[L.voff + r]++] = nde * e + a;
+        }
       }
-    }
+    });
     FETI_TRY(upload(ctx, &ctx->d_kinc_ptr, kptr));
     FETI_TRY(upload(ctx, &ctx->d_kinc, kinc));
     for (const auto& L : ctx->lay) ctx->max_nr = std::max(ctx->max_nr, L.nI + L.nbp);
   }
+  lg.mark("create:   refinement incidences");
   // lumped preconditioner: CSR pattern of K_bb over the global boundary
   // positions, from the boundary DOF pairs that share an element
   std::vector<int32_t> lump_ptr, lump_col;
@@ -920,6 +991,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     }
   }
   ctx->n_own = (int)own_gdof.size();
+  lg.mark("create:   lumped pattern, faces, owners");
   // global non-Dirichlet DOF -> local copies (for residual norms)
   std::vector<int32_t> gs_ptr, gs_pos;
   {
@@ -979,6 +1051,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   // coarse G^T G pair blocks (i <= j, ascending), each with the multiplier
   // rows that couple them, ascending: two passes over the rows, blocks found
   // through a hash of the pair
+  lg.mark("create:   global-DOF and Newton maps, uploads");
   std::vector<int32_t> gi, gj, gptr(1, 0), grows;
   {
     auto pairs_of = [&](int64_t r, uint64_t out[3]) {
@@ -2203,7 +2276,7 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           ctx->tc_m[w] = 0;
           const int ntc = ctx->opt.no_tensor_cores;
           FETI_TRY(build_tensor_maps(ctx));
-          for (int variant = 1; variant <= 5; ++variant) {
+          for (int variant = 1; variant <= 6; ++variant) {
             if (ntc >= 3 && variant != ntc - 2) continue;
             FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
             feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,

@@ -1202,6 +1202,235 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc4(const int32_t* __restrict
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC4_TCOLS) : "memory");
 }
 
+// Persistent warp-specialised tensor-core block GEMM: a fixed grid (two
+// CTAs per SM) walks the 128-row tiles round-robin, and the K-chunk pipeline
+// runs on across tile boundaries, so the per-tile costs of the one-tile
+// kernel (tensor-memory allocation, barrier set-up, pipeline fill, an
+// epilogue that nothing overlaps) are paid once per CTA.  Roles: warp 0 lane
+// 0 issues the tensor-map copies of A, warp 1 lane 0 the MMAs, warps 4-7
+// load the B chunk and write the TF32 tails of A and B, warps 8-11 (one per
+// tensor-memory lane quadrant) drain the accumulators into y.  Two
+// accumulator sets alternate between tiles: the MMAs of tile i + 1 run while
+// the epilogue reads tile i.  Every wait is bounded; a wait that runs out
+// stops all roles, the copies and MMAs already issued are drained, and *err
+// is set.
+constexpr int TC5_NS = 3;
+constexpr int TC5_THREADS = 384;
+constexpr int TC5_TCOLS = 128;  // two accumulator sets of 3 x 16 columns, 64 apart
+constexpr int TC5_SMEM = TC5_NS * TC_STAGE + 1024;
+
+__global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restrict__ blk_sub,
+                                                         const int32_t* __restrict__ blk_row0, int n_tiles,
+                                                         const SubLayout* __restrict__ lay, int which,
+                                                         const CUtensorMap* __restrict__ maps, int nrhs,
+                                                         const float* __restrict__ vloc, double* __restrict__ y,
+                                                         const int* __restrict__ done, int* __restrict__ err,
+                                                         const unsigned long long* __restrict__ spin_cycles) {
+  if (*done) return;
+  constexpr int NS = TC5_NS;
+  extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+  unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
+  __shared__ uint64_t full[NS], ready[NS], empty[NS], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(TC5_TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&ready[i], 4);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  volatile int* ab = &abort_flag;
+  const long long budget = (long long)*spin_cycles;
+  auto rows_of = [&](const SubLayout& L) { return which == 0 ? L.nbp : L.nbp + L.k; };
+  if (wid == 0) {
+    if (lane == 0) {  // producer: global chunk g -> stage g % NS once the MMAs of chunk g - NS are done
+      int g = 0, prev = -1;
+      bool stop = false;
+      for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+        const int s_id = blk_sub[t], r0 = blk_row0[t];
+        const int nk = (rows_of(lay[s_id]) + 31) / 32;
+        const CUtensorMap* tm = maps + s_id;
+        if (s_id != prev) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
+          prev = s_id;
+        }
+        for (int kc = 0; kc < nk; ++kc) {
+          const int st = g % NS;
+          if (g >= NS && !wait_or_abort(&empty[st], (uint32_t)((g / NS) - 1) & 1u, ab, budget)) {
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(&full[st], (uint32_t)TC_A_BYTES);
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+              "[%4];" ::"r"(su32(smem + st * TC_STAGE)),
+              "l"(tm), "r"(kc * 32), "r"(r0), "r"(su32(&full[st]))
+              : "memory");
+          ++g;
+        }
+      }
+      // drain: every copy issued has landed before shared memory is released
+      for (int j = max(0, g - NS); j < g; ++j)
+        if (!mbar_wait_bounded(&full[j % NS], (uint32_t)(j / NS) & 1u)) atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else if (wid == 1) {
+    if (lane == 0) {  // MMA issuer
+      int g = 0, n_commit = 0, i = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++i) {
+        const int nk = (rows_of(lay[blk_sub[t]]) + 31) / 32;
+        const int abuf = i & 1;
+        if (i >= 2 && !wait_or_abort(&tempty[abuf], (uint32_t)((i / 2) - 1) & 1u, ab, budget)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + 64u * (uint32_t)abuf;
+        for (int kc = 0; kc < nk; ++kc) {
+          const int st = g % NS;
+          if (!wait_or_abort(&ready[st], (uint32_t)(g / NS) & 1u, ab, budget)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* Ahi = smem + st * TC_STAGE;
+          unsigned char* Alo = Ahi + TC_A_BYTES;
+          unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+          unsigned char* Blo = Bhi + TC_B_BYTES;
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
+            const uint64_t bh = sw128_desc(Bhi + 32 * j), bl = sw128_desc(Blo + 32 * j);
+            const uint32_t f = (kc > 0 || j > 0) ? 1u : 0u;
+            tc_mma(acc, ah, bh, idesc, f);
+            tc_mma(acc + 16u, ah, bl, idesc, f);
+            tc_mma(acc + 32u, al, bh, idesc, f);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           su32(&empty[st]))
+                       : "memory");
+          ++g;
+          n_commit = g;
+        }
+        if (stop) break;
+        // the tile's accumulator is complete once every MMA issued so far is
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&tfull[abuf]))
+                     : "memory");
+      }
+      if (n_commit > 0 && !mbar_wait_bounded(&empty[(n_commit - 1) % NS], (uint32_t)((n_commit - 1) / NS) & 1u))
+        atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else if (wid >= 4 && wid < 8) {  // A and B tails, B chunk loads
+    const int t4 = tid - 128;
+    int g = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+      const SubLayout L = lay[blk_sub[t]];
+      const int m = rows_of(L);
+      const int nk = (m + 31) / 32;
+      float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+      auto load_b = [&](int kc2) {
+        const int n = t4 >> 3, c = t4 & 7, k0 = kc2 * 32;
+        float v4[4];
+        for (int e = 0; e < 4; ++e) {
+          const int kk = k0 + 4 * c + e;
+          v4[e] = (kk < m && n < nrhs) ? vloc[(size_t)(L.boff + kk) * nrhs + n] : 0.f;
+        }
+        rb = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      };
+      if (nk > 0) load_b(0);
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = g % NS;
+        const float4 cb = rb;
+        if (kc + 1 < nk) load_b(kc + 1);
+        if (!wait_or_abort(&full[st], (uint32_t)(g / NS) & 1u, ab, budget)) {
+          stop = true;
+          break;
+        }
+        unsigned char* Ahi = smem + st * TC_STAGE;
+        unsigned char* Alo = Ahi + TC_A_BYTES;
+        unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+        unsigned char* Blo = Bhi + TC_B_BYTES;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int off = (t4 + q * 128) * 16;
+          const float4 x = *reinterpret_cast<const float4*>(Ahi + off);
+          *reinterpret_cast<float4*>(Alo + off) = make_float4(x.x - tf32_trunc(x.x), x.y - tf32_trunc(x.y),
+                                                              x.z - tf32_trunc(x.z), x.w - tf32_trunc(x.w));
+        }
+        {
+          const int n = t4 >> 3, c = t4 & 7;
+          *reinterpret_cast<float4*>(Bhi + sw_off(n, c)) = cb;
+          *reinterpret_cast<float4*>(Blo + sw_off(n, c)) = make_float4(
+              cb.x - tf32_trunc(cb.x), cb.y - tf32_trunc(cb.y), cb.z - tf32_trunc(cb.z), cb.w - tf32_trunc(cb.w));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&ready[st])) : "memory");
+        ++g;
+      }
+    }
+  } else if (wid >= 8) {  // epilogue: warp 8 + q reads tensor-memory lanes 32 q .. 32 q + 31
+    const int q = wid - 8, te = tid - 256;
+    int i = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+      const SubLayout L = lay[blk_sub[t]];
+      const int r0 = blk_row0[t], m = rows_of(L);
+      if (which == 0 && r0 == 0)  // the fixing rows of F_i's output are zero
+        for (int idx = te; idx < L.k * nrhs; idx += 128) y[(size_t)(L.boff + L.nbp) * nrhs + idx] = 0.0;
+      const int abuf = i & 1;
+      if (!wait_or_abort(&tfull[abuf], (uint32_t)(i / 2) & 1u, ab, budget)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float acc[16];
+#pragma unroll
+      for (int n = 0; n < 16; ++n) acc[n] = 0.f;
+      for (int a = 0; a < 3; ++a) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + ((uint32_t)(q * 32) << 16) + 64u * (uint32_t)abuf + 16u * (uint32_t)a));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int n = 0; n < 16; ++n) acc[n] += __uint_as_float(r[n]);
+      }
+      // the accumulator set is free again for tile i + 2
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[abuf])) : "memory");
+      const int row = r0 + q * 32 + lane;
+      if (row < m)
+        for (int n = 0; n < nrhs; ++n) y[(size_t)(L.boff + row) * nrhs + n] = (double)acc[n];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*ab) {
+    if (tid == 0) atomicExch(err, 1);
+  }
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC5_TCOLS) : "memory");
+}
+
 inline int grid_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -1259,6 +1488,22 @@ void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const f
     cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
     cudaFuncSetAttribute(k_gemm_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
     attr = true;
+  }
+  if (variant == 6) {
+    static int n_sm = 0;
+    if (!n_sm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (n_sm <= 0) n_sm = 1;
+      cudaFuncSetAttribute(k_gemm_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, TC5_SMEM);
+    }
+    const int grid = std::min(cfg.n_blocks, 2 * n_sm);
+    if (grid > 0)
+      k_gemm_tc5<<<grid, TC5_THREADS, TC5_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, cfg.n_blocks, lay, which,
+                                                      static_cast<const CUtensorMap*>(tmaps), nrhs, vloc, y, done, err,
+                                                      spin_cycles);
+    return;
   }
   if (variant == 4 || variant == 5) {
     static bool attr4 = false;

@@ -1,7 +1,7 @@
 """Bounded device waits that run out: FETI_ERR_TIMEOUT, then a usable context.
 
 The streamed symmetric FP32 apply and the warp-specialised tensor-core block
-GEMM wait on mbarriers for their bulk / tensor-map copies and tensor-core
+GEMMs (one tile per CTA, and the persistent kernel) wait on mbarriers for their bulk / tensor-map copies and tensor-core
 products.  Their main-loop waits give up after the context's spin timeout
 (feti_options.spin_timeout_ns, feti_set_spin_timeout).  Here that budget is
 set to zero after set-up, so every main-loop wait gives up at its first check
@@ -57,14 +57,16 @@ def test_streamed_symmetric_apply_times_out_then_recovers(case):
         assert _rel(U, U_ref) <= 1e-8
 
 
-def test_tensor_core_block_gemm_times_out_then_recovers(case):
+@pytest.mark.parametrize("variant,code", [("force_ws3", -3), ("force_persist", -5)])
+def test_tensor_core_block_gemm_times_out_then_recovers(case, variant, code):
+    """The warp-specialised one-tile kernel and the persistent kernel."""
     from paper_1508_02599_gb300 import FetiError, FetiSolver
     prob, U_ref = case
     scales = np.array([1.0, 2.5])
-    with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", tensor_cores="force_ws3",
+    with FetiSolver(prob, method="af", precond="dirichlet", precision="mixed", tensor_cores=variant,
                     tol=1e-10, maxit=60) as s:
         U, _ = s.solve_multi(scales)                     # tunes the block schedules with the default budget
-        assert s.schedule()["block_fp32_F"][0] == -3     # warp-specialised 3-stage kernel
+        assert s.schedule()["block_fp32_F"][0] == code   # that tensor-core kernel
         s.set_spin_timeout(0)
         with pytest.raises(FetiError) as ei:
             s.solve_multi(scales)
