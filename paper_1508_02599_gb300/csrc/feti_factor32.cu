@@ -9,10 +9,13 @@
 // dual right-hand side d~, the outer dual residual, the recovery of u_i)
 // goes through K^+ refined in FP64 (classical mixed-precision iterative
 // refinement, Moler 1967):
-//   x = L^-T L^-1 g (FP32 sweeps);  repeat: r = g - K_rr x (FP64, from the
-//   element matrices);  x += L^-T L^-1 r,
+//   x = L^-T L^-1 g (FP32);  repeat: r = g - K_rr x (FP64, from the element
+//   matrices);  x += L^-T L^-1 r,
 // with zero on the fixing DOFs, which is K^+ g of the fixing-DOF generalized
-// inverse of Sec. 5.2 ("regularization by fixing nodes").
+// inverse of Sec. 5.2 ("regularization by fixing nodes").  Each FP32
+// correction sweeps only the interior block of L and reaches the boundary
+// block through the explicit F_i (k_kp_forward / k_kp_backward); the FP64
+// residual is an element pass and a row pass (k_elem_kx / k_row_resid).
 #include "feti_internal.h"
 
 #include <algorithm>
@@ -75,47 +78,40 @@ __global__ void k_pad_to_sym(const SubLayout* __restrict__ lay, int which, const
   }
 }
 
-// x (+)= L^-T L^-1 r on the rows [0, nr) of every subdomain, nr = nI + nbp,
-// with L the FP32 Cholesky factor of K_rr in the leading block of the FP32
-// workspace: one CTA per subdomain, the right-hand side and the solution in
-// shared memory (FP32), 32-row blocks.  Forward: the warps form the dot
-// products of the block's rows with the solved part (one warp per row, lanes
-// striding the columns), one warp solves the 32 x 32 diagonal triangle with
-// shuffles.  Backward: one warp solves the transposed diagonal triangle, then
-// every thread subtracts the block's contributions from its columns of the
-// unsolved part.  init: x = correction, and zero on the fixing DOFs; else
-// x += correction (the fixing DOFs keep their value).
-__global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
-                                                  const double* __restrict__ rbase, double* __restrict__ xbase,
-                                                  int init) {
+// One FP32 correction x (+)= L^-T L^-1 r on the rows [0, n_I + n_b'), with
+// the triangular sweeps confined to the interior: with K_rr = L L^T and L = [[L_II, 0], [L_bI, L_bb]] (interior rows first,
+// then the boundary rows b' that are not fixing DOFs),
+//   y_I = L_II^-1 r_I,   z_b = r_b - L_bI y_I,   x_b = (L_bb L_bb^T)^-1 z_b = F_i z_b,
+//   x_I = L_II^-T (y_I - L_bI^T x_b),
+// and F_i = S_i[b',b']^-1 is the explicit FP32 operator the PCG already
+// applies.  The dependent 32-row block chains shrink from n_I + n_b' rows to
+// n_I rows; the boundary panel products carry no chain.
+// k_kp_forward: y_I (FP32, into yI at the subdomain's local offset) and z_b
+// (FP32, into zb at the boundary offset; zero on the fixing positions).
+__global__ void __launch_bounds__(kT, 8) k_kp_forward(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
+                                                  const double* __restrict__ rbase, float* __restrict__ yIbase,
+                                                  float* __restrict__ zb) {
   extern __shared__ float ys[];
   const SubLayout L = lay[blockIdx.x];
   const float* A = Abase + L.aoff;
   const size_t ld = L.ld;
   const double* r = rbase + L.voff;
-  double* x = xbase + L.voff;
-  const int nr = L.nI + L.nbp;
+  const int nI = L.nI, nbp = L.nbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kW = kT / 32;
   __shared__ float D[32][33];
   __shared__ float t[32];
-  __shared__ float xs[32];
-  for (int i = tid; i < nr; i += kT) ys[i] = (float)r[i];
-  if (init)
-    for (int i = nr + tid; i < L.n; i += kT) x[i] = 0.0;
+  for (int i = tid; i < nI; i += kT) ys[i] = (float)r[i];
   __syncthreads();
-  for (int I0 = 0; I0 < nr; I0 += 32) {
-    const int nb = min(32, nr - I0);
+  for (int I0 = 0; I0 < nI; I0 += 32) {
+    const int nb = min(32, nI - I0);
     for (int idx = tid; idx < 32 * 32; idx += kT) {
       const int rr = idx >> 5, c = idx & 31;
       D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
     }
     {
-      // warp w: rows w, w + 8, w + 16, w + 24 of the block together, four
-      // column strides at a time, so each lane keeps 16 independent loads in
-      // flight (the sweep is bound by the latency of these loads)
       const float* rp = A + (size_t)I0 * ld;
-      int ro[4];  // row offsets within the 32-row block (< 32 ld)
+      int ro[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nb - 1) * (int)ld;
       float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -157,8 +153,85 @@ __global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restric
     }
     __syncthreads();
   }
-  for (int I0 = nr > 0 ? ((nr - 1) / 32) * 32 : -32; I0 >= 0; I0 -= 32) {
-    const int nb = min(32, nr - I0);
+  float* yI = yIbase + L.voff;
+  for (int i = tid; i < nI; i += kT) yI[i] = ys[i];
+  // z_b = r_b - L_bI y_I: warp w takes boundary rows w, w + 8, w + 16, w + 24
+  // (then the next 32), four column strides at a time
+  for (int p0 = 0; p0 < nbp; p0 += 4 * kW) {
+    const float* rp = A + (size_t)(nI + p0) * ld;
+    int ro[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nbp - 1 - p0) * (int)ld;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int j = lane;
+    for (; j + 96 < nI; j += 128) {
+      float a[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float yv = ys[j + 32 * u];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
+      }
+    }
+    for (; j < nI; j += 32) {
+      const float yv = ys[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float v = f32_warp_sum(acc[q]);
+      const int p = p0 + warp + kW * q;
+      if (lane == 0 && p < nbp) zb[L.boff + p] = (float)(r[nI + p] - (double)v);
+    }
+  }
+  for (int p = nbp + tid; p < nbp + L.k; p += kT) zb[L.boff + p] = 0.0f;
+}
+
+// k_kp_backward: t_I = y_I - L_bI^T x_b, x_I = L_II^-T t_I; then x (+)= x on
+// rows [0, n_I + n_b') (x_b from the F_i apply, FP64 at the boundary offset),
+// and with init x = that correction, zero on the fixing rows.
+__global__ void __launch_bounds__(kT, 8) k_kp_backward(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
+                                                   const float* __restrict__ yIbase, const double* __restrict__ xb,
+                                                   double* __restrict__ xbase, int init) {
+  extern __shared__ float ys[];
+  const SubLayout L = lay[blockIdx.x];
+  const float* A = Abase + L.aoff;
+  const size_t ld = L.ld;
+  double* x = xbase + L.voff;
+  const int nI = L.nI, nbp = L.nbp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float D[32][33];
+  __shared__ float xs[32];
+  float* xbs = ys + nI;  // x_b in FP32 after the interior part
+  const float* yI = yIbase + L.voff;
+  for (int i = tid; i < nI; i += kT) ys[i] = yI[i];
+  for (int p = tid; p < nbp; p += kT) xbs[p] = (float)xb[L.boff + p];
+  __syncthreads();
+  // t_I = y_I - L_bI^T x_b: thread per interior column, 16 boundary rows per step
+  {
+    const float* Pb = A + (size_t)nI * ld;
+    for (int j = tid; j < nI; j += kT) {
+      float acc = 0.0f;
+      int p = 0;
+      for (; p + 16 <= nbp; p += 16) {
+        float a[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) a[u] = __ldg(Pb + (size_t)(p + u) * ld + j);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc += a[u] * xbs[p + u];
+      }
+      for (; p < nbp; ++p) acc += __ldg(Pb + (size_t)p * ld + j) * xbs[p];
+      ys[j] -= acc;
+    }
+  }
+  __syncthreads();
+  for (int I0 = nI > 0 ? ((nI - 1) / 32) * 32 : -32; I0 >= 0; I0 -= 32) {
+    const int nb = min(32, nI - I0);
     for (int idx = tid; idx < 32 * 32; idx += kT) {
       const int rr = idx >> 5, c = idx & 31;
       D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
@@ -176,7 +249,6 @@ __global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restric
       xs[lane] = lane < nb ? xv : 0.0f;
     }
     __syncthreads();
-    // full 32-row panels: 16 independent loads per thread in flight
     if (nb == 32) {
       for (int j = tid; j < I0; j += kT) {
         const float* col = A + (size_t)I0 * ld + j;
@@ -192,39 +264,65 @@ __global__ void __launch_bounds__(kT, 8) k_kplus_corr(const SubLayout* __restric
         ys[j] -= acc;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = tid; i < nr; i += kT) x[i] = (init ? 0.0 : x[i]) + (double)ys[i];
+  for (int i = tid; i < nI; i += kT) x[i] = (init ? 0.0 : x[i]) + (double)ys[i];
+  for (int p = tid; p < nbp; p += kT) x[nI + p] = (init ? 0.0 : x[nI + p]) + xb[L.boff + p];
+  if (init)
+    for (int i = nI + nbp + tid; i < L.n; i += kT) x[i] = 0.0;
 }
 
-// r = g - K_rr x in FP64 on the rows [0, nr) (zero on the fixing rows), K_i
-// applied element by element from the FP64 element matrices: row i sums, in
-// a fixed order, the rows a of the elements listed for it (kinc: nde e + a),
-// columns through the element's dense map (negative: an eliminated DOF).
-__global__ void __launch_bounds__(128) k_kresid(const SubLayout* __restrict__ lay, const int32_t* __restrict__ kinc_ptr,
-                                               const int32_t* __restrict__ kinc, const int32_t* __restrict__ elem_dense,
-                                               const double* __restrict__ Ke, int nde, const double* __restrict__ gbase,
-                                               const double* __restrict__ xbase, double* __restrict__ rbase) {
-  const SubLayout L = lay[blockIdx.x];
-  const int nr = L.nI + L.nbp;
-  const double* x = xbase + L.voff;
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-    const int gi = L.voff + i;
+// r = g - K_rr x in FP64 on the rows [0, n_I + n_b') (zero on the fixing
+// rows), in two deterministic passes: ye[nde e + a] = (K_e x_e)_a
+// for every element (its dense map and the local vector of its subdomain,
+// columns of eliminated DOFs skipped), then per local row r = g - the sum of
+// its (element, row) entries in the order of its incidence list.
+template <int NDE>
+__global__ void __launch_bounds__(128) k_elem_kx(int n_el, const int32_t* __restrict__ elem_sub,
+                                                 const SubLayout* __restrict__ lay,
+                                                 const int32_t* __restrict__ elem_dense, const double* __restrict__ Ke,
+                                                 const double* __restrict__ xbase, double* __restrict__ ye) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_el) return;
+  const double* x = xbase + lay[elem_sub[e]].voff;
+  const int32_t* dm = elem_dense + (size_t)NDE * e;
+  const double* ke = Ke + (size_t)e * ke_packed(NDE);
+  double xe[NDE];
+#pragma unroll
+  for (int b = 0; b < NDE; ++b) {
+    const int c = dm[b];
+    xe[b] = c >= 0 ? x[c] : 0.0;
+  }
+#pragma unroll
+  for (int a = 0; a < NDE; ++a) {
+    double t = 0.0;
+#pragma unroll
+    for (int b = 0; b < NDE; ++b) t += ke[ke_idx(NDE, a, b)] * xe[b];
+    ye[(size_t)NDE * e + a] = t;
+  }
+}
+
+__global__ void k_row_resid(int n, const int32_t* __restrict__ row_sub, const SubLayout* __restrict__ lay,
+                            const int32_t* __restrict__ kinc_ptr, const int32_t* __restrict__ kinc,
+                            const double* __restrict__ ye, const double* __restrict__ g, double* __restrict__ r) {
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < n; gi += gridDim.x * blockDim.x) {
+    const SubLayout L = lay[row_sub[gi]];
     double acc = 0.0;
-    if (i < nr) {
-      acc = gbase[gi];
-      for (int q = kinc_ptr[gi]; q < kinc_ptr[gi + 1]; ++q) {
-        const int ea = kinc[q];
-        const int e = ea / nde, a = ea - nde * e;
-        const double* ke = Ke + (size_t)e * ke_packed(nde);
-        const int32_t* dm = elem_dense + (size_t)nde * e;
-        for (int b = 0; b < nde; ++b) {
-          const int c = dm[b];
-          if (c >= 0) acc -= ke[ke_idx(nde, a, b)] * x[c];
-        }
+    if (gi - L.voff < L.nI + L.nbp) {
+      acc = g[gi];
+      const int q1 = kinc_ptr[gi + 1];
+      int q = kinc_ptr[gi];
+      for (; q + 4 <= q1; q += 4) {
+        const int e0 = kinc[q], e1 = kinc[q + 1], e2 = kinc[q + 2], e3 = kinc[q + 3];
+        const double v0 = ye[e0], v1 = ye[e1], v2 = ye[e2], v3 = ye[e3];
+        acc -= v0;
+        acc -= v1;
+        acc -= v2;
+        acc -= v3;
       }
+      for (; q < q1; ++q) acc -= ye[kinc[q]];
     }
-    rbase[gi] = acc;
+    r[gi] = acc;
   }
 }
 
@@ -289,16 +387,32 @@ void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src,
   k_pad_to_sym<<<P, kT, 0, st>>>(lay, which, src, dst);
 }
 
-void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double* r, double* x, int init, int max_nr,
+void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,
                        cudaStream_t st) {
   const size_t smem = (size_t)max_nr * sizeof(float);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kplus_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_kplus_corr<<<P, kT, smem, st>>>(lay, A, r, x, init);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_kp_forward<<<P, kT, smem, st>>>(lay, A, r, yI, zb);
 }
 
-void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
-                   const double* Ke, int nde, const double* g, const double* x, double* r, cudaStream_t st) {
-  k_kresid<<<P, 128, 0, st>>>(lay, kinc_ptr, kinc, elem_dense, Ke, nde, g, x, r);
+void launch_kp_backward(int P, const SubLayout* lay, const float* A, const float* yI, const double* xb, double* x,
+                        int init, int max_nr, cudaStream_t st) {
+  const size_t smem = (size_t)max_nr * sizeof(float);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_kp_backward<<<P, kT, smem, st>>>(lay, A, yI, xb, x, init);
+}
+
+void launch_kresid2(int n_el, int nde, const int32_t* elem_sub, const int32_t* row_sub, int n_rows, const SubLayout* lay,
+                    const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense, const double* Ke,
+                    const double* g, const double* x, double* ye, double* r, cudaStream_t st) {
+  if (n_el > 0) {
+    if (nde == 30)
+      k_elem_kx<30><<<(n_el + 127) / 128, 128, 0, st>>>(n_el, elem_sub, lay, elem_dense, Ke, x, ye);
+    else
+      k_elem_kx<12><<<(n_el + 127) / 128, 128, 0, st>>>(n_el, elem_sub, lay, elem_dense, Ke, x, ye);
+  }
+  long b = ((long)n_rows + kT - 1) / kT;
+  if (b > 65535) b = 65535;
+  if (n_rows > 0) k_row_resid<<<(int)b, kT, 0, st>>>(n_rows, row_sub, lay, kinc_ptr, kinc, ye, g, r);
 }
 
 void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st) {

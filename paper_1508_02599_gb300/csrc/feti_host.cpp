@@ -191,6 +191,14 @@ struct feti_ctx {
   float* d_A32 = nullptr;
   int32_t *d_kinc_ptr = nullptr, *d_kinc = nullptr;
   double *d_kr = nullptr, *d_kg = nullptr, *d_knorm = nullptr;
+  // interior-sweep corrections: y_I (FP32, local offsets), z_b (FP32) and
+  // x_b = F_i z_b (FP64) at the boundary offsets
+  float *d_kyI = nullptr, *d_kzb = nullptr;
+  double* d_kxb = nullptr;
+  // two-pass FP64 residual: subdomain of each element and of each local row,
+  // and the per-(element, row) products K_e x_e
+  int32_t *d_elem_sub = nullptr, *d_row_sub = nullptr;
+  double* d_kye = nullptr;
   int refine_steps = 0;
   // Newton preconditioner: relative diagonal shift of the local tangents of
   // the last assembly (0 = exact local tangents)
@@ -911,6 +919,15 @@ feti_status build_decomposition(feti_ctx* ctx) {
     });
     FETI_TRY(upload(ctx, &ctx->d_kinc_ptr, kptr));
     FETI_TRY(upload(ctx, &ctx->d_kinc, kinc));
+    {
+      std::vector<int32_t> es(E), rsub(voff);
+      for (int s = 0; s < P; ++s) {
+        for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) es[sub_elems[q]] = s;
+        for (int i = 0; i < ctx->lay[s].n; ++i) rsub[ctx->lay[s].voff + i] = s;
+      }
+      FETI_TRY(upload(ctx, &ctx->d_elem_sub, es));
+      FETI_TRY(upload(ctx, &ctx->d_row_sub, rsub));
+    }
     for (const auto& L : ctx->lay) ctx->max_nr = std::max(ctx->max_nr, L.nI + L.nbp);
   }
   lg.mark("create:   refinement incidences");
@@ -1394,17 +1411,38 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
 // x = K^+ g on full local vectors (zero on the fixing DOFs): FP64 sweeps on the
 // FP64 factor, or, in the FP32-factor form, FP32 sweeps refined against the
 // FP64 element matrices (refine_steps corrections; d_kr is scratch).
+// Dense local apply of F_i (which 0) or the preconditioner block (which 1)
+// on a gathered local vector (default: d_vloc / d_vloc32) into yout
+// (default: d_loc).
+void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32, const void* vin = nullptr,
+                double* yout = nullptr);
+
+// r = g - K_rr x in FP64 from the element matrices (zero on the fixing rows).
+void kresid(feti_ctx* ctx, const double* g, const double* x, double* r) {
+  feti::launch_kresid2(ctx->E, ctx->nde, ctx->d_elem_sub, ctx->d_row_sub, (int)ctx->nloc_total, ctx->d_lay,
+                       ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, g, x, ctx->d_kye, r, ctx->stream);
+}
+
+// One FP32 correction x (+)= L^-T L^-1 r (init: x = it) with the triangular
+// sweeps confined to the interior rows and the boundary block through the
+// explicit FP32 F_i (the autotuned operator kernel of the PCG).
+void kplus_corr(feti_ctx* ctx, const double* r, double* x, bool init) {
+  feti::launch_kp_forward(ctx->P, ctx->d_lay, ctx->d_A32, r, ctx->d_kyI, ctx->d_kzb, ctx->max_nr, ctx->stream);
+  gemv_apply(ctx, 0, ctx->d_zero, true, ctx->d_kzb, ctx->d_kxb);
+  feti::launch_kp_backward(ctx->P, ctx->d_lay, ctx->d_A32, ctx->d_kyI, ctx->d_kxb, x, init ? 1 : 0, ctx->max_nr,
+                           ctx->stream);
+}
+
 void kplus(feti_ctx* ctx, const double* g, double* x) {
   cudaStream_t st = ctx->stream;
   if (!f32_factor(ctx)) {
     feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, g, x, st);
     return;
   }
-  feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, g, x, 1, ctx->max_nr, st);
+  kplus_corr(ctx, g, x, true);
   for (int k = 1; k < ctx->refine_steps; ++k) {
-    feti::launch_kresid(ctx->P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, g, x,
-                        ctx->d_kr, st);
-    feti::launch_kplus_corr(ctx->P, ctx->d_lay, ctx->d_A32, ctx->d_kr, x, 0, ctx->max_nr, st);
+    kresid(ctx, g, x, ctx->d_kr);
+    kplus_corr(ctx, ctx->d_kr, x, false);
   }
 }
 
@@ -1416,13 +1454,12 @@ feti_status tune_refinement(feti_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const int P = ctx->P;
   feti::launch_fill_mix(ctx->nloc_total, ctx->d_kg, st);
-  feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kg, ctx->d_x2, 1, ctx->max_nr, st);
+  kplus_corr(ctx, ctx->d_kg, ctx->d_x2, true);
   std::vector<double> nrm(2 * (size_t)P);
   double prev = 1e300;
   int steps = 1;
   for (; steps <= 12; ++steps) {
-    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, ctx->d_kg,
-                        ctx->d_x2, ctx->d_kr, st);
+    kresid(ctx, ctx->d_kg, ctx->d_x2, ctx->d_kr);
     feti::launch_sub_norm2(P, ctx->d_lay, ctx->d_kr, ctx->d_kg, ctx->d_knorm, st);
     FETI_CK(cudaGetLastError());
     FETI_CK(cudaMemcpyAsync(nrm.data(), ctx->d_knorm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1434,7 +1471,7 @@ feti_status tune_refinement(feti_ctx* ctx) {
     ctx->refine_res = worst;
     if (worst <= 1e-14 || worst > 0.5 * prev || steps == 12) break;
     prev = worst;
-    feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kr, ctx->d_x2, 0, ctx->max_nr, st);
+    kplus_corr(ctx, ctx->d_kr, ctx->d_x2, false);
   }
   if (ctx->refine_res > 1e-6)
     return fail(ctx, FETI_ERR_LOCAL_SINGULAR, "FP32 factor: refinement does not converge (residual " +
@@ -1447,10 +1484,9 @@ feti_status tune_refinement(feti_ctx* ctx) {
     FETI_CK(cudaEventCreate(&b));
     FETI_CK(cudaEventCreate(&c));
     FETI_CK(cudaEventRecord(a, st));
-    feti::launch_kplus_corr(P, ctx->d_lay, ctx->d_A32, ctx->d_kr, ctx->d_x2, 0, ctx->max_nr, st);
+    kplus_corr(ctx, ctx->d_kr, ctx->d_x2, false);
     FETI_CK(cudaEventRecord(b, st));
-    feti::launch_kresid(P, ctx->d_lay, ctx->d_kinc_ptr, ctx->d_kinc, ctx->d_elem_dense, ctx->d_Ke, ctx->nde, ctx->d_kg,
-                        ctx->d_x2, ctx->d_kr, st);
+    kresid(ctx, ctx->d_kg, ctx->d_x2, ctx->d_kr);
     FETI_CK(cudaEventRecord(c, st));
     FETI_CK(cudaEventSynchronize(c));
     float t1 = 0.f, t2 = 0.f;
@@ -1513,7 +1549,6 @@ feti_status factorize_all(feti_ctx* ctx) {
     }
     FETI_CK(cudaGetLastError());
     FETI_TRY(check_status(ctx, "local factorization (FP32)"));
-    if (ctx->refine_steps == 0) FETI_TRY(tune_refinement(ctx));
     return FETI_OK;
   }
   feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0, ctx->d_A,
@@ -1661,31 +1696,33 @@ void project(feti_ctx* ctx, const double* v, double* out, const double* a, bool 
 // on the gathered local vector (d_vloc / d_vloc32) into d_loc: one batched
 // launch over all subdomains, or, in the plain form, the same kernel and
 // schedule launched once per subdomain.
-void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
+void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32, const void* vin, double* yout) {
   const feti::GemvCfg& cfg = f32 ? ctx->cfg32[which] : ctx->cfg64[which];
   const void* M = f32 ? (which == 0 ? (const void*)ctx->d_F32 : (const void*)ctx->d_S32)
                       : (which == 0 ? (const void*)ctx->d_F : (const void*)ctx->d_S);
-  const void* v = f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+  const void* v = vin ? vin : f32 ? (const void*)ctx->d_vloc32 : (const void*)ctx->d_vloc;
+  const float* v32 = static_cast<const float*>(v);
+  double* yo = yout ? yout : ctx->d_loc;
   if (f32 && ctx->sym32[which] == 64 && !ctx->opt.per_subdomain) {
     feti::launch_symv2_f32(ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which], ctx->d_lay, which,
-                           which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc, ctx->d_symp, ctx->maps,
+                           which == 0 ? ctx->d_F32s : ctx->d_S32s, v32, yo, ctx->d_symp, ctx->maps,
                            done, ctx->d_sym_err, ctx->d_spin, ctx->stream);
     return;
   }
   if (f32 && ctx->sym32[which] >= 300 && !ctx->opt.per_subdomain) {
     feti::launch_symv3_f32(ctx->sym32[which] - 300, ctx->P, ctx->d_sym_order[which], ctx->sym_max_m[which],
-                           ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc,
+                           ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, v32, yo,
                            done, ctx->stream);
     return;
   }
   if (f32 && ctx->sym32[which] && !ctx->opt.per_subdomain) {
     feti::launch_symv_f32(ctx->sym32[which], ctx->sym_n[which], ctx->d_sym_sub[which], ctx->d_sym_panel[which],
-                          ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, ctx->d_vloc32, ctx->d_loc,
+                          ctx->d_lay, which, which == 0 ? ctx->d_F32s : ctx->d_S32s, v32, yo,
                           ctx->d_symp, ctx->maps, done, ctx->stream);
     return;
   }
   if (!ctx->opt.per_subdomain) {
-    feti::launch_gemv_loc(cfg, ctx->d_lay, which, M, f32, v, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+    feti::launch_gemv_loc(cfg, ctx->d_lay, which, M, f32, v, yo, ctx->max_nb, done, ctx->stream);
     return;
   }
   int t = 0;
@@ -1696,7 +1733,7 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32) {
     c.n_blocks = ptr[s + 1] - ptr[s];
     c.blk_sub = cfg.blk_sub + ptr[s];
     c.blk_row0 = cfg.blk_row0 + ptr[s];
-    if (c.n_blocks > 0) feti::launch_gemv_loc(c, ctx->d_lay, which, M, f32, v, ctx->d_loc, ctx->max_nb, done, ctx->stream);
+    if (c.n_blocks > 0) feti::launch_gemv_loc(c, ctx->d_lay, which, M, f32, v, yo, ctx->max_nb, done, ctx->stream);
   }
 }
 
@@ -1997,6 +2034,10 @@ feti_status alloc_operators(feti_ctx* ctx) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_kr, (size_t)ctx->nloc_total));
     FETI_TRY(dev_alloc(ctx, &ctx->d_kg, (size_t)ctx->nloc_total));
     FETI_TRY(dev_alloc(ctx, &ctx->d_knorm, 2 * (size_t)ctx->P));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kyI, (size_t)ctx->nloc_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kzb, (size_t)ctx->nb_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kxb, (size_t)ctx->nb_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_kye, (size_t)ctx->nde * ctx->E));
   } else {
     FETI_TRY(dev_alloc(ctx, &ctx->d_A, (size_t)ctx->op_elems[0]));
     FETI_TRY(dev_alloc(ctx, &ctx->d_S, (size_t)ctx->op_elems[1]));
@@ -2032,6 +2073,12 @@ feti_status prepare(feti_ctx* ctx, const double* dU, double tau) {
   lg.mark("setup: coarse problem (joined)");
   if (!ctx->tuned) FETI_TRY(autotune(ctx));
   lg.mark("setup: autotuning");
+  // the refinement count of the FP32-factor K^+ (its corrections apply the
+  // tuned F_i kernel)
+  if (f32_factor(ctx) && ctx->refine_steps == 0) {
+    FETI_TRY(tune_refinement(ctx));
+    lg.mark("setup: refinement count");
+  }
   ctx->prepared = true;
   return FETI_OK;
 }

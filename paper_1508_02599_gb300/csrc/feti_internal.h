@@ -293,13 +293,25 @@ namespace feti {
 void launch_extract32(int P, const SubLayout* lay, int which, const float* A, float* out, cudaStream_t st);
 // Padded FP32 copy -> symmetric-apply panels (which 0: F_i, 1: preconditioner block).
 void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src, float* dst, cudaStream_t st);
-// x (+)= L^-T L^-1 r on rows [0, nI + nbp) (FP32 sweeps, FP64 vectors); init:
-// x = correction and zero on the fixing DOFs.  max_nr: largest nI + nbp.
-void launch_kplus_corr(int P, const SubLayout* lay, const float* A, const double* r, double* x, int init, int max_nr,
+// One FP32 correction x (+)= L^-T L^-1 r of the FP32-factor K^+ (L the FP32
+// Cholesky factor of K_rr), the sweeps confined to the interior rows:
+// forward: y_I = L_II^-1 r_I (FP32 into yI, local offsets) and
+// z_b = r_b - L_bI y_I (FP32 into zb, boundary offsets, zero on the fixing
+// positions); the caller then applies the FP32 F_i to zb (x_b, FP64 at the
+// boundary offsets); backward: x_I = L_II^-T (y_I - L_bI^T x_b) and
+// x (+)= [x_I, x_b] (init: x = that, zero on the fixing rows).
+void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,
                        cudaStream_t st);
-// r = g - K_rr x (FP64, element by element; zero on the fixing rows).
-void launch_kresid(int P, const SubLayout* lay, const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense,
-                   const double* Ke, int nde, const double* g, const double* x, double* r, cudaStream_t st);
+void launch_kp_backward(int P, const SubLayout* lay, const float* A, const float* yI, const double* xb, double* x,
+                        int init, int max_nr, cudaStream_t st);
+// r = g - K_rr x in FP64 from the element matrices (zero on the fixing rows),
+// in two passes: ye (nde doubles per element) = K_e x_e
+// for all elements (elem_sub: the subdomain of each element), then per local
+// row (row_sub: the subdomain of each of the n_rows local rows) g minus its
+// incidence entries of ye in list order (kinc entries index ye directly).
+void launch_kresid2(int n_el, int nde, const int32_t* elem_sub, const int32_t* row_sub, int n_rows, const SubLayout* lay,
+                    const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense, const double* Ke,
+                    const double* g, const double* x, double* ye, double* r, cudaStream_t st);
 // out = boundary vector loc placed at the boundary positions, zero interior.
 void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st);
 // out[2 s], out[2 s + 1] = squared norms of r and g over rows [0, nI + nbp) of subdomain s.
