@@ -163,6 +163,10 @@ struct feti_ctx {
   int steps0 = 0;
   std::vector<int32_t> env0;
   int32_t* d_env0 = nullptr;
+  // the same for the FP32 elimination's kChol32Block-column steps
+  int steps0_32 = 0;
+  std::vector<int32_t> env0_32;
+  int32_t* d_env0_32 = nullptr;
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
   double elem_ms = 0.0, elem_bytes = 0.0;
   // sizes (elements) of d_A, d_S, d_F, d_F32, d_S32, d_F32s, d_S32s, d_symp
@@ -595,6 +599,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   // per subdomain: free DOFs, kernels, fixing DOFs, dense order
   ctx->lay.assign(P, SubLayout{});
   std::vector<std::vector<int32_t>> env0(P);  // per interior-elimination step: (eI, nbact)
+  std::vector<std::vector<int32_t>> env0w(P);  // the same for kChol32Block-column steps
   ctx->fix_ptr.assign(P + 1, 0);
   ctx->fix_ldof.clear();
   std::vector<std::vector<int32_t>> dense_ldof(P);  // dense index -> local DOF
@@ -761,11 +766,14 @@ feti_status build_decomposition(feti_ctx* ctx) {
       for (int v = 1; v <= nI; ++v) last[v] = std::max(last[v], last[v - 1]);
       std::vector<int32_t> bfirst(nbp);
       for (int i = 0; i < nbp; ++i) bfirst[i] = dof_first[bsort[i]];
-      auto& ev = env0[s];
-      for (int kb = 0; kb < nI; kb += 32) {
-        const int r0 = kb + std::min(32, nI - kb);
-        ev.push_back(std::max(r0, last[r0] + 1));
-        ev.push_back((int32_t)(std::lower_bound(bfirst.begin(), bfirst.end(), r0) - bfirst.begin()));
+      for (int w = 0; w < 2; ++w) {
+        auto& ev = w == 0 ? env0[s] : env0w[s];
+        const int B = w == 0 ? 32 : feti::kChol32Block;
+        for (int kb = 0; kb < nI; kb += B) {
+          const int r0 = kb + std::min(B, nI - kb);
+          ev.push_back(std::max(r0, last[r0] + 1));
+          ev.push_back((int32_t)(std::lower_bound(bfirst.begin(), bfirst.end(), r0) - bfirst.begin()));
+        }
       }
     }
     for (int d : fix) dl.push_back(d);
@@ -824,6 +832,17 @@ feti_status build_decomposition(feti_ctx* ctx) {
       ctx->env0[2 * (t * P + s) + 1] = env0[s][2 * t + 1];
     }
   FETI_TRY(upload(ctx, &ctx->d_env0, ctx->env0));
+  if (ctx->opt.precision == FETI_MIXED_F32FACTOR) {
+    ctx->steps0_32 = 0;
+    for (int s = 0; s < P; ++s) ctx->steps0_32 = std::max(ctx->steps0_32, (int)env0w[s].size() / 2);
+    ctx->env0_32.assign(2 * (size_t)ctx->steps0_32 * P, 0);
+    for (int s = 0; s < P; ++s)
+      for (size_t t = 0; t < env0w[s].size() / 2; ++t) {
+        ctx->env0_32[2 * (t * P + s)] = env0w[s][2 * t];
+        ctx->env0_32[2 * (t * P + s) + 1] = env0w[s][2 * t + 1];
+      }
+    FETI_TRY(upload(ctx, &ctx->d_env0_32, ctx->env0_32));
+  }
   ctx->nloc_total = voff;
   ctx->cd = coff;
   // dense position lookup per subdomain: local DOF -> dense index
@@ -1510,20 +1529,24 @@ feti_status factorize_all(feti_ctx* ctx) {
     else
       feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
   }
-  // per step, the largest trailing chunk count over the subdomains
+  // per step, the largest trailing chunk count over the subdomains (steps of
+  // 32 columns, kChol32Block in the FP32 elimination)
+  const bool f32f = f32_factor(ctx);
+  const int B = f32f ? feti::kChol32Block : 32;
+  const std::vector<int32_t>& envt = f32f ? ctx->env0_32 : ctx->env0;
   std::vector<int> chunks[2];
   for (int phase = 0; phase < 2; ++phase)
     for (const auto& L : ctx->lay) {
       const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp;
       const int s = (int)(&L - ctx->lay.data());
-      for (int t = 0, kb = c0; kb < c1; ++t, kb += 32) {
-        const int r0 = kb + std::min(32, c1 - kb);
+      for (int t = 0, kb = c0; kb < c1; ++t, kb += B) {
+        const int r0 = kb + std::min(B, c1 - kb);
         // phase 0: the rows inside the envelope (interior rows up to eI, the
         // first nbact boundary rows, the fixing rows); phase 1: all remaining
         // rows plus the augmentation rows of the columns eliminated so far
         int m;
         if (phase == 0) {
-          const int32_t* ev = &ctx->env0[2 * ((size_t)t * ctx->P + s)];
+          const int32_t* ev = &envt[2 * ((size_t)t * ctx->P + s)];
           m = (ev[0] - r0) + ev[1] + L.k;
         } else {
           m = std::min(L.ld, L.n + r0 - L.nI) - r0;
@@ -1533,9 +1556,9 @@ feti_status factorize_all(feti_ctx* ctx) {
         chunks[phase][t] = std::max(chunks[phase][t], ch);
       }
     }
-  if (f32_factor(ctx)) {
+  if (f32f) {
     // FP32 elimination; S_i and F_i go straight into the FP32 operator layouts
-    feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0,
+    feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0_32,
                               ctx->d_A32, ctx->d_status, st);
     if (ctx->opt.precond == FETI_PREC_DIRICHLET)
       feti::launch_extract32(ctx->P, ctx->d_lay, 0, ctx->d_A32, ctx->d_S32, st);

@@ -2167,26 +2167,45 @@ __device__ __forceinline__ ActiveRows active_rows(const SubLayout& L, int phase,
   return a;
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int step, T* __restrict__ Abase,
                            int* status) {
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
-  const int kb = pr.c0 + step * NB;
+  const int kb = pr.c0 + step * B;
   if (kb >= pr.c1) return;
-  const int nk = min(NB, pr.c1 - kb);
+  const int nk = min(B, pr.c1 - kb);
   T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ T D[NB][NB + 1];
+  __shared__ T D[B][B + 1];
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx / NB, j = idx % NB;
+  for (int idx = tid; idx < B * B; idx += blockDim.x) {
+    const int i = idx / B, j = idx % B;
     D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : (T)0;
   }
   __syncthreads();
-  if (tid < 32) {
+  if (B == 32) {
+    if (tid < 32) {
+      const int i = tid;
+      for (int j = 0; j < nk; ++j) {
+        if (i == j) {
+          const T d = D[j][j];
+          if (!(d > 0.0) || !isfinite(d)) bad = 1;
+          D[j][j] = sqrt(d);
+        }
+        __syncwarp();
+        if (bad) break;
+        if (i > j && i < nk) D[i][j] /= D[j][j];
+        __syncwarp();
+        if (i > j && i < nk)
+          for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
+        __syncwarp();
+      }
+    }
+  } else {
+    // wider blocks: row i by thread i, every thread through the block barriers
     const int i = tid;
     for (int j = 0; j < nk; ++j) {
       if (i == j) {
@@ -2194,13 +2213,13 @@ __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int ste
         if (!(d > 0.0) || !isfinite(d)) bad = 1;
         D[j][j] = sqrt(d);
       }
-      __syncwarp();
+      __syncthreads();
       if (bad) break;
       if (i > j && i < nk) D[i][j] /= D[j][j];
-      __syncwarp();
+      __syncthreads();
       if (i > j && i < nk)
         for (int l = j + 1; l <= i; ++l) D[i][l] -= D[i][j] * D[l][j];
-      __syncwarp();
+      __syncthreads();
     }
   }
   __syncthreads();
@@ -2214,67 +2233,67 @@ __global__ void k_bat_diag(const SubLayout* __restrict__ lay, int phase, int ste
   }
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void k_bat_trsm(const SubLayout* __restrict__ lay, int phase, int step,
                            const int32_t* __restrict__ env0, T* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
-  const int kb = pr.c0 + step * NB;
+  const int kb = pr.c0 + step * B;
   if (kb >= pr.c1) return;
-  const int nk = min(NB, pr.c1 - kb);
+  const int nk = min(B, pr.c1 - kb);
   const ActiveRows ar = active_rows(L, phase, step, kb, nk, env0);
   const int q0 = blockIdx.x * TT;
   if (q0 >= ar.m) return;
   const int nr = min(TT, ar.m - q0);
   T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ T D[NB][NB + 1];
-  __shared__ T Pa[TT][NB + 1];
+  __shared__ T D[B][B + 1];
+  __shared__ T Pa[TT][B + 1];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx / NB, j = idx % NB;
+  for (int idx = tid; idx < B * B; idx += blockDim.x) {
+    const int i = idx / B, j = idx % B;
     D[i][j] = (i < nk && j <= i) ? A[(kb + i) * ld + kb + j] : (T)0;
   }
-  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-    const int r = idx / NB, l = idx % NB;
+  for (int idx = tid; idx < TT * B; idx += blockDim.x) {
+    const int r = idx / B, l = idx % B;
     Pa[r][l] = (r < nr && l < nk) ? A[(size_t)ar.row(q0 + r) * ld + kb + l] : (T)0;
   }
   __syncthreads();
   if (tid < nr) {
-    T xr[NB];
+    T xr[B];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) xr[j] = Pa[tid][j];
+    for (int j = 0; j < B; ++j) xr[j] = Pa[tid][j];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
+    for (int j = 0; j < B; ++j) {
       if (j < nk) {
         T v = xr[j];
 #pragma unroll
-        for (int l = 0; l < NB; ++l)
+        for (int l = 0; l < B; ++l)
           if (l < j) v -= xr[l] * D[j][l];
         xr[j] = v / D[j][j];
       }
     }
 #pragma unroll
-    for (int j = 0; j < NB; ++j) Pa[tid][j] = xr[j];
+    for (int j = 0; j < B; ++j) Pa[tid][j] = xr[j];
   }
   __syncthreads();
-  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-    const int r = idx / NB, l = idx % NB;
+  for (int idx = tid; idx < TT * B; idx += blockDim.x) {
+    const int r = idx / B, l = idx % B;
     if (r < nr && l < nk) A[(size_t)ar.row(q0 + r) * ld + kb + l] = Pa[r][l];
   }
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __restrict__ lay, int phase, int step,
                                                          const int32_t* __restrict__ env0,
                                                          T* __restrict__ Abase, const int* status) {
   if (*status) return;
   const SubLayout L = lay[blockIdx.y];
   const PhaseRange pr = phase_range(L, phase);
-  const int kb = pr.c0 + step * NB;
+  const int kb = pr.c0 + step * B;
   if (kb >= pr.c1) return;
-  const int nk = min(NB, pr.c1 - kb);
+  const int nk = min(B, pr.c1 - kb);
   const ActiveRows ar = active_rows(L, phase, step, kb, nk, env0);
   const int m = ar.m;
   const int chunks = (m + TT - 1) / TT;
@@ -2287,11 +2306,11 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
   const int ib = ti * TT, jb = tj * TT;  // positions in the active-row list
   T* A = Abase + L.aoff;
   const size_t ld = L.ld;
-  __shared__ T Pa[TT][NB + 1];
-  __shared__ T Pb[TT][NB + 1];
+  __shared__ T Pa[TT][B + 1];
+  __shared__ T Pb[TT][B + 1];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < TT * NB; idx += blockDim.x) {
-    const int r = idx / NB, l = idx % NB;
+  for (int idx = tid; idx < TT * B; idx += blockDim.x) {
+    const int r = idx / B, l = idx % B;
     Pa[r][l] = (ib + r < m && l < nk) ? A[(size_t)ar.row(ib + r) * ld + kb + l] : (T)0;
     Pb[r][l] = (jb + r < m && l < nk) ? A[(size_t)ar.row(jb + r) * ld + kb + l] : (T)0;
   }
@@ -2324,27 +2343,27 @@ __global__ void __launch_bounds__(kThreads) k_bat_update(const SubLayout* __rest
 }
 }  // namespace
 
-template <typename T>
+template <typename T, int B>
 void chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
                   const int32_t* env0, T* A, int* status, cudaStream_t st) {
   for (int t = 0; t < n_steps; ++t) {
     const int chunks = step_chunks[t];
-    k_bat_diag<T><<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
+    k_bat_diag<T, B><<<dim3(1, P), kThreads, 0, st>>>(lay, phase, t, A, status);
     if (chunks <= 0) continue;
-    k_bat_trsm<T><<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
+    k_bat_trsm<T, B><<<dim3(chunks, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
     const long tiles = (long)chunks * (chunks + 1) / 2;
-    k_bat_update<T><<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
+    k_bat_update<T, B><<<dim3((unsigned)tiles, P), kThreads, 0, st>>>(lay, phase, t, env0, A, status);
   }
 }
 
 void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
                          const int32_t* env0, double* A, int* status, cudaStream_t st) {
-  chol_batched<double>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
+  chol_batched<double, 32>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
 }
 
 void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step_chunks, int n_steps,
                          const int32_t* env0, float* A, int* status, cudaStream_t st) {
-  chol_batched<float>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
+  chol_batched<float, kChol32Block>(P, lay, phase, step_chunks, n_steps, env0, A, status, st);
 }
 
 namespace {
