@@ -137,11 +137,13 @@ typedef struct {
   int32_t max_outer;   /* FETI_MIXED: limit on refinement passes (0: 20) */
   int32_t no_tensor_cores; /* FP32 block GEMM: 0 = autotuner picks tensor cores if faster,
                               1 = CUDA cores only, 2 = tensor cores whenever they run cleanly
-                              (fastest staging variant), 3 / 4 / 5 / 6 / 7 / 8 = only the
+                              (fastest staging variant), 3 / 4 / 5 / 6 / 7 = only the
                               register-staged / bulk-copy staged / tensor-map (TMA) fed /
-                              warp-specialised TMA-fed 3-stage / 2-stage / persistent
-                              (two CTAs per SM over all tiles, double-buffered accumulators)
-                              tensor-core kernel */
+                              warp-specialised TMA-fed 3-stage / 2-stage tensor-core kernel,
+                              8 / 9 / 10 = only the persistent kernel (over all tiles,
+                              double-buffered accumulators) with 3 / 3 / 2 raw A copies
+                              and 2 / 3 / 2 tail slots in flight, two / two / three CTAs
+                              per SM */
   int32_t per_subdomain;   /* nonzero: the dense local applies of F_i and S_i are launched once per
                               subdomain (p launches per apply, the plain non-batched form) instead
                               of one batched launch over all subdomains; same results, for

@@ -75,7 +75,7 @@ class FetiSolver:
                             float(inner_tol), int(max_outer),
                             {"auto": 0, False: 1, "off": 1, True: 2, "force": 2, "force_reg": 3,
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7,
-                             "force_persist": 8}[tensor_cores],
+                             "force_persist": 8, "force_persist_q3": 9, "force_persist_c3": 10}[tensor_cores],
                             int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
                             int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse])
         st = None if stream is None else C.c_void_p(int(stream))

@@ -2346,7 +2346,7 @@ feti_status autotune_m(feti_ctx* ctx, int nrhs) {
           ctx->tc_m[w] = 0;
           const int ntc = ctx->opt.no_tensor_cores;
           FETI_TRY(build_tensor_maps(ctx));
-          for (int variant = 1; variant <= 6; ++variant) {
+          for (int variant = 1; variant <= 8; ++variant) {
             if (ntc >= 3 && variant != ntc - 2) continue;
             FETI_CK(cudaMemsetAsync(ctx->d_tc_err, 0, sizeof(int), st));
             feti::launch_gemm_tc(ctx->tab[w][2], ctx->d_lay, w, Mf, nrhs, vf, ctx->dm_loc, ctx->d_zero, ctx->d_tc_err,

@@ -351,11 +351,12 @@ void launch_gemm_loc(const GemvCfg& cfg, const SubLayout* lay, int which, const 
 // timed out.
 // Tensor-core block GEMM on the FP32 copies: variant 1 register-staged,
 // 2 bulk-copy staged, 3 tensor-map (TMA) fed, 4 / 5 warp-specialised
-// TMA-fed with 3 / 2 stages, 6 persistent warp-specialised (two CTAs per SM
-// over all tiles); tmaps = one CUtensorMap per subdomain for the matrix
-// `which` (variants 3-6).
+// TMA-fed with 3 / 2 stages, 6 / 7 / 8 persistent warp-specialised over all
+// tiles (3 / 3 / 2 raw A slots and 2 / 3 / 2 tail slots; two / two / three
+// CTAs per SM);
+// tmaps = one CUtensorMap per subdomain for the matrix `which` (variants 3-8).
 // spin_cycles: device word, the main-loop wait budget (SM clock cycles) of the
-// warp-specialised variants (4-6); their drain waits keep a fixed budget.
+// warp-specialised variants (4-8); their drain waits keep a fixed budget.
 void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const float* M, int nrhs, const float* vloc,
                     double* y, const int* done, int* err, int variant, const void* tmaps,
                     const unsigned long long* spin_cycles, cudaStream_t st);

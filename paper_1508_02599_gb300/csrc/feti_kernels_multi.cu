@@ -1202,23 +1202,26 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc4(const int32_t* __restrict
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC4_TCOLS) : "memory");
 }
 
-// Persistent warp-specialised tensor-core block GEMM: a fixed grid (two
-// CTAs per SM) walks the 128-row tiles round-robin, and the K-chunk pipeline
-// runs on across tile boundaries, so the per-tile costs of the one-tile
-// kernel (tensor-memory allocation, barrier set-up, pipeline fill, an
-// epilogue that nothing overlaps) are paid once per CTA.  Roles: warp 0 lane
-// 0 issues the tensor-map copies of A, warp 1 lane 0 the MMAs, warps 4-7
-// load the B chunk and write the TF32 tails of A and B, warps 8-11 (one per
-// tensor-memory lane quadrant) drain the accumulators into y.  Two
-// accumulator sets alternate between tiles: the MMAs of tile i + 1 run while
-// the epilogue reads tile i.  Every wait is bounded; a wait that runs out
-// stops all roles, the copies and MMAs already issued are drained, and *err
-// is set.
-constexpr int TC5_NS = 3;
+// Persistent warp-specialised tensor-core block GEMM: a fixed grid walks the
+// 128-row tiles round-robin, and the K-chunk pipeline runs on across tile
+// boundaries, so the per-tile costs of the one-tile kernel (tensor-memory
+// allocation, barrier set-up, pipeline fill, an epilogue that nothing
+// overlaps) are paid once per CTA.  The raw A chunks (16 KB, the TF32 head
+// read by the MMAs straight from the copy) live in a ring of R slots, the
+// TF32 tails of A and B (20 KB) in a separate ring of Q slots, so that many
+// copies are in flight while only a few tails exist.  Roles: warp 0 lane 0
+// issues the tensor-map copies of A, warp 1 lane 0 the MMAs, warps 4-7 load
+// the B chunk and write the tails, warps 8-11 (one per tensor-memory lane
+// quadrant) drain the accumulators into y.  Two accumulator sets alternate
+// between tiles: the MMAs of tile i + 1 run while the epilogue reads tile i.
+// Every wait is bounded; a wait that runs out stops all roles, the copies and
+// MMAs already issued are drained, and *err is set.
 constexpr int TC5_THREADS = 384;
 constexpr int TC5_TCOLS = 128;  // two accumulator sets of 3 x 16 columns, 64 apart
-constexpr int TC5_SMEM = TC5_NS * TC_STAGE + 1024;
+constexpr int TC5_OP = TC_A_BYTES + 2 * TC_B_BYTES;  // A tail, B head and tail
+__host__ __device__ constexpr int tc5_smem(int R, int Q) { return R * TC_A_BYTES + Q * TC5_OP + 1024; }
 
+template <int R, int Q>
 __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restrict__ blk_sub,
                                                          const int32_t* __restrict__ blk_row0, int n_tiles,
                                                          const SubLayout* __restrict__ lay, int which,
@@ -1227,10 +1230,11 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
                                                          const int* __restrict__ done, int* __restrict__ err,
                                                          const unsigned long long* __restrict__ spin_cycles) {
   if (*done) return;
-  constexpr int NS = TC5_NS;
   extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
   unsigned char* smem = tc_smem_dyn + ((1024 - (su32(tc_smem_dyn) & 1023)) & 1023);
-  __shared__ uint64_t full[NS], ready[NS], empty[NS], tfull[2], tempty[2];
+  unsigned char* raw = smem;                      // R x 16 KB
+  unsigned char* ops = smem + R * TC_A_BYTES;     // Q x (A tail, B head, B tail)
+  __shared__ uint64_t rfull[R], rempty[R], oready[Q], oempty[Q], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -1242,10 +1246,13 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
   }
   if (tid == 0) {
     abort_flag = 0;
-    for (int i = 0; i < NS; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&ready[i], 4);
-      mbar_init(&empty[i], 1);
+    for (int i = 0; i < R; ++i) {
+      mbar_init(&rfull[i], 1);
+      mbar_init(&rempty[i], 1);
+    }
+    for (int i = 0; i < Q; ++i) {
+      mbar_init(&oready[i], 4);
+      mbar_init(&oempty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
@@ -1262,7 +1269,7 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
   const long long budget = (long long)*spin_cycles;
   auto rows_of = [&](const SubLayout& L) { return which == 0 ? L.nbp : L.nbp + L.k; };
   if (wid == 0) {
-    if (lane == 0) {  // producer: global chunk g -> stage g % NS once the MMAs of chunk g - NS are done
+    if (lane == 0) {  // producer: chunk g -> raw slot g % R once the MMAs of chunk g - R are done
       int g = 0, prev = -1;
       bool stop = false;
       for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
@@ -1274,23 +1281,23 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
           prev = s_id;
         }
         for (int kc = 0; kc < nk; ++kc) {
-          const int st = g % NS;
-          if (g >= NS && !wait_or_abort(&empty[st], (uint32_t)((g / NS) - 1) & 1u, ab, budget)) {
+          const int st = g % R;
+          if (g >= R && !wait_or_abort(&rempty[st], (uint32_t)((g / R) - 1) & 1u, ab, budget)) {
             stop = true;
             break;
           }
-          mbar_expect_tx(&full[st], (uint32_t)TC_A_BYTES);
+          mbar_expect_tx(&rfull[st], (uint32_t)TC_A_BYTES);
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-              "[%4];" ::"r"(su32(smem + st * TC_STAGE)),
-              "l"(tm), "r"(kc * 32), "r"(r0), "r"(su32(&full[st]))
+              "[%4];" ::"r"(su32(raw + st * TC_A_BYTES)),
+              "l"(tm), "r"(kc * 32), "r"(r0), "r"(su32(&rfull[st]))
               : "memory");
           ++g;
         }
       }
       // drain: every copy issued has landed before shared memory is released
-      for (int j = max(0, g - NS); j < g; ++j)
-        if (!mbar_wait_bounded(&full[j % NS], (uint32_t)(j / NS) & 1u)) atomicExch(err, 1);
+      for (int j = max(0, g - R); j < g; ++j)
+        if (!mbar_wait_bounded(&rfull[j % R], (uint32_t)(j / R) & 1u)) atomicExch(err, 1);
     }
     __syncwarp();
   } else if (wid == 1) {
@@ -1304,15 +1311,16 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + 64u * (uint32_t)abuf;
         for (int kc = 0; kc < nk; ++kc) {
-          const int st = g % NS;
-          if (!wait_or_abort(&ready[st], (uint32_t)(g / NS) & 1u, ab, budget)) {
+          const int rs = g % R, os = g % Q;
+          // the tails are written after the copy landed: one wait covers both
+          if (!wait_or_abort(&oready[os], (uint32_t)(g / Q) & 1u, ab, budget)) {
             stop = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          unsigned char* Ahi = smem + st * TC_STAGE;
-          unsigned char* Alo = Ahi + TC_A_BYTES;
-          unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+          unsigned char* Ahi = raw + rs * TC_A_BYTES;
+          unsigned char* Alo = ops + os * TC5_OP;
+          unsigned char* Bhi = Alo + TC_A_BYTES;
           unsigned char* Blo = Bhi + TC_B_BYTES;
           for (int j = 0; j < 4; ++j) {
             const uint64_t ah = sw128_desc(Ahi + 32 * j), al = sw128_desc(Alo + 32 * j);
@@ -1323,7 +1331,10 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
             tc_mma(acc + 32u, al, bh, idesc, f);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           su32(&empty[st]))
+                           su32(&rempty[rs]))
+                       : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           su32(&oempty[os]))
                        : "memory");
           ++g;
           n_commit = g;
@@ -1334,7 +1345,7 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
                          su32(&tfull[abuf]))
                      : "memory");
       }
-      if (n_commit > 0 && !mbar_wait_bounded(&empty[(n_commit - 1) % NS], (uint32_t)((n_commit - 1) / NS) & 1u))
+      if (n_commit > 0 && !mbar_wait_bounded(&oempty[(n_commit - 1) % Q], (uint32_t)((n_commit - 1) / Q) & 1u))
         atomicExch(err, 1);
     }
     __syncwarp();
@@ -1358,16 +1369,20 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
       };
       if (nk > 0) load_b(0);
       for (int kc = 0; kc < nk; ++kc) {
-        const int st = g % NS;
+        const int rs = g % R, os = g % Q;
         const float4 cb = rb;
         if (kc + 1 < nk) load_b(kc + 1);
-        if (!wait_or_abort(&full[st], (uint32_t)(g / NS) & 1u, ab, budget)) {
+        if (!wait_or_abort(&rfull[rs], (uint32_t)(g / R) & 1u, ab, budget)) {
           stop = true;
           break;
         }
-        unsigned char* Ahi = smem + st * TC_STAGE;
-        unsigned char* Alo = Ahi + TC_A_BYTES;
-        unsigned char* Bhi = Ahi + 2 * TC_A_BYTES;
+        if (g >= Q && !wait_or_abort(&oempty[os], (uint32_t)((g / Q) - 1) & 1u, ab, budget)) {
+          stop = true;
+          break;
+        }
+        unsigned char* Ahi = raw + rs * TC_A_BYTES;
+        unsigned char* Alo = ops + os * TC5_OP;
+        unsigned char* Bhi = Alo + TC_A_BYTES;
         unsigned char* Blo = Bhi + TC_B_BYTES;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -1384,7 +1399,7 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&ready[st])) : "memory");
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&oready[os])) : "memory");
         ++g;
       }
     }
@@ -1429,6 +1444,24 @@ __global__ void __launch_bounds__(TC5_THREADS) k_gemm_tc5(const int32_t* __restr
   }
   if (wid == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC5_TCOLS) : "memory");
+}
+
+template <int R, int Q>
+void launch_tc5(int ctas_per_sm, const GemvCfg& cfg, const SubLayout* lay, int which, const CUtensorMap* maps, int nrhs,
+                const float* vloc, double* y, const int* done, int* err, const unsigned long long* spin_cycles,
+                cudaStream_t st) {
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+    cudaFuncSetAttribute(k_gemm_tc5<R, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc5_smem(R, Q));
+  }
+  const int grid = std::min(cfg.n_blocks, ctas_per_sm * n_sm);
+  if (grid > 0)
+    k_gemm_tc5<R, Q><<<grid, TC5_THREADS, tc5_smem(R, Q), st>>>(cfg.blk_sub, cfg.blk_row0, cfg.n_blocks, lay, which,
+                                                               maps, nrhs, vloc, y, done, err, spin_cycles);
 }
 
 inline int grid_for(long n) {
@@ -1489,20 +1522,14 @@ void launch_gemm_tc(const GemvCfg& cfg, const SubLayout* lay, int which, const f
     cudaFuncSetAttribute(k_gemm_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
     attr = true;
   }
-  if (variant == 6) {
-    static int n_sm = 0;
-    if (!n_sm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      if (n_sm <= 0) n_sm = 1;
-      cudaFuncSetAttribute(k_gemm_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, TC5_SMEM);
-    }
-    const int grid = std::min(cfg.n_blocks, 2 * n_sm);
-    if (grid > 0)
-      k_gemm_tc5<<<grid, TC5_THREADS, TC5_SMEM, st>>>(cfg.blk_sub, cfg.blk_row0, cfg.n_blocks, lay, which,
-                                                      static_cast<const CUtensorMap*>(tmaps), nrhs, vloc, y, done, err,
-                                                      spin_cycles);
+  if (variant >= 6 && variant <= 8) {
+    const CUtensorMap* mp = static_cast<const CUtensorMap*>(tmaps);
+    if (variant == 6)  // 3 raw + 2 tail slots, two CTAs per SM
+      launch_tc5<3, 2>(2, cfg, lay, which, mp, nrhs, vloc, y, done, err, spin_cycles, st);
+    else if (variant == 7)  // 3 raw + 3 tail slots, two CTAs per SM
+      launch_tc5<3, 3>(2, cfg, lay, which, mp, nrhs, vloc, y, done, err, spin_cycles, st);
+    else  // 2 raw + 2 tail slots, three CTAs per SM
+      launch_tc5<2, 2>(3, cfg, lay, which, mp, nrhs, vloc, y, done, err, spin_cycles, st);
     return;
   }
   if (variant == 4 || variant == 5) {

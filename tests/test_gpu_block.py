@@ -68,7 +68,8 @@ JITTER = mesh.jittered_cylinder_problem(6, 24, 12, 24, mesh_seed=7, part_seed=8)
 
 @pytest.mark.parametrize("prob", [TUBE_FLOAT, JITTER], ids=["tube", "jittered"])
 @pytest.mark.parametrize("variant,code", [("force_reg", 0), ("force_bulk", -1), ("force_tma", -2),
-                                          ("force_ws3", -3), ("force_ws2", -4), ("force_persist", -5)])
+                                          ("force_ws3", -3), ("force_ws2", -4), ("force_persist", -5),
+                                          ("force_persist_q3", -6), ("force_persist_c3", -7)])
 def test_tensor_core_block_gemm_matches_cuda_cores(prob, variant, code):
     """Each tcgen05 3xTF32 block GEMM (register-staged, bulk-copy staged,
     tensor-map fed, warp-specialised with 3 and 2 stages, persistent) against the CUDA-core FP32 GEMM on the same FP32 operator

@@ -57,7 +57,7 @@ def test_streamed_symmetric_apply_times_out_then_recovers(case):
         assert _rel(U, U_ref) <= 1e-8
 
 
-@pytest.mark.parametrize("variant,code", [("force_ws3", -3), ("force_persist", -5)])
+@pytest.mark.parametrize("variant,code", [("force_ws3", -3), ("force_persist", -5), ("force_persist_c3", -7)])
 def test_tensor_core_block_gemm_times_out_then_recovers(case, variant, code):
     """The warp-specialised one-tile kernel and the persistent kernel."""
     from paper_1508_02599_gb300 import FetiError, FetiSolver
