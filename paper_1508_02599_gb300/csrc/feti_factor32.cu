@@ -30,51 +30,47 @@ __device__ __forceinline__ float f32_warp_sum(float v) {
   return v;
 }
 
-// FP32 workspace -> padded FP32 operator copies (row stride padded to 4):
-// which 0: the preconditioner block S_i (trailing block after the interior
-// elimination), which 1: F_i = minus the eliminated augmentation block.
-__global__ void k_extract32(const SubLayout* __restrict__ lay, int which, const float* __restrict__ Abase,
-                            float* __restrict__ out) {
-  const SubLayout L = lay[blockIdx.x];
-  const float* A = Abase + L.aoff;
+// Both FP32 layouts of one operator in one pass, one CTA per 32 x 32 output
+// tile (I, J) of one subdomain: the source tile (max(I,J), min(I,J)) of the
+// eliminated workspace's lower triangle is read row by row into shared
+// memory, then written transposed or not into the padded row-major copy and,
+// for J <= I, into the 32-row lower panels of the symmetric apply (zero
+// beyond the matrix).  which 0: the preconditioner block S_i; which 1: F_i
+// (the negated augmentation block).
+__global__ void __launch_bounds__(256) k_extract32_tiles(const SubLayout* __restrict__ lay, int which,
+                                                         const float* __restrict__ Abase, float* __restrict__ out,
+                                                         float* __restrict__ sym) {
+  const SubLayout L = lay[blockIdx.y];
+  const int m = which == 0 ? L.nbp + L.k : L.nbp;
+  const int nT = (m + 31) / 32;
+  const int I = blockIdx.x / nT, J = blockIdx.x - (blockIdx.x / nT) * nT;
+  if (I >= nT) return;
   const size_t ld = L.ld;
-  if (which == 0) {
-    const int nb = L.nbp + L.k, ldo = (nb + 3) & ~3;
-    float* S = out + L.soff32;
-    for (int idx = threadIdx.x; idx < nb * ldo; idx += blockDim.x) {
-      const int i = idx / ldo, j = idx % ldo;
-      const int ii = max(i, j), jj = min(i, j);
-      S[idx] = j < nb ? A[(size_t)(L.nI + ii) * ld + L.nI + jj] : 0.0f;
-    }
-  } else {
-    const int m = L.nbp, ldo = (m + 3) & ~3;
-    float* F = out + L.foff32;
-    for (int idx = threadIdx.x; idx < m * ldo; idx += blockDim.x) {
-      const int i = idx / ldo, j = idx % ldo;
-      const int ii = max(i, j), jj = min(i, j);
-      F[idx] = j < m ? -A[(size_t)(L.n + ii) * ld + L.n + jj] : 0.0f;
-    }
+  const int base = which == 0 ? L.nI : L.n;
+  const float sgn = which == 0 ? 1.0f : -1.0f;
+  const float* A = Abase + L.aoff + (size_t)base * ld + base;
+  __shared__ float T[32][33];
+  const int Ts = max(I, J), Tc = min(I, J);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows per pass
+  for (int r = ty; r < 32; r += 8) {
+    const int gr = 32 * Ts + r, gc = 32 * Tc + tx;
+    // lower triangle only (the diagonal tile's upper half is filled by symmetry)
+    T[r][tx] = (gr < m && gc < m && gc <= gr) ? A[(size_t)gr * ld + gc] : 0.0f;
   }
-}
-
-// Padded FP32 copy -> lower block-triangle panels of the symmetric apply
-// (which 0: F_i, which 1: preconditioner block; the layout of k_symv_f32).
-__global__ void k_pad_to_sym(const SubLayout* __restrict__ lay, int which, const float* __restrict__ src,
-                             float* __restrict__ dst) {
-  const SubLayout L = lay[blockIdx.x];
-  const int m = which == 0 ? L.nbp : L.nbp + L.k;
-  const int lds = (m + 3) & ~3;
-  const float* a = src + (which == 0 ? L.foff32 : L.soff32);
-  float* b = dst + (which == 0 ? L.fsym32 : L.ssym32);
-  constexpr int PH = kSymPH;
-  const int nP = (m + PH - 1) / PH;
-  for (int I = 0; I < nP; ++I) {
-    const int w = PH * (I + 1);
-    float* bp = b + (size_t)(PH * PH / 2) * I * (I + 1);
-    for (int idx = threadIdx.x; idx < PH * w; idx += blockDim.x) {
-      const int r = PH * I + idx / w, c = idx % w;
-      bp[idx] = (r < m && c < m) ? a[(size_t)r * lds + c] : 0.0f;
-    }
+  __syncthreads();
+  const int ldo = (m + 3) & ~3;
+  float* o = out + (which == 0 ? L.soff32 : L.foff32);
+  float* sp = sym ? sym + (which == 0 ? L.ssym32 : L.fsym32) + (size_t)512 * I * (I + 1) : nullptr;
+  const int w = 32 * (I + 1);
+  for (int r = ty; r < 32; r += 8) {
+    const int gr = 32 * I + r, gc = 32 * J + tx;
+    float v;
+    if (I > J) v = T[r][tx];
+    else if (I < J) v = T[tx][r];
+    else v = tx <= r ? T[r][tx] : T[tx][r];
+    v *= sgn;
+    if (gr < m && gc < ldo) o[(size_t)gr * ldo + gc] = gc < m ? v : 0.0f;
+    if (sp && J <= I) sp[(size_t)r * w + 32 * J + tx] = (gr < m && gc < m) ? v : 0.0f;
   }
 }
 
@@ -379,12 +375,10 @@ __global__ void k_fill_mix(long n, double* __restrict__ x) {
 
 }  // namespace
 
-void launch_extract32(int P, const SubLayout* lay, int which, const float* A, float* out, cudaStream_t st) {
-  k_extract32<<<P, kT, 0, st>>>(lay, which, A, out);
-}
-
-void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src, float* dst, cudaStream_t st) {
-  k_pad_to_sym<<<P, kT, 0, st>>>(lay, which, src, dst);
+void launch_extract32_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, float* out, float* sym,
+                            cudaStream_t st) {
+  const int nT = (max_m + 31) / 32;
+  if (P > 0 && nT > 0) k_extract32_tiles<<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out, sym);
 }
 
 void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,

@@ -294,11 +294,11 @@ void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step
 
 namespace feti {
 // ---- FP32 factorization with FP64-refined K^+ (feti_factor32.cu) ----
-// FP32 workspace -> padded FP32 copies: which 0 the preconditioner block
-// (S_i), which 1 F_i (minus the eliminated augmentation block).
-void launch_extract32(int P, const SubLayout* lay, int which, const float* A, float* out, cudaStream_t st);
-// Padded FP32 copy -> symmetric-apply panels (which 0: F_i, 1: preconditioner block).
-void launch_pad_to_sym(int P, const SubLayout* lay, int which, const float* src, float* dst, cudaStream_t st);
+// FP32 workspace -> the padded FP32 copy and (sym != NULL) the symmetric-apply
+// panels in one tiled pass; which 0: the preconditioner block (S_i), which 1:
+// F_i; max_m: the largest operator size over the subdomains.
+void launch_extract32_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, float* out, float* sym,
+                            cudaStream_t st);
 // One FP32 correction x (+)= L^-T L^-1 r of the FP32-factor K^+ (L the FP32
 // Cholesky factor of K_rr), the sweeps confined to the interior rows:
 // forward: y_I = L_II^-1 r_I (FP32 into yI, local offsets) and
