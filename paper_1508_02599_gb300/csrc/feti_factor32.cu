@@ -30,16 +30,19 @@ __device__ __forceinline__ float f32_warp_sum(float v) {
   return v;
 }
 
-// Both FP32 layouts of one operator in one pass, one CTA per 32 x 32 output
-// tile (I, J) of one subdomain: the source tile (max(I,J), min(I,J)) of the
-// eliminated workspace's lower triangle is read row by row into shared
-// memory, then written transposed or not into the padded row-major copy and,
-// for J <= I, into the 32-row lower panels of the symmetric apply (zero
-// beyond the matrix).  which 0: the preconditioner block S_i; which 1: F_i
-// (the negated augmentation block).
-__global__ void __launch_bounds__(256) k_extract32_tiles(const SubLayout* __restrict__ lay, int which,
-                                                         const float* __restrict__ Abase, float* __restrict__ out,
-                                                         float* __restrict__ sym) {
+// The dense local operators out of the eliminated workspace in one pass, one
+// CTA per 32 x 32 output tile (I, J) of one subdomain: the source tile
+// (max(I,J), min(I,J)) of the workspace's lower triangle is read row by row
+// into shared memory and written transposed or not into each requested
+// layout: FP64 row-major (out64, stride m), the FP32 copy with rows padded to
+// 4 (out32), and for J <= I the FP32 32-row lower panels of the symmetric
+// apply (sym32; zero beyond the matrix).  which 0: the preconditioner block
+// S_i (m = n_b' + k), which 1: F_i = minus the eliminated augmentation block
+// (m = n_b').
+template <typename TS>
+__global__ void __launch_bounds__(256) k_extract_tiles(const SubLayout* __restrict__ lay, int which,
+                                                       const TS* __restrict__ Abase, double* __restrict__ out64,
+                                                       float* __restrict__ out32, float* __restrict__ sym32) {
   const SubLayout L = lay[blockIdx.y];
   const int m = which == 0 ? L.nbp + L.k : L.nbp;
   const int nT = (m + 31) / 32;
@@ -47,30 +50,32 @@ __global__ void __launch_bounds__(256) k_extract32_tiles(const SubLayout* __rest
   if (I >= nT) return;
   const size_t ld = L.ld;
   const int base = which == 0 ? L.nI : L.n;
-  const float sgn = which == 0 ? 1.0f : -1.0f;
-  const float* A = Abase + L.aoff + (size_t)base * ld + base;
-  __shared__ float T[32][33];
+  const TS sgn = which == 0 ? (TS)1 : (TS)-1;
+  const TS* A = Abase + L.aoff + (size_t)base * ld + base;
+  __shared__ TS T[32][33];
   const int Ts = max(I, J), Tc = min(I, J);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows per pass
   for (int r = ty; r < 32; r += 8) {
     const int gr = 32 * Ts + r, gc = 32 * Tc + tx;
     // lower triangle only (the diagonal tile's upper half is filled by symmetry)
-    T[r][tx] = (gr < m && gc < m && gc <= gr) ? A[(size_t)gr * ld + gc] : 0.0f;
+    T[r][tx] = (gr < m && gc < m && gc <= gr) ? A[(size_t)gr * ld + gc] : (TS)0;
   }
   __syncthreads();
   const int ldo = (m + 3) & ~3;
-  float* o = out + (which == 0 ? L.soff32 : L.foff32);
-  float* sp = sym ? sym + (which == 0 ? L.ssym32 : L.fsym32) + (size_t)512 * I * (I + 1) : nullptr;
+  double* o64 = out64 ? out64 + (which == 0 ? L.soff : L.foff) : nullptr;
+  float* o32 = out32 ? out32 + (which == 0 ? L.soff32 : L.foff32) : nullptr;
+  float* sp = sym32 ? sym32 + (which == 0 ? L.ssym32 : L.fsym32) + (size_t)512 * I * (I + 1) : nullptr;
   const int w = 32 * (I + 1);
   for (int r = ty; r < 32; r += 8) {
     const int gr = 32 * I + r, gc = 32 * J + tx;
-    float v;
+    TS v;
     if (I > J) v = T[r][tx];
     else if (I < J) v = T[tx][r];
     else v = tx <= r ? T[r][tx] : T[tx][r];
     v *= sgn;
-    if (gr < m && gc < ldo) o[(size_t)gr * ldo + gc] = gc < m ? v : 0.0f;
-    if (sp && J <= I) sp[(size_t)r * w + 32 * J + tx] = (gr < m && gc < m) ? v : 0.0f;
+    if (o64 && gr < m && gc < m) o64[(size_t)gr * m + gc] = (double)v;
+    if (o32 && gr < m && gc < ldo) o32[(size_t)gr * ldo + gc] = gc < m ? (float)v : 0.0f;
+    if (sp && J <= I) sp[(size_t)r * w + 32 * J + tx] = (gr < m && gc < m) ? (float)v : 0.0f;
   }
 }
 
@@ -375,10 +380,16 @@ __global__ void k_fill_mix(long n, double* __restrict__ x) {
 
 }  // namespace
 
-void launch_extract32_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, float* out, float* sym,
-                            cudaStream_t st) {
+void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, double* out64, float* out32,
+                          float* sym32, cudaStream_t st) {
   const int nT = (max_m + 31) / 32;
-  if (P > 0 && nT > 0) k_extract32_tiles<<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out, sym);
+  if (P > 0 && nT > 0) k_extract_tiles<float><<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out64, out32, sym32);
+}
+
+void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, const double* A, double* out64,
+                          float* out32, float* sym32, cudaStream_t st) {
+  const int nT = (max_m + 31) / 32;
+  if (P > 0 && nT > 0) k_extract_tiles<double><<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out64, out32, sym32);
 }
 
 void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,

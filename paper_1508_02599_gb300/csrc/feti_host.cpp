@@ -1561,29 +1561,25 @@ feti_status factorize_all(feti_ctx* ctx) {
     feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0_32,
                               ctx->d_A32, ctx->d_status, st);
     if (ctx->opt.precond == FETI_PREC_DIRICHLET)
-      feti::launch_extract32_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 0, ctx->d_A32, ctx->d_S32, ctx->d_S32s, st);
+      feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 0, ctx->d_A32, nullptr, ctx->d_S32, ctx->d_S32s, st);
     feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A32,
                               ctx->d_status, st);
-    feti::launch_extract32_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 1, ctx->d_A32, ctx->d_F32, ctx->d_F32s, st);
+    feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 1, ctx->d_A32, nullptr, ctx->d_F32, ctx->d_F32s, st);
     FETI_CK(cudaGetLastError());
     FETI_TRY(check_status(ctx, "local factorization (FP32)"));
     return FETI_OK;
   }
   feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0, ctx->d_A,
                             ctx->d_status, st);
-  if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_extract(ctx->P, ctx->d_lay, 0, ctx->d_A, ctx->d_S, st);
+  // FP64 operators, and in the FP32-local form their FP32 copies, in one pass each
+  const bool mix = ctx->opt.precision == FETI_MIXED;
+  if (ctx->opt.precond == FETI_PREC_DIRICHLET)
+    feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 0, ctx->d_A, ctx->d_S, mix ? ctx->d_S32 : nullptr,
+                               mix ? ctx->d_S32s : nullptr, st);
   feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A,
                             ctx->d_status, st);
-  feti::launch_extract(ctx->P, ctx->d_lay, 1, ctx->d_A, ctx->d_F, st);
-  if (ctx->opt.precision == FETI_MIXED) {
-    feti::launch_to_f32(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32, st);
-    if (ctx->opt.precond == FETI_PREC_DIRICHLET) feti::launch_to_f32(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32, st);
-    if (ctx->d_F32s) {
-      feti::launch_to_f32_sym(ctx->P, ctx->d_lay, 0, ctx->d_F, ctx->d_F32s, st);
-      if (ctx->opt.precond == FETI_PREC_DIRICHLET)
-        feti::launch_to_f32_sym(ctx->P, ctx->d_lay, 1, ctx->d_S, ctx->d_S32s, st);
-    }
-  }
+  feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 1, ctx->d_A, ctx->d_F, mix ? ctx->d_F32 : nullptr,
+                             mix ? ctx->d_F32s : nullptr, st);
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_status(ctx, "local factorization"));
   return FETI_OK;

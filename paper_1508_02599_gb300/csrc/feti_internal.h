@@ -196,10 +196,8 @@ void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, c
 // pass; max_m: the largest operator size.  G = 8, 16 or 32.
 void launch_symv3_f32(int G, int P, const int32_t* order, int max_m, const SubLayout* lay, int which,
                       const float* Msym, const float* vloc, double* y, const int* done, cudaStream_t st);
-void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // FP32 signed gather (input of the FP32 apply).
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st);
-void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st);
 // a += b
 void launch_vadd(int n, double* a, const double* b, cudaStream_t st);
 }  // namespace feti
@@ -294,11 +292,15 @@ void launch_chol_batched(int P, const SubLayout* lay, int phase, const int* step
 
 namespace feti {
 // ---- FP32 factorization with FP64-refined K^+ (feti_factor32.cu) ----
-// FP32 workspace -> the padded FP32 copy and (sym != NULL) the symmetric-apply
-// panels in one tiled pass; which 0: the preconditioner block (S_i), which 1:
-// F_i; max_m: the largest operator size over the subdomains.
-void launch_extract32_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, float* out, float* sym,
-                            cudaStream_t st);
+// Eliminated workspace (FP32 or FP64) -> the dense local operator in each
+// requested layout (NULL: skipped) in one tiled pass: FP64 row-major (out64),
+// the FP32 copy with rows padded to 4 (out32), the FP32 symmetric-apply
+// panels (sym32); which 0: the preconditioner block (S_i), which 1: F_i;
+// max_m: the largest operator size over the subdomains.
+void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, const float* A, double* out64, float* out32,
+                          float* sym32, cudaStream_t st);
+void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, const double* A, double* out64,
+                          float* out32, float* sym32, cudaStream_t st);
 // One FP32 correction x (+)= L^-T L^-1 r of the FP32-factor K^+ (L the FP32
 // Cholesky factor of K_rr), the sweeps confined to the interior rows:
 // forward: y_I = L_II^-1 r_I (FP32 into yI, local offsets) and

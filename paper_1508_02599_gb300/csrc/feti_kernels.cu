@@ -1077,41 +1077,6 @@ __global__ void k_symv_fix(Maps mp, const SubLayout* __restrict__ lay, int which
   }
 }
 
-// FP64 -> FP32 lower block-triangle (panels of kSymPH rows) of a symmetric local operator.
-__global__ void k_to_f32_sym(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
-                             float* __restrict__ dst) {
-  const int s = blockIdx.x;
-  const SubLayout L = lay[s];
-  const int m = which == 0 ? L.nbp : L.nbp + L.k;
-  const double* a = src + (which == 0 ? L.foff : L.soff);
-  float* b = dst + (which == 0 ? L.fsym32 : L.ssym32);
-  constexpr int PH = kSymPH;
-  const int nP = (m + PH - 1) / PH;
-  for (int I = 0; I < nP; ++I) {
-    const int w = PH * (I + 1);
-    float* bp = b + (size_t)(PH * PH / 2) * I * (I + 1);
-    for (int idx = threadIdx.x; idx < PH * w; idx += blockDim.x) {
-      const int r = PH * I + idx / w, c = idx % w;
-      bp[idx] = (r < m && c < m) ? (float)a[(size_t)r * m + c] : 0.0f;
-    }
-  }
-}
-
-// FP64 -> FP32 copy of the dense local operators (row stride padded to 4).
-__global__ void k_to_f32(const SubLayout* __restrict__ lay, int which, const double* __restrict__ src,
-                         float* __restrict__ dst) {
-  const int s = blockIdx.x;
-  const SubLayout L = lay[s];
-  const int m = which == 0 ? L.nbp : L.nbp + L.k;
-  const int ld = pad4(m);
-  const double* a = src + (which == 0 ? L.foff : L.soff);
-  float* b = dst + (which == 0 ? L.foff32 : L.soff32);
-  for (int idx = threadIdx.x; idx < m * ld; idx += blockDim.x) {
-    const int i = idx / ld, j = idx % ld;
-    b[idx] = j < m ? (float)a[(size_t)i * m + j] : 0.0f;
-  }
-}
-
 __global__ void k_vadd(int n, double* __restrict__ a, const double* __restrict__ b) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] += b[i];
 }
@@ -1757,16 +1722,8 @@ void launch_symv2_f32(int n_warps, const int32_t* wsub, const int32_t* wpanel, c
   k_symv_fix<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, lay, which, part, y, done);
 }
 
-void launch_to_f32_sym(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st) {
-  k_to_f32_sym<<<P, kThreads, 0, st>>>(lay, which, src, dst);
-}
-
 void launch_gather32(const Maps& mp, const double* x, const double* wv, float* y, const int* done, cudaStream_t st) {
   k_gather32<<<grid_for(mp.nb_total), kThreads, 0, st>>>(mp, x, wv, y, done);
-}
-
-void launch_to_f32(int P, const SubLayout* lay, int which, const double* src, float* dst, cudaStream_t st) {
-  k_to_f32<<<P, kThreads, 0, st>>>(lay, which, src, dst);
 }
 
 void launch_vadd(int n, double* a, const double* b, cudaStream_t st) {
