@@ -555,6 +555,19 @@ feti_status build_decomposition(feti_ctx* ctx) {
   auto& rw = ctx->weight;
   auto& rb = ctx->bvec;
   rs.clear(); rl.clear(); rg.clear(); rw.clear(); rb.clear();
+  {
+    // row count first: every node shared by m subdomains gives m (m - 1) / 2
+    // rows per component (all-floating: plus one per subdomain copy of a
+    // Dirichlet DOF)
+    int64_t nrow = 0;
+    for (int n = 0; n < N; ++n) {
+      const int64_t m = nptr[n + 1] - nptr[n];
+      nrow += 3 * (m * (m - 1) / 2);
+    }
+    if (af)
+      for (size_t q = 0; q < ctx->dir_dof.size(); ++q) nrow += nptr[ctx->dir_dof[q] / 3 + 1] - nptr[ctx->dir_dof[q] / 3];
+    rs.reserve(2 * nrow); rl.reserve(2 * nrow); rg.reserve(2 * nrow); rw.reserve(nrow); rb.reserve(nrow);
+  }
   for (int n = 0; n < N; ++n) {
     const int m = nptr[n + 1] - nptr[n];
     if (m < 2) continue;
@@ -1084,56 +1097,56 @@ feti_status build_decomposition(feti_ctx* ctx) {
   ctx->U_init.assign(3 * (size_t)N, 0.0);
   if (!af)
     for (size_t i = 0; i < ctx->dir_dof.size(); ++i) ctx->U_init[ctx->dir_dof[i]] = ctx->dir_val[i];
-  // coarse G^T G pair blocks (i <= j, ascending), each with the multiplier
-  // rows that couple them, ascending: two passes over the rows, blocks found
-  // through a hash of the pair
   lg.mark("create:   global-DOF and Newton maps, uploads");
+  // coarse G^T G pair blocks (i <= j, ascending), each with the multiplier
+  // rows that couple them, ascending
   std::vector<int32_t> gi, gj, gptr(1, 0), grows;
   {
-    auto pairs_of = [&](int64_t r, uint64_t out[3]) {
-      int ss[2], cnt = 0;
-      for (int e = 0; e < 2; ++e) {
-        const int s = rs[2 * r + e];
-        if (s >= 0 && ctx->lay[s].k > 0) ss[cnt++] = s;
-      }
-      int m = 0;
-      if (cnt >= 1) out[m++] = (uint64_t)ss[0] * P + ss[0];
-      if (cnt == 2) {
-        out[m++] = (uint64_t)ss[1] * P + ss[1];
-        out[m++] = (uint64_t)std::min(ss[0], ss[1]) * P + std::max(ss[0], ss[1]);
-      }
-      return m;
+    // per subdomain i with a kernel (in parallel): the multiplier rows of its
+    // boundary positions, ascending, grouped by the other subdomain j of each
+    // row (j > i with a kernel; the diagonal block takes every row), so the
+    // blocks come out in (i, j) order; then concatenated
+    struct SubBlocks {
+      std::vector<int32_t> j, ptr, rows;
     };
-    std::unordered_map<uint64_t, int32_t> id;
-    std::vector<uint64_t> keys;
-    std::vector<int32_t> cnt;
-    uint64_t k3[3];
-    for (int64_t r = 0; r < ctx->n_lambda; ++r) {
-      const int m = pairs_of(r, k3);
-      for (int q = 0; q < m; ++q) {
-        auto it = id.find(k3[q]);
-        if (it == id.end()) {
-          it = id.emplace(k3[q], (int32_t)keys.size()).first;
-          keys.push_back(k3[q]);
-          cnt.push_back(0);
-        }
-        cnt[it->second]++;
+    std::vector<SubBlocks> sb(P);
+    par_for(P, 4, [&](int64_t i) {
+      const SubLayout& L = ctx->lay[i];
+      if (L.k == 0) return;
+      std::vector<int32_t> rr;
+      for (int p = 0; p < L.nbp + L.k; ++p)
+        for (int e = bt_cnt[L.boff + p]; e < bt_cnt[L.boff + p + 1]; ++e) rr.push_back(bt_row[e]);
+      std::sort(rr.begin(), rr.end());
+      rr.erase(std::unique(rr.begin(), rr.end()), rr.end());
+      // (other subdomain, row) for the off-diagonal blocks
+      std::vector<std::pair<int32_t, int32_t>> od;
+      for (int32_t r : rr) {
+        const int a0 = rs[2 * (int64_t)r], a1 = rs[2 * (int64_t)r + 1];
+        const int j = a0 == (int)i ? a1 : a0;
+        if (j > (int)i && ctx->lay[j].k > 0) od.emplace_back(j, r);
       }
-    }
-    std::vector<int32_t> order(keys.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return keys[a] < keys[b]; });
-    std::vector<int32_t> start(keys.size());
-    for (int32_t o : order) {
-      start[o] = gptr.back();
-      gi.push_back((int32_t)(keys[o] / P));
-      gj.push_back((int32_t)(keys[o] % P));
-      gptr.push_back(gptr.back() + cnt[o]);
-    }
-    grows.assign(gptr.back(), 0);
-    for (int64_t r = 0; r < ctx->n_lambda; ++r) {  // rows in increasing order within each block
-      const int m = pairs_of(r, k3);
-      for (int q = 0; q < m; ++q) grows[start[id[k3[q]]]++] = (int32_t)r;
+      std::sort(od.begin(), od.end());
+      SubBlocks& B = sb[i];
+      B.j.push_back((int32_t)i);
+      B.ptr.push_back(0);
+      B.rows = rr;
+      for (size_t q = 0; q < od.size(); ++q) {
+        if (q == 0 || od[q].first != od[q - 1].first) {
+          B.ptr.push_back((int32_t)B.rows.size());
+          B.j.push_back(od[q].first);
+        }
+        B.rows.push_back(od[q].second);
+      }
+      B.ptr.push_back((int32_t)B.rows.size());
+    });
+    for (int i = 0; i < P; ++i) {
+      const SubBlocks& B = sb[i];
+      for (size_t q = 0; q < B.j.size(); ++q) {
+        gi.push_back(i);
+        gj.push_back(B.j[q]);
+        grows.insert(grows.end(), B.rows.begin() + B.ptr[q], B.rows.begin() + B.ptr[q + 1]);
+        gptr.push_back((int32_t)grows.size());
+      }
     }
   }
   ctx->n_gtg = (int)gi.size();
@@ -1177,7 +1190,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   ctx->n_chunks = (int)chunk_sub.size();
   std::vector<double> Rall(roff);
-  for (int s = 0; s < P; ++s) std::copy(Rd[s].begin(), Rd[s].end(), Rall.begin() + ctx->lay[s].roff);
+  par_for(P, 8, [&](int64_t s) { std::copy(Rd[s].begin(), Rd[s].end(), Rall.begin() + ctx->lay[s].roff); });
 
   lg.mark("create: tables");
   // ---- uploads and allocations
