@@ -200,6 +200,7 @@ def main():
                          "captures); the applies run the same kernels")
     ap.add_argument("--f32factor", type=int, default=1,
                     help="also run the form with FP32 local factorizations and refined K^+ (0: skip)")
+    ap.add_argument("--implicit", type=int, default=1, help="also measure the implicit FP64 local form (0: skip)")
     ap.add_argument("--block", type=int, default=1, help="also measure the 16-RHS block form (0: skip)")
     ap.add_argument("--block-fp64", type=int, default=1, help="include the FP64 16-RHS block leg (0: skip)")
     ap.add_argument("--elements", type=int, default=1,
@@ -260,13 +261,13 @@ def main():
     peaks, src = _peaks()
     fp64_peak = 1.259  # TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
 
-    def measure(precision: str, batched: bool = True, n_apply: int = 0, steps: int = 0):
+    def measure(precision: str, batched: bool = True, n_apply: int = 0, steps: int = 0, local_form: str = "auto"):
         """Full solve once, then `steps` timed blocks of n_apply dual applies."""
         n_apply = n_apply or args.n_apply
         steps = steps or args.steps
         solver = FetiSolver(prob, method="af", precond="dirichlet", tol=1e-8, maxit=3000, coarse=args.coarse,
                             stream=stream.cuda_stream, precision=precision, batched=batched,
-                            symmetric=args.symmetric)
+                            symmetric=args.symmetric, local_form=local_form)
         if args.apply_only:
             solver.prepare()
             U, rep = np.zeros(3 * prob.n_nodes), {"t_pcg_ms": None, "iterations": 0, "outer_iterations": 0,
@@ -395,6 +396,9 @@ def main():
     # per subdomain (p launches per apply instead of one batched launch)
     mp = (measure("fp64", batched=False, n_apply=max(1, args.n_apply // 4), steps=max(1, args.steps // 4))
           if args.plain else None)
+    # the implicit FP64 form: F_i v by forward and backward sweeps over the local factor
+    mi = (measure("fp64", n_apply=max(1, args.n_apply // 4), steps=max(1, args.steps // 4), local_form="implicit")
+          if args.implicit else None)
     b64 = measure_block("fp64") if args.block and args.block_fp64 else None
     b32 = measure_block("mixed") if args.block else None
     n64 = np.linalg.norm(m64["U"])
@@ -473,6 +477,13 @@ def main():
                 "local_apply_kernel_ms": mp["kern_ms"],
                 "note": "plain form: FP64, one local-apply launch per subdomain instead of one batched launch; "
                         "same kernels, graphs and schedule"},
+            "fp64_implicit": None if mi is None else {
+                "value": mi["value"], "unit": UNIT, "ms_per_step": mi["ms"] / mi["steps"],
+                "time_to_tol_ms": mi["rep"]["t_pcg_ms"], "iterations": mi["rep"]["iterations"],
+                "local_apply_ms": mi["kern_ms"],
+                "note": "implicit local form: each F_i v is a forward and a backward sweep over the FP64 "
+                        "local Cholesky factor on the placed boundary vector (gather, place, sweeps, boundary "
+                        "take); local_apply_ms spans those launches per apply"},
             "roofline": {"bound": "hbm",
                          "kernel": ("k_symv2_f32 + k_symv_fix (F_i apply, FP32 lower block-triangle, streamed)"
                                     if m32["sched"]["fp32_F"][0] == -64 else

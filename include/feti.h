@@ -170,6 +170,12 @@ typedef struct {
                                order of the subdomain graph (fronts eliminated level by level),
                                each projection a forward and a backward sweep over the supernodes
                                run as one task-graph kernel whose waits are bounded as above */
+  int32_t local_form;       /* the local apply y_i = K_i^+ v_i of F inside the PCG (Sec. 4.3):
+                               0 = automatic (explicit), 1 = explicit F_i = (S_i[b',b'])^-1 applied
+                               as a dense matvec, 2 = implicit: forward and backward triangular
+                               sweeps over the local Cholesky factor on the placed boundary
+                               vector every iteration, the paper's sparse-direct form (FETI_FP64
+                               only; the block form and the preconditioner stay explicit) */
 } feti_options;
 
 typedef struct {

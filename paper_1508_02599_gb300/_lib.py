@@ -43,7 +43,7 @@ class FetiOptions(C.Structure):
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32),
                 ("per_subdomain", C.c_int32), ("symmetric", C.c_int32), ("spin_timeout_ns", C.c_uint64),
-                ("coarse_form", C.c_int32)]
+                ("coarse_form", C.c_int32), ("local_form", C.c_int32)]
 
 
 class FetiCheckpointInfo(C.Structure):

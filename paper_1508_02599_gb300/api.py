@@ -40,7 +40,7 @@ class FetiSolver:
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
                  tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0,
-                 coarse: str = "auto"):
+                 coarse: str = "auto", local_form: str = "auto"):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -77,7 +77,8 @@ class FetiSolver:
                              "force_bulk": 4, "force_tma": 5, "force_ws3": 6, "force_ws2": 7,
                              "force_persist": 8, "force_persist_q3": 9, "force_persist_c3": 10}[tensor_cores],
                             int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
-                            int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse])
+                            int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse],
+                            {"auto": 0, "explicit": 1, "implicit": 2}[local_form])
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

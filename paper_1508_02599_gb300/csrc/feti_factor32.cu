@@ -329,7 +329,9 @@ __global__ void k_row_resid(int n, const int32_t* __restrict__ row_sub, const Su
 
 // out (full local vectors) = the boundary vector loc at the boundary
 // positions [nI, n), zero on the interior.
-__global__ void k_place(const SubLayout* __restrict__ lay, const double* __restrict__ loc, double* __restrict__ out) {
+__global__ void k_place(const SubLayout* __restrict__ lay, const double* __restrict__ loc, double* __restrict__ out,
+                        const int* __restrict__ done) {
+  if (done && *done) return;
   const SubLayout L = lay[blockIdx.x];
   for (int i = threadIdx.x; i < L.n; i += blockDim.x)
     out[L.voff + i] = i < L.nI ? 0.0 : loc[L.boff + i - L.nI];
@@ -420,8 +422,8 @@ void launch_kresid2(int n_el, int nde, const int32_t* elem_sub, const int32_t* r
   if (n_rows > 0) k_row_resid<<<(int)b, kT, 0, st>>>(n_rows, row_sub, lay, kinc_ptr, kinc, ye, g, r);
 }
 
-void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st) {
-  k_place<<<P, kT, 0, st>>>(lay, loc, out);
+void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st, const int* done) {
+  k_place<<<P, kT, 0, st>>>(lay, loc, out, done);
 }
 
 void launch_sub_norm2(int P, const SubLayout* lay, const double* r, const double* g, double* out, cudaStream_t st) {

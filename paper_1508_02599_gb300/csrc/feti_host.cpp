@@ -199,6 +199,8 @@ struct feti_ctx {
   // x_b = F_i z_b (FP64) at the boundary offsets
   float *d_kyI = nullptr, *d_kzb = nullptr;
   double* d_kxb = nullptr;
+  // implicit local form: the placed boundary vector and K^+ of it (full local vectors)
+  double *d_ix = nullptr, *d_ix2 = nullptr;
   // two-pass FP64 residual: subdomain of each element and of each local row,
   // and the per-(element, row) products K_e x_e
   int32_t *d_elem_sub = nullptr, *d_row_sub = nullptr;
@@ -1767,6 +1769,14 @@ void gemv_apply(feti_ctx* ctx, int which, const int* done, bool f32, const void*
 // Signed gather of x (weights wv or none) and the dense local apply of F_i
 // (which 0) or the preconditioner block (which 1) into d_loc.
 void local_apply(feti_ctx* ctx, int which, const double* x, const double* wv, const int* done, bool f32) {
+  if (which == 0 && !f32 && ctx->opt.local_form == 2) {
+    // implicit: y_b = [K^+ (0 ; B^T x)]_b by the triangular sweeps of the factor
+    feti::launch_gather(ctx->maps, x, wv, ctx->d_vloc, done, ctx->stream);
+    feti::launch_place(ctx->P, ctx->d_lay, ctx->d_vloc, ctx->d_ix, ctx->stream, done);
+    feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, ctx->d_ix, ctx->d_ix2, ctx->stream, done);
+    feti::launch_take_boundary(ctx->P, ctx->d_lay, ctx->d_ix2, ctx->d_loc, ctx->stream, done);
+    return;
+  }
   if (f32)
     feti::launch_gather32(ctx->maps, x, wv, ctx->d_vloc32, done, ctx->stream);
   else
@@ -2080,6 +2090,10 @@ feti_status alloc_operators(feti_ctx* ctx) {
       FETI_TRY(dev_alloc(ctx, &ctx->d_sym_err, 1));
       FETI_CK(cudaMemsetAsync(ctx->d_sym_err, 0, sizeof(int), ctx->stream));
     }
+  }
+  if (ctx->opt.local_form == 2) {
+    FETI_TRY(dev_alloc(ctx, &ctx->d_ix, (size_t)ctx->nloc_total));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_ix2, (size_t)ctx->nloc_total));
   }
   return FETI_OK;
 }
@@ -2747,6 +2761,9 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   if (opt->precision != FETI_FP64 && opt->precision != FETI_MIXED && opt->precision != FETI_MIXED_F32FACTOR)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported precision");
   if (opt->coarse_form < 0 || opt->coarse_form > 2) return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported coarse_form");
+  if (opt->local_form < 0 || opt->local_form > 2) return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported local_form");
+  if (opt->local_form == 2 && opt->precision != FETI_FP64)
+    return fail(ctx, FETI_ERR_INVALID_ARG, "the implicit local form needs FETI_FP64");
   if (!(opt->tol > 0.0) || opt->maxit <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "tol and maxit must be positive");
   if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE && mat->kind != FETI_LINEAR_ISO_P0)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown material");
@@ -3315,7 +3332,17 @@ feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z
     cudaGraph_t g = nullptr;
     FETI_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const bool f32 = f32_ops(ctx);
+    const bool implicit = !f32 && ctx->opt.local_form == 2;
     for (int i = 0; i < n_apply; ++i) {
+      if (implicit) {
+        // the timed span is the whole implicit local apply (gather, sweeps, boundary take)
+        FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[2 + 2 * i], st, cudaEventRecordExternal));
+        local_apply(ctx, 0, v, nullptr, zero, false);
+        FETI_CK(cudaEventRecordWithFlags(ctx->dual_events[3 + 2 * i], st, cudaEventRecordExternal));
+        feti::launch_scatter(ctx->maps, ctx->d_loc, nullptr, q, nullptr, nullptr, zero, st);
+        apply_M(ctx, q, z, zero, f32);
+        continue;
+      }
       if (f32)
         feti::launch_gather32(ctx->maps, v, nullptr, ctx->d_vloc32, zero, st);
       else

@@ -93,7 +93,8 @@ void launch_augment(int P, const SubLayout* lay, float* A, cudaStream_t st);
 // or minus the augmentation block into F (which=1).
 void launch_extract(int P, const SubLayout* lay, int which, const double* A, double* out, cudaStream_t st);
 // x = K_i^+ g per subdomain (fixing-DOF generalized inverse; zero on fixing DOFs).
-void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st);
+void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st,
+                  const int* done = nullptr);
 
 // Multiplier maps ----------------------------------------------------------
 struct Maps {
@@ -156,7 +157,8 @@ namespace feti {
 void launch_rtx(int P, const SubLayout* lay, const double* R, const double* x, double scale, double* e,
                 cudaStream_t st);
 // loc_b = boundary slice of the full local vectors x.
-void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st);
+void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st,
+                          const int* done = nullptr);
 // rhs_i = f_i - (boundary vector loc placed at the boundary positions).
 void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
                       cudaStream_t st);
@@ -321,7 +323,8 @@ void launch_kresid2(int n_el, int nde, const int32_t* elem_sub, const int32_t* r
                     const int32_t* kinc_ptr, const int32_t* kinc, const int32_t* elem_dense, const double* Ke,
                     const double* g, const double* x, double* ye, double* r, cudaStream_t st);
 // out = boundary vector loc placed at the boundary positions, zero interior.
-void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st);
+void launch_place(int P, const SubLayout* lay, const double* loc, double* out, cudaStream_t st,
+                  const int* done = nullptr);
 // out[2 s], out[2 s + 1] = squared norms of r and g over rows [0, nI + nbp) of subdomain s.
 void launch_sub_norm2(int P, const SubLayout* lay, const double* r, const double* g, double* out, cudaStream_t st);
 // x[i] = deterministic pseudo-random value in [-1, 1).

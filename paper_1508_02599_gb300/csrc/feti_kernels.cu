@@ -513,7 +513,9 @@ __global__ void k_extract(const SubLayout* __restrict__ lay, int which, const do
 // the unsolved part.  The fixing DOFs get zero.
 __global__ void __launch_bounds__(kThreads) k_kplus(const SubLayout* __restrict__ lay,
                                                     const double* __restrict__ Abase,
-                                                    const double* __restrict__ gbase, double* __restrict__ xbase) {
+                                                    const double* __restrict__ gbase, double* __restrict__ xbase,
+                                                    const int* __restrict__ done) {
+  if (done && *done) return;
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
   const double* A = Abase + L.aoff;
@@ -1470,7 +1472,8 @@ __global__ void __launch_bounds__(kThreads) k_rtx(const SubLayout* __restrict__ 
 }
 
 __global__ void k_take_boundary(const SubLayout* __restrict__ lay, const double* __restrict__ xbase,
-                                double* __restrict__ loc) {
+                                double* __restrict__ loc, const int* __restrict__ done) {
+  if (done && *done) return;
   const int s = blockIdx.x;
   const SubLayout L = lay[s];
   for (int p = threadIdx.x; p < L.nbp + L.k; p += blockDim.x) loc[L.boff + p] = xbase[L.voff + L.nI + p];
@@ -1578,8 +1581,9 @@ void launch_extract(int P, const SubLayout* lay, int which, const double* A, dou
   k_extract<<<P, kThreads, 0, st>>>(lay, which, A, out);
 }
 
-void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st) {
-  k_kplus<<<P, kThreads, 0, st>>>(lay, A, g, x);
+void launch_kplus(int P, const SubLayout* lay, const double* A, const double* g, double* x, cudaStream_t st,
+                  const int* done) {
+  k_kplus<<<P, kThreads, 0, st>>>(lay, A, g, x, done);
 }
 
 void launch_gather(const Maps& mp, const double* x, const double* wv, double* y, const int* done,
@@ -1637,8 +1641,9 @@ void launch_rtx(int P, const SubLayout* lay, const double* R, const double* x, d
                 cudaStream_t st) {
   k_rtx<<<P, kThreads, 0, st>>>(lay, R, x, scale, e);
 }
-void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st) {
-  k_take_boundary<<<P, kThreads, 0, st>>>(lay, x, loc);
+void launch_take_boundary(int P, const SubLayout* lay, const double* x, double* loc, cudaStream_t st,
+                          const int* done) {
+  k_take_boundary<<<P, kThreads, 0, st>>>(lay, x, loc, done);
 }
 void launch_local_sub(int P, const SubLayout* lay, const double* f, const double* loc, double* out,
                       cudaStream_t st) {
