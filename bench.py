@@ -276,6 +276,7 @@ def main():
             U, rep = solver.solve()      # full hot path once: setup + PCG + recovery
         sizes = solver.sizes()
         sizes["coarse"] = solver.coarse_info()
+        sizes["factor"] = solver.factor_info()
         nl = sizes["n_lambda"]
         g = torch.Generator(device="cuda").manual_seed(1234 + rank)
         v = torch.randn(nl, dtype=torch.float64, device="cuda", generator=g)
@@ -451,7 +452,12 @@ def main():
             "config": dict(workload_cfg, precision="FP32 local operators, FP64 vectors/projection/coarse/outer "
                                                     "residual", n_apply_per_step=args.n_apply,
                            n_lambda=m32["sizes"]["n_lambda"], coarse_dim=m32["sizes"]["coarse_dim"],
-                           coarse=m32["sizes"]["coarse"]),
+                           coarse=m32["sizes"]["coarse"],
+                           local_factor_storage={k: {**v, "workspace_gb": v["workspace"] * v["elem_bytes"] / 1e9,
+                                                     "full_workspace_gb": v["full_workspace"] * v["elem_bytes"] / 1e9,
+                                                     "compact_gb": v["compact"] * v["elem_bytes"] / 1e9}
+                                                 for k, v in (("fp32_local", m32["sizes"]["factor"]),
+                                                              ("fp64", m64["sizes"]["factor"]))}),
             "pcg": {"tol": 1e-8,
                     "fp32_local": {"time_to_tol_ms": r32["t_pcg_ms"], "inner_iterations": r32["iterations"],
                                    "outer_iterations": r32["outer_iterations"], "rel_err_vs_fp64": err},

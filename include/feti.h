@@ -176,6 +176,16 @@ typedef struct {
                                sweeps over the local Cholesky factor on the placed boundary
                                vector every iteration, the paper's sparse-direct form (FETI_FP64
                                only; the block form and the preconditioner stay explicit) */
+  int32_t workspace_mb;     /* device memory of the dense elimination workspace (Sec. 4.4: the
+                               local factorizations and the Schur complements S_i, F_i): the
+                               subdomains are eliminated in consecutive groups whose (n + n_b')^2
+                               matrices fit this many MiB (at least one subdomain per group), one
+                               workspace reused by every group, and after each group the
+                               interior columns of its factor (L_II, L_bI) are copied into a
+                               compact array that the K^+ solves use (the boundary block of K^+
+                               through the explicit F_i).  0 = automatic (12288 MiB), -1 = one
+                               group holding every subdomain.  The implicit local form keeps the
+                               whole factor (one group). */
 } feti_options;
 
 typedef struct {
@@ -284,6 +294,14 @@ feti_status feti_get_sizes(const feti_ctx* ctx, int64_t out[5]);
  * sweep, out[5] doubles of the factorization workspace (held only during
  * set-up); for the dense form out[3] = coarse_dim^2. */
 feti_status feti_get_coarse_info(const feti_ctx* ctx, int64_t out[6]);
+
+/* Storage of the local factorizations (Sec. 4.4) chosen at feti_create:
+ * out[0] groups of subdomains eliminated one after another in the reused
+ * workspace, out[1] elements of that workspace, out[2] elements the whole
+ * dense workspace would take (every subdomain at once), out[3] elements of the
+ * compact interior factor kept for the K^+ solves (0 when the whole factor is
+ * kept), out[4] bytes per element (8 FP64, 4 FP32 factorizations). */
+feti_status feti_get_factor_info(const feti_ctx* ctx, int64_t out[5]);
 
 /* Multiplier rows in canonical order (Sec. 4.1, Fig. 3a, fully redundant):
  * interface rows by (global node, component, subdomain pair i<j) with +1 on

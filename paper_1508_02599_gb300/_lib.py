@@ -43,7 +43,7 @@ class FetiOptions(C.Structure):
                 ("n_load_steps", C.c_int32), ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("no_tensor_cores", C.c_int32),
                 ("per_subdomain", C.c_int32), ("symmetric", C.c_int32), ("spin_timeout_ns", C.c_uint64),
-                ("coarse_form", C.c_int32), ("local_form", C.c_int32)]
+                ("coarse_form", C.c_int32), ("local_form", C.c_int32), ("workspace_mb", C.c_int32)]
 
 
 class FetiCheckpointInfo(C.Structure):
@@ -59,6 +59,7 @@ class FetiReport(C.Structure):
 
 EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_newton_steps",
            "feti_checkpoint_write", "feti_checkpoint_read", "feti_elements", "feti_get_sizes", "feti_get_coarse_info",
+           "feti_get_factor_info",
            "feti_get_index_maps",
            "feti_get_fixing", "feti_dual_apply", "feti_dual_apply_multi", "feti_dual_apply_noalloc", "feti_prepare", "feti_kernel_stats", "feti_element_stats", "feti_get_schedule",
            "feti_set_spin_timeout", "feti_get_refinement", "feti_last_error",
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
     lib.feti_checkpoint_read.argtypes = [C.c_char_p, vp, C.c_int64, C.POINTER(FetiCheckpointInfo)]
     lib.feti_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.feti_get_coarse_info.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.feti_get_factor_info.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.feti_elements.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32]
     lib.feti_get_index_maps.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.feti_get_fixing.argtypes = [vp, vp, vp]

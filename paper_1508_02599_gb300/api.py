@@ -40,7 +40,7 @@ class FetiSolver:
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
                  tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0,
-                 coarse: str = "auto", local_form: str = "auto"):
+                 coarse: str = "auto", local_form: str = "auto", workspace_mb: int = 0):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -78,7 +78,7 @@ class FetiSolver:
                              "force_persist": 8, "force_persist_q3": 9, "force_persist_c3": 10}[tensor_cores],
                             int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
                             int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse],
-                            {"auto": 0, "explicit": 1, "implicit": 2}[local_form])
+                            {"auto": 0, "explicit": 1, "implicit": 2}[local_form], int(workspace_mb))
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))
@@ -121,6 +121,15 @@ class FetiSolver:
         v = list(out)
         return {"form": ["none", "dense", "sparse"][v[0]], "supernodes": v[1], "height": v[2],
                 "factor_entries": v[3], "tasks": v[4], "workspace": v[5]}
+
+    def factor_info(self) -> dict:
+        """Storage of the local factorizations: groups eliminated one after
+        another in the reused workspace, its elements, the elements of the
+        whole dense workspace, the compact interior factor's elements (0 when
+        the whole factor is kept) and bytes per element."""
+        out = (C.c_int64 * 5)()
+        self._check(self._lib.feti_get_factor_info(self._ctx, out))
+        return dict(zip(["groups", "workspace", "full_workspace", "compact", "elem_bytes"], list(out)))
 
     def index_maps(self) -> dict:
         n = self.sizes()["n_lambda"]

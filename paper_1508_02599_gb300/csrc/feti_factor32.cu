@@ -25,11 +25,6 @@ namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ float f32_warp_sum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // The dense local operators out of the eliminated workspace in one pass, one
 // CTA per 32 x 32 output tile (I, J) of one subdomain: the source tile
 // (max(I,J), min(I,J)) of the workspace's lower triangle is read row by row
@@ -87,140 +82,152 @@ __global__ void __launch_bounds__(256) k_extract_tiles(const SubLayout* __restri
 // and F_i = S_i[b',b']^-1 is the explicit FP32 operator the PCG already
 // applies.  The dependent 32-row block chains shrink from n_I + n_b' rows to
 // n_I rows; the boundary panel products carry no chain.
-// k_kp_forward: y_I (FP32, into yI at the subdomain's local offset) and z_b
-// (FP32, into zb at the boundary offset; zero on the fixing positions).
-__global__ void __launch_bounds__(kT, 8) k_kp_forward(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
-                                                  const double* __restrict__ rbase, float* __restrict__ yIbase,
-                                                  float* __restrict__ zb) {
-  extern __shared__ float ys[];
+// k_kp_forward: y_I (into yI at the subdomain's local offset) and z_b (into
+// zb at the boundary offset; zero on the fixing positions), in the factor's
+// precision T.  Both kernels read the compact interior factor (rows
+// [0, n_I + n_b') x columns [0, n_I) at L.loff, row stride kp_ld).
+template <typename T>
+__device__ __forceinline__ T kp_warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
+    k_kp_forward(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const double* __restrict__ rbase,
+                 T* __restrict__ yIbase, T* __restrict__ zb) {
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  T* ys = reinterpret_cast<T*>(kp_smem);
   const SubLayout L = lay[blockIdx.x];
-  const float* A = Abase + L.aoff;
-  const size_t ld = L.ld;
+  const T* A = Lbase + L.loff;
+  const size_t ld = kp_ld(L);
   const double* r = rbase + L.voff;
   const int nI = L.nI, nbp = L.nbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kW = kT / 32;
-  __shared__ float D[32][33];
-  __shared__ float t[32];
-  for (int i = tid; i < nI; i += kT) ys[i] = (float)r[i];
+  __shared__ T D[32][33];
+  __shared__ T t[32];
+  for (int i = tid; i < nI; i += kT) ys[i] = (T)r[i];
   __syncthreads();
   for (int I0 = 0; I0 < nI; I0 += 32) {
     const int nb = min(32, nI - I0);
     for (int idx = tid; idx < 32 * 32; idx += kT) {
       const int rr = idx >> 5, c = idx & 31;
-      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
+      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : (T)0;
     }
     {
-      const float* rp = A + (size_t)I0 * ld;
+      const T* rp = A + (size_t)I0 * ld;
       int ro[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nb - 1) * (int)ld;
-      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      T acc[4] = {0, 0, 0, 0};
       int j = lane;
       for (; j + 96 < I0; j += 128) {
-        float a[4][4];
+        T a[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float yv = ys[j + 32 * u];
+          const T yv = ys[j + 32 * u];
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
         }
       }
       for (; j < I0; j += 32) {
-        const float yv = ys[j];
+        const T yv = ys[j];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float v = f32_warp_sum(acc[q]);
+        const T v = kp_warp_sum(acc[q]);
         if (lane == 0 && warp + kW * q < nb) t[warp + kW * q] = v;
       }
     }
     __syncthreads();
     if (warp == 0) {
-      float b = lane < nb ? ys[I0 + lane] - t[lane] : 0.0f;
-      float xv = 0.0f;
+      T b = lane < nb ? ys[I0 + lane] - t[lane] : (T)0;
+      T xv = 0;
       for (int c = 0; c < nb; ++c) {
         if (lane == c) xv = b / D[c][c];
-        const float xc = __shfl_sync(0xffffffffu, xv, c);
+        const T xc = __shfl_sync(0xffffffffu, xv, c);
         if (lane > c) b -= D[lane][c] * xc;
       }
       if (lane < nb) ys[I0 + lane] = xv;
     }
     __syncthreads();
   }
-  float* yI = yIbase + L.voff;
+  T* yI = yIbase + L.voff;
   for (int i = tid; i < nI; i += kT) yI[i] = ys[i];
   // z_b = r_b - L_bI y_I: warp w takes boundary rows w, w + 8, w + 16, w + 24
   // (then the next 32), four column strides at a time
   for (int p0 = 0; p0 < nbp; p0 += 4 * kW) {
-    const float* rp = A + (size_t)(nI + p0) * ld;
+    const T* rp = A + (size_t)(nI + p0) * ld;
     int ro[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nbp - 1 - p0) * (int)ld;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    T acc[4] = {0, 0, 0, 0};
     int j = lane;
     for (; j + 96 < nI; j += 128) {
-      float a[4][4];
+      T a[4][4];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float yv = ys[j + 32 * u];
+        const T yv = ys[j + 32 * u];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
       }
     }
     for (; j < nI; j += 32) {
-      const float yv = ys[j];
+      const T yv = ys[j];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float v = f32_warp_sum(acc[q]);
+      const T v = kp_warp_sum(acc[q]);
       const int p = p0 + warp + kW * q;
-      if (lane == 0 && p < nbp) zb[L.boff + p] = (float)(r[nI + p] - (double)v);
+      if (lane == 0 && p < nbp) zb[L.boff + p] = (T)(r[nI + p] - (double)v);
     }
   }
-  for (int p = nbp + tid; p < nbp + L.k; p += kT) zb[L.boff + p] = 0.0f;
+  for (int p = nbp + tid; p < nbp + L.k; p += kT) zb[L.boff + p] = (T)0;
 }
 
 // k_kp_backward: t_I = y_I - L_bI^T x_b, x_I = L_II^-T t_I; then x (+)= x on
 // rows [0, n_I + n_b') (x_b from the F_i apply, FP64 at the boundary offset),
 // and with init x = that correction, zero on the fixing rows.
-__global__ void __launch_bounds__(kT, 8) k_kp_backward(const SubLayout* __restrict__ lay, const float* __restrict__ Abase,
-                                                   const float* __restrict__ yIbase, const double* __restrict__ xb,
-                                                   double* __restrict__ xbase, int init) {
-  extern __shared__ float ys[];
+template <typename T>
+__global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
+    k_kp_backward(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const T* __restrict__ yIbase,
+                  const double* __restrict__ xb, double* __restrict__ xbase, int init) {
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  T* ys = reinterpret_cast<T*>(kp_smem);
   const SubLayout L = lay[blockIdx.x];
-  const float* A = Abase + L.aoff;
-  const size_t ld = L.ld;
+  const T* A = Lbase + L.loff;
+  const size_t ld = kp_ld(L);
   double* x = xbase + L.voff;
   const int nI = L.nI, nbp = L.nbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ float D[32][33];
-  __shared__ float xs[32];
-  float* xbs = ys + nI;  // x_b in FP32 after the interior part
-  const float* yI = yIbase + L.voff;
+  __shared__ T D[32][33];
+  __shared__ T xs[32];
+  T* xbs = ys + nI;  // x_b in precision T after the interior part
+  const T* yI = yIbase + L.voff;
   for (int i = tid; i < nI; i += kT) ys[i] = yI[i];
-  for (int p = tid; p < nbp; p += kT) xbs[p] = (float)xb[L.boff + p];
+  for (int p = tid; p < nbp; p += kT) xbs[p] = (T)xb[L.boff + p];
   __syncthreads();
   // t_I = y_I - L_bI^T x_b: thread per interior column, 16 boundary rows per step
   {
-    const float* Pb = A + (size_t)nI * ld;
+    const T* Pb = A + (size_t)nI * ld;
     for (int j = tid; j < nI; j += kT) {
-      float acc = 0.0f;
+      T acc = 0;
       int p = 0;
       for (; p + 16 <= nbp; p += 16) {
-        float a[16];
+        T a[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) a[u] = __ldg(Pb + (size_t)(p + u) * ld + j);
 #pragma unroll
@@ -235,32 +242,32 @@ __global__ void __launch_bounds__(kT, 8) k_kp_backward(const SubLayout* __restri
     const int nb = min(32, nI - I0);
     for (int idx = tid; idx < 32 * 32; idx += kT) {
       const int rr = idx >> 5, c = idx & 31;
-      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : 0.0f;
+      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : (T)0;
     }
     __syncthreads();
     if (warp == 0) {
-      float b = lane < nb ? ys[I0 + lane] : 0.0f;
-      float xv = 0.0f;
+      T b = lane < nb ? ys[I0 + lane] : (T)0;
+      T xv = 0;
       for (int c = nb - 1; c >= 0; --c) {
         if (lane == c) xv = b / D[c][c];
-        const float xc = __shfl_sync(0xffffffffu, xv, c);
+        const T xc = __shfl_sync(0xffffffffu, xv, c);
         if (lane < c) b -= D[c][lane] * xc;
       }
       if (lane < nb) ys[I0 + lane] = xv;
-      xs[lane] = lane < nb ? xv : 0.0f;
+      xs[lane] = lane < nb ? xv : (T)0;
     }
     __syncthreads();
     if (nb == 32) {
       for (int j = tid; j < I0; j += kT) {
-        const float* col = A + (size_t)I0 * ld + j;
-        float acc = 0.0f;
+        const T* col = A + (size_t)I0 * ld + j;
+        T acc = 0;
 #pragma unroll 16
         for (int rr = 0; rr < 32; ++rr) acc += col[(size_t)rr * ld] * xs[rr];
         ys[j] -= acc;
       }
     } else {
       for (int j = tid; j < I0; j += kT) {
-        float acc = 0.0f;
+        T acc = 0;
         for (int rr = 0; rr < nb; ++rr) acc += A[(size_t)(I0 + rr) * ld + j] * xs[rr];
         ys[j] -= acc;
       }
@@ -271,6 +278,26 @@ __global__ void __launch_bounds__(kT, 8) k_kp_backward(const SubLayout* __restri
   for (int p = tid; p < nbp; p += kT) x[nI + p] = (init ? 0.0 : x[nI + p]) + xb[L.boff + p];
   if (init)
     for (int i = nI + nbp + tid; i < L.n; i += kT) x[i] = 0.0;
+}
+
+// Compact interior factor: one CTA per 32 rows of one subdomain, a warp per
+// row, lanes along the columns (coalesced on both sides).
+template <typename T>
+__global__ void __launch_bounds__(256) k_compact_factor(const SubLayout* __restrict__ lay, const T* __restrict__ Abase,
+                                                        T* __restrict__ Lbase) {
+  const SubLayout L = lay[blockIdx.y];
+  const int rows = L.nI + L.nbp;
+  const int r0 = blockIdx.x * 32;
+  if (r0 >= rows) return;
+  const int ldo = kp_ld(L);
+  const size_t ld = L.ld;
+  const T* A = Abase + L.aoff;
+  T* out = Lbase + L.loff;
+  for (int r = r0 + (threadIdx.x >> 5); r < min(r0 + 32, rows); r += 8) {
+    const int cmax = r < L.nI ? r : L.nI - 1;  // L_II lower triangle, L_bI whole rows
+    for (int c = threadIdx.x & 31; c < ldo; c += 32)
+      out[(size_t)r * ldo + c] = c <= cmax ? A[(size_t)r * ld + c] : (T)0;
+  }
 }
 
 // r = g - K_rr x in FP64 on the rows [0, n_I + n_b') (zero on the fixing
@@ -394,18 +421,49 @@ void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, con
   if (P > 0 && nT > 0) k_extract_tiles<double><<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out64, out32, sym32);
 }
 
-void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,
-                       cudaStream_t st) {
-  const size_t smem = (size_t)max_nr * sizeof(float);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_kp_forward<<<P, kT, smem, st>>>(lay, A, r, yI, zb);
+template <typename T>
+void kp_forward(int P, const SubLayout* lay, const T* Lc, const double* r, T* yI, T* zb, int max_nr, cudaStream_t st) {
+  const size_t smem = (size_t)max_nr * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (P > 0) k_kp_forward<T><<<P, kT, smem, st>>>(lay, Lc, r, yI, zb);
 }
 
-void launch_kp_backward(int P, const SubLayout* lay, const float* A, const float* yI, const double* xb, double* x,
+template <typename T>
+void kp_backward(int P, const SubLayout* lay, const T* Lc, const T* yI, const double* xb, double* x, int init,
+                 int max_nr, cudaStream_t st) {
+  const size_t smem = (size_t)max_nr * sizeof(T);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (P > 0) k_kp_backward<T><<<P, kT, smem, st>>>(lay, Lc, yI, xb, x, init);
+}
+
+void launch_kp_forward(int P, const SubLayout* lay, const float* Lc, const double* r, float* yI, float* zb, int max_nr,
+                       cudaStream_t st) {
+  kp_forward<float>(P, lay, Lc, r, yI, zb, max_nr, st);
+}
+
+void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, const float* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st) {
-  const size_t smem = (size_t)max_nr * sizeof(float);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_kp_backward<<<P, kT, smem, st>>>(lay, A, yI, xb, x, init);
+  kp_backward<float>(P, lay, Lc, yI, xb, x, init, max_nr, st);
+}
+
+void launch_kp_forward(int P, const SubLayout* lay, const double* Lc, const double* r, double* yI, double* zb,
+                       int max_nr, cudaStream_t st) {
+  kp_forward<double>(P, lay, Lc, r, yI, zb, max_nr, st);
+}
+
+void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, const double* yI, const double* xb, double* x,
+                        int init, int max_nr, cudaStream_t st) {
+  kp_backward<double>(P, lay, Lc, yI, xb, x, init, max_nr, st);
+}
+
+void launch_compact_factor(int P, int max_rows, const SubLayout* lay, const double* A, double* Lc, cudaStream_t st) {
+  const int nt = (max_rows + 31) / 32;
+  if (P > 0 && nt > 0) k_compact_factor<double><<<dim3(nt, P), 256, 0, st>>>(lay, A, Lc);
+}
+
+void launch_compact_factor(int P, int max_rows, const SubLayout* lay, const float* A, float* Lc, cudaStream_t st) {
+  const int nt = (max_rows + 31) / 32;
+  if (P > 0 && nt > 0) k_compact_factor<float><<<dim3(nt, P), 256, 0, st>>>(lay, A, Lc);
 }
 
 void launch_kresid2(int n_el, int nde, const int32_t* elem_sub, const int32_t* row_sub, int n_rows, const SubLayout* lay,

@@ -160,13 +160,29 @@ struct feti_ctx {
   // interior elimination restricted to the envelope: per step and subdomain
   // the end eI of the interior rows and the count nbact of boundary rows that
   // the step's block column can reach ([step][subdomain][2])
-  int steps0 = 0;
+  // ([step][subdomain of the group][2] per elimination group, the groups'
+  // tables one after another from env_off[g])
   std::vector<int32_t> env0;
+  std::vector<int64_t> env_off;
   int32_t* d_env0 = nullptr;
   // the same for the FP32 elimination's kChol32Block-column steps
-  int steps0_32 = 0;
   std::vector<int32_t> env0_32;
+  std::vector<int64_t> env32_off;
   int32_t* d_env0_32 = nullptr;
+  // local factorizations in groups: subdomains [grp[g], grp[g + 1]) are
+  // eliminated together in the one workspace d_A / d_A32 of ws_elems
+  // elements (ws_full: every subdomain at once); d_lay_ws holds the layouts
+  // with aoff relative to the group's first matrix.  keep_factor: the whole
+  // factor stays (implicit local form; one group, no compact copy), else the
+  // compact interior factor d_Lc / d_Lc32 (lc_elems) serves every K^+.
+  std::vector<int32_t> grp;
+  SubLayout* d_lay_ws = nullptr;
+  int64_t ws_elems = 0, ws_full = 0, lc_elems = 0;
+  bool keep_factor = false;
+  double* d_Lc = nullptr;
+  float* d_Lc32 = nullptr;
+  double *d_kyI64 = nullptr, *d_kzb64 = nullptr;  // FP64 K^+: y_I and z_b
+  std::vector<int64_t> lump_grp;  // first lumped-preconditioner entry of each group
   double gemv_ms = 0.0, gemv_bytes = 0.0, gemv_flops = 0.0;
   double elem_ms = 0.0, elem_bytes = 0.0;
   // sizes (elements) of d_A, d_S, d_F, d_F32, d_S32, d_F32s, d_S32s, d_symp
@@ -837,27 +853,67 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   lg.mark("create: kernels, fixing, dense order");
   ctx->nb_total = boff;
-  // envelope table of the interior elimination, [step][subdomain][2]
-  ctx->steps0 = 0;
-  for (int s = 0; s < P; ++s) ctx->steps0 = std::max(ctx->steps0, (int)env0[s].size() / 2);
-  ctx->env0.assign(2 * (size_t)ctx->steps0 * P, 0);
-  for (int s = 0; s < P; ++s)
-    for (size_t t = 0; t < env0[s].size() / 2; ++t) {
-      ctx->env0[2 * (t * P + s)] = env0[s][2 * t];
-      ctx->env0[2 * (t * P + s) + 1] = env0[s][2 * t + 1];
+  // compact interior factor: rows [0, nI + nbp) x columns [0, nI) per subdomain
+  {
+    int64_t lo = 0;
+    for (auto& L : ctx->lay) {
+      L.loff = lo;
+      lo += (int64_t)(L.nI + L.nbp) * feti::kp_ld(L);
     }
+    ctx->lc_elems = lo;
+  }
+  // elimination groups: consecutive subdomains whose dense matrices fit the
+  // workspace budget (at least one per group)
+  {
+    ctx->keep_factor = ctx->opt.local_form == 2;
+    const int64_t esz = ctx->opt.precision == FETI_MIXED_F32FACTOR ? 4 : 8;
+    const int64_t mb = ctx->opt.workspace_mb == 0 ? 12288 : ctx->opt.workspace_mb;
+    const int64_t cap = (ctx->keep_factor || mb < 0) ? INT64_MAX : (mb << 20) / esz;
+    ctx->grp.assign(1, 0);
+    ctx->ws_full = aoff;
+    ctx->ws_elems = 0;
+    int64_t acc = 0;
+    for (int s = 0; s < P; ++s) {
+      const int64_t m = (int64_t)ctx->lay[s].ld * ctx->lay[s].ld;
+      if (acc > 0 && acc + m > cap) {
+        ctx->grp.push_back(s);
+        acc = 0;
+      }
+      acc += m;
+      ctx->ws_elems = std::max(ctx->ws_elems, acc);
+    }
+    ctx->grp.push_back(P);
+  }
+  const int n_grp = (int)ctx->grp.size() - 1;
+  std::vector<SubLayout> lay_ws(ctx->lay);
+  for (int g = 0; g < n_grp; ++g)
+    for (int s = ctx->grp[g]; s < ctx->grp[g + 1]; ++s) lay_ws[s].aoff -= ctx->lay[ctx->grp[g]].aoff;
+  FETI_TRY(upload(ctx, &ctx->d_lay_ws, lay_ws));
+  // envelope tables of the interior elimination, [step][subdomain of the group][2] per group
+  auto env_tables = [&](const std::vector<std::vector<int32_t>>& ev, std::vector<int32_t>& tab,
+                        std::vector<int64_t>& off) {
+    tab.clear();
+    off.assign(n_grp, 0);
+    for (int g = 0; g < n_grp; ++g) {
+      const int s0 = ctx->grp[g], pg = ctx->grp[g + 1] - s0;
+      int steps = 0;
+      for (int s = s0; s < s0 + pg; ++s) steps = std::max(steps, (int)ev[s].size() / 2);
+      off[g] = (int64_t)tab.size();
+      tab.resize(tab.size() + 2 * (size_t)steps * pg, 0);
+      for (int s = s0; s < s0 + pg; ++s)
+        for (size_t t = 0; t < ev[s].size() / 2; ++t) {
+          tab[off[g] + 2 * (t * pg + (s - s0))] = ev[s][2 * t];
+          tab[off[g] + 2 * (t * pg + (s - s0)) + 1] = ev[s][2 * t + 1];
+        }
+    }
+  };
+  env_tables(env0, ctx->env0, ctx->env_off);
   FETI_TRY(upload(ctx, &ctx->d_env0, ctx->env0));
   if (ctx->opt.precision == FETI_MIXED_F32FACTOR) {
-    ctx->steps0_32 = 0;
-    for (int s = 0; s < P; ++s) ctx->steps0_32 = std::max(ctx->steps0_32, (int)env0w[s].size() / 2);
-    ctx->env0_32.assign(2 * (size_t)ctx->steps0_32 * P, 0);
-    for (int s = 0; s < P; ++s)
-      for (size_t t = 0; t < env0w[s].size() / 2; ++t) {
-        ctx->env0_32[2 * (t * P + s)] = env0w[s][2 * t];
-        ctx->env0_32[2 * (t * P + s) + 1] = env0w[s][2 * t + 1];
-      }
+    env_tables(env0w, ctx->env0_32, ctx->env32_off);
     FETI_TRY(upload(ctx, &ctx->d_env0_32, ctx->env0_32));
   }
+  for (const auto& L : ctx->lay) ctx->max_nr = std::max(ctx->max_nr, L.nI + L.nbp);
   ctx->nloc_total = voff;
   ctx->cd = coff;
   // dense position lookup per subdomain: local DOF -> dense index
@@ -962,7 +1018,6 @@ feti_status build_decomposition(feti_ctx* ctx) {
       FETI_TRY(upload(ctx, &ctx->d_elem_sub, es));
       FETI_TRY(upload(ctx, &ctx->d_row_sub, rsub));
     }
-    for (const auto& L : ctx->lay) ctx->max_nr = std::max(ctx->max_nr, L.nI + L.nbp);
   }
   lg.mark("create:   refinement incidences");
   // lumped preconditioner: CSR pattern of K_bb over the global boundary
@@ -982,8 +1037,10 @@ feti_status build_decomposition(feti_ctx* ctx) {
         for (int y = 0; y < nbq; ++y) rows[L.boff + bp[x]].push_back(L.boff + bp[y]);
     }
     lump_ptr.assign(1, 0);
+    ctx->lump_grp.clear();
     for (int s = 0; s < P; ++s) {
-      const SubLayout& L = ctx->lay[s];
+      const SubLayout& L = lay_ws[s];
+      if (std::binary_search(ctx->grp.begin(), ctx->grp.end(), s)) ctx->lump_grp.push_back((int64_t)lump_col.size());
       for (int p = 0; p < L.nbp + L.k; ++p) {
         auto& r = rows[L.boff + p];
         std::sort(r.begin(), r.end());
@@ -998,6 +1055,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
       }
     }
     ctx->lump_nnz = (int64_t)lump_col.size();
+    ctx->lump_grp.push_back(ctx->lump_nnz);
   }
   // faces grouped by owning subdomain
   const int nf = ctx->n_press + ctx->n_trac;
@@ -1272,7 +1330,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   // the dense local operators (the bulk of the memory) are allocated by the
   // first setup, so that element-only use of a context does not hold them
-  ctx->op_elems[0] = aoff;
+  ctx->op_elems[0] = ctx->ws_elems;
   ctx->op_elems[1] = ctx->opt.precond == FETI_PREC_DIRICHLET ? soff : 1;
   ctx->op_elems[2] = foff;
   ctx->op_elems[3] = foff32;
@@ -1405,20 +1463,6 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
   const bool hgo = ctx->mat.kind == FETI_HGO_TWO_FIBRE;
   launch_elements(ctx, dU);
   FETI_CK(cudaGetLastError());
-  size_t abytes = 0;
-  for (const auto& L : ctx->lay) abytes += (size_t)L.ld * L.ld;
-  if (f32_factor(ctx)) {
-    FETI_CK(cudaMemsetAsync(ctx->d_A32, 0, abytes * sizeof(float), st));
-    feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
-                          ctx->nde, ctx->d_A32, st);
-    feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A32, st);
-  } else {
-    FETI_CK(cudaMemsetAsync(ctx->d_A, 0, abytes * sizeof(double), st));
-    feti::launch_assemble(ctx->P, ctx->d_lay, ctx->d_sub_elem_ptr, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke,
-                          ctx->nde, ctx->d_A, st);
-    if (ctx->shift > 0.0) feti::launch_shift_diag(ctx->P, ctx->d_lay, ctx->d_A, ctx->shift, st);
-    feti::launch_augment(ctx->P, ctx->d_lay, ctx->d_A, st);
-  }
   // face forces (grouped order; kind per face)
   const int nf = ctx->n_press + ctx->n_trac;
   if (nf > 0) {
@@ -1461,16 +1505,26 @@ void kresid(feti_ctx* ctx, const double* g, const double* x, double* r) {
 // sweeps confined to the interior rows and the boundary block through the
 // explicit FP32 F_i (the autotuned operator kernel of the PCG).
 void kplus_corr(feti_ctx* ctx, const double* r, double* x, bool init) {
-  feti::launch_kp_forward(ctx->P, ctx->d_lay, ctx->d_A32, r, ctx->d_kyI, ctx->d_kzb, ctx->max_nr, ctx->stream);
+  feti::launch_kp_forward(ctx->P, ctx->d_lay, ctx->d_Lc32, r, ctx->d_kyI, ctx->d_kzb, ctx->max_nr, ctx->stream);
   gemv_apply(ctx, 0, ctx->d_zero, true, ctx->d_kzb, ctx->d_kxb);
-  feti::launch_kp_backward(ctx->P, ctx->d_lay, ctx->d_A32, ctx->d_kyI, ctx->d_kxb, x, init ? 1 : 0, ctx->max_nr,
+  feti::launch_kp_backward(ctx->P, ctx->d_lay, ctx->d_Lc32, ctx->d_kyI, ctx->d_kxb, x, init ? 1 : 0, ctx->max_nr,
                            ctx->stream);
 }
 
+// FP64 factorizations: the whole factor kept (sweeps over all of it), or
+// K_rr^-1 by its block form from the compact interior factor and the FP64
+// F_i = S_i[b',b']^-1: y_I = L_II^-1 g_I, z_b = g_b - L_bI y_I, x_b = F_i z_b,
+// x_I = L_II^-T (y_I - L_bI^T x_b).
 void kplus(feti_ctx* ctx, const double* g, double* x) {
   cudaStream_t st = ctx->stream;
-  if (!f32_factor(ctx)) {
+  if (ctx->keep_factor) {
     feti::launch_kplus(ctx->P, ctx->d_lay, ctx->d_A, g, x, st);
+    return;
+  }
+  if (!f32_factor(ctx)) {
+    feti::launch_kp_forward(ctx->P, ctx->d_lay, ctx->d_Lc, g, ctx->d_kyI64, ctx->d_kzb64, ctx->max_nr, st);
+    gemv_apply(ctx, 0, ctx->d_zero, false, ctx->d_kzb64, ctx->d_kxb);
+    feti::launch_kp_backward(ctx->P, ctx->d_lay, ctx->d_Lc, ctx->d_kyI64, ctx->d_kxb, x, 1, ctx->max_nr, st);
     return;
   }
   kplus_corr(ctx, g, x, true);
@@ -1536,24 +1590,36 @@ feti_status tune_refinement(feti_ctx* ctx) {
 }
 
 // Local factorizations, dense local operators, coarse problem.
-feti_status factorize_all(feti_ctx* ctx) {
+// One elimination group in the workspace: assembly of the dense matrices,
+// interior elimination, S_i, boundary elimination, F_i, and the compact
+// interior factor.  T is the factorization's precision.
+template <typename T>
+void factorize_group(feti_ctx* ctx, int g, T* A, const std::vector<int32_t>& envt, const std::vector<int64_t>& eoff,
+                     const int32_t* d_env, int B, double* S64, float* S32,
+                     float* S32s, double* F64, float* F32, float* F32s, T* Lc) {
   cudaStream_t st = ctx->stream;
-  if (ctx->opt.precond == FETI_PREC_LUMPED) {
-    if (f32_factor(ctx))
-      feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A32, ctx->d_lump_val, st);
-    else
-      feti::launch_lump_fill(ctx->lump_nnz, ctx->d_lump_src, ctx->d_A, ctx->d_lump_val, st);
+  const int s0 = ctx->grp[g], pg = ctx->grp[g + 1] - s0;
+  const SubLayout* lw = ctx->d_lay_ws + s0;
+  int64_t elems = 0;
+  for (int s = s0; s < s0 + pg; ++s) elems += (int64_t)ctx->lay[s].ld * ctx->lay[s].ld;
+  cudaMemsetAsync(A, 0, (size_t)elems * sizeof(T), st);
+  feti::launch_assemble(pg, lw, ctx->d_sub_elem_ptr + s0, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke, ctx->nde,
+                        A, st);
+  if constexpr (sizeof(T) == 8) {
+    if (ctx->shift > 0.0) feti::launch_shift_diag(pg, lw, A, ctx->shift, st);
   }
-  // per step, the largest trailing chunk count over the subdomains (steps of
-  // 32 columns, kChol32Block in the FP32 elimination)
-  const bool f32f = f32_factor(ctx);
-  const int B = f32f ? feti::kChol32Block : 32;
-  const std::vector<int32_t>& envt = f32f ? ctx->env0_32 : ctx->env0;
+  feti::launch_augment(pg, lw, A, st);
+  if (ctx->opt.precond == FETI_PREC_LUMPED) {
+    const int64_t i0 = ctx->lump_grp[g], i1 = ctx->lump_grp[g + 1];
+    feti::launch_lump_fill((long)(i1 - i0), ctx->d_lump_src + i0, A, ctx->d_lump_val + i0, st);
+  }
+  // per step, the largest trailing chunk count over the group's subdomains
+  // (steps of B columns)
   std::vector<int> chunks[2];
   for (int phase = 0; phase < 2; ++phase)
-    for (const auto& L : ctx->lay) {
+    for (int s = s0; s < s0 + pg; ++s) {
+      const SubLayout& L = ctx->lay[s];
       const int c0 = phase == 0 ? 0 : L.nI, c1 = phase == 0 ? L.nI : L.nI + L.nbp;
-      const int s = (int)(&L - ctx->lay.data());
       for (int t = 0, kb = c0; kb < c1; ++t, kb += B) {
         const int r0 = kb + std::min(B, c1 - kb);
         // phase 0: the rows inside the envelope (interior rows up to eI, the
@@ -1561,7 +1627,7 @@ feti_status factorize_all(feti_ctx* ctx) {
         // rows plus the augmentation rows of the columns eliminated so far
         int m;
         if (phase == 0) {
-          const int32_t* ev = &envt[2 * ((size_t)t * ctx->P + s)];
+          const int32_t* ev = &envt[eoff[g] + 2 * ((size_t)t * pg + (s - s0))];
           m = (ev[0] - r0) + ev[1] + L.k;
         } else {
           m = std::min(L.ld, L.n + r0 - L.nI) - r0;
@@ -1571,30 +1637,34 @@ feti_status factorize_all(feti_ctx* ctx) {
         chunks[phase][t] = std::max(chunks[phase][t], ch);
       }
     }
-  if (f32f) {
+  feti::launch_chol_batched(pg, lw, 0, chunks[0].data(), (int)chunks[0].size(), d_env + eoff[g], A, ctx->d_status,
+                            st);
+  if (ctx->opt.precond == FETI_PREC_DIRICHLET)
+    feti::launch_extract_tiles(pg, ctx->max_nb, lw, 0, A, S64, S32, S32s, st);
+  feti::launch_chol_batched(pg, lw, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, A, ctx->d_status, st);
+  feti::launch_extract_tiles(pg, ctx->max_nb, lw, 1, A, F64, F32, F32s, st);
+  if (Lc) feti::launch_compact_factor(pg, ctx->max_nr, lw, A, Lc, st);
+}
+
+feti_status factorize_all(feti_ctx* ctx) {
+  const int n_grp = (int)ctx->grp.size() - 1;
+  if (f32_factor(ctx)) {
     // FP32 elimination; S_i and F_i go straight into the FP32 operator layouts
-    feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0_32,
-                              ctx->d_A32, ctx->d_status, st);
-    if (ctx->opt.precond == FETI_PREC_DIRICHLET)
-      feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 0, ctx->d_A32, nullptr, ctx->d_S32, ctx->d_S32s, st);
-    feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A32,
-                              ctx->d_status, st);
-    feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 1, ctx->d_A32, nullptr, ctx->d_F32, ctx->d_F32s, st);
+    for (int g = 0; g < n_grp; ++g)
+      factorize_group<float>(ctx, g, ctx->d_A32, ctx->env0_32, ctx->env32_off, ctx->d_env0_32,
+                             feti::kChol32Block, nullptr, ctx->d_S32, ctx->d_S32s, nullptr, ctx->d_F32, ctx->d_F32s,
+                             ctx->d_Lc32);
     FETI_CK(cudaGetLastError());
     FETI_TRY(check_status(ctx, "local factorization (FP32)"));
     return FETI_OK;
   }
-  feti::launch_chol_batched(ctx->P, ctx->d_lay, 0, chunks[0].data(), (int)chunks[0].size(), ctx->d_env0, ctx->d_A,
-                            ctx->d_status, st);
   // FP64 operators, and in the FP32-local form their FP32 copies, in one pass each
   const bool mix = ctx->opt.precision == FETI_MIXED;
-  if (ctx->opt.precond == FETI_PREC_DIRICHLET)
-    feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 0, ctx->d_A, ctx->d_S, mix ? ctx->d_S32 : nullptr,
-                               mix ? ctx->d_S32s : nullptr, st);
-  feti::launch_chol_batched(ctx->P, ctx->d_lay, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, ctx->d_A,
-                            ctx->d_status, st);
-  feti::launch_extract_tiles(ctx->P, ctx->max_nb, ctx->d_lay, 1, ctx->d_A, ctx->d_F, mix ? ctx->d_F32 : nullptr,
-                             mix ? ctx->d_F32s : nullptr, st);
+  for (int g = 0; g < n_grp; ++g)
+    factorize_group<double>(ctx, g, ctx->d_A, ctx->env0, ctx->env_off, ctx->d_env0, 32, ctx->d_S,
+                            mix ? ctx->d_S32 : nullptr, mix ? ctx->d_S32s : nullptr, ctx->d_F,
+                            mix ? ctx->d_F32 : nullptr, mix ? ctx->d_F32s : nullptr,
+                            ctx->keep_factor ? nullptr : ctx->d_Lc);
   FETI_CK(cudaGetLastError());
   FETI_TRY(check_status(ctx, "local factorization"));
   return FETI_OK;
@@ -2075,10 +2145,17 @@ feti_status alloc_operators(feti_ctx* ctx) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_kzb, (size_t)ctx->nb_total));
     FETI_TRY(dev_alloc(ctx, &ctx->d_kxb, (size_t)ctx->nb_total));
     FETI_TRY(dev_alloc(ctx, &ctx->d_kye, (size_t)ctx->nde * ctx->E));
+    FETI_TRY(dev_alloc(ctx, &ctx->d_Lc32, (size_t)ctx->lc_elems));
   } else {
     FETI_TRY(dev_alloc(ctx, &ctx->d_A, (size_t)ctx->op_elems[0]));
     FETI_TRY(dev_alloc(ctx, &ctx->d_S, (size_t)ctx->op_elems[1]));
     FETI_TRY(dev_alloc(ctx, &ctx->d_F, (size_t)ctx->op_elems[2]));
+    if (!ctx->keep_factor) {
+      FETI_TRY(dev_alloc(ctx, &ctx->d_Lc, (size_t)ctx->lc_elems));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_kyI64, (size_t)ctx->nloc_total));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_kzb64, (size_t)ctx->nb_total));
+      FETI_TRY(dev_alloc(ctx, &ctx->d_kxb, (size_t)ctx->nb_total));
+    }
   }
   if (f32_ops(ctx)) {
     FETI_TRY(dev_alloc(ctx, &ctx->d_F32, (size_t)ctx->op_elems[3]));
@@ -2764,6 +2841,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   if (opt->local_form < 0 || opt->local_form > 2) return fail(ctx, FETI_ERR_INVALID_ARG, "unsupported local_form");
   if (opt->local_form == 2 && opt->precision != FETI_FP64)
     return fail(ctx, FETI_ERR_INVALID_ARG, "the implicit local form needs FETI_FP64");
+  if (opt->workspace_mb < -1) return fail(ctx, FETI_ERR_INVALID_ARG, "workspace_mb must be >= -1");
   if (!(opt->tol > 0.0) || opt->maxit <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "tol and maxit must be positive");
   if (mat->kind != FETI_LINEAR_ISO && mat->kind != FETI_HGO_TWO_FIBRE && mat->kind != FETI_LINEAR_ISO_P0)
     return fail(ctx, FETI_ERR_INVALID_ARG, "unknown material");
@@ -3289,6 +3367,16 @@ feti_status feti_get_coarse_info(const feti_ctx* ctx, int64_t out[6]) {
   for (const auto& F : cp.fronts) out[3] += (int64_t)F.w * (F.w + 1) / 2 + (int64_t)F.w * F.p;
   out[4] = (int64_t)cp.tasks.size();
   out[5] = cp.ws;
+  return FETI_OK;
+}
+
+feti_status feti_get_factor_info(const feti_ctx* ctx, int64_t out[5]) {
+  if (!ctx || !out) return FETI_ERR_INVALID_ARG;
+  out[0] = (int64_t)ctx->grp.size() - 1;
+  out[1] = ctx->ws_elems;
+  out[2] = ctx->ws_full;
+  out[3] = ctx->keep_factor ? 0 : ctx->lc_elems;
+  out[4] = ctx->opt.precision == FETI_MIXED_F32FACTOR ? 4 : 8;
   return FETI_OK;
 }
 

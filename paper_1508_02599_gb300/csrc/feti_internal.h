@@ -44,7 +44,11 @@ struct SubLayout {
   int64_t fsym32;
   int64_t ssym32;
   int64_t psym;   // offset (floats) of the transposed-product partials: PH I floats per panel I
+  int64_t loff;   // offset of the compact interior factor: rows [0, nI + nbp) x columns [0, nI)
+                  // of the Cholesky factor (L_II lower, L_bI), row stride kp_ld
 };
+// Row stride of the compact interior factor (a multiple of 4 elements).
+__host__ __device__ inline int kp_ld(const SubLayout& L) { return (L.nI + 3) & ~3; }
 constexpr int kSymPH = 32;  // panel height of the symmetric FP32 apply
 
 // Element kernels ------------------------------------------------------------
@@ -310,10 +314,24 @@ void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, con
 // positions); the caller then applies the FP32 F_i to zb (x_b, FP64 at the
 // boundary offsets); backward: x_I = L_II^-T (y_I - L_bI^T x_b) and
 // x (+)= [x_I, x_b] (init: x = that, zero on the fixing rows).
-void launch_kp_forward(int P, const SubLayout* lay, const float* A, const double* r, float* yI, float* zb, int max_nr,
+// Both read the compact interior factor (SubLayout::loff, row stride kp_ld).
+// The FP64 overloads give the FP64 K^+ of the FP64 factorizations in one
+// pass (forward, FP64 F_i apply, backward: K_rr^-1 by its block form with
+// the Schur complement inverse F_i).
+void launch_kp_forward(int P, const SubLayout* lay, const float* Lc, const double* r, float* yI, float* zb, int max_nr,
                        cudaStream_t st);
-void launch_kp_backward(int P, const SubLayout* lay, const float* A, const float* yI, const double* xb, double* x,
+void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, const float* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st);
+void launch_kp_forward(int P, const SubLayout* lay, const double* Lc, const double* r, double* yI, double* zb,
+                       int max_nr, cudaStream_t st);
+void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, const double* yI, const double* xb, double* x,
+                        int init, int max_nr, cudaStream_t st);
+// Copies rows [0, nI + nbp) x columns [0, nI) of each eliminated workspace
+// matrix (at lay[s].aoff in A) into the compact interior factor Lc (at
+// lay[s].loff, row stride kp_ld; zero above the diagonal of L_II and in the
+// padding).  max_rows: the largest nI + nbp over the P subdomains.
+void launch_compact_factor(int P, int max_rows, const SubLayout* lay, const double* A, double* Lc, cudaStream_t st);
+void launch_compact_factor(int P, int max_rows, const SubLayout* lay, const float* A, float* Lc, cudaStream_t st);
 // r = g - K_rr x in FP64 from the element matrices (zero on the fixing rows),
 // in two passes: ye (nde doubles per element) = K_e x_e
 // for all elements (elem_sub: the subdomain of each element), then per local
