@@ -14,7 +14,7 @@
 // with zero on the fixing DOFs, which is K^+ g of the fixing-DOF generalized
 // inverse of Sec. 5.2 ("regularization by fixing nodes").  Each FP32
 // correction sweeps only the interior block of L and reaches the boundary
-// block through the explicit F_i (k_kp_forward / k_kp_backward); the FP64
+// block through the explicit F_i (k_kp_fwd_* / k_kp_bwd_*); the FP64
 // residual is an element pass and a row pass (k_elem_kx / k_row_resid).
 #include "feti_internal.h"
 
@@ -82,73 +82,94 @@ __global__ void __launch_bounds__(256) k_extract_tiles(const SubLayout* __restri
 // and F_i = S_i[b',b']^-1 is the explicit FP32 operator the PCG already
 // applies.  The dependent 32-row block chains shrink from n_I + n_b' rows to
 // n_I rows; the boundary panel products carry no chain.
-// k_kp_forward: y_I (into yI at the subdomain's local offset) and z_b (into
-// zb at the boundary offset; zero on the fixing positions), in the factor's
-// precision T.  Both kernels read the compact interior factor (rows
-// [0, n_I + n_b') x columns [0, n_I) at L.loff, row stride kp_ld).
+// The sweeps in four kernels: the two triangular chains over L_II run one
+// CTA per subdomain (k_kp_fwd_interior, k_kp_bwd_interior: 32-row blocks one
+// after another), and the two products with L_bI, which carry no chain and
+// hold most of the factor's bytes, run many CTAs per subdomain
+// (k_kp_fwd_boundary: 32 boundary rows per CTA; k_kp_bwd_boundary: 32
+// interior columns per CTA).  T is the factor's precision; every kernel reads
+// the compact interior factor (rows [0, n_I + n_b') x columns [0, n_I) at
+// L.loff, row stride kp_ld).
 template <typename T>
 __device__ __forceinline__ T kp_warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+// Diagonal block [I0, I0 + 32) of L_II (lower triangle, zero elsewhere) into D.
+template <typename T>
+__device__ __forceinline__ void kp_load_diag(const T* __restrict__ A, size_t ld, int nI, int I0, T (*D)[33]) {
+  const int nb = min(32, nI - I0);
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += kT) {
+    const int rr = idx >> 5, c = idx & 31;
+    D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : (T)0;
+  }
+}
+
+// ys[i] -= L[i, I0 : I0 + 32] . xs for the rows i in [i0, nI), a thread per
+// row, the 32 entries read as 16-byte vectors (rows and I0 are multiples of 4
+// elements apart from an aligned base).
+__device__ __forceinline__ void kp_row_update(const float* __restrict__ A, size_t ld, int I0, int i0, int nI,
+                                              const float* xs, float* ys) {
+  // two halves of 16 entries: the FP32 sweeps run 8 CTAs of 256 threads per
+  // SM (one wave over a thousand subdomains), 32 registers a thread
+  for (int i = i0 + threadIdx.x; i < nI; i += kT) {
+    const float4* row = reinterpret_cast<const float4*>(A + (size_t)i * ld + I0);
+    float acc = 0.0f;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      float4 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = __ldg(row + 4 * h + u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* xv = xs + 16 * h + 4 * u;
+        acc += a[u].x * xv[0] + a[u].y * xv[1] + a[u].z * xv[2] + a[u].w * xv[3];
+      }
+    }
+    ys[i] -= acc;
+  }
+}
+__device__ __forceinline__ void kp_row_update(const double* __restrict__ A, size_t ld, int I0, int i0, int nI,
+                                              const double* xs, double* ys) {
+  for (int i = i0 + threadIdx.x; i < nI; i += kT) {
+    const double2* row = reinterpret_cast<const double2*>(A + (size_t)i * ld + I0);
+    double2 a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] = __ldg(row + u);
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc += a[u].x * xs[2 * u] + a[u].y * xs[2 * u + 1];
+    ys[i] -= acc;
+  }
+}
+
+// y_I = L_II^-1 r_I (into yI at the subdomain's local offset), right-looking
+// by 32-column blocks: warp 0 solves the diagonal block, then every thread
+// updates the rows below it with the block's 32 solved values while the next
+// diagonal block is fetched into the other buffer.
 template <typename T>
 __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
-    k_kp_forward(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const double* __restrict__ rbase,
-                 T* __restrict__ yIbase, T* __restrict__ zb) {
+    k_kp_fwd_interior(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const double* __restrict__ rbase,
+                      T* __restrict__ yIbase) {
   extern __shared__ __align__(16) unsigned char kp_smem[];
   T* ys = reinterpret_cast<T*>(kp_smem);
   const SubLayout L = lay[blockIdx.x];
   const T* A = Lbase + L.loff;
   const size_t ld = kp_ld(L);
   const double* r = rbase + L.voff;
-  const int nI = L.nI, nbp = L.nbp;
+  const int nI = L.nI;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kT / 32;
-  __shared__ T D[32][33];
-  __shared__ T t[32];
+  __shared__ T Db[2][32][33];
+  __shared__ __align__(16) T xs[32];
   for (int i = tid; i < nI; i += kT) ys[i] = (T)r[i];
+  if (nI > 0) kp_load_diag(A, ld, nI, 0, Db[0]);
   __syncthreads();
-  for (int I0 = 0; I0 < nI; I0 += 32) {
+  for (int I0 = 0, k = 0; I0 < nI; I0 += 32, ++k) {
     const int nb = min(32, nI - I0);
-    for (int idx = tid; idx < 32 * 32; idx += kT) {
-      const int rr = idx >> 5, c = idx & 31;
-      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : (T)0;
-    }
-    {
-      const T* rp = A + (size_t)I0 * ld;
-      int ro[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nb - 1) * (int)ld;
-      T acc[4] = {0, 0, 0, 0};
-      int j = lane;
-      for (; j + 96 < I0; j += 128) {
-        T a[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const T yv = ys[j + 32 * u];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
-        }
-      }
-      for (; j < I0; j += 32) {
-        const T yv = ys[j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T v = kp_warp_sum(acc[q]);
-        if (lane == 0 && warp + kW * q < nb) t[warp + kW * q] = v;
-      }
-    }
-    __syncthreads();
+    T (*D)[33] = Db[k & 1];
     if (warp == 0) {
-      T b = lane < nb ? ys[I0 + lane] - t[lane] : (T)0;
+      T b = lane < nb ? ys[I0 + lane] : (T)0;
       T xv = 0;
       for (int c = 0; c < nb; ++c) {
         if (lane == c) xv = b / D[c][c];
@@ -156,55 +177,128 @@ __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
         if (lane > c) b -= D[lane][c] * xc;
       }
       if (lane < nb) ys[I0 + lane] = xv;
+      xs[lane] = lane < nb ? xv : (T)0;
+    }
+    __syncthreads();
+    const int I1 = I0 + 32;
+    if (I1 < nI) {  // then nb == 32
+      kp_load_diag(A, ld, nI, I1, Db[(k + 1) & 1]);
+      kp_row_update(A, ld, I0, I1, nI, xs, ys);
     }
     __syncthreads();
   }
   T* yI = yIbase + L.voff;
   for (int i = tid; i < nI; i += kT) yI[i] = ys[i];
-  // z_b = r_b - L_bI y_I: warp w takes boundary rows w, w + 8, w + 16, w + 24
-  // (then the next 32), four column strides at a time
-  for (int p0 = 0; p0 < nbp; p0 += 4 * kW) {
-    const T* rp = A + (size_t)(nI + p0) * ld;
-    int ro[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nbp - 1 - p0) * (int)ld;
-    T acc[4] = {0, 0, 0, 0};
-    int j = lane;
-    for (; j + 96 < nI; j += 128) {
-      T a[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const T yv = ys[j + 32 * u];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
-      }
-    }
-    for (; j < nI; j += 32) {
-      const T yv = ys[j];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const T v = kp_warp_sum(acc[q]);
-      const int p = p0 + warp + kW * q;
-      if (lane == 0 && p < nbp) zb[L.boff + p] = (T)(r[nI + p] - (double)v);
-    }
-  }
-  for (int p = nbp + tid; p < nbp + L.k; p += kT) zb[L.boff + p] = (T)0;
 }
 
-// k_kp_backward: t_I = y_I - L_bI^T x_b, x_I = L_II^-T t_I; then x (+)= x on
+// z_b = r_b - L_bI y_I for 32 boundary rows per CTA (grid.x over row blocks,
+// grid.y over subdomains; warp w takes rows w, w + 8, w + 16, w + 24 of the
+// block, four column strides at a time); the CTA with block 0 also zeros z on
+// the fixing positions.
+template <typename T>
+__global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
+    k_kp_fwd_boundary(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const double* __restrict__ rbase,
+                      const T* __restrict__ yIbase, T* __restrict__ zb) {
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  T* ys = reinterpret_cast<T*>(kp_smem);
+  const SubLayout L = lay[blockIdx.y];
+  const int nI = L.nI, nbp = L.nbp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kT / 32;
+  if (blockIdx.x == 0)
+    for (int p = nbp + tid; p < nbp + L.k; p += kT) zb[L.boff + p] = (T)0;
+  const int p0 = blockIdx.x * 32;
+  if (p0 >= nbp) return;
+  const T* yI = yIbase + L.voff;
+  for (int i = tid; i < nI; i += kT) ys[i] = yI[i];
+  __syncthreads();
+  const size_t ld = kp_ld(L);
+  const T* rp = Lbase + L.loff + (size_t)(nI + p0) * ld;
+  const double* r = rbase + L.voff;
+  int ro[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ro[q] = min(warp + kW * q, nbp - 1 - p0) * (int)ld;
+  T acc[4] = {0, 0, 0, 0};
+  int j = lane;
+  for (; j + 96 < nI; j += 128) {
+    T a[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[q][u] = __ldg(rp + ro[q] + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T yv = ys[j + 32 * u];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += a[q][u] * yv;
+    }
+  }
+  for (; j < nI; j += 32) {
+    const T yv = ys[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += __ldg(rp + ro[q] + j) * yv;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T v = kp_warp_sum(acc[q]);
+    const int p = p0 + warp + kW * q;
+    if (lane == 0 && p < min(nbp, p0 + 32)) zb[L.boff + p] = (T)(r[nI + p] - (double)v);
+  }
+}
+
+// t_I = y_I - L_bI^T x_b in place in yI, 32 interior columns per CTA: lane =
+// column, warp w = boundary rows w, w + 8, ..., eight rows in flight per
+// thread, the eight warps' partial sums added in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
+    k_kp_bwd_boundary(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const double* __restrict__ xb,
+                      T* __restrict__ yIbase) {
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  T* xbs = reinterpret_cast<T*>(kp_smem);
+  const SubLayout L = lay[blockIdx.y];
+  const int nI = L.nI, nbp = L.nbp;
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= nI) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kT / 32;
+  __shared__ T part[kW][32];
+  for (int p = tid; p < nbp; p += kT) xbs[p] = (T)xb[L.boff + p];
+  __syncthreads();
+  const size_t ld = kp_ld(L);
+  const int c = c0 + lane;
+  const T* col = Lbase + L.loff + (size_t)nI * ld + min(c, nI - 1);
+  T acc = 0;
+  int p = warp;
+  for (; p + 7 * kW < nbp; p += 8 * kW) {
+    T a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = __ldg(col + (size_t)(p + kW * u) * ld);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += a[u] * xbs[p + kW * u];
+  }
+  for (; p < nbp; p += kW) acc += __ldg(col + (size_t)p * ld) * xbs[p];
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < nI) {
+    T s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < kW; ++w) s += part[w][lane];
+    T* yI = yIbase + L.voff;
+    yI[c] -= s;
+  }
+}
+
+// x_I = L_II^-T t_I (t_I in yI after k_kp_bwd_boundary), by 32-column
+// blocks from the last: warp 0 solves the transposed diagonal block, then a
+// thread per column j below the block's start subtracts L[I0 : I0 + 32, j]^T
+// times the block's solved values (32 loads in flight per thread) while the
+// previous diagonal block is fetched into the other buffer; then x (+)= x on
 // rows [0, n_I + n_b') (x_b from the F_i apply, FP64 at the boundary offset),
 // and with init x = that correction, zero on the fixing rows.
 template <typename T>
 __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
-    k_kp_backward(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const T* __restrict__ yIbase,
-                  const double* __restrict__ xb, double* __restrict__ xbase, int init) {
+    k_kp_bwd_interior(const SubLayout* __restrict__ lay, const T* __restrict__ Lbase, const T* __restrict__ yIbase,
+                      const double* __restrict__ xb, double* __restrict__ xbase, int init) {
   extern __shared__ __align__(16) unsigned char kp_smem[];
   T* ys = reinterpret_cast<T*>(kp_smem);
   const SubLayout L = lay[blockIdx.x];
@@ -213,38 +307,16 @@ __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
   double* x = xbase + L.voff;
   const int nI = L.nI, nbp = L.nbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ T D[32][33];
+  __shared__ T Db[2][32][33];
   __shared__ T xs[32];
-  T* xbs = ys + nI;  // x_b in precision T after the interior part
   const T* yI = yIbase + L.voff;
   for (int i = tid; i < nI; i += kT) ys[i] = yI[i];
-  for (int p = tid; p < nbp; p += kT) xbs[p] = (T)xb[L.boff + p];
+  const int Ilast = nI > 0 ? ((nI - 1) / 32) * 32 : -32;
+  if (Ilast >= 0) kp_load_diag(A, ld, nI, Ilast, Db[0]);
   __syncthreads();
-  // t_I = y_I - L_bI^T x_b: thread per interior column, 16 boundary rows per step
-  {
-    const T* Pb = A + (size_t)nI * ld;
-    for (int j = tid; j < nI; j += kT) {
-      T acc = 0;
-      int p = 0;
-      for (; p + 16 <= nbp; p += 16) {
-        T a[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) a[u] = __ldg(Pb + (size_t)(p + u) * ld + j);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) acc += a[u] * xbs[p + u];
-      }
-      for (; p < nbp; ++p) acc += __ldg(Pb + (size_t)p * ld + j) * xbs[p];
-      ys[j] -= acc;
-    }
-  }
-  __syncthreads();
-  for (int I0 = nI > 0 ? ((nI - 1) / 32) * 32 : -32; I0 >= 0; I0 -= 32) {
+  for (int I0 = Ilast, k = 0; I0 >= 0; I0 -= 32, ++k) {
     const int nb = min(32, nI - I0);
-    for (int idx = tid; idx < 32 * 32; idx += kT) {
-      const int rr = idx >> 5, c = idx & 31;
-      D[rr][c] = (rr < nb && c <= rr) ? A[(size_t)(I0 + rr) * ld + I0 + c] : (T)0;
-    }
-    __syncthreads();
+    T (*D)[33] = Db[k & 1];
     if (warp == 0) {
       T b = lane < nb ? ys[I0 + lane] : (T)0;
       T xv = 0;
@@ -257,18 +329,22 @@ __global__ void __launch_bounds__(kT, sizeof(T) == 4 ? 8 : 4)
       xs[lane] = lane < nb ? xv : (T)0;
     }
     __syncthreads();
-    if (nb == 32) {
-      for (int j = tid; j < I0; j += kT) {
-        const T* col = A + (size_t)I0 * ld + j;
-        T acc = 0;
-#pragma unroll 16
-        for (int rr = 0; rr < 32; ++rr) acc += col[(size_t)rr * ld] * xs[rr];
-        ys[j] -= acc;
-      }
-    } else {
+    if (I0 > 0) {
+      kp_load_diag(A, ld, nI, I0 - 32, Db[(k + 1) & 1]);
+      const T* blk = A + (size_t)I0 * ld;
       for (int j = tid; j < I0; j += kT) {
         T acc = 0;
-        for (int rr = 0; rr < nb; ++rr) acc += A[(size_t)(I0 + rr) * ld + j] * xs[rr];
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          T a[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int rr = 16 * h + u;
+            a[u] = rr < nb ? __ldg(blk + (size_t)rr * ld + j) : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc += a[u] * xs[16 * h + u];
+        }
         ys[j] -= acc;
       }
     }
@@ -421,19 +497,32 @@ void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, con
   if (P > 0 && nT > 0) k_extract_tiles<double><<<dim3(nT * nT, P), 256, 0, st>>>(lay, which, A, out64, out32, sym32);
 }
 
-template <typename T>
-void kp_forward(int P, const SubLayout* lay, const T* Lc, const double* r, T* yI, T* zb, int max_nr, cudaStream_t st) {
-  const size_t smem = (size_t)max_nr * sizeof(T);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (P > 0) k_kp_forward<T><<<P, kT, smem, st>>>(lay, Lc, r, yI, zb);
+template <typename K>
+void kp_smem_attr(K kern, size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
-void kp_backward(int P, const SubLayout* lay, const T* Lc, const T* yI, const double* xb, double* x, int init,
+void kp_forward(int P, const SubLayout* lay, const T* Lc, const double* r, T* yI, T* zb, int max_nr, cudaStream_t st) {
+  if (P <= 0) return;
+  const size_t smem = (size_t)std::max(max_nr, 1) * sizeof(T);
+  kp_smem_attr(k_kp_fwd_interior<T>, smem);
+  kp_smem_attr(k_kp_fwd_boundary<T>, smem);
+  k_kp_fwd_interior<T><<<P, kT, smem, st>>>(lay, Lc, r, yI);
+  const int nblk = std::max(1, (max_nr + 31) / 32);
+  k_kp_fwd_boundary<T><<<dim3(nblk, P), kT, smem, st>>>(lay, Lc, r, yI, zb);
+}
+
+template <typename T>
+void kp_backward(int P, const SubLayout* lay, const T* Lc, T* yI, const double* xb, double* x, int init,
                  int max_nr, cudaStream_t st) {
-  const size_t smem = (size_t)max_nr * sizeof(T);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_kp_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (P > 0) k_kp_backward<T><<<P, kT, smem, st>>>(lay, Lc, yI, xb, x, init);
+  if (P <= 0) return;
+  const size_t smem = (size_t)std::max(max_nr, 1) * sizeof(T);
+  kp_smem_attr(k_kp_bwd_boundary<T>, smem);
+  kp_smem_attr(k_kp_bwd_interior<T>, smem);
+  const int nblk = std::max(1, (max_nr + 31) / 32);
+  k_kp_bwd_boundary<T><<<dim3(nblk, P), kT, smem, st>>>(lay, Lc, xb, yI);
+  k_kp_bwd_interior<T><<<P, kT, smem, st>>>(lay, Lc, yI, xb, x, init);
 }
 
 void launch_kp_forward(int P, const SubLayout* lay, const float* Lc, const double* r, float* yI, float* zb, int max_nr,
@@ -441,7 +530,7 @@ void launch_kp_forward(int P, const SubLayout* lay, const float* Lc, const doubl
   kp_forward<float>(P, lay, Lc, r, yI, zb, max_nr, st);
 }
 
-void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, const float* yI, const double* xb, double* x,
+void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, float* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st) {
   kp_backward<float>(P, lay, Lc, yI, xb, x, init, max_nr, st);
 }
@@ -451,7 +540,7 @@ void launch_kp_forward(int P, const SubLayout* lay, const double* Lc, const doub
   kp_forward<double>(P, lay, Lc, r, yI, zb, max_nr, st);
 }
 
-void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, const double* yI, const double* xb, double* x,
+void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, double* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st) {
   kp_backward<double>(P, lay, Lc, yI, xb, x, init, max_nr, st);
 }

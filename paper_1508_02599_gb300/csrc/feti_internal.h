@@ -314,17 +314,18 @@ void launch_extract_tiles(int P, int max_m, const SubLayout* lay, int which, con
 // positions); the caller then applies the FP32 F_i to zb (x_b, FP64 at the
 // boundary offsets); backward: x_I = L_II^-T (y_I - L_bI^T x_b) and
 // x (+)= [x_I, x_b] (init: x = that, zero on the fixing rows).
-// Both read the compact interior factor (SubLayout::loff, row stride kp_ld).
+// Both read the compact interior factor (SubLayout::loff, row stride kp_ld);
+// the backward sweep overwrites yI (with y_I - L_bI^T x_b).
 // The FP64 overloads give the FP64 K^+ of the FP64 factorizations in one
 // pass (forward, FP64 F_i apply, backward: K_rr^-1 by its block form with
 // the Schur complement inverse F_i).
 void launch_kp_forward(int P, const SubLayout* lay, const float* Lc, const double* r, float* yI, float* zb, int max_nr,
                        cudaStream_t st);
-void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, const float* yI, const double* xb, double* x,
+void launch_kp_backward(int P, const SubLayout* lay, const float* Lc, float* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st);
 void launch_kp_forward(int P, const SubLayout* lay, const double* Lc, const double* r, double* yI, double* zb,
                        int max_nr, cudaStream_t st);
-void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, const double* yI, const double* xb, double* x,
+void launch_kp_backward(int P, const SubLayout* lay, const double* Lc, double* yI, const double* xb, double* x,
                         int init, int max_nr, cudaStream_t st);
 // Copies rows [0, nI + nbp) x columns [0, nI) of each eliminated workspace
 // matrix (at lay[s].aoff in A) into the compact interior factor Lc (at

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from feti_inputs import mesh
+from pcg_counts import count_matches
 from oracle import fem, feti
 
 torch = pytest.importorskip("torch")
@@ -54,7 +55,7 @@ def test_kelvin_512_matches_oracle(method):
     with FetiSolver(prob, method=method, precond="dirichlet", tol=1e-8) as s:
         _, rep8 = s.solve()
     assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
-    assert abs(rep8["iterations"] - res8.iterations) <= 1
+    assert count_matches(rep8["iterations"], res.res_hist, 1e-8), (rep8["iterations"], res8.iterations)
 
 
 def test_kelvin_table2_trends_and_convergence():
