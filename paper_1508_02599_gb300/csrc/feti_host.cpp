@@ -1592,9 +1592,10 @@ feti_status tune_refinement(feti_ctx* ctx) {
 // Local factorizations, dense local operators, coarse problem.
 // One elimination group in the workspace: assembly of the dense matrices,
 // interior elimination, S_i, boundary elimination, F_i, and the compact
-// interior factor.  T is the factorization's precision.
+// interior factor.  T is the factorization's precision.  Returns the first
+// error of the enqueueing calls.
 template <typename T>
-void factorize_group(feti_ctx* ctx, int g, T* A, const std::vector<int32_t>& envt, const std::vector<int64_t>& eoff,
+cudaError_t factorize_group(feti_ctx* ctx, int g, T* A, const std::vector<int32_t>& envt, const std::vector<int64_t>& eoff,
                      const int32_t* d_env, int B, double* S64, float* S32,
                      float* S32s, double* F64, float* F32, float* F32s, T* Lc) {
   cudaStream_t st = ctx->stream;
@@ -1602,7 +1603,8 @@ void factorize_group(feti_ctx* ctx, int g, T* A, const std::vector<int32_t>& env
   const SubLayout* lw = ctx->d_lay_ws + s0;
   int64_t elems = 0;
   for (int s = s0; s < s0 + pg; ++s) elems += (int64_t)ctx->lay[s].ld * ctx->lay[s].ld;
-  cudaMemsetAsync(A, 0, (size_t)elems * sizeof(T), st);
+  const cudaError_t e = cudaMemsetAsync(A, 0, (size_t)elems * sizeof(T), st);
+  if (e != cudaSuccess) return e;
   feti::launch_assemble(pg, lw, ctx->d_sub_elem_ptr + s0, ctx->d_sub_elems, ctx->d_elem_dense, ctx->d_Ke, ctx->nde,
                         A, st);
   if constexpr (sizeof(T) == 8) {
@@ -1644,6 +1646,7 @@ void factorize_group(feti_ctx* ctx, int g, T* A, const std::vector<int32_t>& env
   feti::launch_chol_batched(pg, lw, 1, chunks[1].data(), (int)chunks[1].size(), nullptr, A, ctx->d_status, st);
   feti::launch_extract_tiles(pg, ctx->max_nb, lw, 1, A, F64, F32, F32s, st);
   if (Lc) feti::launch_compact_factor(pg, ctx->max_nr, lw, A, Lc, st);
+  return cudaGetLastError();
 }
 
 feti_status factorize_all(feti_ctx* ctx) {
@@ -1651,21 +1654,19 @@ feti_status factorize_all(feti_ctx* ctx) {
   if (f32_factor(ctx)) {
     // FP32 elimination; S_i and F_i go straight into the FP32 operator layouts
     for (int g = 0; g < n_grp; ++g)
-      factorize_group<float>(ctx, g, ctx->d_A32, ctx->env0_32, ctx->env32_off, ctx->d_env0_32,
+      FETI_CK(factorize_group<float>(ctx, g, ctx->d_A32, ctx->env0_32, ctx->env32_off, ctx->d_env0_32,
                              feti::kChol32Block, nullptr, ctx->d_S32, ctx->d_S32s, nullptr, ctx->d_F32, ctx->d_F32s,
-                             ctx->d_Lc32);
-    FETI_CK(cudaGetLastError());
+                             ctx->d_Lc32));
     FETI_TRY(check_status(ctx, "local factorization (FP32)"));
     return FETI_OK;
   }
   // FP64 operators, and in the FP32-local form their FP32 copies, in one pass each
   const bool mix = ctx->opt.precision == FETI_MIXED;
   for (int g = 0; g < n_grp; ++g)
-    factorize_group<double>(ctx, g, ctx->d_A, ctx->env0, ctx->env_off, ctx->d_env0, 32, ctx->d_S,
+    FETI_CK(factorize_group<double>(ctx, g, ctx->d_A, ctx->env0, ctx->env_off, ctx->d_env0, 32, ctx->d_S,
                             mix ? ctx->d_S32 : nullptr, mix ? ctx->d_S32s : nullptr, ctx->d_F,
                             mix ? ctx->d_F32 : nullptr, mix ? ctx->d_F32s : nullptr,
-                            ctx->keep_factor ? nullptr : ctx->d_Lc);
-  FETI_CK(cudaGetLastError());
+                            ctx->keep_factor ? nullptr : ctx->d_Lc));
   FETI_TRY(check_status(ctx, "local factorization"));
   return FETI_OK;
 }
