@@ -204,7 +204,7 @@ struct feti_ctx {
   // main-loop wait budget (SM clock cycles) of the streamed symmetric apply
   // and the warp-specialised tensor-core GEMM: a device word read at every launch
   unsigned long long* d_spin = nullptr;
-  // FP32-factor form: FP32 elimination workspace (same offsets as d_A), per
+  // FP32-factor form: FP32 elimination workspace (the group workspace, as d_A), per
   // local row its (element, element row) incidences for the FP64 residual of
   // the refined K^+, refinement scratch, per-subdomain norms, and the number
   // of refinement corrections chosen at setup (with the residual they reach)
@@ -1486,9 +1486,6 @@ feti_status assemble_all(feti_ctx* ctx, const double* dU, double tau) {
   return check_status(ctx, "element/assembly");
 }
 
-// x = K^+ g on full local vectors (zero on the fixing DOFs): FP64 sweeps on the
-// FP64 factor, or, in the FP32-factor form, FP32 sweeps refined against the
-// FP64 element matrices (refine_steps corrections; d_kr is scratch).
 // Dense local apply of F_i (which 0) or the preconditioner block (which 1)
 // on a gathered local vector (default: d_vloc / d_vloc32) into yout
 // (default: d_loc).
@@ -1511,10 +1508,13 @@ void kplus_corr(feti_ctx* ctx, const double* r, double* x, bool init) {
                            ctx->stream);
 }
 
-// FP64 factorizations: the whole factor kept (sweeps over all of it), or
-// K_rr^-1 by its block form from the compact interior factor and the FP64
-// F_i = S_i[b',b']^-1: y_I = L_II^-1 g_I, z_b = g_b - L_bI y_I, x_b = F_i z_b,
-// x_I = L_II^-T (y_I - L_bI^T x_b).
+// x = K^+ g on full local vectors (zero on the fixing DOFs).  FP64
+// factorizations: sweeps over the whole factor where it is kept (implicit
+// local form), else K_rr^-1 in its block form from the compact interior
+// factor and the FP64 F_i = S_i[b',b']^-1: y_I = L_II^-1 g_I,
+// z_b = g_b - L_bI y_I, x_b = F_i z_b, x_I = L_II^-T (y_I - L_bI^T x_b).
+// FP32 factorizations: the same block form in FP32, refined against the FP64
+// element matrices (refine_steps corrections; d_kr is scratch).
 void kplus(feti_ctx* ctx, const double* g, double* x) {
   cudaStream_t st = ctx->stream;
   if (ctx->keep_factor) {
