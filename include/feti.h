@@ -212,6 +212,17 @@ typedef struct feti_ctx feti_ctx;
 feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat,
                         const feti_bc* bc, const feti_options* opt, void* stream);
 
+/* The same argument checks and host decomposition as feti_create (Sec. 4.1
+ * tearing and the multiplier rows, Sec. 4.3 kernels R_i and the coarse space,
+ * Sec. 5.2 fixing DOFs, the sparse coarse ordering, the workspace groups)
+ * without any CUDA device or device memory: a host plan for checking and
+ * sizing a decomposition.  Only the host getters accept the context
+ * (feti_get_sizes, feti_get_coarse_info, feti_get_factor_info,
+ * feti_get_index_maps, feti_get_fixing, feti_last_error); every call that
+ * needs the device returns FETI_ERR_STATE.  Free with feti_destroy. */
+feti_status feti_create_plan(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat,
+                             const feti_bc* bc, const feti_options* opt);
+
 /* Linear problem: element matrices, local assembly, local factorizations,
  * dense local operators, coarse problem, then projected PCG and recovery.
  * Writes the displacement [n_nodes*3] to u_out (host or device pointer;

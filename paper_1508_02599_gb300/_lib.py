@@ -57,7 +57,7 @@ class FetiReport(C.Structure):
                 ("newton_iters", C.c_int32), ("newton_rel_res", C.c_double), ("outer_iterations", C.c_int32)]
 
 
-EXPORTS = ["feti_create", "feti_solve", "feti_solve_multi", "feti_newton", "feti_newton_steps",
+EXPORTS = ["feti_create", "feti_create_plan", "feti_solve", "feti_solve_multi", "feti_newton", "feti_newton_steps",
            "feti_checkpoint_write", "feti_checkpoint_read", "feti_elements", "feti_get_sizes", "feti_get_coarse_info",
            "feti_get_factor_info",
            "feti_get_index_maps",
@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH):
     vp = C.c_void_p
     lib.feti_create.argtypes = [C.POINTER(vp), C.POINTER(FetiMesh), C.POINTER(FetiMaterial), C.POINTER(FetiBC),
                                 C.POINTER(FetiOptions), vp]
+    lib.feti_create_plan.argtypes = [C.POINTER(vp), C.POINTER(FetiMesh), C.POINTER(FetiMaterial),
+                                     C.POINTER(FetiBC), C.POINTER(FetiOptions)]
     lib.feti_solve.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_newton.argtypes = [vp, vp, C.c_int32, C.POINTER(FetiReport)]
     lib.feti_newton_steps.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(FetiReport)]

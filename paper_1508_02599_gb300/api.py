@@ -33,6 +33,9 @@ class FetiSolver:
     [N,3] float64, tets [E,4] int32, part [E] int32, n_parts, dir_dof,
     dir_val, press_tri, press_owner, pressure, trac_tri, trac_owner,
     traction, material (dict: kind, E, nu, c, k1, k2, kappa), fibres.
+    plan_only: the host decomposition only, without a device
+    (feti_create_plan); the size, map, fixing, coarse and factor getters
+    answer, every solve raises.
     """
 
     def __init__(self, prob, method: str = "af", precond: str = "dirichlet", tol: float = 1e-10,
@@ -40,7 +43,8 @@ class FetiSolver:
                  n_load_steps: int = 10, newton_tol: float = 1e-8, newton_maxit: int = 25,
                  precision: str = "fp64", inner_tol: float = 0.0, max_outer: int = 0,
                  tensor_cores="auto", batched: bool = True, symmetric="auto", spin_timeout_ns: int = 0,
-                 coarse: str = "auto", local_form: str = "auto", workspace_mb: int = 0):
+                 coarse: str = "auto", local_form: str = "auto", workspace_mb: int = 0,
+                 plan_only: bool = False):
         self._lib = L.load()
         self._ctx = C.c_void_p()
         self._keep = []
@@ -79,6 +83,11 @@ class FetiSolver:
                             int(not batched), {"auto": 0, "off": 1, False: 1, "force": 2, True: 2, "force_streamed": 3, "force_cta": 4}[symmetric],
                             int(spin_timeout_ns), {"auto": 0, "dense": 1, "sparse": 2}[coarse],
                             {"auto": 0, "explicit": 1, "implicit": 2}[local_form], int(workspace_mb))
+        if plan_only:
+            # host decomposition only (no device): the getters work, solves do not
+            self._check(self._lib.feti_create_plan(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
+                                                   C.byref(opt)))
+            return
         st = None if stream is None else C.c_void_p(int(stream))
         self._check(self._lib.feti_create(C.byref(self._ctx), C.byref(mesh), C.byref(mat), C.byref(bc),
                                           C.byref(opt), st))

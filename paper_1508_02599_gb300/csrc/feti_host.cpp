@@ -153,6 +153,9 @@ struct feti_ctx {
   int *h_status = nullptr;  // pinned
   feti::Maps maps{};
   bool prepared = false;
+  // host plan (feti_create_plan): the decomposition without any device state;
+  // only the host getters accept it
+  bool dry = false;
   cudaGraphExec_t pcg_graph = nullptr;
   int pcg_graph_chunk = 0;
   bool pcg_graph_mixed = false;
@@ -276,6 +279,12 @@ feti_status fail(feti_ctx* ctx, feti_status st, const std::string& msg) {
   return st;
 }
 
+// Entry points that need device state refuse a host plan.
+feti_status need_device(feti_ctx* ctx) {
+  if (ctx->dry) return fail(ctx, FETI_ERR_STATE, "host plan context (feti_create_plan): no device state");
+  return FETI_OK;
+}
+
 // Precision forms: FP32 elimination (refined K^+); FP32 operators inside the
 // PCG (both mixed forms); FP64 explicit F_i and S_i (FP64 and mixed forms).
 bool f32_factor(const feti_ctx* ctx) { return ctx->opt.precision == FETI_MIXED_F32FACTOR; }
@@ -284,6 +293,10 @@ bool fp64_ops(const feti_ctx* ctx) { return ctx->opt.precision != FETI_MIXED_F32
 
 template <class T>
 feti_status dev_alloc(feti_ctx* ctx, T** out, size_t count) {
+  if (ctx->dry) {
+    *out = nullptr;
+    return FETI_OK;
+  }
   void* p = nullptr;
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   cudaError_t e = cudaMalloc(&p, bytes);
@@ -298,6 +311,7 @@ feti_status dev_alloc(feti_ctx* ctx, T** out, size_t count) {
 
 template <class T>
 feti_status upload(feti_ctx* ctx, T** out, const std::vector<T>& v) {
+  if (ctx->dry) return FETI_OK;
   FETI_TRY(dev_alloc(ctx, out, v.size()));
   if (!v.empty()) FETI_CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
   return FETI_OK;
@@ -442,6 +456,7 @@ constexpr int kCoarseMergeBytes = 98304;
 // Uploads the coarse plan and allocates the factor, the sweep scratch (for up
 // to kMaxRhs vectors), the task flags and counters (zero) and the wait flag.
 feti_status upload_coarse(feti_ctx* ctx) {
+  if (ctx->dry) return FETI_OK;
   const feti::CoarsePlan& cp = ctx->cplan;
   std::vector<int32_t> lvl;
   ctx->cdev.lvl_off.clear();
@@ -1389,6 +1404,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   FETI_TRY(dev_alloc(ctx, &ctx->d_status, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_zero, 1));
   FETI_TRY(dev_alloc(ctx, &ctx->d_spin, 1));
+  if (ctx->dry) return FETI_OK;  // host plan: nothing on a device
   FETI_TRY(set_spin_budget(ctx, ctx->opt.spin_timeout_ns ? ctx->opt.spin_timeout_ns : kDefaultSpinNs));
   FETI_CK(cudaMemsetAsync(ctx->d_zero, 0, sizeof(int), ctx->stream));
   FETI_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
@@ -2755,6 +2771,7 @@ namespace feti {
 feti_status set_error(feti_ctx* ctx, feti_status st, const std::string& msg) { return fail(ctx, st, msg); }
 
 feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double* z) {
+  FETI_TRY(need_device(ctx));
   if (!v || !q || !z) return fail(ctx, FETI_ERR_INVALID_ARG, "feti_dual_apply_noalloc: null vector");
   if (!ctx->noalloc_scratch)
     return fail(ctx, FETI_ERR_CUDA, "feti_dual_apply_noalloc: static scratch unavailable (" + ctx->noalloc_err + ")");
@@ -2822,13 +2839,20 @@ feti_status dual_apply_noalloc(feti_ctx* ctx, const double* v, double* q, double
 
 extern "C" {
 
-feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat, const feti_bc* bc,
-                        const feti_options* opt, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// feti_create and feti_create_plan: argument checks, then (dry = false) the
+// device and stream set-up, then the host decomposition and its upload.
+feti_status create_context(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat, const feti_bc* bc,
+                           const feti_options* opt, void* stream, bool dry) {
   if (!out) return FETI_ERR_INVALID_ARG;
   *out = nullptr;
   feti_ctx* ctx = new (std::nothrow) feti_ctx();
   if (!ctx) return FETI_ERR_OOM;
   *out = ctx;
+  ctx->dry = dry;
   if (!mesh || !mat || !bc || !opt) return fail(ctx, FETI_ERR_INVALID_ARG, "null argument");
   if (mesh->n_nodes <= 0 || mesh->n_tets <= 0 || mesh->n_parts <= 0 || !mesh->coords || !mesh->tets || !mesh->part)
     return fail(ctx, FETI_ERR_INVALID_ARG, "empty or missing mesh arrays");
@@ -2890,6 +2914,7 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   for (int32_t v : ctx->face_tri)
     if (v < 0 || v >= ctx->N) return fail(ctx, FETI_ERR_INVALID_ARG, "face node out of range");
   ctx->opt = *opt;
+  if (dry) return build_decomposition(ctx);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     (void)cudaGetLastError();
@@ -2919,8 +2944,23 @@ feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_materi
   return st;
 }
 
+}  // namespace
+
+extern "C" {
+
+feti_status feti_create(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat, const feti_bc* bc,
+                        const feti_options* opt, void* stream) {
+  return create_context(out, mesh, mat, bc, opt, stream, false);
+}
+
+feti_status feti_create_plan(feti_ctx** out, const feti_mesh* mesh, const feti_material* mat, const feti_bc* bc,
+                             const feti_options* opt) {
+  return create_context(out, mesh, mat, bc, opt, nullptr, true);
+}
+
 feti_status feti_prepare(feti_ctx* ctx) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   (void)cudaGetLastError();  // drop a non-sticky error left by an earlier, unrelated runtime call
   auto t0 = std::chrono::steady_clock::now();
   ctx->shift = 0.0;  // exact local operators (a Newton run may have left a shift)
@@ -2931,6 +2971,7 @@ feti_status feti_prepare(feti_ctx* ctx) {
 
 feti_status feti_solve(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   (void)cudaGetLastError();
   if (!u_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null output");
   auto t0 = std::chrono::steady_clock::now();
@@ -3185,6 +3226,7 @@ static feti_status newton_run(feti_ctx* ctx, const double* U_start, int32_t u_st
 
 feti_status feti_newton(feti_ctx* ctx, double* u_out, int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   const int nsteps = ctx->opt.n_load_steps > 0 ? ctx->opt.n_load_steps : 1;
   return newton_run(ctx, nullptr, 0, 1, nsteps, u_out, u_on_device, nullptr, nullptr, report);
 }
@@ -3193,6 +3235,7 @@ feti_status feti_newton_steps(feti_ctx* ctx, const double* U_start, int32_t firs
                               double* u_out, int32_t u_on_device, int32_t* pcg_per_step, int32_t* newton_per_step,
                               feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   return newton_run(ctx, U_start, u_on_device, first_step, last_step, u_out, u_on_device, pcg_per_step,
                     newton_per_step, report);
 }
@@ -3200,6 +3243,7 @@ feti_status feti_newton_steps(feti_ctx* ctx, const double* U_start, int32_t firs
 feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, double* Ke_out, double* fe_out,
                           int32_t out_on_device) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   if (!Ke_out) return fail(ctx, FETI_ERR_INVALID_ARG, "null Ke_out");
   (void)cudaGetLastError();
   cudaStream_t st = ctx->stream;
@@ -3255,6 +3299,7 @@ feti_status feti_elements(feti_ctx* ctx, const double* U, int32_t u_on_device, d
 feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nrhs, double* u_out,
                              int32_t u_on_device, feti_report* report) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   if (!u_out || !load_scale) return fail(ctx, FETI_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > feti::kMaxRhs) return fail(ctx, FETI_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
   (void)cudaGetLastError();
@@ -3276,6 +3321,7 @@ feti_status feti_solve_multi(feti_ctx* ctx, const double* load_scale, int32_t nr
 feti_status feti_dual_apply_multi(feti_ctx* ctx, const double* v, double* q, double* z, int32_t nrhs,
                                   int32_t n_apply, double* ms_per_apply) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   if (!v || !q || !z || n_apply <= 0 || nrhs < 1 || nrhs > feti::kMaxRhs)
     return fail(ctx, FETI_ERR_INVALID_ARG, "bad dual_apply_multi arguments");
   if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
@@ -3403,6 +3449,7 @@ feti_status feti_get_fixing(const feti_ctx* ctx, int32_t* fix_ptr, int32_t* fix_
 feti_status feti_dual_apply(feti_ctx* ctx, const double* v, double* q, double* z, int32_t n_apply,
                             double* ms_per_apply) {
   if (!ctx) return FETI_ERR_INVALID_ARG;
+  FETI_TRY(need_device(ctx));
   if (!v || !q || !z || n_apply <= 0) return fail(ctx, FETI_ERR_INVALID_ARG, "bad dual_apply arguments");
   if (!ctx->prepared) return fail(ctx, FETI_ERR_STATE, "call feti_prepare or feti_solve first");
   (void)cudaGetLastError();
