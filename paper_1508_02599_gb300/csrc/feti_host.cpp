@@ -546,12 +546,21 @@ feti_status build_decomposition(feti_ctx* ctx) {
   }
   ctx->nodes.assign(P, {});
   par_for(P, 4, [&](int64_t s) {
+    // first visits marked in a per-thread table (cleared again below), so
+    // only the distinct nodes are sorted
+    thread_local std::vector<char> seen;
+    if (seen.size() < (size_t)N) seen.assign(N, 0);
     auto& v = ctx->nodes[s];
-    v.reserve((size_t)ctx->npe * (sub_elem_ptr[s + 1] - sub_elem_ptr[s]));
     for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q)
-      for (int a = 0; a < ctx->npe; ++a) v.push_back(ctx->tets[(size_t)ctx->npe * sub_elems[q] + a]);
+      for (int a = 0; a < ctx->npe; ++a) {
+        const int n = ctx->tets[(size_t)ctx->npe * sub_elems[q] + a];
+        if (!seen[n]) {
+          seen[n] = 1;
+          v.push_back(n);
+        }
+      }
+    for (int n : v) seen[n] = 0;
     std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
   });
   lg.mark("create:   local node lists");
   // node -> subdomains (ascending)
@@ -980,16 +989,25 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (double v : ctx->dir_val)
       if (v != 0.0) ctx->any_dirval = true;
   if (ctx->any_dirval) elem_dirval.assign((size_t)nde * E, 0.0);
-  par_for(E, 4096, [&](int64_t e) {
-    const int s = ctx->part[e];
-    for (int a = 0; a < npe; ++a) {
-      const int n = ctx->tets[(size_t)npe * e + a];
-      const int l = lnode(s, n);
-      for (int c = 0; c < 3; ++c) {
-        elem_dense[(size_t)nde * e + 3 * a + c] = pos_of[s][3 * l + c];
-        if (ctx->any_dirval && is_dir[3 * (size_t)n + c]) elem_dirval[(size_t)nde * e + 3 * a + c] = dval[3 * (size_t)n + c];
+  par_for(P, 4, [&](int64_t s) {
+    // the subdomain's local node numbers in a per-thread table (cleared again below)
+    thread_local std::vector<int32_t> lof;
+    if (lof.size() < (size_t)N) lof.assign(N, -1);
+    const auto& nd = ctx->nodes[s];
+    for (size_t l = 0; l < nd.size(); ++l) lof[nd[l]] = (int32_t)l;
+    for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
+      const int e = sub_elems[q];
+      for (int a = 0; a < npe; ++a) {
+        const int n = ctx->tets[(size_t)npe * e + a];
+        const int l = lof[n];
+        for (int c = 0; c < 3; ++c) {
+          elem_dense[(size_t)nde * e + 3 * a + c] = pos_of[s][3 * l + c];
+          if (ctx->any_dirval && is_dir[3 * (size_t)n + c])
+            elem_dirval[(size_t)nde * e + 3 * a + c] = dval[3 * (size_t)n + c];
+        }
       }
     }
+    for (int n : nd) lof[n] = -1;
   });
   lg.mark("create:   element dense maps");
   // FP32-factor form: per local row (global local index voff + dense row) the
