@@ -309,8 +309,31 @@ feti_status dev_alloc(feti_ctx* ctx, T** out, size_t count) {
   return FETI_OK;
 }
 
+// Allocator that leaves the elements of a resized vector uninitialised: for
+// large host arrays that are written completely before they are read.
 template <class T>
-feti_status upload(feti_ctx* ctx, T** out, const std::vector<T>& v) {
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using hvec = std::vector<T, NoInitAlloc<T>>;
+
+template <class T, class Al>
+feti_status upload(feti_ctx* ctx, T** out, const std::vector<T, Al>& v) {
   if (ctx->dry) return FETI_OK;
   FETI_TRY(dev_alloc(ctx, out, v.size()));
   if (!v.empty()) FETI_CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
@@ -982,7 +1005,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
   lg.mark("create:   multiplier maps");
   // dense maps of the elements (grouped by subdomain above)
   const int npe = ctx->npe, nde = ctx->nde, fpn = ctx->fpn;
-  std::vector<int32_t> elem_dense((size_t)nde * E);
+  hvec<int32_t> elem_dense((size_t)nde * E);  // every entry written below
   std::vector<double> elem_dirval;
   ctx->any_dirval = false;
   if (!af)
@@ -1029,7 +1052,8 @@ feti_status build_decomposition(feti_ctx* ctx) {
       }
     });
     for (int i = 0; i < voff; ++i) kptr[i + 1] += kptr[i];
-    std::vector<int32_t> kinc(kptr[voff]), kf(kptr.begin(), kptr.end() - 1);
+    hvec<int32_t> kinc(kptr[voff]);  // every slot written below
+    std::vector<int32_t> kf(kptr.begin(), kptr.end() - 1);
     par_for(P, 4, [&](int64_t s) {
       const SubLayout& L = ctx->lay[s];
       for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) {
@@ -1282,7 +1306,7 @@ feti_status build_decomposition(feti_ctx* ctx) {
     for (int a = 0; a < L.k; ++a) col_sub[L.coff + a] = s;
   }
   ctx->n_chunks = (int)chunk_sub.size();
-  std::vector<double> Rall(roff);
+  hvec<double> Rall(roff);  // every subdomain's n x k block copied below
   par_for(P, 8, [&](int64_t s) { std::copy(Rd[s].begin(), Rd[s].end(), Rall.begin() + ctx->lay[s].roff); });
 
   lg.mark("create: tables");
