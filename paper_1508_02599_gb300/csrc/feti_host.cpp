@@ -1067,11 +1067,11 @@ feti_status build_decomposition(feti_ctx* ctx) {
     FETI_TRY(upload(ctx, &ctx->d_kinc_ptr, kptr));
     FETI_TRY(upload(ctx, &ctx->d_kinc, kinc));
     {
-      std::vector<int32_t> es(E), rsub(voff);
-      for (int s = 0; s < P; ++s) {
-        for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) es[sub_elems[q]] = s;
-        for (int i = 0; i < ctx->lay[s].n; ++i) rsub[ctx->lay[s].voff + i] = s;
-      }
+      hvec<int32_t> es(E), rsub(voff);  // every element and every local row belongs to one subdomain
+      par_for(P, 16, [&](int64_t s) {
+        for (int q = sub_elem_ptr[s]; q < sub_elem_ptr[s + 1]; ++q) es[sub_elems[q]] = (int32_t)s;
+        for (int i = 0; i < ctx->lay[s].n; ++i) rsub[ctx->lay[s].voff + i] = (int32_t)s;
+      });
       FETI_TRY(upload(ctx, &ctx->d_elem_sub, es));
       FETI_TRY(upload(ctx, &ctx->d_row_sub, rsub));
     }
