@@ -175,7 +175,8 @@ typedef struct {
                                as a dense matvec, 2 = implicit: forward and backward triangular
                                sweeps over the local Cholesky factor on the placed boundary
                                vector every iteration, the paper's sparse-direct form (FETI_FP64
-                               only; the block form and the preconditioner stay explicit) */
+                               only; the block form, the allocation-free apply and the
+                               preconditioner stay explicit) */
   int32_t workspace_mb;     /* device memory of the dense elimination workspace (Sec. 4.4: the
                                local factorizations and the Schur complements S_i, F_i): the
                                subdomains are eliminated in consecutive groups whose (n + n_b')^2
