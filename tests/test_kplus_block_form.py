@@ -92,3 +92,46 @@ def test_compact_layout_keeps_only_what_the_sweeps_read():
     assert np.array_equal(A[:nI, :nI], np.tril(Lf[:nI, :nI]))
     assert np.array_equal(A[nI:, :nI], Lf[nI:, :nI])
     assert not A[:, nI:].any()                      # padding
+
+
+@pytest.mark.parametrize("method", ["af", "classical"])
+def test_block_form_equals_oracle_kplus_on_tube_subdomains(method):
+    """On the subdomains of a small tube (with their fixing DOFs): the dense
+    local order [interior | boundary minus fixing], the compact interior
+    factor and F_i = S_i[b',b']^-1 give the oracle's generalized inverse
+    K_i^+ g (Sec. 4.3, fixing-DOF inverse zero on the fixing DOFs), and the
+    boundary block of K_i^+ is F_i itself."""
+    from feti_inputs import mesh
+    from oracle import feti
+    prob = mesh.cylinder_problem(4, 16, 8, (2, 4, 2))
+    o = feti.FetiOracle(prob, feti.ALL_FLOATING if method == "af" else feti.CLASSICAL, "dirichlet")
+    o.assemble()
+    o.factorize()
+    rng = np.random.default_rng(11)
+    for sd in o.subs[:6]:
+        n = sd.free.size
+        fixpos = np.searchsorted(sd.free, sd.fix)
+        bp = np.setdiff1d(sd.bnd, fixpos)                         # boundary minus fixing
+        inner = np.setdiff1d(np.arange(n), np.union1d(sd.bnd, fixpos))
+        order = np.concatenate([inner, bp])
+        nI, nbp = inner.size, bp.size
+        Krr = sd.K[np.ix_(order, order)]
+        Lf = np.linalg.cholesky(Krr)
+        A = _compact(Lf, nI, nbp)
+        S = Krr[nI:, nI:] - (Krr[nI:, :nI] @ np.linalg.solve(Krr[:nI, :nI], Krr[:nI, nI:]) if nI else 0.0)
+        F = np.linalg.inv(S)
+        g = rng.normal(size=n)
+        yI = _fwd_interior(A, nI, g[order])
+        zb = g[bp] - A[nI:, :nI] @ yI
+        xb = F @ zb
+        xI = _bwd_interior(A, nI, yI - A[nI:, :nI].T @ xb)
+        x = np.zeros(n)
+        x[order] = np.concatenate([xI, xb])
+        ref = o.kplus(sd, g)
+        assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert not x[fixpos].any()
+        # the boundary block of the generalized inverse is F_i
+        E = np.zeros((n, nbp))
+        E[bp, np.arange(nbp)] = 1.0
+        KpB = np.column_stack([o.kplus(sd, E[:, j]) for j in range(nbp)])[bp]
+        assert np.abs(KpB - F).max() <= 1e-10 * np.abs(F).max()
